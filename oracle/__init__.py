@@ -1,0 +1,209 @@
+"""ctypes front end of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package.  The product path (the CUDA library and its Python binding) never does.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "oracle.cpp"
+_LIB = _HERE / "liboracle.so"
+
+HVP_ANALYTIC = 0
+HVP_COMPLEX = 1
+HVP_FD_EQ5 = 2
+
+
+def build(force: bool = False) -> Path:
+    """Compile oracle.cpp into liboracle.so (g++ -O2, OpenMP)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(".so.tmp")
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", str(tmp), str(_SRC)]
+        subprocess.run(cmd, check=True)
+        tmp.replace(_LIB)
+    return _LIB
+
+
+class OrcSystem(C.Structure):
+    _fields_ = [
+        ("Q", C.c_int32), ("n_types", C.c_int32), ("box", C.c_double * 3),
+        ("type", C.c_void_p), ("sigma", C.c_void_p), ("eps", C.c_void_p),
+        ("charge", C.c_void_p), ("mass", C.c_void_p),
+        ("mol_id", C.c_void_p), ("mol_local", C.c_void_p),
+        ("n_bonds", C.c_int32), ("bond_ij", C.c_void_p), ("bond_r0", C.c_void_p), ("bond_k", C.c_void_p),
+        ("n_angles", C.c_int32), ("angle_ijk", C.c_void_p), ("angle_th0", C.c_void_p), ("angle_k", C.c_void_p),
+        ("rc", C.c_double), ("eps_rf", C.c_double), ("cutoff_mode", C.c_int32),
+        ("dt_path", C.c_double), ("nu_path", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(str(build()))
+        d, i, p = C.c_double, C.c_int, C.c_void_p
+        _lib.orc_forces.argtypes = [p, p, p, p, i]
+        _lib.orc_forces_complex.argtypes = [p, p, p, d, p, p, p]
+        _lib.orc_hvp.argtypes = [p, p, p, p, i, d]
+        _lib.orc_hessian_dense.argtypes = [p, p, p]
+        _lib.orc_veff.argtypes = [p, i, p, i, d, p, p, p, p, p, p]
+        _lib.orc_veff_complex_dir.argtypes = [p, i, p, p, d, p]
+        _lib.orc_philox4x32_10.argtypes = [p, p, p]
+        _lib.orc_gauss3.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, p]
+        _lib.orc_cv_distance.argtypes = [p, p, p, i, p, i, p, d]
+        _lib.orc_cv_distance.restype = d
+        _lib.orc_bias.argtypes = [p, i, p, p, i, p, i, i, i, p, p, p, p, p]
+        _lib.orc_bias.restype = d
+        _lib.orc_step.argtypes = [p, i, p, p, p, d, d, d, C.c_uint64, C.c_uint64, i]
+        _lib.orc_step.restype = d
+        _lib.orc_num_threads.restype = i
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class Oracle:
+    """Holds the contiguous parameter arrays of one system and calls the C++ oracle."""
+
+    def __init__(self, system):
+        s = system
+        self.system = s
+        self.Q = s.n_atoms
+        keep = dict(
+            type=np.ascontiguousarray(s.type, np.int32),
+            sigma=np.ascontiguousarray(s.lj_sigma, np.float64),
+            eps=np.ascontiguousarray(s.lj_eps, np.float64),
+            charge=np.ascontiguousarray(s.charge, np.float64),
+            mass=np.ascontiguousarray(s.mass, np.float64),
+            mol_id=np.ascontiguousarray(s.mol_id, np.int32),
+            mol_local=np.ascontiguousarray(s.mol_local, np.int32),
+            bond_ij=np.ascontiguousarray(s.bond_ij, np.int32).reshape(-1),
+            bond_r0=np.ascontiguousarray(s.bond_r0, np.float64),
+            bond_k=np.ascontiguousarray(s.bond_k, np.float64),
+            angle_ijk=np.ascontiguousarray(s.angle_ijk, np.int32).reshape(-1),
+            angle_th0=np.ascontiguousarray(s.angle_th0, np.float64),
+            angle_k=np.ascontiguousarray(s.angle_k, np.float64),
+        )
+        self._keep = keep
+        st = OrcSystem()
+        st.Q = self.Q
+        st.n_types = s.n_types
+        for k in range(3):
+            st.box[k] = float(s.box[k])
+        for name in ("type", "sigma", "eps", "charge", "mass", "mol_id", "mol_local",
+                     "bond_ij", "bond_r0", "bond_k", "angle_ijk", "angle_th0", "angle_k"):
+            setattr(st, name, keep[name].ctypes.data)
+        st.n_bonds = int(s.bond_ij.shape[0])
+        st.n_angles = int(s.angle_ijk.shape[0])
+        st.rc = float(s.rc)
+        st.eps_rf = float(s.eps_rf)
+        st.cutoff_mode = int(s.cutoff_mode)
+        st.dt_path = float(s.dt_path)
+        st.nu_path = float(s.nu_path)
+        self._st = st
+        self._sp = C.cast(C.pointer(st), C.c_void_p)
+        self.L = lib()
+
+    # --- single configuration -----------------------------------------------------------
+    def forces(self, x, method: int = 0):
+        x = np.ascontiguousarray(x, np.float64).reshape(self.Q, 3)
+        F = np.zeros((self.Q, 3))
+        U = np.zeros(1)
+        self.L.orc_forces(self._sp, _ptr(x), _ptr(F), _ptr(U), method)
+        return F, float(U[0])
+
+    def forces_complex(self, x, v, h):
+        x = np.ascontiguousarray(x, np.float64).reshape(self.Q, 3)
+        v = np.ascontiguousarray(v, np.float64).reshape(self.Q, 3)
+        Fr, Fi, Uc = np.zeros((self.Q, 3)), np.zeros((self.Q, 3)), np.zeros(2)
+        self.L.orc_forces_complex(self._sp, _ptr(x), _ptr(v), float(h), _ptr(Fr), _ptr(Fi), _ptr(Uc))
+        return Fr, Fi, Uc
+
+    def hvp(self, x, v, mode: int = HVP_ANALYTIC, h: float = 0.0):
+        x = np.ascontiguousarray(x, np.float64).reshape(self.Q, 3)
+        v = np.ascontiguousarray(v, np.float64).reshape(self.Q, 3)
+        out = np.zeros((self.Q, 3))
+        self.L.orc_hvp(self._sp, _ptr(x), _ptr(v), _ptr(out), mode, float(h))
+        return out
+
+    def hessian(self, x):
+        x = np.ascontiguousarray(x, np.float64).reshape(self.Q, 3)
+        H = np.zeros((3 * self.Q, 3 * self.Q))
+        self.L.orc_hessian_dense(self._sp, _ptr(x), _ptr(H))
+        return H
+
+    # --- paths --------------------------------------------------------------------------
+    def veff(self, X, hvp_mode: int = HVP_ANALYTIC, fd_h: float = 0.0, want=("G",)):
+        X = np.ascontiguousarray(X, np.float64)
+        N = X.shape[0]
+        shp = (N, self.Q, 3)
+        out = {k: (np.zeros(shp) if k in want else None) for k in ("G", "F", "eta", "Heta")}
+        v = np.zeros(1)
+        parts = np.zeros(2)
+        self.L.orc_veff(self._sp, N, _ptr(X), hvp_mode, float(fd_h), _ptr(v), _ptr(out["G"]), _ptr(out["F"]),
+                        _ptr(out["eta"]), _ptr(out["Heta"]), _ptr(parts))
+        res = {k: a for k, a in out.items() if a is not None}
+        res.update(veff=float(v[0]), U1=float(parts[0]), Espring=float(parts[1]))
+        return res
+
+    def veff_complex_dir(self, X, D, h: float = 1e-20) -> float:
+        X = np.ascontiguousarray(X, np.float64)
+        D = np.ascontiguousarray(D, np.float64)
+        out = np.zeros(1)
+        self.L.orc_veff_complex_dir(self._sp, X.shape[0], _ptr(X), _ptr(D), float(h), _ptr(out))
+        return float(out[0])
+
+    def cv_distance(self, x, ga, gb):
+        x = np.ascontiguousarray(x, np.float64)
+        ga = np.ascontiguousarray(ga, np.int32)
+        gb = np.ascontiguousarray(gb, np.int32)
+        ds = np.zeros((self.Q, 3))
+        s = self.L.orc_cv_distance(self._sp, _ptr(x), _ptr(ga), len(ga), _ptr(gb), len(gb), _ptr(ds), 1.0)
+        return s, ds
+
+    def bias(self, X, ga, gb, centers, heights, widths, e2e: bool = False):
+        X = np.ascontiguousarray(X, np.float64)
+        ga = np.ascontiguousarray(ga, np.int32)
+        gb = np.ascontiguousarray(gb, np.int32)
+        c = np.ascontiguousarray(centers, np.float64)
+        h = np.ascontiguousarray(heights, np.float64)
+        w = np.ascontiguousarray(widths, np.float64)
+        G = np.zeros(X.shape)
+        cv = np.zeros(1)
+        V = self.L.orc_bias(self._sp, X.shape[0], _ptr(X), _ptr(ga), len(ga), _ptr(gb), len(gb), int(e2e),
+                            len(c), _ptr(c), _ptr(h), _ptr(w), _ptr(G), _ptr(cv))
+        return V, G, float(cv[0])
+
+    def step(self, X, V, G, dt, gamma, temperature, seed, step, round_f32=True):
+        """One BAOAB / velocity-Verlet step in place; returns V_eff at the new positions."""
+        return self.L.orc_step(self._sp, X.shape[0], _ptr(X), _ptr(V), _ptr(G), float(dt), float(gamma),
+                               float(temperature), int(seed), int(step), int(round_f32))
+
+
+def philox4x32_10(counter, key):
+    c = np.ascontiguousarray(counter, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def gauss3(seed, step, bead, atom):
+    out = np.zeros(3)
+    lib().orc_gauss3(int(seed), int(step), int(bead), int(atom), _ptr(out))
+    return out
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
