@@ -1,0 +1,174 @@
+/*
+ * mop.h - C ABI of the B300 engine for the metadynamics-of-paths effective potential.
+ *
+ * The engine evaluates, for one or more discretised trajectories ("paths") of N beads each,
+ * the Onsager-Machlup effective potential of Eq. 3 of the paper (arXiv 2501.11962, Sec. 1.1)
+ *
+ *     V_eff = U(R^1) + sum_{n=1}^{N-1} K/2 |R^{n+1} - R^n - L^n|^2,
+ *     K_i = m_i nu / (2 dt),   L^n_i = (dt / (m_i nu)) F^n_i,   F = -grad U,
+ *
+ * and its exact gradient dV_eff/dR, which is minus the effective force of Eqs. 5-7.  The
+ * Hessian-vector product H(R^n) eta^n that the gradient needs (the finite-difference term of
+ * Eq. 5) is computed by an adjoint kernel (MOP_HVP_ADJOINT) or, for comparison, by the paper's
+ * central difference F(R + eps eta) - F(R - eps eta) (MOP_HVP_FD).  The physical potential U is
+ * Lennard-Jones (Lorentz-Berthelot) + reaction-field Coulomb with a cutoff modifier, plus
+ * harmonic bonds and angles.  A metadynamics bias on a centroid-distance CV (Sec. 1.2, Eq. 8)
+ * and path dynamics (Eq. 4) are provided as well.
+ *
+ * Conventions
+ *   - Every call returns a mop_status; nothing throws across the ABI.  On failure the handle
+ *     keeps a one-line message, read with mop_last_error().
+ *   - Units: nm, ps, atomic mass units, elementary charges, kJ/mol.
+ *   - Coordinate arrays are [bead][atom][3], atoms in the caller's order, unwrapped; the engine
+ *     applies periodic wrapping only for its neighbour search and pair minimum images.  Bead
+ *     differences R^{n+1} - R^n are taken on the caller's coordinates as given.
+ *   - Pointers are host pointers unless flags contain MOP_DEVPTR, in which case they are device
+ *     pointers on the handle's device and the work is only enqueued on `cuda_stream` (a
+ *     cudaStream_t; NULL = the legacy default stream).  Host-pointer calls are synchronous.
+ *   - The caller owns every buffer it passes; the handle owns all memory it allocates.
+ *   - A handle is not thread safe; use one handle per host thread.
+ */
+#ifndef MOP_H_
+#define MOP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mop_handle mop_handle; /* opaque; owns all device memory of one system */
+
+typedef enum {
+  MOP_OK = 0,
+  MOP_ERR_ARG = 1,       /* invalid argument (NULL pointer, size out of range, ...) */
+  MOP_ERR_CUDA = 2,      /* a CUDA runtime call failed; see mop_last_error() */
+  MOP_ERR_OOM = 3,       /* device allocation failed */
+  MOP_ERR_NONFINITE = 4, /* NaN or Inf in the input coordinates, parameters or result */
+  MOP_ERR_BOX = 5,       /* cutoff not below half the shortest box edge, or box edge <= 0 */
+  MOP_ERR_STATE = 6,     /* call out of order (e.g. evaluating a path that was never set) */
+  MOP_ERR_TIMEOUT = 7    /* a bounded device-side wait gave up */
+} mop_status;
+
+/* cutoff modifiers of the nonbonded potential phi(r), r < rc */
+enum { MOP_SHIFTED_FORCE = 0, /* phi(r) - phi(rc) - (r - rc) phi'(rc) (default) */
+       MOP_POT_SHIFT = 1 };   /* phi(r) - phi(rc) */
+/* Hessian-vector product of the spring-term gradient */
+enum { MOP_HVP_ADJOINT = 0, /* exact, forward-over-reverse pair/bond/angle kernels */
+       MOP_HVP_FD = 1 };    /* paper Eq. 5: [F(R + eps eta) - F(R - eps eta)] / (2 eps),
+                               eps = fd_h / max_i |eta_i| per bead */
+/* arithmetic of the pair kernels */
+enum { MOP_PREC_MIXED = 0, /* FP32 pair arithmetic, FP64 accumulation and path terms */
+       MOP_PREC_FP64 = 1 };/* FP64 everywhere */
+
+/* call flags */
+#define MOP_DEVPTR 1       /* pointer arguments are device pointers; call is asynchronous */
+#define MOP_INPUT_F64 2    /* mop_set_path: xyz is double* instead of float* */
+#define MOP_E2E 4          /* mop_add_bias: CV = s(R^N) - s(R^1) (Eq. 8) instead of s(R^N) */
+
+/* fields for mop_get_field, each [N][Q][3] FP64 in the caller's atom order */
+enum { MOP_FIELD_FORCE = 0, /* F^n = -grad U(R^n) on the beads that need it */
+       MOP_FIELD_ETA = 1,   /* eta^n = R^{n+1} - R^n - L^n, n < N */
+       MOP_FIELD_HETA = 2 };/* H(R^n) eta^n (adjoint) or its FD estimate, n < N */
+
+/* Host description of a system; every pointer is a host array read during mop_create only. */
+typedef struct {
+  int32_t n_atoms;           /* Q >= 1 */
+  double box[3];             /* rectangular periodic box edges, nm */
+  const int32_t* type;       /* [Q] LJ type, 0 <= type < n_types */
+  int32_t n_types;           /* 1 <= n_types <= 16 */
+  const double* lj_sigma;    /* [n_types] nm; pairs use sigma_ij = (sigma_i + sigma_j) / 2 */
+  const double* lj_eps;      /* [n_types] kJ/mol; pairs use eps_ij = sqrt(eps_i eps_j) */
+  const double* charge;      /* [Q] e */
+  const double* mass;        /* [Q] u, > 0 */
+  const int32_t* mol_id;     /* [Q] molecule id */
+  const int32_t* mol_local;  /* [Q] index inside the molecule; pairs with equal mol_id and
+                                |mol_local_i - mol_local_j| <= 2 have no nonbonded term */
+  int32_t n_bonds;
+  const int32_t* bond_ij;    /* [n_bonds][2] */
+  const double* bond_r0;     /* [n_bonds] nm */
+  const double* bond_k;      /* [n_bonds] kJ/mol/nm^2; U = k/2 (d - r0)^2 */
+  int32_t n_angles;
+  const int32_t* angle_ijk;  /* [n_angles][3], j is the vertex */
+  const double* angle_th0;   /* [n_angles] rad */
+  const double* angle_k;     /* [n_angles] kJ/mol/rad^2; U = k/2 (theta - theta0)^2 */
+  double rc;                 /* cutoff, nm; 0 < rc < min(box) / 2 */
+  double eps_rf;             /* reaction-field dielectric (>= 1) */
+  int32_t cutoff_mode;       /* MOP_SHIFTED_FORCE | MOP_POT_SHIFT */
+  double dt_path;            /* ps, time step of the discretised trajectory (Sec. 1.1) */
+  double nu_path;            /* 1/ps, friction coefficient nu of Eq. 1 */
+  double temperature;        /* K, used by mop_step's thermostat */
+  int32_t hvp_mode;          /* MOP_HVP_ADJOINT | MOP_HVP_FD */
+  double fd_h;               /* nm, largest atomic displacement of the FD mode */
+  int32_t precision;         /* MOP_PREC_MIXED | MOP_PREC_FP64 */
+} mop_system_desc;
+
+/* Validates `desc` and uploads it to `device`.  Errors: MOP_ERR_ARG (bad sizes, indices or
+ * masses), MOP_ERR_NONFINITE, MOP_ERR_BOX (rc >= min(box)/2), MOP_ERR_CUDA, MOP_ERR_OOM.
+ * On success *out owns the device memory until mop_destroy. */
+mop_status mop_create(const mop_system_desc* desc, int device, mop_handle** out);
+
+/* Frees everything the handle owns (NULL is allowed). */
+mop_status mop_destroy(mop_handle* h);
+
+/* Stores the coordinates of path `path_id` (0 <= path_id < 64): n_beads >= 1 beads of
+ * [n_beads][Q][3] float (double with MOP_INPUT_F64), copied into the handle.  Resets the
+ * path's velocities to zero.  Errors: MOP_ERR_ARG, MOP_ERR_NONFINITE (host input is checked
+ * here; device input is checked by mop_veff_and_grad through the result), MOP_ERR_CUDA,
+ * MOP_ERR_OOM. */
+mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const void* xyz,
+                        int32_t flags, void* cuda_stream);
+
+/* Copies the current coordinates of a path (after mop_step) into xyz [N][Q][3] float. */
+mop_status mop_get_path(mop_handle* h, int32_t path_id, float* xyz, int32_t flags, void* cuda_stream);
+
+/* Evaluates V_eff (Eq. 3, plus the bias if one is set) and its gradient for path `path_id`, or
+ * for every set path when path_id = -1, in one pass of the kernels.  veff: [1] or [P] doubles
+ * (P = number of set paths, in path-id order); grad: [N][Q][3] doubles (concatenated over
+ * paths in path-id order when path_id = -1), dV_eff/dR (not the force); grad may be NULL.
+ * Errors: MOP_ERR_STATE (path not set), MOP_ERR_NONFINITE (non-finite V_eff, host calls
+ * only), MOP_ERR_CUDA, MOP_ERR_OOM. */
+mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, double* grad,
+                             int32_t flags, void* cuda_stream);
+
+/* Copies one field of the last evaluation of `path_id` into out [N][Q][3] doubles (rows of
+ * beads where the field is undefined are zero). */
+mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* out,
+                         int32_t flags, void* cuda_stream);
+
+/* Parts of the last evaluation of `path_id`: out[0] = U(R^1), out[1] = spring energy,
+ * out[2] = bias energy, out[3] = CV value (0 without a bias).  Synchronous. */
+mop_status mop_get_energies(mop_handle* h, int32_t path_id, double out[4]);
+
+/* Metadynamics bias (Sec. 1.2): defines the CV of path `path_id` as the distance between the
+ * centroids of atom groups A and B (minimum image; each centroid taken with its group
+ * unwrapped relative to the group's first atom) at the last bead, or, with MOP_E2E, its
+ * difference between the last and the first bead (Eq. 8); then appends one Gaussian
+ * height * exp(-(S - s_center)^2 / (2 width^2)).  grpA/grpB may be NULL to keep the groups of
+ * the previous call.  Groups hold 1..1024 atom indices (host pointers); at most 4096
+ * Gaussians per path.  Errors: MOP_ERR_ARG, MOP_ERR_STATE (no groups yet), MOP_ERR_CUDA. */
+mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const int32_t* grpB,
+                        int32_t nB, double s_center, double height, double width,
+                        int32_t path_id, int32_t flags);
+
+/* Advances every set path by n_steps of the path dynamics M d2R/dt2 = -dV_eff/dR (Eq. 4),
+ * fictitious masses = physical masses: velocity Verlet when gamma = 0, BAOAB Langevin at the
+ * system temperature otherwise (noise from Philox-4x32-10 keyed by seed, counter = (atom,
+ * bead, step)).  Positions are kept in FP64 and the force is evaluated at their float32
+ * rounding (MOP_PREC_MIXED).  Errors: MOP_ERR_STATE, MOP_ERR_ARG, MOP_ERR_CUDA. */
+mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed,
+                    void* cuda_stream);
+
+/* Kinetic energy sum_i m_i |v_i|^2 / 2 over all beads of `path_id` (synchronous). */
+mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke);
+
+/* Number of kernel launches the last mop_veff_and_grad made (instrumentation). */
+int32_t mop_last_launch_count(const mop_handle* h);
+
+/* Text of the last error of the handle ("" if none); valid until the next call. */
+const char* mop_last_error(const mop_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOP_H_ */
