@@ -1,0 +1,112 @@
+// Host-side state of the engine and the kernel launchers of each translation unit.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mop_internal.cuh"
+
+namespace mop {
+
+// Grow-only device buffer.  ensure() reports allocation failure through its return value.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;  // elements
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = n > 0 ? n : 1;
+    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// Geometry of the spatial sort of one path (host copy, fixed per system).
+struct Grid {
+  int ncx, ncy;           // columns of the cluster sort
+  double wx, wy;          // column widths
+  int nb[3];              // bins of the pair search
+  double bw[3];           // bin widths
+  int max_clu;            // upper bound of the cluster count
+};
+
+struct PathHost {
+  bool set = false;
+  int N = 0;
+  int n_clu = 0;
+  long long n_ent = 0;
+  // state
+  DevBuf<float> x32;      // [N][Q][3]
+  DevBuf<double> x64;     // [N][Q][3] master positions (FP64)
+  DevBuf<double> vel;     // [N][Q][3]
+  bool have_grad = false; // grad_int holds dV/dR at the current positions
+  // sort and clusters
+  DevBuf<double> ref;     // [Q][3]
+  DevBuf<int> colid, colcnt, colinfo, colatoms, perm, slot, ts;
+  DevBuf<double> center;  // [max_clu][3]
+  DevBuf<float> hext;     // [max_clu][3]
+  DevBuf<int> molr;       // [max_clu][2]
+  DevBuf<unsigned> emax;  // [3] float bits
+  DevBuf<int> cbin, bincnt, binstart, bincur, binlist;
+  DevBuf<double> cwrap;   // [max_clu][3]
+  DevBuf<int> lcnt, loff;
+  DevBuf<int> meta;       // [4]: n_clu, n_ent, overflow, spare
+  DevBuf<float4> xq;
+  DevBuf<double4> xq64;
+  DevBuf<int4> ent;
+  DevBuf<double4> ent64;
+  DevBuf<unsigned long long> emask;
+  // fields
+  DevBuf<double> Fnb, F, eta, Hnb, Heta, grad_int;
+  DevBuf<float4> eta32;
+  DevBuf<unsigned> etamax;
+  DevBuf<double> e_pair, diag, veff_int;
+  // bias
+  std::vector<int> hA, hB;
+  std::vector<double> hc, hh, hw;
+  int e2e = 0;
+  DevBuf<int> gA, gB;
+  DevBuf<double> gc, gh, gw;
+};
+
+struct Launch {
+  cudaStream_t st;
+  int* counter;   // launches issued
+};
+
+// --- mop_prep.cu: spatial sort, clusters, local coordinates, cluster-pair list ------------
+cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L,
+                      std::string* err);
+
+// --- mop_pair.cu: pair kernels over every unit of every path -------------------------------
+// mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP
+cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
+                        int mode, int num_sms, Launch L);
+
+// --- mop_path.cu: bonded terms, eta, path gradient, bias, reductions, integrator ----------
+cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
+                      double* e_bond, int e_bond_stride);
+cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
+                      double* e_spring, int e_spring_stride);
+cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L);
+cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L,
+                          const double* e_bond, int e_bond_stride, int n_e1_blocks,
+                          const double* e_spring, int e_spring_stride, int n_e2_blocks);
+cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, int N, double half_dt, Launch L);
+cudaError_t launch_drift(const SysConsts& sc, double* x64, double* vel, float* x32, int N, double dt,
+                         double gamma, double kT, uint64_t seed, uint64_t step, int path_bead0, Launch L);
+cudaError_t launch_kinetic(const SysConsts& sc, const double* vel, int N, double* out, Launch L);
+
+}  // namespace mop

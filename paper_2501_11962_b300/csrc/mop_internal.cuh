@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libmop.
+//
+// Data layout in HBM (per path p with N beads, Q atoms, Qpad = 8 * n_clu slots):
+//   x32/x64 [N][Q][3]      caller-order coordinates (the path state)
+//   perm[Qpad], slot[Q]    spatial order: slot -> atom (-1 = padding), atom -> slot
+//   xq/xq64 [N][Qpad]      cluster-local coordinates (x - C_cluster) and sqrt(f) q
+//   ent/ent64/emask [E]    cluster-pair list shared by all beads of the path
+//   Fnb, F, eta, Hnb, Heta [N][Qpad][3] FP64 fields in slot order; eta32 [N][Qpad] float4
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mop {
+
+constexpr int kCL = 8;            // atoms per cluster
+constexpr int kMaxTypes = 16;
+constexpr int kMaxPaths = 64;
+constexpr int kMaxGroup = 1024;   // atoms per CV group
+constexpr int kMaxGauss = 4096;   // Gaussians per path
+constexpr int kRedBlock = 256;    // threads of the elementwise kernels
+constexpr double kCoulombF = 138.935458;   // kJ mol^-1 nm e^-2
+constexpr double kBoltz = 0.0083144626;    // kJ mol^-1 K^-1
+constexpr float kDummyCoord = 1.0e5f;      // padding slots sit far outside every cutoff
+
+// System-wide constants, passed by value to kernels.
+struct SysConsts {
+  int Q, n_types, cutoff_mode, precision, hvp_mode;
+  double L[3], invL[3];
+  float Lf[3], halfLf[3];
+  double rc, rc2, krf, crf, k2rf, drf;   // RF constants; drf = phi'_RF(rc) / (f qi qj) if shifted
+  float rcf, rc2f, krff, crff, k2rff, drff;
+  double fd_h;
+  // per-atom arrays in caller order
+  const double* mass;
+  const double* Kspr;   // m nu / (2 dt)
+  const double* cL;     // dt / (m nu)
+  const double* qs;     // q sqrt(f)
+  const int* type;
+  const int* mol;
+  const int* loc;
+  // bonded incidence: for atom a, terms inc[inc_off[a] .. inc_off[a+1])
+  const int* inc_off;
+  const int4* inc;      // x = kind (0 bond, 1 angle) | role << 2, y,z,w = atoms (w = -1 for bonds)
+  const double2* incp;  // (r0 or theta0, k)
+  // type-pair tables: (12 c12, 6 c6, phi'_LJ(rc) if shifted else 0, phi_LJ(rc))
+  const float4* tab;
+  const double4* tab64;
+};
+
+// Device view of one path of a multi-path launch.
+struct PathDev {
+  int N, n_force, Q, Qpad, n_clu;
+  long long unit_off;      // first pair-kernel unit of this path
+  int blk_off_e1, blk_off_e2;
+  const float* x32;
+  const double* x64;
+  const int* perm;
+  const int* slot;
+  const float4* xq;
+  const double4* xq64;
+  const int* ts;
+  const int* loff;
+  const int4* ent;
+  const double4* ent64;
+  const unsigned long long* emask;
+  double* Fnb;
+  double* F;
+  double* eta;
+  float4* eta32;
+  double* Hnb;
+  double* Heta;
+  unsigned* etamax;        // [N] float bits of max_i |eta_i|
+  double* e_pair;          // [n_clu]
+  double* grad;            // [N][Q][3] caller order
+  // bias
+  int nA, nB, n_gauss, e2e;
+  const int* gA;
+  const int* gB;
+  const double* gc;        // centres, heights, widths [n_gauss]
+  const double* gh;
+  const double* gw;
+  double* diag;            // [8]: U1, E_spring, E_bias, CV, V_eff, U_pair, U_bonded
+  double* veff_out;        // one double
+};
+
+// ------------------------------------------------------------------------------------------
+// small device helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed tree); every thread must call it.  Result valid in thread 0.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (l < BS / 32) ? sh[l] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// Knuth's TwoSum: (hi, lo) += a without loss (FP32 error-free transformation).
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float a) {
+  const float s = hi + a;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (a - bp);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ double aligned_coord(double v, double ref, double L, double invL) {
+  return v - L * rint((v - ref) * invL);
+}
+
+}  // namespace mop
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers implemented in the .cu files
+
+namespace mop {
+
+struct PrepBuffers;   // defined in mop_host.h
+
+}  // namespace mop
