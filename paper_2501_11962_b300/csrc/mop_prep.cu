@@ -1,0 +1,457 @@
+// Spatial sort, clusters and the cluster-pair list of one path.
+//
+// The paper evaluates each bead's forces with GROMACS' own neighbour search (Sec. 2.1, one
+// bead per processing element).  Here all beads of a path share ONE sort and ONE cluster-pair
+// list: atoms are ordered by the reference bead (bead 1) into x-y columns and z, cut into
+// clusters of 8, and every cluster gets the union of its bounding boxes over all beads (each
+// bead's atom taken at the periodic image nearest its reference position).  A cluster pair is
+// listed (with its periodic image) when the union boxes are closer than rc, so the list is
+// exact for every bead without a Verlet buffer.  Coordinates are stored relative to the
+// cluster centre so that FP32 pair differences stay accurate in large boxes.
+#include <cstdio>
+
+#include "mop_host.h"
+
+namespace mop {
+namespace {
+
+__device__ __forceinline__ double coord(const float* x32, const double* x64, size_t k) {
+  return x64 ? x64[k] : (double)x32[k];
+}
+
+// exclusive scan of one value per thread over a 1024-thread block; *total gets the block sum
+__device__ int block_excl_scan(int v, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  const int pre = (w > 0 ? sh[w - 1] : 0) + x - v;
+  *total = sh[nw - 1];
+  __syncthreads();
+  return pre;
+}
+
+// reference wrap of bead 1, column index and column counts
+__global__ void k_ref_columns(SysConsts sc, const float* x32, const double* x64, int ncx, int ncy, double wx,
+                              double wy, double* ref, int* colid, int* colcnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.Q) return;
+  double r[3];
+  for (int d = 0; d < 3; ++d) {
+    const double v = coord(x32, x64, 3 * (size_t)i + d);
+    double w = v - sc.L[d] * floor(v * sc.invL[d]);
+    if (w >= sc.L[d]) w -= sc.L[d];
+    if (w < 0.0) w = 0.0;
+    r[d] = w;
+    ref[3 * i + d] = w;
+  }
+  const int cx = min((int)(r[0] / wx), ncx - 1);
+  const int cy = min((int)(r[1] / wy), ncy - 1);
+  const int col = cx * ncy + cy;
+  colid[i] = col;
+  atomicAdd(&colcnt[col], 1);
+}
+
+// colinfo[3c] = first atom of column c in colatoms, [3c+1] = first slot (padded to 8),
+// [3c+2] = fill cursor; meta[0] = number of clusters
+__global__ void k_scan_columns(const int* colcnt, int ncol, int* colinfo, int* meta) {
+  __shared__ int sh[32];
+  int carry = 0, pcarry = 0;
+  for (int base = 0; base < ncol; base += blockDim.x) {
+    const int c = base + threadIdx.x;
+    const int cnt = c < ncol ? colcnt[c] : 0;
+    const int pad = (cnt + kCL - 1) / kCL * kCL;
+    int tot, ptot;
+    const int pre = block_excl_scan(cnt, sh, &tot);
+    const int ppre = block_excl_scan(pad, sh, &ptot);
+    if (c < ncol) {
+      colinfo[3 * c] = carry + pre;
+      colinfo[3 * c + 1] = pcarry + ppre;
+      colinfo[3 * c + 2] = carry + pre;
+    }
+    carry += tot;
+    pcarry += ptot;
+  }
+  if (threadIdx.x == 0) meta[0] = pcarry / kCL;
+}
+
+__global__ void k_fill_columns(int Q, const int* colid, int* colinfo, int* colatoms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const int pos = atomicAdd(&colinfo[3 * colid[i] + 2], 1);
+  colatoms[pos] = i;
+}
+
+// rank inside the column by (z, atom index): deterministic slot of every atom
+__global__ void k_rank(int Q, const double* ref, const int* colid, const int* colcnt, const int* colinfo,
+                       const int* colatoms, int* perm, int* slot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Q) return;
+  const int col = colid[i];
+  const int st = colinfo[3 * col], cnt = colcnt[col];
+  const double zi = ref[3 * i + 2];
+  int rank = 0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = colatoms[st + k];
+    const double zj = ref[3 * j + 2];
+    rank += (zj < zi) || (zj == zi && j < i);
+  }
+  const int s = colinfo[3 * col + 1] + rank;
+  perm[s] = i;
+  slot[i] = s;
+}
+
+// union bounding box of each cluster over all beads; one warp per cluster, lanes over beads
+__global__ void k_cluster_bbox(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
+                               const int* perm, const int* meta, int max_clu, double margin, double* center,
+                               float* hext, int* molr, unsigned* emax) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= max_clu || c >= meta[0]) return;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  int atoms[kCL];
+#pragma unroll
+  for (int k = 0; k < kCL; ++k) atoms[k] = perm[c * kCL + k];
+  const size_t Q3 = 3 * (size_t)sc.Q;
+  for (int b = lane; b < N; b += 32) {
+#pragma unroll
+    for (int k = 0; k < kCL; ++k) {
+      const int a = atoms[k];
+      if (a < 0) continue;
+      for (int d = 0; d < 3; ++d) {
+        const double v = aligned_coord(coord(x32, x64, b * Q3 + 3 * (size_t)a + d), ref[3 * a + d], sc.L[d],
+                                       sc.invL[d]);
+        lo[d] = fmin(lo[d], v);
+        hi[d] = fmax(hi[d], v);
+      }
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+  }
+  if (lane == 0) {
+    int m0 = 0x7fffffff, m1 = -0x7fffffff;
+    for (int k = 0; k < kCL; ++k)
+      if (atoms[k] >= 0) {
+        m0 = min(m0, sc.mol[atoms[k]]);
+        m1 = max(m1, sc.mol[atoms[k]]);
+      }
+    molr[2 * c] = m0;
+    molr[2 * c + 1] = m1;
+    for (int d = 0; d < 3; ++d) {
+      const double cen = (double)(float)(0.5 * (lo[d] + hi[d]));   // exactly representable in FP32
+      const double ext = fmax(hi[d] - cen, cen - lo[d]) + margin;
+      const float e = __double2float_ru(ext);
+      center[3 * c + d] = cen;
+      hext[3 * c + d] = e;
+      atomicMax(&emax[d], __float_as_uint(e));
+    }
+  }
+}
+
+// cluster-local coordinates of every bead (and the slot types, from bead 1)
+template <bool F64>
+__global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
+                               const int* perm, const int* meta, int max_slots, const double* center, float4* xq,
+                               double4* xq64, int* ts) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Qpad = meta[0] * kCL;
+  const int s = (int)(t % max_slots);
+  const int b = (int)(t / max_slots);
+  if (b >= N || s >= Qpad) return;
+  const int a = perm[s];
+  const size_t o = (size_t)b * Qpad + s;
+  if (a < 0) {
+    const double dmy = (double)kDummyCoord + 3.0 * (s & (kCL - 1));
+    if (F64) xq64[o] = make_double4(dmy, dmy, dmy, 0.0);
+    else xq[o] = make_float4((float)dmy, (float)dmy, (float)dmy, 0.0f);
+    if (b == 0) ts[s] = 0;
+    return;
+  }
+  const int c = s / kCL;
+  const size_t Q3 = 3 * (size_t)sc.Q;
+  double v[3];
+  for (int d = 0; d < 3; ++d)
+    v[d] = aligned_coord(coord(x32, x64, b * Q3 + 3 * (size_t)a + d), ref[3 * a + d], sc.L[d], sc.invL[d]) -
+           center[3 * c + d];
+  if (F64) xq64[o] = make_double4(v[0], v[1], v[2], sc.qs[a]);
+  else xq[o] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)sc.qs[a]);
+  if (b == 0) ts[s] = sc.type[a];
+}
+
+__global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const double* center, int nb0, int nb1,
+                               int nb2, double bw0, double bw1, double bw2, double* cwrap, int* cbin, int* bincnt) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= max_clu || c >= meta[0]) return;
+  int bidx[3];
+  const int nb[3] = {nb0, nb1, nb2};
+  const double bw[3] = {bw0, bw1, bw2};
+  for (int d = 0; d < 3; ++d) {
+    double w = center[3 * c + d] - sc.L[d] * floor(center[3 * c + d] * sc.invL[d]);
+    if (w >= sc.L[d]) w -= sc.L[d];
+    if (w < 0.0) w = 0.0;
+    cwrap[3 * c + d] = w;
+    bidx[d] = min((int)(w / bw[d]), nb[d] - 1);
+  }
+  const int bin = (bidx[0] * nb1 + bidx[1]) * nb2 + bidx[2];
+  cbin[c] = bin;
+  atomicAdd(&bincnt[bin], 1);
+}
+
+// exclusive scan of n ints (single block); out[n] = total; optional copy to cur; meta slot
+__global__ void k_scan(const int* in, int n, int* out, int* cur, int* meta_total) {
+  __shared__ int sh[32];
+  int carry = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    int tot;
+    const int pre = block_excl_scan(v, sh, &tot);
+    if (i < n) {
+      out[i] = carry + pre;
+      if (cur) cur[i] = carry + pre;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    out[n] = carry;
+    if (meta_total) *meta_total = carry;
+  }
+}
+
+__global__ void k_fill_bins(const int* meta, int max_clu, const int* cbin, int* bincur, int* binlist) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= max_clu || c >= meta[0]) return;
+  binlist[atomicAdd(&bincur[cbin[c]], 1)] = c;
+}
+
+__global__ void k_sort_bins(int nbins, const int* binstart, int* binlist) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const int s = binstart[b], e = binstart[b + 1];
+  for (int i = s + 1; i < e; ++i) {
+    const int v = binlist[i];
+    int j = i - 1;
+    while (j >= s && binlist[j] > v) {
+      binlist[j + 1] = binlist[j];
+      --j;
+    }
+    binlist[j + 1] = v;
+  }
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// cluster-pair list of one i-cluster: count pass (FILL = false) or fill pass
+template <bool FILL, bool F64>
+__global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const double* cwrap, const float* hext,
+                            const unsigned* emax, const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
+                            double bw2, const int* binstart, const int* binlist, const int* perm, const int* molr,
+                            int* lcnt, const int* loff, int4* ent, double4* ent64, unsigned long long* emask) {
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ci >= max_clu) return;
+  if (ci >= meta[0]) {
+    if (!FILL) lcnt[ci] = 0;
+    return;
+  }
+  const int nb[3] = {nb0, nb1, nb2};
+  const double bw[3] = {bw0, bw1, bw2};
+  double wi[3], ei[3];
+  int bi[3], R[3];
+  const int binc = cbin[ci];
+  bi[2] = binc % nb2;
+  bi[1] = (binc / nb2) % nb1;
+  bi[0] = binc / (nb1 * nb2);
+  for (int d = 0; d < 3; ++d) {
+    wi[d] = cwrap[3 * ci + d];
+    ei[d] = hext[3 * ci + d];
+    const double em = __uint_as_float(emax[d]);
+    R[d] = (int)floor((sc.rc + ei[d] + em) / bw[d] + 1e-6) + 1;
+  }
+  const int mi0 = molr[2 * ci], mi1 = molr[2 * ci + 1];
+  long long out = FILL ? loff[ci] : 0;
+  int count = 0;
+  for (int dx = -R[0]; dx <= R[0]; ++dx) {
+    const int Bx = bi[0] + dx, kx = floor_div(Bx, nb[0]), wx = Bx - kx * nb[0];
+    for (int dy = -R[1]; dy <= R[1]; ++dy) {
+      const int By = bi[1] + dy, ky = floor_div(By, nb[1]), wy = By - ky * nb[1];
+      for (int dz = -R[2]; dz <= R[2]; ++dz) {
+        const int Bz = bi[2] + dz, kz = floor_div(Bz, nb[2]), wz = Bz - kz * nb[2];
+        const int bin = (wx * nb1 + wy) * nb2 + wz;
+        const int kk[3] = {kx, ky, kz};
+        for (int t = binstart[bin]; t < binstart[bin + 1]; ++t) {
+          const int cj = binlist[t];
+          double D[3], g2 = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
+            const double gap = fmax(0.0, fabs(D[d]) - ei[d] - (double)hext[3 * cj + d]);
+            g2 += gap * gap;
+          }
+          if (!(g2 < sc.rc2)) continue;
+          if (FILL) {
+            unsigned long long m = 0ull;
+            const int mj0 = molr[2 * cj], mj1 = molr[2 * cj + 1];
+            if (mi0 <= mj1 && mj0 <= mi1) {
+              for (int i = 0; i < kCL; ++i) {
+                const int a = perm[ci * kCL + i];
+                if (a < 0) continue;
+                for (int j = 0; j < kCL; ++j) {
+                  const int b = perm[cj * kCL + j];
+                  if (b < 0) continue;
+                  if (sc.mol[a] == sc.mol[b] && abs(sc.loc[a] - sc.loc[b]) <= 2) m |= 1ull << (i * kCL + j);
+                }
+              }
+            }
+            const float fx = (float)D[0], fy = (float)D[1], fz = (float)D[2];
+            ent[out] = make_int4(cj | (m ? (int)0x80000000 : 0), __float_as_int(fx), __float_as_int(fy),
+                                 __float_as_int(fz));
+            if (F64) ent64[out] = make_double4(D[0], D[1], D[2], 0.0);
+            emask[out] = m;
+            ++out;
+          }
+          ++count;
+        }
+      }
+    }
+  }
+  if (!FILL) lcnt[ci] = count;
+}
+
+inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace
+
+#define MOP_CK(x)                                          \
+  do {                                                     \
+    cudaError_t e_ = (x);                                  \
+    if (e_ != cudaSuccess) {                               \
+      if (err) *err = std::string(#x) + ": " + cudaGetErrorString(e_); \
+      return e_;                                           \
+    }                                                      \
+  } while (0)
+#define MOP_KL()                                          \
+  do {                                                    \
+    ++*L.counter;                                         \
+    MOP_CK(cudaGetLastError());                           \
+  } while (0)
+
+cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L, std::string* err) {
+  const int Q = sc.Q, N = P.N;
+  const int ncol = g.ncx * g.ncy;
+  const int max_clu = g.max_clu;
+  const int max_slots = max_clu * kCL;
+  const int nbins = g.nb[0] * g.nb[1] * g.nb[2];
+  const bool f64 = sc.precision == 1;
+  const float* x32 = f64 ? nullptr : P.x32.p;
+  const double* x64 = f64 ? P.x64.p : nullptr;
+  cudaStream_t st = L.st;
+
+  MOP_CK(P.ref.ensure(3 * (size_t)Q));
+  MOP_CK(P.colid.ensure(Q));
+  MOP_CK(P.colcnt.ensure(ncol));
+  MOP_CK(P.colinfo.ensure(3 * (size_t)ncol));
+  MOP_CK(P.colatoms.ensure(Q));
+  MOP_CK(P.perm.ensure(max_slots));
+  MOP_CK(P.slot.ensure(Q));
+  MOP_CK(P.ts.ensure(max_slots));
+  MOP_CK(P.center.ensure(3 * (size_t)max_clu));
+  MOP_CK(P.hext.ensure(3 * (size_t)max_clu));
+  MOP_CK(P.molr.ensure(2 * (size_t)max_clu));
+  MOP_CK(P.emax.ensure(3));
+  MOP_CK(P.cbin.ensure(max_clu));
+  MOP_CK(P.cwrap.ensure(3 * (size_t)max_clu));
+  MOP_CK(P.bincnt.ensure(nbins));
+  MOP_CK(P.binstart.ensure(nbins + 1));
+  MOP_CK(P.bincur.ensure(nbins));
+  MOP_CK(P.binlist.ensure(max_clu));
+  MOP_CK(P.lcnt.ensure(max_clu));
+  MOP_CK(P.loff.ensure(max_clu + 1));
+  MOP_CK(P.meta.ensure(4));
+  if (f64) MOP_CK(P.xq64.ensure((size_t)N * max_slots));
+  else MOP_CK(P.xq.ensure((size_t)N * max_slots));
+
+  MOP_CK(cudaMemsetAsync(P.colcnt.p, 0, sizeof(int) * ncol, st));
+  MOP_CK(cudaMemsetAsync(P.perm.p, 0xff, sizeof(int) * max_slots, st));
+  MOP_CK(cudaMemsetAsync(P.emax.p, 0, sizeof(unsigned) * 3, st));
+  MOP_CK(cudaMemsetAsync(P.bincnt.p, 0, sizeof(int) * nbins, st));
+  MOP_CK(cudaMemsetAsync(P.meta.p, 0, sizeof(int) * 4, st));
+
+  const int bs = 256;
+  k_ref_columns<<<nblk(Q, bs), bs, 0, st>>>(sc, x32, x64, g.ncx, g.ncy, g.wx, g.wy, P.ref.p, P.colid.p, P.colcnt.p);
+  MOP_KL();
+  k_scan_columns<<<1, 1024, 0, st>>>(P.colcnt.p, ncol, P.colinfo.p, P.meta.p);
+  MOP_KL();
+  k_fill_columns<<<nblk(Q, bs), bs, 0, st>>>(Q, P.colid.p, P.colinfo.p, P.colatoms.p);
+  MOP_KL();
+  k_rank<<<nblk(Q, bs), bs, 0, st>>>(Q, P.ref.p, P.colid.p, P.colcnt.p, P.colinfo.p, P.colatoms.p, P.perm.p,
+                                     P.slot.p);
+  MOP_KL();
+  k_cluster_bbox<<<nblk((long long)max_clu * 32, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p,
+                                                                   max_clu, margin, P.center.p, P.hext.p, P.molr.p,
+                                                                   P.emax.p);
+  MOP_KL();
+  if (f64)
+    k_local_coords<true><<<nblk((long long)N * max_slots, bs), bs, 0, st>>>(
+        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, nullptr, P.xq64.p, P.ts.p);
+  else
+    k_local_coords<false><<<nblk((long long)N * max_slots, bs), bs, 0, st>>>(
+        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, P.xq.p, nullptr, P.ts.p);
+  MOP_KL();
+  k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, g.nb[0], g.nb[1], g.nb[2],
+                                                   g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cbin.p, P.bincnt.p);
+  MOP_KL();
+  k_scan<<<1, 1024, 0, st>>>(P.bincnt.p, nbins, P.binstart.p, P.bincur.p, nullptr);
+  MOP_KL();
+  k_fill_bins<<<nblk(max_clu, bs), bs, 0, st>>>(P.meta.p, max_clu, P.cbin.p, P.bincur.p, P.binlist.p);
+  MOP_KL();
+  k_sort_bins<<<nblk(nbins, bs), bs, 0, st>>>(nbins, P.binstart.p, P.binlist.p);
+  MOP_KL();
+  k_pair_list<false, false><<<nblk(max_clu, 128), 128, 0, st>>>(
+      sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1],
+      g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.lcnt.p, nullptr, nullptr, nullptr, nullptr);
+  MOP_KL();
+  k_scan<<<1, 1024, 0, st>>>(P.lcnt.p, max_clu, P.loff.p, nullptr, P.meta.p + 1);
+  MOP_KL();
+  int meta[4];
+  MOP_CK(cudaMemcpyAsync(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost, st));
+  MOP_CK(cudaStreamSynchronize(st));
+  P.n_clu = meta[0];
+  P.n_ent = meta[1];
+  const size_t ne = (size_t)P.n_ent;
+  MOP_CK(P.ent.ensure(ne + ne / 8 + 64));
+  MOP_CK(P.emask.ensure(ne + ne / 8 + 64));
+  if (f64) MOP_CK(P.ent64.ensure(ne + ne / 8 + 64));
+  if (f64)
+    k_pair_list<true, true><<<nblk(max_clu, 128), 128, 0, st>>>(
+        sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0],
+        g.bw[1], g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.lcnt.p, P.loff.p, P.ent.p, P.ent64.p,
+        P.emask.p);
+  else
+    k_pair_list<true, false><<<nblk(max_clu, 128), 128, 0, st>>>(
+        sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0],
+        g.bw[1], g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.lcnt.p, P.loff.p, P.ent.p, nullptr,
+        P.emask.p);
+  MOP_KL();
+  return cudaSuccess;
+}
+
+}  // namespace mop
