@@ -64,9 +64,9 @@ struct PathHost {
   DevBuf<int> lcnt, loff;
   DevBuf<int> meta;       // [4]: n_clu, n_ent, overflow, spare
   DevBuf<float4> xq;
-  DevBuf<double4> xq64;
+  DevBuf<double4_32a> xq64;
   DevBuf<int4> ent;
-  DevBuf<double4> ent64;
+  DevBuf<double4_32a> ent64;
   DevBuf<unsigned long long> emask;
   // fields
   DevBuf<double> Fnb, F, eta, Hnb, Heta, grad_int;

@@ -44,7 +44,7 @@ struct SysConsts {
   const double2* incp;  // (r0 or theta0, k)
   // type-pair tables: (12 c12, 6 c6, phi'_LJ(rc) if shifted else 0, phi_LJ(rc))
   const float4* tab;
-  const double4* tab64;
+  const double4_32a* tab64;
 };
 
 // Device view of one path of a multi-path launch.
@@ -57,11 +57,11 @@ struct PathDev {
   const int* perm;
   const int* slot;
   const float4* xq;
-  const double4* xq64;
+  const double4_32a* xq64;
   const int* ts;
   const int* loff;
   const int4* ent;
-  const double4* ent64;
+  const double4_32a* ent64;
   const unsigned long long* emask;
   double* Fnb;
   double* F;

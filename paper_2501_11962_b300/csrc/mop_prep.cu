@@ -172,7 +172,7 @@ __global__ void k_cluster_bbox(SysConsts sc, const float* x32, const double* x64
 template <bool F64>
 __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
                                const int* perm, const int* meta, int max_slots, const double* center, float4* xq,
-                               double4* xq64, int* ts) {
+                               double4_32a* xq64, int* ts) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int Qpad = meta[0] * kCL;
   const int s = (int)(t % max_slots);
@@ -182,7 +182,7 @@ __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64
   const size_t o = (size_t)b * Qpad + s;
   if (a < 0) {
     const double dmy = (double)kDummyCoord + 3.0 * (s & (kCL - 1));
-    if (F64) xq64[o] = make_double4(dmy, dmy, dmy, 0.0);
+    if (F64) xq64[o] = make_double4_32a(dmy, dmy, dmy, 0.0);
     else xq[o] = make_float4((float)dmy, (float)dmy, (float)dmy, 0.0f);
     if (b == 0) ts[s] = 0;
     return;
@@ -193,7 +193,7 @@ __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64
   for (int d = 0; d < 3; ++d)
     v[d] = aligned_coord(coord(x32, x64, b * Q3 + 3 * (size_t)a + d), ref[3 * a + d], sc.L[d], sc.invL[d]) -
            center[3 * c + d];
-  if (F64) xq64[o] = make_double4(v[0], v[1], v[2], sc.qs[a]);
+  if (F64) xq64[o] = make_double4_32a(v[0], v[1], v[2], sc.qs[a]);
   else xq[o] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)sc.qs[a]);
   if (b == 0) ts[s] = sc.type[a];
 }
@@ -266,7 +266,7 @@ template <bool FILL, bool F64>
 __global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const double* cwrap, const float* hext,
                             const unsigned* emax, const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
                             double bw2, const int* binstart, const int* binlist, const int* perm, const int* molr,
-                            int* lcnt, const int* loff, int4* ent, double4* ent64, unsigned long long* emask) {
+                            int* lcnt, const int* loff, int4* ent, double4_32a* ent64, unsigned long long* emask) {
   const int ci = blockIdx.x * blockDim.x + threadIdx.x;
   if (ci >= max_clu) return;
   if (ci >= meta[0]) {
@@ -324,7 +324,7 @@ __global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const do
             const float fx = (float)D[0], fy = (float)D[1], fz = (float)D[2];
             ent[out] = make_int4(cj | (m ? (int)0x80000000 : 0), __float_as_int(fx), __float_as_int(fy),
                                  __float_as_int(fz));
-            if (F64) ent64[out] = make_double4(D[0], D[1], D[2], 0.0);
+            if (F64) ent64[out] = make_double4_32a(D[0], D[1], D[2], 0.0);
             emask[out] = m;
             ++out;
           }
