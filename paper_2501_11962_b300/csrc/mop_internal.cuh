@@ -49,8 +49,9 @@ struct SysConsts {
 
 // Device view of one path of a multi-path launch.
 struct PathDev {
-  int N, n_force, Q, Qpad, n_clu;
-  long long unit_off;      // first pair-kernel unit of this path
+  int N, n_force, n_hvp, Q, Qpad, n_clu;
+  long long unit_off;      // first force-kernel unit of this path
+  long long unit_off_h;    // first HVP-kernel unit of this path
   int blk_off_e1, blk_off_e2;
   const float* x32;
   const double* x64;
@@ -123,11 +124,3 @@ __device__ __forceinline__ double aligned_coord(double v, double ref, double L, 
 
 }  // namespace mop
 
-// ------------------------------------------------------------------------------------------
-// host-side launchers implemented in the .cu files
-
-namespace mop {
-
-struct PrepBuffers;   // defined in mop_host.h
-
-}  // namespace mop

@@ -1,0 +1,290 @@
+// Pair kernels of the hot path: nonbonded force F(R^n), adjoint Hessian-vector product
+// H(R^n) eta^n, and the paper's finite-difference stand-in F(R + eps eta) - F(R - eps eta).
+//
+// Paper: the three do_force calls per bead of Sec. 2.1 (Fig. 2) carry "the majority of the
+// computational effort"; the FD term is the last term of Eq. 5.  Here one persistent launch
+// covers every (path, bead, i-cluster) unit of every path.
+//
+// Work unit = one warp x one i-cluster (8 atoms) x one bead, over the i-cluster's full list of
+// j-clusters (both directions are listed, so no j-force is written and no atomics are needed).
+// Lane l handles i-atom (l & 7) against j-atoms (l >> 3) and (l >> 3) + 4 of each j-cluster.
+// Pair arithmetic is FP32 (MOP_PREC_MIXED) or FP64; FP32 partial sums over 16 j-clusters are
+// folded into an FP32 (hi, lo) pair by TwoSum, and the four lanes of an i-atom are summed in
+// FP64.  Pair potential (r < rc, shifted-force modifier by default):
+//   phi(r) = c12 r^-12 - c6 r^-6 + f q_i q_j (1/r + k_rf r^2 - c_rf)
+//   g  = -phi'_sf(r)/r                     force on i: g d,  d = r_i - r_j
+//   b  = (phi''(r) + g) / r^2              H block A = b d d^T - g I,  A u with u = eta_i - eta_j
+#include "mop_host.h"
+
+namespace mop {
+namespace {
+
+template <class R> struct Tr;
+
+template <> struct Tr<float> {
+  using V4 = float4;
+  static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ V4 xq(const PathDev& P, size_t k) { return __ldg(&P.xq[k]); }
+  static __device__ __forceinline__ void delta(const PathDev&, long long, const int4& en, float* D) {
+    D[0] = __int_as_float(en.y);
+    D[1] = __int_as_float(en.z);
+    D[2] = __int_as_float(en.w);
+  }
+  static __device__ __forceinline__ void eta(const PathDev& P, size_t k, float* u) {
+    const float4 v = __ldg(&P.eta32[k]);
+    u[0] = v.x;
+    u[1] = v.y;
+    u[2] = v.z;
+  }
+  static __device__ __forceinline__ V4 tab(const SysConsts& sc, int k) { return sc.tab[k]; }
+};
+
+template <> struct Tr<double> {
+  using V4 = double4_32a;
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ V4 xq(const PathDev& P, size_t k) { return P.xq64[k]; }
+  static __device__ __forceinline__ void delta(const PathDev& P, long long e, const int4&, double* D) {
+    const double4_32a v = P.ent64[e];
+    D[0] = v.x;
+    D[1] = v.y;
+    D[2] = v.z;
+  }
+  static __device__ __forceinline__ void eta(const PathDev& P, size_t k, double* u) {
+    u[0] = P.eta[3 * k];
+    u[1] = P.eta[3 * k + 1];
+    u[2] = P.eta[3 * k + 2];
+  }
+  static __device__ __forceinline__ V4 tab(const SysConsts& sc, int k) { return sc.tab64[k]; }
+};
+
+// Three-component accumulator: FP32 chunk sums folded into (hi, lo) by TwoSum, or plain FP64.
+template <class R> struct Acc3;
+template <> struct Acc3<float> {
+  float a[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      two_sum_add(h[k], l[k], a[k]);
+      a[k] = 0.f;
+    }
+  }
+  __device__ __forceinline__ double get(int k) const { return ((double)h[k] + (double)l[k]) + (double)a[k]; }
+};
+template <> struct Acc3<double> {
+  double a[3] = {0.0, 0.0, 0.0};
+  __device__ __forceinline__ void fold() {}
+  __device__ __forceinline__ double get(int k) const { return a[k]; }
+};
+template <class R> struct Acc1;
+template <> struct Acc1<float> {
+  float a = 0.f, h = 0.f, l = 0.f;
+  __device__ __forceinline__ void fold() { two_sum_add(h, l, a); a = 0.f; }
+  __device__ __forceinline__ double get() const { return ((double)h + (double)l) + (double)a; }
+};
+template <> struct Acc1<double> {
+  double a = 0.0;
+  __device__ __forceinline__ void fold() {}
+  __device__ __forceinline__ double get() const { return a; }
+};
+
+template <class R> struct Cst {
+  R rc, rc2, krf, crf, k2rf, drf;
+  __device__ __forceinline__ explicit Cst(const SysConsts& sc);
+};
+template <> __device__ __forceinline__ Cst<float>::Cst(const SysConsts& sc)
+    : rc(sc.rcf), rc2(sc.rc2f), krf(sc.krff), crf(sc.crff), k2rf(sc.k2rff), drf(sc.drff) {}
+template <> __device__ __forceinline__ Cst<double>::Cst(const SysConsts& sc)
+    : rc(sc.rc), rc2(sc.rc2), krf(sc.krf), crf(sc.crf), k2rf(sc.k2rf), drf(sc.drf) {}
+
+// g = -phi'_sf(r)/r from r^-1 powers; p = (12 c12, 6 c6, phi'_LJ(rc), phi_LJ(rc)), sh = phi'(rc)
+template <class R, class V4>
+__device__ __forceinline__ R pair_g(R rinv, R rinv2, R rinv6, const V4& p, R qq, R sh, R k2rf) {
+  return rinv6 * fma(p.x, rinv6, -p.y) * rinv2 + qq * fma(rinv, rinv2, -k2rf) + sh * rinv;
+}
+
+template <class R, int MODE, bool ENERGY>
+__device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab,
+                                          const PathDev& P, int n, int ci, int lane) {
+  using V4 = typename Tr<R>::V4;
+  const Cst<R> k(sc);
+  const int i = lane & 7, jj = lane >> 3;
+  const size_t bo = (size_t)n * P.Qpad;
+  const int si = ci * kCL + i;
+  const V4 xi = Tr<R>::xq(P, bo + si);
+  const int ti = __ldg(&P.ts[si]) * sc.n_types;
+  R ei[3] = {R(0), R(0), R(0)};
+  R eps = R(0);
+  if (MODE >= 1) Tr<R>::eta(P, bo + si, ei);
+  if (MODE == 2) {
+    const float mx = __uint_as_float(P.etamax[n]);
+    eps = (R)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
+  }
+  Acc3<R> acc;
+  Acc1<R> eacc;
+  const int e0 = __ldg(&P.loff[ci]), e1 = __ldg(&P.loff[ci + 1]);
+  int chunk = 0;
+  for (int e = e0; e < e1; ++e) {
+    const int4 en = __ldg(&P.ent[e]);
+    const unsigned long long m = (en.x < 0) ? __ldg(&P.emask[e]) : 0ull;
+    const int cj = en.x & 0x7fffffff;
+    R D[3];
+    Tr<R>::delta(P, e, en, D);
+    const R xs = xi.x + D[0], ys = xi.y + D[1], zs = xi.z + D[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jl = jj + 4 * h;
+      const int sj = cj * kCL + jl;
+      const V4 xj = Tr<R>::xq(P, bo + sj);
+      const int tj = __ldg(&P.ts[sj]);
+      const V4 p = tab[ti + tj];
+      const bool ex = (m >> (i * kCL + jl)) & 1ull;
+      const R qq = xi.w * xj.w;
+      const R sh = fma(qq, k.drf, p.z);
+      const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
+      if (MODE == 0) {
+        const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const bool in = (r2 < k.rc2) && !ex;
+        const R rinv = Tr<R>::rsq(r2);
+        const R rinv2 = rinv * rinv;
+        const R rinv6 = rinv2 * rinv2 * rinv2;
+        R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+        g = in ? g : R(0);
+        acc.a[0] = fma(g, dx, acc.a[0]);
+        acc.a[1] = fma(g, dy, acc.a[1]);
+        acc.a[2] = fma(g, dz, acc.a[2]);
+        if (ENERGY) {
+          // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
+          const R r = r2 * rinv;
+          const R elj = rinv6 * fma(p.x * R(1.0 / 12.0), rinv6, -p.y * R(1.0 / 6.0));
+          const R erf = qq * (rinv + fma(k.krf, r2, -k.crf));
+          const R E = elj + erf - p.w - (r - k.rc) * sh;
+          eacc.a += in ? E : R(0);
+        }
+      } else if (MODE == 1) {
+        R ej[3];
+        Tr<R>::eta(P, bo + sj, ej);
+        const R ux = ei[0] - ej[0], uy = ei[1] - ej[1], uz = ei[2] - ej[2];
+        const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const bool in = (r2 < k.rc2) && !ex;
+        const R rinv = Tr<R>::rsq(r2);
+        const R rinv2 = rinv * rinv;
+        const R rinv3 = rinv * rinv2;
+        const R rinv6 = rinv2 * rinv2 * rinv2;
+        R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+        const R b = rinv6 * fma(R(14) * p.x, rinv6, R(-8) * p.y) * rinv2 * rinv2 + fma(R(3) * qq, rinv2, sh) * rinv3;
+        const R s = fma(dx, ux, fma(dy, uy, dz * uz));
+        const R t = in ? b * s : R(0);
+        g = in ? g : R(0);
+        acc.a[0] += fma(t, dx, -g * ux);
+        acc.a[1] += fma(t, dy, -g * uy);
+        acc.a[2] += fma(t, dz, -g * uz);
+      } else {
+        R ej[3];
+        Tr<R>::eta(P, bo + sj, ej);
+        const R ux = eps * (ei[0] - ej[0]), uy = eps * (ei[1] - ej[1]), uz = eps * (ei[2] - ej[2]);
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          const R px = sgn ? dx - ux : dx + ux, py = sgn ? dy - uy : dy + uy, pz = sgn ? dz - uz : dz + uz;
+          const R r2 = fma(px, px, fma(py, py, pz * pz));
+          const bool in = (r2 < k.rc2) && !ex;
+          const R rinv = Tr<R>::rsq(r2);
+          const R rinv2 = rinv * rinv;
+          const R rinv6 = rinv2 * rinv2 * rinv2;
+          R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+          g = in ? (sgn ? -g : g) : R(0);
+          acc.a[0] = fma(g, px, acc.a[0]);
+          acc.a[1] = fma(g, py, acc.a[1]);
+          acc.a[2] = fma(g, pz, acc.a[2]);
+        }
+      }
+    }
+    if (++chunk == 16) {
+      acc.fold();
+      if (ENERGY) eacc.fold();
+      chunk = 0;
+    }
+  }
+  const bool valid = __ldg(&P.perm[si]) >= 0;
+  double out[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double v = acc.get(c);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    out[c] = valid ? v : 0.0;
+  }
+  if (jj == 0) {
+    double* dst = (MODE == 0 ? P.Fnb : P.Hnb) + 3 * (bo + si);
+    const double scale = (MODE == 2) ? -0.5 / (double)eps : 1.0;
+    dst[0] = out[0] * scale;
+    dst[1] = out[1] * scale;
+    dst[2] = out[2] * scale;
+  }
+  if (ENERGY) {
+    double ev = valid ? eacc.get() : 0.0;
+    ev = warp_sum(ev);
+    if (lane == 0) P.e_pair[ci] = 0.5 * ev;   // full list: every pair seen twice
+  }
+}
+
+template <class R, int MODE>
+__global__ void __launch_bounds__(128) k_pair(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+                                              long long n_units) {
+  using V4 = typename Tr<R>::V4;
+  __shared__ V4 tab[kMaxTypes * kMaxTypes];
+  const int nt2 = sc.n_types * sc.n_types;
+  for (int k = threadIdx.x; k < nt2; k += blockDim.x) tab[k] = Tr<R>::tab(sc, k);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nw) {
+    int p = 0;
+    if (MODE == 0) {
+      while (p + 1 < n_paths && paths[p + 1].unit_off <= u) ++p;
+    } else {
+      while (p + 1 < n_paths && paths[p + 1].unit_off_h <= u) ++p;
+    }
+    const PathDev& P = paths[p];
+    const int nb = MODE == 0 ? P.n_force : P.n_hvp;
+    const long long v = u - (MODE == 0 ? P.unit_off : P.unit_off_h);
+    const int n = (int)(v % nb);
+    const int ci = (int)(v / nb);
+    if (MODE == 0 && n == 0) pair_unit<R, 0, true>(sc, tab, P, n, ci, lane);
+    else pair_unit<R, MODE, false>(sc, tab, P, n, ci, lane);
+  }
+}
+
+template <class R, int MODE>
+cudaError_t launch_one(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int num_sms,
+                       Launch L) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R, MODE>, 128, 0);
+    if (e != cudaSuccess || per_sm <= 0) per_sm = 4;
+  }
+  const long long want_blocks = (n_units + 3) / 4;
+  long long blocks = (long long)num_sms * per_sm;
+  if (blocks > want_blocks) blocks = want_blocks;
+  if (blocks < 1) blocks = 1;
+  k_pair<R, MODE><<<(int)blocks, 128, 0, L.st>>>(sc, d_paths, n_paths, n_units);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
+                        int num_sms, Launch L) {
+  if (n_units <= 0) return cudaSuccess;
+  const bool f64 = sc.precision == 1;
+  switch (mode) {
+    case 0: return f64 ? launch_one<double, 0>(sc, d_paths, n_paths, n_units, num_sms, L)
+                       : launch_one<float, 0>(sc, d_paths, n_paths, n_units, num_sms, L);
+    case 1: return f64 ? launch_one<double, 1>(sc, d_paths, n_paths, n_units, num_sms, L)
+                       : launch_one<float, 1>(sc, d_paths, n_paths, n_units, num_sms, L);
+    default: return f64 ? launch_one<double, 2>(sc, d_paths, n_paths, n_units, num_sms, L)
+                        : launch_one<float, 2>(sc, d_paths, n_paths, n_units, num_sms, L);
+  }
+}
+
+}  // namespace mop
