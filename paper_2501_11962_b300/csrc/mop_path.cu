@@ -1,0 +1,537 @@
+// Elementwise kernels of the path: bonded terms and eta (after the force pass), bonded HVP and
+// the path gradient (after the HVP pass), the metadynamics bias, the deterministic V_eff
+// reduction, and the path-dynamics integrator.
+//
+// Paper: the seven PMD kernels of Sec. 2.1 (Fig. 2): eta^n = R^{n+1} - R^n - L^n (kernel 1),
+// the effective forces of Eqs. 5, 6, 7 (kernels 4-6), the spring energy (kernel 7); the bias of
+// Sec. 1.2 with the CV of Eq. 8; the dynamics of Eq. 4.  The exact gradient written here,
+//   G^1 = -F^1 - K eta^1 + H eta^1 / 2,   G^n = K eta^{n-1} - K eta^n + H eta^n / 2,
+//   G^N = K eta^{N-1},
+// equals minus the effective force of Eqs. 5-7 once the FD term is replaced by -H eta / 2
+// (K_i L^n_i = F^n_i / 2 turns K eta^{n-1} into K (R^n - R^{n-1}) - F^{n-1} / 2).
+#include "mop_host.h"
+
+namespace mop {
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// forward-mode dual numbers (value, tangent) for the bonded Hessian-vector product
+
+template <class R> struct Dl {
+  R v, d;
+};
+template <class R> __device__ __forceinline__ Dl<R> operator+(Dl<R> a, Dl<R> b) { return {a.v + b.v, a.d + b.d}; }
+template <class R> __device__ __forceinline__ Dl<R> operator-(Dl<R> a, Dl<R> b) { return {a.v - b.v, a.d - b.d}; }
+template <class R> __device__ __forceinline__ Dl<R> operator-(Dl<R> a) { return {-a.v, -a.d}; }
+template <class R> __device__ __forceinline__ Dl<R> operator*(Dl<R> a, Dl<R> b) {
+  return {a.v * b.v, a.v * b.d + a.d * b.v};
+}
+template <class R> __device__ __forceinline__ Dl<R> operator*(R s, Dl<R> a) { return {s * a.v, s * a.d}; }
+template <class R> __device__ __forceinline__ Dl<R> operator/(Dl<R> a, Dl<R> b) {
+  const R iv = R(1) / b.v;
+  return {a.v * iv, (a.d - a.v * iv * b.d) * iv};
+}
+template <class R> __device__ __forceinline__ Dl<R> dsqrt(Dl<R> a) {
+  const R s = sqrt(a.v);
+  return {s, a.d / (R(2) * s)};
+}
+template <class R> __device__ __forceinline__ Dl<R> dacos(Dl<R> a) {
+  return {acos(a.v), -a.d / sqrt(R(1) - a.v * a.v)};
+}
+__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float dacos(float a) { return acosf(a); }
+__device__ __forceinline__ double dacos(double a) { return acos(a); }
+template <class R> __device__ __forceinline__ R cst(double c) { return (R)c; }
+
+template <class T, class R> struct Mk {
+  static __device__ __forceinline__ T c(R v) { return v; }
+};
+template <class R> struct Mk<Dl<R>, R> {
+  static __device__ __forceinline__ Dl<R> c(R v) { return {v, R(0)}; }
+};
+
+// harmonic bond k/2 (|d| - r0)^2, d = x_i - x_j: force on the atom with the given role
+template <class T, class R>
+__device__ __forceinline__ void bond_force(const T* d, R r0, R k, int role, T* f, R* U) {
+  const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const T r = dsqrt(r2);
+  const T dr = r - Mk<T, R>::c(r0);
+  const T s = (-k) * (dr / r);
+  const R sg = role == 0 ? R(1) : R(-1);
+  for (int c = 0; c < 3; ++c) f[c] = sg * (s * d[c]);
+  if (U) {
+    const T u = dr * dr;
+    if constexpr (sizeof(T) == sizeof(R)) *U = R(0.5) * k * u;
+  }
+}
+
+// harmonic angle k/2 (theta - theta0)^2 at vertex j; p = x_i - x_j, q = x_k - x_j
+template <class T, class R>
+__device__ __forceinline__ void angle_force(const T* p, const T* q, R th0, R k, int role, T* f, R* U) {
+  const T pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+  const T qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+  const T pq = p[0] * q[0] + p[1] * q[1] + p[2] * q[2];
+  const T inpq = Mk<T, R>::c(R(1)) / (dsqrt(pp) * dsqrt(qq));
+  const T c = pq * inpq;
+  const T th = dacos(c);
+  const T dth = th - Mk<T, R>::c(th0);
+  const T sn = dsqrt(Mk<T, R>::c(R(1)) - c * c);
+  const T G = k * (dth / sn);   // -dU/dcos
+  const T cp = c / pp, cq = c / qq;
+  for (int m = 0; m < 3; ++m) {
+    const T dcp = q[m] * inpq - cp * p[m];
+    const T dcq = p[m] * inpq - cq * q[m];
+    const T fi = G * dcp, fk = G * dcq;
+    f[m] = role == 0 ? fi : (role == 2 ? fk : -(fi + fk));
+  }
+  if (U) {
+    if constexpr (sizeof(T) == sizeof(R)) *U = R(0.5) * k * dth * dth;
+  }
+}
+
+// minimum-image difference x_a - x_b of bead n in the caller's coordinates
+template <class R>
+__device__ __forceinline__ void mi_diff(const SysConsts& sc, const PathDev& P, int n, int a, int b, R* d) {
+  const size_t base = (size_t)n * 3 * P.Q;
+  if (P.x64) {
+    for (int c = 0; c < 3; ++c) {
+      double v = P.x64[base + 3 * (size_t)a + c] - P.x64[base + 3 * (size_t)b + c];
+      v -= sc.L[c] * rint(v * sc.invL[c]);
+      d[c] = (R)v;
+    }
+    return;
+  }
+  for (int c = 0; c < 3; ++c) {
+    const float xa = P.x32[base + 3 * (size_t)a + c], xb = P.x32[base + 3 * (size_t)b + c];
+    float v = xa - xb;   // exact when both lie in the same periodic image
+    if (fabsf(v) > sc.halfLf[c]) {
+      double w = (double)xa - (double)xb;
+      w -= sc.L[c] * rint(w * sc.invL[c]);
+      v = (float)w;
+    }
+    d[c] = (R)v;
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void eta_of(const PathDev& P, int n, int atom, R* e) {
+  const size_t k = (size_t)n * P.Qpad + P.slot[atom];
+  if (sizeof(R) == 4) {
+    const float4 v = P.eta32[k];
+    e[0] = (R)v.x;
+    e[1] = (R)v.y;
+    e[2] = (R)v.z;
+  } else {
+    e[0] = (R)P.eta[3 * k];
+    e[1] = (R)P.eta[3 * k + 1];
+    e[2] = (R)P.eta[3 * k + 2];
+  }
+}
+
+// Bonded force on atom a at bead n, accumulated in FP64; U (if non-NULL) gets the energy of
+// the terms for which a has role 0 (so that every term is counted once).
+template <class R>
+__device__ void bonded_force(const SysConsts& sc, const PathDev& P, int a, int n, double* F, double* U) {
+  for (int t = sc.inc_off[a]; t < sc.inc_off[a + 1]; ++t) {
+    const int4 in = sc.inc[t];
+    const double2 pr = sc.incp[t];
+    const int kind = in.x & 3, role = in.x >> 2;
+    R f[3];
+    R u = R(0);
+    if (kind == 0) {
+      R d[3];
+      mi_diff<R>(sc, P, n, in.y, in.z, d);
+      bond_force<R, R>(d, (R)pr.x, (R)pr.y, role, f, U && role == 0 ? &u : nullptr);
+    } else {
+      R p[3], q[3];
+      mi_diff<R>(sc, P, n, in.y, in.z, p);
+      mi_diff<R>(sc, P, n, in.w, in.z, q);
+      angle_force<R, R>(p, q, (R)pr.x, (R)pr.y, role, f, U && role == 0 ? &u : nullptr);
+    }
+    F[0] += (double)f[0];
+    F[1] += (double)f[1];
+    F[2] += (double)f[2];
+    if (U && role == 0) *U += (double)u;
+  }
+}
+
+// Bonded H eta on atom a at bead n: adjoint (dual numbers) or central difference with eps.
+template <class R, bool FD>
+__device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, double eps, double* H) {
+  for (int t = sc.inc_off[a]; t < sc.inc_off[a + 1]; ++t) {
+    const int4 in = sc.inc[t];
+    const double2 pr = sc.incp[t];
+    const int kind = in.x & 3, role = in.x >> 2;
+    // relative vectors and their tangents (differences of eta)
+    R v1[3], v2[3], t1[3], t2[3];
+    R ei[3], ej[3], ek[3];
+    eta_of<R>(P, n, in.y, ei);
+    eta_of<R>(P, n, in.z, ej);
+    mi_diff<R>(sc, P, n, in.y, in.z, v1);
+    for (int c = 0; c < 3; ++c) t1[c] = ei[c] - ej[c];
+    if (kind == 1) {
+      eta_of<R>(P, n, in.w, ek);
+      mi_diff<R>(sc, P, n, in.w, in.z, v2);
+      for (int c = 0; c < 3; ++c) t2[c] = ek[c] - ej[c];
+    }
+    if (!FD) {
+      Dl<R> d1[3], d2[3], f[3];
+      for (int c = 0; c < 3; ++c) {
+        d1[c] = {v1[c], t1[c]};
+        d2[c] = {kind == 1 ? v2[c] : R(0), kind == 1 ? t2[c] : R(0)};
+      }
+      if (kind == 0) bond_force<Dl<R>, R>(d1, (R)pr.x, (R)pr.y, role, f, nullptr);
+      else angle_force<Dl<R>, R>(d1, d2, (R)pr.x, (R)pr.y, role, f, nullptr);
+      for (int c = 0; c < 3; ++c) H[c] -= (double)f[c].d;   // H eta = -d/dt F(x + t eta)
+    } else {
+      R fp[3], fm[3], a1[3], a2[3];
+      const R e = (R)eps;
+      for (int s = 0; s < 2; ++s) {
+        const R sg = s == 0 ? e : -e;
+        for (int c = 0; c < 3; ++c) {
+          a1[c] = v1[c] + sg * t1[c];
+          a2[c] = kind == 1 ? v2[c] + sg * t2[c] : R(0);
+        }
+        R* f = s == 0 ? fp : fm;
+        if (kind == 0) bond_force<R, R>(a1, (R)pr.x, (R)pr.y, role, f, nullptr);
+        else angle_force<R, R>(a1, a2, (R)pr.x, (R)pr.y, role, f, nullptr);
+      }
+      for (int c = 0; c < 3; ++c) H[c] -= ((double)fp[c] - (double)fm[c]) / (2.0 * eps);
+    }
+  }
+}
+
+// E1: F^n = F_nonbonded + F_bonded, eta^n = R^{n+1} - R^n - c F^n (FP64), bonded energy of bead 1
+template <class R>
+__global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+                                                  double* e_bond, int stride) {
+  __shared__ double sh[32];
+  const int p = blockIdx.y;
+  if (p >= n_paths) return;
+  const PathDev& P = paths[p];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)P.n_force * P.Qpad;
+  double eb = 0.0;
+  if (t < total) {
+    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+    const size_t k = (size_t)n * P.Qpad + s;
+    const int a = P.perm[s];
+    double F[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
+    if (a >= 0) {
+      F[0] = P.Fnb[3 * k];
+      F[1] = P.Fnb[3 * k + 1];
+      F[2] = P.Fnb[3 * k + 2];
+      bonded_force<R>(sc, P, a, n, F, n == 0 ? &eb : nullptr);
+      if (P.N > 1) {
+        const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
+        const double c = sc.cL[a];
+        for (int d = 0; d < 3; ++d) {
+          const double x0 = P.x64 ? P.x64[b0 + d] : (double)P.x32[b0 + d];
+          const double x1 = P.x64 ? P.x64[b1 + d] : (double)P.x32[b1 + d];
+          e[d] = (x1 - x0) - c * F[d];
+        }
+        if (sc.hvp_mode == 1) {
+          const double nrm = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+          atomicMax(&P.etamax[n], __float_as_uint(__double2float_ru(nrm)));
+        }
+      }
+    }
+    P.F[3 * k] = F[0];
+    P.F[3 * k + 1] = F[1];
+    P.F[3 * k + 2] = F[2];
+    if (P.N > 1) {
+      P.eta[3 * k] = e[0];
+      P.eta[3 * k + 1] = e[1];
+      P.eta[3 * k + 2] = e[2];
+      P.eta32[k] = make_float4((float)e[0], (float)e[1], (float)e[2], 0.f);
+    }
+  }
+  const double tot = block_sum<kRedBlock>(eb, sh);
+  if (threadIdx.x == 0) e_bond[(size_t)p * stride + blockIdx.x] = tot;
+}
+
+// E2: bonded H eta, H eta total, path gradient (caller order), spring energy
+template <class R, bool FD>
+__global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+                                                  double* e_spring, int stride) {
+  __shared__ double sh[32];
+  const int p = blockIdx.y;
+  if (p >= n_paths) return;
+  const PathDev& P = paths[p];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)P.N * P.Qpad;
+  double es = 0.0;
+  if (t < total) {
+    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+    const int a = P.perm[s];
+    const size_t k = (size_t)n * P.Qpad + s;
+    if (a >= 0) {
+      const double K = sc.Kspr[a];
+      double g[3] = {0.0, 0.0, 0.0};
+      if (n == 0)
+        for (int c = 0; c < 3; ++c) g[c] -= P.F[3 * (size_t)s + c];
+      if (n > 0) {
+        const size_t km = k - P.Qpad;
+        for (int c = 0; c < 3; ++c) g[c] += K * P.eta[3 * km + c];
+      }
+      if (n < P.N - 1) {
+        double H[3] = {P.Hnb[3 * k], P.Hnb[3 * k + 1], P.Hnb[3 * k + 2]};
+        double eps = 0.0;
+        if (FD) {
+          const float mx = __uint_as_float(P.etamax[n]);
+          eps = mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h;
+          // the pair kernel used the same eps rounded to the pair precision
+          eps = (double)(R)eps;
+        }
+        bonded_hvp<R, FD>(sc, P, a, n, eps, H);
+        double e2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          const double e = P.eta[3 * k + c];
+          P.Heta[3 * k + c] = H[c];
+          g[c] += -K * e + 0.5 * H[c];
+          e2 += e * e;
+        }
+        es = 0.5 * K * e2;
+      }
+      double* G = P.grad + 3 * ((size_t)n * P.Q + a);
+      G[0] = g[0];
+      G[1] = g[1];
+      G[2] = g[2];
+    }
+  }
+  const double tot = block_sum<kRedBlock>(es, sh);
+  if (threadIdx.x == 0) e_spring[(size_t)p * stride + blockIdx.x] = tot;
+}
+
+// centroid of a group at bead n, each atom unwrapped relative to the group's first atom
+__device__ void centroid(const SysConsts& sc, const PathDev& P, int n, const int* g, int ng, double* c) {
+  const size_t base = (size_t)n * 3 * P.Q;
+  double x0[3], acc[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < 3; ++d) x0[d] = P.x64 ? P.x64[base + 3 * (size_t)g[0] + d] : (double)P.x32[base + 3 * (size_t)g[0] + d];
+  for (int k = 0; k < ng; ++k)
+    for (int d = 0; d < 3; ++d) {
+      const double v = P.x64 ? P.x64[base + 3 * (size_t)g[k] + d] : (double)P.x32[base + 3 * (size_t)g[k] + d];
+      double w = v - x0[d];
+      w -= sc.L[d] * rint(w * sc.invL[d]);
+      acc[d] += w;
+    }
+  for (int d = 0; d < 3; ++d) c[d] = x0[d] + acc[d] / ng;
+}
+
+// distance CV s = |c_A - c_B| (minimum image) at bead n; u = (c_A - c_B) / s
+__device__ double cv_at(const SysConsts& sc, const PathDev& P, int n, double* u) {
+  double ca[3], cb[3];
+  centroid(sc, P, n, P.gA, P.nA, ca);
+  centroid(sc, P, n, P.gB, P.nB, cb);
+  double s2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double w = ca[d] - cb[d];
+    w -= sc.L[d] * rint(w * sc.invL[d]);
+    u[d] = w;
+    s2 += w * w;
+  }
+  const double s = sqrt(s2);
+  for (int d = 0; d < 3; ++d) u[d] /= s;
+  return s;
+}
+
+// metadynamics bias (one block per path)
+__global__ void k_bias(SysConsts sc, const PathDev* __restrict__ paths, int n_paths) {
+  __shared__ double sh[32];
+  __shared__ double sS;
+  const PathDev& P = paths[blockIdx.x];
+  const bool on = P.n_gauss > 0 && P.nA > 0 && P.nB > 0;
+  double uN[3], u1[3];
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    if (on) {
+      S = cv_at(sc, P, P.N - 1, uN);
+      if (P.e2e) S -= cv_at(sc, P, 0, u1);
+    }
+    sS = S;
+  }
+  __syncthreads();
+  const double S = sS;
+  double V = 0.0, dV = 0.0;
+  if (on)
+    for (int k = threadIdx.x; k < P.n_gauss; k += blockDim.x) {
+      const double z = (S - P.gc[k]) / P.gw[k];
+      const double e = P.gh[k] * exp(-0.5 * z * z);
+      V += e;
+      dV -= e * z / P.gw[k];
+    }
+  V = block_sum<kRedBlock>(V, sh);
+  dV = block_sum<kRedBlock>(dV, sh);
+  if (threadIdx.x == 0) {
+    if (on && P.grad) {
+      const int nl = P.N - 1;
+      for (int k = 0; k < P.nA; ++k)
+        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gA[k]) + d] += dV * uN[d] / P.nA;
+      for (int k = 0; k < P.nB; ++k)
+        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gB[k]) + d] -= dV * uN[d] / P.nB;
+      if (P.e2e) {
+        for (int k = 0; k < P.nA; ++k)
+          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gA[k]) + d] -= dV * u1[d] / P.nA;
+        for (int k = 0; k < P.nB; ++k)
+          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gB[k]) + d] += dV * u1[d] / P.nB;
+      }
+    }
+    P.diag[2] = on ? V : 0.0;
+    P.diag[3] = S;
+  }
+}
+
+// fixed-order sums of the partial energies -> V_eff (one block per path)
+__global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const double* e_bond, int sb, int nb1,
+                         const double* e_spring, int ss, int nb2) {
+  __shared__ double sh[32];
+  const int p = blockIdx.x;
+  const PathDev& P = paths[p];
+  double up = 0.0, ub = 0.0, es = 0.0;
+  for (int k = threadIdx.x; k < P.n_clu; k += blockDim.x) up += P.e_pair[k];
+  for (int k = threadIdx.x; k < nb1; k += blockDim.x) ub += e_bond[(size_t)p * sb + k];
+  for (int k = threadIdx.x; k < nb2; k += blockDim.x) es += e_spring[(size_t)p * ss + k];
+  up = block_sum<kRedBlock>(up, sh);
+  ub = block_sum<kRedBlock>(ub, sh);
+  es = block_sum<kRedBlock>(es, sh);
+  if (threadIdx.x == 0) {
+    const double U1 = up + ub;
+    const double V = U1 + es + P.diag[2];
+    P.diag[0] = U1;
+    P.diag[1] = es;
+    P.diag[4] = V;
+    P.diag[5] = up;
+    P.diag[6] = ub;
+    if (P.veff_out) *P.veff_out = V;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// integrator
+
+// Philox-4x32-10 (Salmon et al., SC'11): four 32-bit words per (counter, key)
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__global__ void k_kick(int n3Q, int Q, int N, const double* mass, double* vel, const double* grad, double half_dt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * n3Q) return;
+  const int a = (int)((t % n3Q) / 3);
+  vel[t] -= half_dt * grad[t] / mass[a];
+}
+
+__global__ void k_drift(int Q, int N, const double* mass, double* x64, double* vel, float* x32, double dt, double c1,
+                        double c2, double kT, uint64_t seed, uint64_t step) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * Q) return;
+  const int a = (int)(t % Q), n = (int)(t / Q);
+  double* x = x64 + 3 * t;
+  double* v = vel + 3 * t;
+  for (int d = 0; d < 3; ++d) x[d] += 0.5 * dt * v[d];
+  if (c2 > 0.0) {
+    const uint4 w = philox(make_uint4((uint32_t)a, (uint32_t)n, (uint32_t)step, (uint32_t)(step >> 32)),
+                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double inv32 = 2.3283064365386963e-10;   // 2^-32
+    const double u1 = ((double)w.x + 1.0) * inv32, u2 = (double)w.y * inv32;
+    const double u3 = ((double)w.z + 1.0) * inv32, u4 = (double)w.w * inv32;
+    const double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u3));
+    double s1, c1p, s2, c2p;
+    sincospi(2.0 * u2, &s1, &c1p);
+    sincospi(2.0 * u4, &s2, &c2p);
+    const double g[3] = {r1 * c1p, r1 * s1, r2 * c2p};
+    const double sd = c2 * sqrt(kT / mass[a]);
+    for (int d = 0; d < 3; ++d) v[d] = c1 * v[d] + sd * g[d];
+  }
+  for (int d = 0; d < 3; ++d) {
+    x[d] += 0.5 * dt * v[d];
+    x32[3 * t + d] = (float)x[d];
+  }
+}
+
+__global__ void k_kinetic(int Q, int N, const double* mass, const double* vel, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < (long long)N * Q; t += blockDim.x) {
+    const double* v = vel + 3 * t;
+    s += 0.5 * mass[t % Q] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  }
+  s = block_sum<kRedBlock>(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
+                      double* e_bond, int stride) {
+  dim3 grid(nblk(max_threads, kRedBlock), n_paths);
+  if (sc.precision == 1) k_e1<double><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
+  else k_e1<float><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
+                      double* e_spring, int stride) {
+  dim3 grid(nblk(max_threads, kRedBlock), n_paths);
+  const bool fd = sc.hvp_mode == 1;
+  if (sc.precision == 1) {
+    if (fd) k_e2<double, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+    else k_e2<double, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+  } else {
+    if (fd) k_e2<float, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+    else k_e2<float, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+  }
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L) {
+  k_bias<<<n_paths, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L, const double* e_bond,
+                          int sb, int nb1, const double* e_spring, int ss, int nb2) {
+  (void)sc;
+  k_reduce<<<n_paths, kRedBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, int N, double half_dt, Launch L) {
+  const long long n = (long long)N * 3 * sc.Q;
+  k_kick<<<nblk(n, kRedBlock), kRedBlock, 0, L.st>>>(3 * sc.Q, sc.Q, N, sc.mass, vel, grad, half_dt);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drift(const SysConsts& sc, double* x64, double* vel, float* x32, int N, double dt, double gamma,
+                         double kT, uint64_t seed, uint64_t step, int, Launch L) {
+  const double c1 = gamma > 0.0 ? exp(-gamma * dt) : 1.0;
+  const double c2 = gamma > 0.0 ? sqrt(1.0 - c1 * c1) : 0.0;
+  const long long n = (long long)N * sc.Q;
+  k_drift<<<nblk(n, kRedBlock), kRedBlock, 0, L.st>>>(sc.Q, N, sc.mass, x64, vel, x32, dt, c1, c2, kT, seed, step);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic(const SysConsts& sc, const double* vel, int N, double* out, Launch L) {
+  k_kinetic<<<1, kRedBlock, 0, L.st>>>(sc.Q, N, sc.mass, vel, out);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+}  // namespace mop
