@@ -114,11 +114,16 @@ struct PairParams {
 struct Model {
   const orc_system& s;
   double krf, crf;
+  double rc6, rc7, rc12, rc13;     // powers of rc for the cutoff constants
   std::vector<double> c6t, c12t;   // per type pair, Lorentz-Berthelot
   explicit Model(const orc_system& sys) : s(sys) {
     const double rc = s.rc;
     krf = (s.eps_rf - 1.0) / ((2.0 * s.eps_rf + 1.0) * rc * rc * rc);
     crf = 1.0 / rc + krf * rc * rc;
+    rc6 = std::pow(rc, 6);
+    rc7 = std::pow(rc, 7);
+    rc12 = std::pow(rc, 12);
+    rc13 = std::pow(rc, 13);
     const int nt = s.n_types;
     c6t.resize(nt * nt);
     c12t.resize(nt * nt);
@@ -141,8 +146,8 @@ struct Model {
     p.c12 = c12t[t];
     p.qq = kCoulomb * s.charge[i] * s.charge[j];
     const double rc = s.rc;
-    p.phi_rc = p.c12 / std::pow(rc, 12) - p.c6 / std::pow(rc, 6) + p.qq * (1.0 / rc + krf * rc * rc - crf);
-    p.dphi_rc = -12.0 * p.c12 / std::pow(rc, 13) + 6.0 * p.c6 / std::pow(rc, 7) +
+    p.phi_rc = p.c12 / rc12 - p.c6 / rc6 + p.qq * (1.0 / rc + krf * rc * rc - crf);
+    p.dphi_rc = -12.0 * p.c12 / rc13 + 6.0 * p.c6 / rc7 +
                 p.qq * (-1.0 / (rc * rc) + 2.0 * krf * rc);
     return p;
   }

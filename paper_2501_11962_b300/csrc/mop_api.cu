@@ -1,0 +1,625 @@
+// C ABI of the engine (include/mop.h): handle, validation, uploads, and the order of the
+// kernel passes of one evaluation of V_eff and its gradient (Eq. 3, Eqs. 5-7):
+//   per path: spatial sort + cluster-pair list (mop_prep.cu)
+//   all paths, one launch each: pair force -> bonded + eta -> pair HVP (adjoint or FD) ->
+//   bonded HVP + gradient -> bias -> V_eff reduction
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mop.h"
+#include "mop_host.h"
+
+using namespace mop;
+
+struct mop_handle {
+  int device = 0;
+  int num_sms = 148;
+  SysConsts sc{};
+  Grid grid{};
+  int hvp_mode = 0, precision = 0;
+  double temperature = 300.0, fd_h = 1e-5;
+  std::string err;
+  int launches = 0;
+  uint64_t step_count = 0;
+  // device copies of the system
+  DevBuf<double> mass, Kspr, cL, qs;
+  DevBuf<int> type, mol, loc, inc_off;
+  DevBuf<int4> inc;
+  DevBuf<double2> incp;
+  DevBuf<float4> tab;
+  DevBuf<double4_32a> tab64;
+  // paths
+  PathHost paths[kMaxPaths];
+  DevBuf<PathDev> d_paths;
+  DevBuf<double> e_bond, e_spring, scratch;
+};
+
+namespace {
+
+mop_status fail(mop_handle* h, mop_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return s;
+}
+
+mop_status cuda_fail(mop_handle* h, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(h, e == cudaErrorMemoryAllocation ? MOP_ERR_OOM : MOP_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(h, x)                                   \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #x); \
+  } while (0)
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+__global__ void k_f2d(const float* in, double* out, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (double)in[t];
+}
+__global__ void k_d2f(const double* in, float* out, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (float)in[t];
+}
+
+// slot-ordered field -> caller-ordered [N][Q][3], zero rows outside [0, n_rows)
+__global__ void k_gather_field(const double* f, const int* slot, int Q, int Qpad, int N, int n_rows, double* out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * Q) return;
+  const int a = (int)(t % Q), n = (int)(t / Q);
+  for (int c = 0; c < 3; ++c)
+    out[3 * t + c] = n < n_rows ? f[3 * ((size_t)n * Qpad + slot[a]) + c] : 0.0;
+}
+
+inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+template <class T>
+mop_status upload(mop_handle* h, DevBuf<T>& b, const T* src, size_t n) {
+  CK(h, b.ensure(n));
+  if (n) CK(h, cudaMemcpy(b.p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return MOP_OK;
+}
+
+// Evaluates the listed paths.  dev_veff/dev_grad: caller device pointers (or NULL for the
+// handle's buffers).  Enqueues everything on st; the only host synchronisation is the read of
+// the cluster and pair counts in prep_path.
+mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff, double* dev_grad,
+                    cudaStream_t st) {
+  SysConsts& sc = h->sc;
+  Launch L{st, &h->launches};
+  const bool fd = h->hvp_mode == MOP_HVP_FD;
+  const double margin = fd ? h->fd_h : 0.0;
+  std::vector<PathDev> pd(ids.size());
+  long long units = 0, units_h = 0;
+  long long max_e1 = 0, max_e2 = 0;
+  size_t goff = 0;
+  for (size_t k = 0; k < ids.size(); ++k) {
+    PathHost& P = h->paths[ids[k]];
+    std::string err;
+    cudaError_t e = prep_path(sc, h->grid, P, margin, L, &err);
+    if (e != cudaSuccess) return fail(h, e == cudaErrorMemoryAllocation ? MOP_ERR_OOM : MOP_ERR_CUDA, "%s", err.c_str());
+    const int N = P.N, Qpad = P.n_clu * kCL;
+    const int n_force = N == 1 ? 1 : N - 1, n_hvp = N - 1;
+    const size_t nq3 = 3 * (size_t)N * Qpad;
+    CK(h, P.Fnb.ensure(3 * (size_t)n_force * Qpad));
+    CK(h, P.F.ensure(nq3));
+    CK(h, P.eta.ensure(nq3));
+    CK(h, P.eta32.ensure((size_t)N * Qpad));
+    CK(h, P.Hnb.ensure(nq3));
+    CK(h, P.Heta.ensure(nq3));
+    CK(h, P.etamax.ensure(N));
+    CK(h, P.e_pair.ensure(P.n_clu));
+    CK(h, P.diag.ensure(8));
+    CK(h, P.veff_int.ensure(1));
+    CK(h, P.grad_int.ensure(3 * (size_t)N * sc.Q));
+    CK(h, cudaMemsetAsync(P.etamax.p, 0, sizeof(unsigned) * N, st));
+    PathDev& D = pd[k];
+    memset(&D, 0, sizeof(D));
+    D.N = N;
+    D.n_force = n_force;
+    D.n_hvp = n_hvp;
+    D.Q = sc.Q;
+    D.Qpad = Qpad;
+    D.n_clu = P.n_clu;
+    D.unit_off = units;
+    D.unit_off_h = units_h;
+    units += (long long)n_force * P.n_clu;
+    units_h += (long long)n_hvp * P.n_clu;
+    max_e1 = std::max(max_e1, (long long)n_force * Qpad);
+    max_e2 = std::max(max_e2, (long long)N * Qpad);
+    D.x32 = h->precision == MOP_PREC_FP64 ? nullptr : P.x32.p;
+    D.x64 = h->precision == MOP_PREC_FP64 ? P.x64.p : nullptr;
+    D.perm = P.perm.p;
+    D.slot = P.slot.p;
+    D.xq = P.xq.p;
+    D.xq64 = P.xq64.p;
+    D.ts = P.ts.p;
+    D.loff = P.loff.p;
+    D.ent = P.ent.p;
+    D.ent64 = P.ent64.p;
+    D.emask = P.emask.p;
+    D.Fnb = P.Fnb.p;
+    D.F = P.F.p;
+    D.eta = P.eta.p;
+    D.eta32 = P.eta32.p;
+    D.Hnb = P.Hnb.p;
+    D.Heta = P.Heta.p;
+    D.etamax = P.etamax.p;
+    D.e_pair = P.e_pair.p;
+    D.grad = dev_grad ? dev_grad + goff : P.grad_int.p;
+    goff += 3 * (size_t)N * sc.Q;
+    D.nA = (int)P.hA.size();
+    D.nB = (int)P.hB.size();
+    D.n_gauss = (int)P.hc.size();
+    D.e2e = P.e2e;
+    D.gA = P.gA.p;
+    D.gB = P.gB.p;
+    D.gc = P.gc.p;
+    D.gh = P.gh.p;
+    D.gw = P.gw.p;
+    D.diag = P.diag.p;
+    D.veff_out = dev_veff ? dev_veff + k : P.veff_int.p;
+  }
+  const int np = (int)ids.size();
+  const int sb = nblk(max_e1, kRedBlock), ss = nblk(max_e2, kRedBlock);
+  CK(h, h->e_bond.ensure((size_t)np * sb));
+  CK(h, h->e_spring.ensure((size_t)np * ss));
+  CK(h, h->d_paths.ensure(np));
+  CK(h, cudaMemcpyAsync(h->d_paths.p, pd.data(), sizeof(PathDev) * np, cudaMemcpyHostToDevice, st));
+  CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
+  CK(h, launch_e1(sc, h->d_paths.p, np, (int)max_e1, L, h->e_bond.p, sb));
+  if (units_h > 0) CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+  CK(h, launch_e2(sc, h->d_paths.p, np, (int)max_e2, L, h->e_spring.p, ss));
+  CK(h, launch_bias(sc, h->d_paths.p, np, L));
+  CK(h, launch_reduce(sc, h->d_paths.p, np, L, h->e_bond.p, sb, sb, h->e_spring.p, ss, ss));
+  for (int id : ids) h->paths[id].have_grad = dev_grad == nullptr;
+  return MOP_OK;
+}
+
+mop_status select_paths(mop_handle* h, int32_t path_id, std::vector<int>* ids) {
+  ids->clear();
+  if (path_id >= 0) {
+    if (path_id >= kMaxPaths) return fail(h, MOP_ERR_ARG, "path_id %d out of range", path_id);
+    if (!h->paths[path_id].set) return fail(h, MOP_ERR_STATE, "path %d was never set", path_id);
+    ids->push_back(path_id);
+  } else {
+    for (int p = 0; p < kMaxPaths; ++p)
+      if (h->paths[p].set) ids->push_back(p);
+    if (ids->empty()) return fail(h, MOP_ERR_STATE, "no path set");
+  }
+  return MOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
+  if (!out) return MOP_ERR_ARG;
+  *out = nullptr;
+  if (!d) return MOP_ERR_ARG;
+  const int Q = d->n_atoms, nt = d->n_types;
+  if (Q < 1 || nt < 1 || nt > kMaxTypes) return MOP_ERR_ARG;
+  if (!d->type || !d->lj_sigma || !d->lj_eps || !d->charge || !d->mass || !d->mol_id || !d->mol_local)
+    return MOP_ERR_ARG;
+  if (d->n_bonds < 0 || d->n_angles < 0) return MOP_ERR_ARG;
+  if (d->n_bonds > 0 && (!d->bond_ij || !d->bond_r0 || !d->bond_k)) return MOP_ERR_ARG;
+  if (d->n_angles > 0 && (!d->angle_ijk || !d->angle_th0 || !d->angle_k)) return MOP_ERR_ARG;
+  if (d->cutoff_mode != MOP_SHIFTED_FORCE && d->cutoff_mode != MOP_POT_SHIFT) return MOP_ERR_ARG;
+  if (d->hvp_mode != MOP_HVP_ADJOINT && d->hvp_mode != MOP_HVP_FD) return MOP_ERR_ARG;
+  if (d->precision != MOP_PREC_MIXED && d->precision != MOP_PREC_FP64) return MOP_ERR_ARG;
+  const double scal[] = {d->box[0], d->box[1], d->box[2], d->rc, d->eps_rf, d->dt_path, d->nu_path, d->temperature, d->fd_h};
+  if (!finite_all(scal, 9) || !finite_all(d->lj_sigma, nt) || !finite_all(d->lj_eps, nt) ||
+      !finite_all(d->charge, Q) || !finite_all(d->mass, Q))
+    return MOP_ERR_NONFINITE;
+  if (d->n_bonds && (!finite_all(d->bond_r0, d->n_bonds) || !finite_all(d->bond_k, d->n_bonds)))
+    return MOP_ERR_NONFINITE;
+  if (d->n_angles && (!finite_all(d->angle_th0, d->n_angles) || !finite_all(d->angle_k, d->n_angles)))
+    return MOP_ERR_NONFINITE;
+  if (d->box[0] <= 0 || d->box[1] <= 0 || d->box[2] <= 0 || d->rc <= 0) return MOP_ERR_BOX;
+  if (d->rc >= 0.5 * std::min(d->box[0], std::min(d->box[1], d->box[2]))) return MOP_ERR_BOX;
+  if (d->eps_rf < 1.0 || d->dt_path <= 0 || d->nu_path <= 0 || d->temperature < 0) return MOP_ERR_ARG;
+  if (d->hvp_mode == MOP_HVP_FD && !(d->fd_h > 0)) return MOP_ERR_ARG;
+  for (int i = 0; i < Q; ++i)
+    if (d->type[i] < 0 || d->type[i] >= nt || !(d->mass[i] > 0)) return MOP_ERR_ARG;
+  for (int t = 0; t < nt; ++t)
+    if (d->lj_sigma[t] < 0 || d->lj_eps[t] < 0) return MOP_ERR_ARG;
+  for (int b = 0; b < d->n_bonds; ++b) {
+    const int i = d->bond_ij[2 * b], j = d->bond_ij[2 * b + 1];
+    if (i < 0 || j < 0 || i >= Q || j >= Q || i == j) return MOP_ERR_ARG;
+  }
+  for (int a = 0; a < d->n_angles; ++a) {
+    const int i = d->angle_ijk[3 * a], j = d->angle_ijk[3 * a + 1], k = d->angle_ijk[3 * a + 2];
+    if (i < 0 || j < 0 || k < 0 || i >= Q || j >= Q || k >= Q || i == j || j == k || i == k) return MOP_ERR_ARG;
+  }
+
+  int sms = 0;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return MOP_ERR_CUDA;
+  }
+  mop_handle* h = new mop_handle();
+  h->device = device;
+  h->num_sms = sms > 0 ? sms : 148;
+  h->hvp_mode = d->hvp_mode;
+  h->precision = d->precision;
+  h->temperature = d->temperature;
+  h->fd_h = d->fd_h;
+
+  SysConsts& sc = h->sc;
+  sc.Q = Q;
+  sc.n_types = nt;
+  sc.cutoff_mode = d->cutoff_mode;
+  sc.precision = d->precision;
+  sc.hvp_mode = d->hvp_mode;
+  for (int k = 0; k < 3; ++k) {
+    sc.L[k] = d->box[k];
+    sc.invL[k] = 1.0 / d->box[k];
+    sc.Lf[k] = (float)d->box[k];
+    sc.halfLf[k] = (float)(0.5 * d->box[k]);
+  }
+  const double rc = d->rc;
+  const bool shifted = d->cutoff_mode == MOP_SHIFTED_FORCE;
+  sc.rc = rc;
+  sc.rc2 = rc * rc;
+  sc.krf = (d->eps_rf - 1.0) / ((2.0 * d->eps_rf + 1.0) * rc * rc * rc);
+  sc.crf = 1.0 / rc + sc.krf * rc * rc;
+  sc.k2rf = 2.0 * sc.krf;
+  sc.drf = shifted ? (-1.0 / (rc * rc) + 2.0 * sc.krf * rc) : 0.0;
+  sc.rcf = (float)sc.rc;
+  sc.rc2f = (float)sc.rc2;
+  sc.krff = (float)sc.krf;
+  sc.crff = (float)sc.crf;
+  sc.k2rff = (float)sc.k2rf;
+  sc.drff = (float)sc.drf;
+  sc.fd_h = d->fd_h;
+
+  std::vector<double> Kspr(Q), cL(Q), qs(Q);
+  const double sqf = std::sqrt(kCoulombF);
+  for (int i = 0; i < Q; ++i) {
+    Kspr[i] = d->mass[i] * d->nu_path / (2.0 * d->dt_path);
+    cL[i] = d->dt_path / (d->mass[i] * d->nu_path);
+    qs[i] = d->charge[i] * sqf;
+  }
+  // type-pair table (Lorentz-Berthelot)
+  std::vector<float4> tab(kMaxTypes * kMaxTypes);
+  std::vector<double4_32a> tab64(kMaxTypes * kMaxTypes);
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const double sig = 0.5 * (d->lj_sigma[a] + d->lj_sigma[b]);
+      const double eps = std::sqrt(d->lj_eps[a] * d->lj_eps[b]);
+      const double s6 = std::pow(sig, 6);
+      const double c6 = 4.0 * eps * s6, c12 = 4.0 * eps * s6 * s6;
+      const double dlj = shifted ? (-12.0 * c12 / std::pow(rc, 13) + 6.0 * c6 / std::pow(rc, 7)) : 0.0;
+      const double plj = c12 / std::pow(rc, 12) - c6 / std::pow(rc, 6);
+      tab[a * nt + b] = make_float4((float)(12.0 * c12), (float)(6.0 * c6), (float)dlj, (float)plj);
+      tab64[a * nt + b] = make_double4_32a(12.0 * c12, 6.0 * c6, dlj, plj);
+    }
+  // bonded incidence lists
+  std::vector<int> cnt(Q + 1, 0);
+  for (int b = 0; b < d->n_bonds; ++b) { cnt[d->bond_ij[2 * b]]++; cnt[d->bond_ij[2 * b + 1]]++; }
+  for (int a = 0; a < d->n_angles; ++a)
+    for (int r = 0; r < 3; ++r) cnt[d->angle_ijk[3 * a + r]]++;
+  std::vector<int> off(Q + 1, 0);
+  for (int i = 0; i < Q; ++i) off[i + 1] = off[i] + cnt[i];
+  std::vector<int4> inc(std::max(off[Q], 1));
+  std::vector<double2> incp(std::max(off[Q], 1));
+  std::vector<int> cur(off.begin(), off.end() - 1);
+  for (int b = 0; b < d->n_bonds; ++b) {
+    const int i = d->bond_ij[2 * b], j = d->bond_ij[2 * b + 1];
+    for (int r = 0; r < 2; ++r) {
+      const int a = r == 0 ? i : j;
+      inc[cur[a]] = make_int4(0 | (r << 2), i, j, -1);
+      incp[cur[a]++] = make_double2(d->bond_r0[b], d->bond_k[b]);
+    }
+  }
+  for (int t = 0; t < d->n_angles; ++t) {
+    const int i = d->angle_ijk[3 * t], j = d->angle_ijk[3 * t + 1], k = d->angle_ijk[3 * t + 2];
+    for (int r = 0; r < 3; ++r) {
+      const int a = r == 0 ? i : (r == 1 ? j : k);
+      inc[cur[a]] = make_int4(1 | (r << 2), i, j, k);
+      incp[cur[a]++] = make_double2(d->angle_th0[t], d->angle_k[t]);
+    }
+  }
+  mop_status s;
+  if ((s = upload(h, h->mass, d->mass, Q)) || (s = upload(h, h->Kspr, Kspr.data(), Q)) ||
+      (s = upload(h, h->cL, cL.data(), Q)) || (s = upload(h, h->qs, qs.data(), Q)) ||
+      (s = upload(h, h->type, d->type, Q)) || (s = upload(h, h->mol, d->mol_id, Q)) ||
+      (s = upload(h, h->loc, d->mol_local, Q)) || (s = upload(h, h->inc_off, off.data(), Q + 1)) ||
+      (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
+      (s = upload(h, h->tab, tab.data(), tab.size())) || (s = upload(h, h->tab64, tab64.data(), tab64.size()))) {
+    mop_destroy(h);
+    return s;
+  }
+  sc.mass = h->mass.p;
+  sc.Kspr = h->Kspr.p;
+  sc.cL = h->cL.p;
+  sc.qs = h->qs.p;
+  sc.type = h->type.p;
+  sc.mol = h->mol.p;
+  sc.loc = h->loc.p;
+  sc.inc_off = h->inc_off.p;
+  sc.inc = h->inc.p;
+  sc.incp = h->incp.p;
+  sc.tab = h->tab.p;
+  sc.tab64 = h->tab64.p;
+
+  // column grid of the cluster sort (near-cubic clusters of 8) and bins of the pair search
+  Grid& g = h->grid;
+  const double vol = d->box[0] * d->box[1] * d->box[2];
+  const double w = std::cbrt(kCL * vol / Q);
+  g.ncx = std::max(1, (int)std::lround(d->box[0] / w));
+  g.ncy = std::max(1, (int)std::lround(d->box[1] / w));
+  g.wx = d->box[0] / g.ncx;
+  g.wy = d->box[1] / g.ncy;
+  g.max_clu = (Q + kCL - 1) / kCL + g.ncx * g.ncy;
+  for (int k = 0; k < 3; ++k) {
+    g.nb[k] = std::max(1, (int)std::floor(d->box[k] / (0.5 * rc)));
+    g.bw[k] = d->box[k] / g.nb[k];
+  }
+  *out = h;
+  return MOP_OK;
+}
+
+mop_status mop_destroy(mop_handle* h) {
+  if (!h) return MOP_OK;
+  cudaSetDevice(h->device);
+  h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release();
+  h->type.release(); h->mol.release(); h->loc.release(); h->inc_off.release();
+  h->inc.release(); h->incp.release(); h->tab.release(); h->tab64.release();
+  h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release();
+  for (auto& P : h->paths) {
+    P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.colid.release();
+    P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();
+    P.ts.release(); P.center.release(); P.hext.release(); P.molr.release(); P.emax.release();
+    P.cbin.release(); P.bincnt.release(); P.binstart.release(); P.bincur.release(); P.binlist.release();
+    P.cwrap.release(); P.lcnt.release(); P.loff.release(); P.meta.release(); P.xq.release();
+    P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
+    P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
+    P.eta32.release(); P.etamax.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
+    P.gA.release(); P.gB.release(); P.gc.release(); P.gh.release(); P.gw.release();
+  }
+  delete h;
+  return MOP_OK;
+}
+
+mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const void* xyz, int32_t flags,
+                        void* cuda_stream) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (path_id < 0 || path_id >= kMaxPaths) return fail(h, MOP_ERR_ARG, "path_id %d out of range", path_id);
+  if (n_beads < 1) return fail(h, MOP_ERR_ARG, "n_beads must be >= 1");
+  if (!xyz) return fail(h, MOP_ERR_ARG, "xyz is NULL");
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  PathHost& P = h->paths[path_id];
+  const size_t n = 3 * (size_t)n_beads * h->sc.Q;
+  const bool dev = flags & MOP_DEVPTR, f64 = flags & MOP_INPUT_F64;
+  if (!dev) {
+    if (f64) {
+      if (!finite_all((const double*)xyz, n)) return fail(h, MOP_ERR_NONFINITE, "non-finite coordinate");
+    } else {
+      const float* x = (const float*)xyz;
+      for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return fail(h, MOP_ERR_NONFINITE, "non-finite coordinate");
+    }
+  }
+  CK(h, P.x32.ensure(n));
+  CK(h, P.x64.ensure(n));
+  CK(h, P.vel.ensure(n));
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (f64) {
+    CK(h, cudaMemcpyAsync(P.x64.p, xyz, n * sizeof(double), kind, st));
+    k_d2f<<<nblk(n, 256), 256, 0, st>>>(P.x64.p, P.x32.p, (long long)n);
+  } else {
+    CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), kind, st));
+    k_f2d<<<nblk(n, 256), 256, 0, st>>>(P.x32.p, P.x64.p, (long long)n);
+  }
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
+  if (!dev) CK(h, cudaStreamSynchronize(st));
+  P.N = n_beads;
+  P.set = true;
+  P.have_grad = false;
+  return MOP_OK;
+}
+
+mop_status mop_get_path(mop_handle* h, int32_t path_id, float* xyz, int32_t flags, void* cuda_stream) {
+  if (!h) return MOP_ERR_ARG;
+  if (!xyz) return fail(h, MOP_ERR_ARG, "xyz is NULL");
+  std::vector<int> ids;
+  mop_status s = select_paths(h, path_id, &ids);
+  if (s || path_id < 0) return s ? s : fail(h, MOP_ERR_ARG, "path_id must be >= 0");
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  PathHost& P = h->paths[path_id];
+  const size_t n = 3 * (size_t)P.N * h->sc.Q;
+  CK(h, cudaMemcpyAsync(xyz, P.x32.p, n * sizeof(float), (flags & MOP_DEVPTR) ? cudaMemcpyDeviceToDevice
+                                                                                 : cudaMemcpyDeviceToHost, st));
+  if (!(flags & MOP_DEVPTR)) CK(h, cudaStreamSynchronize(st));
+  return MOP_OK;
+}
+
+mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, double* grad, int32_t flags,
+                             void* cuda_stream) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  h->launches = 0;
+  std::vector<int> ids;
+  mop_status s = select_paths(h, path_id, &ids);
+  if (s) return s;
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool dev = flags & MOP_DEVPTR;
+  s = evaluate(h, ids, dev ? veff : nullptr, dev ? grad : nullptr, st);
+  if (s) return s;
+  if (!dev) {
+    size_t goff = 0;
+    std::vector<double> v(ids.size());
+    for (size_t k = 0; k < ids.size(); ++k) {
+      PathHost& P = h->paths[ids[k]];
+      CK(h, cudaMemcpyAsync(&v[k], P.veff_int.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+      const size_t n = 3 * (size_t)P.N * h->sc.Q;
+      if (grad) CK(h, cudaMemcpyAsync(grad + goff, P.grad_int.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      goff += n;
+    }
+    CK(h, cudaStreamSynchronize(st));
+    for (size_t k = 0; k < ids.size(); ++k) {
+      if (veff) veff[k] = v[k];
+      if (!std::isfinite(v[k])) return fail(h, MOP_ERR_NONFINITE, "V_eff of path %d is not finite", ids[k]);
+    }
+  }
+  return MOP_OK;
+}
+
+mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* out, int32_t flags,
+                         void* cuda_stream) {
+  if (!h) return MOP_ERR_ARG;
+  if (!out) return fail(h, MOP_ERR_ARG, "out is NULL");
+  if (path_id < 0 || path_id >= kMaxPaths) return fail(h, MOP_ERR_ARG, "path_id out of range");
+  PathHost& P = h->paths[path_id];
+  if (!P.set || P.n_clu == 0 || !P.F.p) return fail(h, MOP_ERR_STATE, "path %d has no evaluation", path_id);
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int N = P.N, Qpad = P.n_clu * kCL;
+  const double* f;
+  int rows;
+  switch (field) {
+    case MOP_FIELD_FORCE: f = P.F.p; rows = N == 1 ? 1 : N - 1; break;
+    case MOP_FIELD_ETA: f = P.eta.p; rows = N - 1; break;
+    case MOP_FIELD_HETA: f = P.Heta.p; rows = N - 1; break;
+    default: return fail(h, MOP_ERR_ARG, "unknown field %d", field);
+  }
+  const size_t n = 3 * (size_t)N * h->sc.Q;
+  double* dst = out;
+  if (!(flags & MOP_DEVPTR)) {
+    CK(h, h->scratch.ensure(n));
+    dst = h->scratch.p;
+  }
+  k_gather_field<<<nblk((long long)N * h->sc.Q, 256), 256, 0, st>>>(f, P.slot.p, h->sc.Q, Qpad, N, rows, dst);
+  CK(h, cudaGetLastError());
+  if (!(flags & MOP_DEVPTR)) {
+    CK(h, cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+  }
+  return MOP_OK;
+}
+
+mop_status mop_get_energies(mop_handle* h, int32_t path_id, double out[4]) {
+  if (!h) return MOP_ERR_ARG;
+  if (!out) return fail(h, MOP_ERR_ARG, "out is NULL");
+  if (path_id < 0 || path_id >= kMaxPaths) return fail(h, MOP_ERR_ARG, "path_id out of range");
+  PathHost& P = h->paths[path_id];
+  if (!P.set || !P.diag.p) return fail(h, MOP_ERR_STATE, "path %d has no evaluation", path_id);
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaDeviceSynchronize());
+  CK(h, cudaMemcpy(out, P.diag.p, 4 * sizeof(double), cudaMemcpyDeviceToHost));
+  return MOP_OK;
+}
+
+mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const int32_t* grpB, int32_t nB,
+                        double s_center, double height, double width, int32_t path_id, int32_t flags) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (path_id < 0 || path_id >= kMaxPaths) return fail(h, MOP_ERR_ARG, "path_id out of range");
+  if (!std::isfinite(s_center) || !std::isfinite(height) || !std::isfinite(width))
+    return fail(h, MOP_ERR_NONFINITE, "non-finite Gaussian parameter");
+  if (!(width > 0)) return fail(h, MOP_ERR_ARG, "width must be > 0");
+  CK(h, cudaSetDevice(h->device));
+  PathHost& P = h->paths[path_id];
+  if (grpA || grpB) {
+    if (!grpA || !grpB || nA < 1 || nB < 1 || nA > kMaxGroup || nB > kMaxGroup)
+      return fail(h, MOP_ERR_ARG, "groups need 1..%d atoms each", kMaxGroup);
+    for (int k = 0; k < nA; ++k)
+      if (grpA[k] < 0 || grpA[k] >= h->sc.Q) return fail(h, MOP_ERR_ARG, "group A index out of range");
+    for (int k = 0; k < nB; ++k)
+      if (grpB[k] < 0 || grpB[k] >= h->sc.Q) return fail(h, MOP_ERR_ARG, "group B index out of range");
+    P.hA.assign(grpA, grpA + nA);
+    P.hB.assign(grpB, grpB + nB);
+    P.e2e = (flags & MOP_E2E) ? 1 : 0;
+    mop_status s;
+    if ((s = upload(h, P.gA, P.hA.data(), P.hA.size())) || (s = upload(h, P.gB, P.hB.data(), P.hB.size())))
+      return s;
+  } else if (P.hA.empty()) {
+    return fail(h, MOP_ERR_STATE, "no CV groups defined for path %d", path_id);
+  }
+  if ((int)P.hc.size() >= kMaxGauss) return fail(h, MOP_ERR_ARG, "more than %d Gaussians", kMaxGauss);
+  P.hc.push_back(s_center);
+  P.hh.push_back(height);
+  P.hw.push_back(width);
+  mop_status s;
+  if ((s = upload(h, P.gc, P.hc.data(), P.hc.size())) || (s = upload(h, P.gh, P.hh.data(), P.hh.size())) ||
+      (s = upload(h, P.gw, P.hw.data(), P.hw.size())))
+    return s;
+  P.have_grad = false;
+  return MOP_OK;
+}
+
+mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed, void* cuda_stream) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (n_steps < 0 || !(dt_md > 0) || !(gamma >= 0) || !std::isfinite(dt_md) || !std::isfinite(gamma))
+    return fail(h, MOP_ERR_ARG, "invalid step parameters");
+  std::vector<int> ids;
+  mop_status s = select_paths(h, -1, &ids);
+  if (s) return s;
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Launch L{st, &h->launches};
+  bool need = false;
+  for (int id : ids) need |= !h->paths[id].have_grad;
+  if (need && (s = evaluate(h, ids, nullptr, nullptr, st))) return s;
+  const double kT = kBoltz * h->temperature;
+  for (int k = 0; k < n_steps; ++k) {
+    for (int id : ids) {
+      PathHost& P = h->paths[id];
+      CK(h, launch_kick(h->sc, P.vel.p, P.grad_int.p, P.N, 0.5 * dt_md, L));
+      CK(h, launch_drift(h->sc, P.x64.p, P.vel.p, P.x32.p, P.N, dt_md, gamma, kT, seed, h->step_count, 0, L));
+    }
+    if ((s = evaluate(h, ids, nullptr, nullptr, st))) return s;
+    for (int id : ids) {
+      PathHost& P = h->paths[id];
+      CK(h, launch_kick(h->sc, P.vel.p, P.grad_int.p, P.N, 0.5 * dt_md, L));
+    }
+    ++h->step_count;
+  }
+  CK(h, cudaStreamSynchronize(st));
+  return MOP_OK;
+}
+
+mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke) {
+  if (!h) return MOP_ERR_ARG;
+  if (!ke) return fail(h, MOP_ERR_ARG, "ke is NULL");
+  std::vector<int> ids;
+  mop_status s = select_paths(h, path_id, &ids);
+  if (s || path_id < 0) return s ? s : fail(h, MOP_ERR_ARG, "path_id must be >= 0");
+  CK(h, cudaSetDevice(h->device));
+  PathHost& P = h->paths[path_id];
+  CK(h, h->scratch.ensure(1));
+  Launch L{nullptr, &h->launches};
+  CK(h, launch_kinetic(h->sc, P.vel.p, P.N, h->scratch.p, L));
+  CK(h, cudaMemcpy(ke, h->scratch.p, sizeof(double), cudaMemcpyDeviceToHost));
+  return MOP_OK;
+}
+
+int32_t mop_last_launch_count(const mop_handle* h) { return h ? h->launches : 0; }
+
+const char* mop_last_error(const mop_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"
