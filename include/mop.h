@@ -165,6 +165,19 @@ mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke);
 /* Number of kernel launches the last mop_veff_and_grad made (instrumentation). */
 int32_t mop_last_launch_count(const mop_handle* h);
 
+/* Instrumentation.  With profiling on, mop_veff_and_grad records CUDA events on its stream
+ * around each pass; mop_last_pass_ms then returns the device time of the last call's passes in
+ * milliseconds: out[0] sort + pair list, [1] pair force, [2] bonded + eta, [3] pair HVP (or
+ * FD), [4] bonded HVP + gradient, [5] bias + V_eff reduction (n <= 6 values, synchronous). */
+mop_status mop_set_profiling(mop_handle* h, int32_t on);
+mop_status mop_last_pass_ms(mop_handle* h, float* out, int32_t n);
+
+/* Counts, for the last evaluation of `path_id`, the nonbonded pairs inside the cutoff (minus
+ * exclusions) over all beads that need forces: *unique = number of unordered pairs, *listed =
+ * number of atom pairs the cluster-pair list makes the force kernel evaluate (ordered, padding
+ * included).  Synchronous. */
+mop_status mop_count_pairs(mop_handle* h, int32_t path_id, int64_t* unique, int64_t* listed);
+
 /* Text of the last error of the handle ("" if none); valid until the next call. */
 const char* mop_last_error(const mop_handle* h);
 

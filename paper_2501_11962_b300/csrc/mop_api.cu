@@ -34,8 +34,14 @@ struct mop_handle {
   DevBuf<double4_32a> tab64;
   // paths
   PathHost paths[kMaxPaths];
-  DevBuf<PathDev> d_paths;
+  DevBuf<PathDev> d_paths, d_one;
   DevBuf<double> e_bond, e_spring, scratch;
+  DevBuf<unsigned long long> counts;
+  std::vector<int> last_ids;
+  std::vector<PathDev> last_pd;
+  // instrumentation
+  bool profiling = false;
+  cudaEvent_t ev[7] = {};
 };
 
 namespace {
@@ -105,6 +111,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   const bool fd = h->hvp_mode == MOP_HVP_FD;
   const double margin = fd ? h->fd_h : 0.0;
   std::vector<PathDev> pd(ids.size());
+  if (h->profiling) CK(h, cudaEventRecord(h->ev[0], st));
   long long units = 0, units_h = 0;
   long long max_e1 = 0, max_e2 = 0;
   size_t goff = 0;
@@ -181,13 +188,22 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, h->e_spring.ensure((size_t)np * ss));
   CK(h, h->d_paths.ensure(np));
   CK(h, cudaMemcpyAsync(h->d_paths.p, pd.data(), sizeof(PathDev) * np, cudaMemcpyHostToDevice, st));
+  auto mark = [&](int k) { return h->profiling ? cudaEventRecord(h->ev[k], st) : cudaSuccess; };
+  CK(h, mark(1));
   CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
+  CK(h, mark(2));
   CK(h, launch_e1(sc, h->d_paths.p, np, (int)max_e1, L, h->e_bond.p, sb));
+  CK(h, mark(3));
   if (units_h > 0) CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+  CK(h, mark(4));
   CK(h, launch_e2(sc, h->d_paths.p, np, (int)max_e2, L, h->e_spring.p, ss));
+  CK(h, mark(5));
   CK(h, launch_bias(sc, h->d_paths.p, np, L));
   CK(h, launch_reduce(sc, h->d_paths.p, np, L, h->e_bond.p, sb, sb, h->e_spring.p, ss, ss));
+  CK(h, mark(6));
   for (int id : ids) h->paths[id].have_grad = dev_grad == nullptr;
+  h->last_ids = ids;
+  h->last_pd = pd;
   return MOP_OK;
 }
 
@@ -383,6 +399,9 @@ mop_status mop_destroy(mop_handle* h) {
   h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release();
   h->type.release(); h->mol.release(); h->loc.release(); h->inc_off.release();
   h->inc.release(); h->incp.release(); h->tab.release(); h->tab64.release();
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  h->d_one.release(); h->counts.release();
   h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release();
   for (auto& P : h->paths) {
     P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.colid.release();
@@ -619,6 +638,49 @@ mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke) {
 }
 
 int32_t mop_last_launch_count(const mop_handle* h) { return h ? h->launches : 0; }
+
+mop_status mop_set_profiling(mop_handle* h, int32_t on) {
+  if (!h) return MOP_ERR_ARG;
+  CK(h, cudaSetDevice(h->device));
+  if (on && !h->ev[0])
+    for (auto& e : h->ev) CK(h, cudaEventCreate(&e));
+  h->profiling = on != 0;
+  return MOP_OK;
+}
+
+mop_status mop_last_pass_ms(mop_handle* h, float* out, int32_t n) {
+  if (!h) return MOP_ERR_ARG;
+  if (!out || n < 0 || n > 6) return fail(h, MOP_ERR_ARG, "need 0 <= n <= 6 and an output array");
+  if (!h->profiling) return fail(h, MOP_ERR_STATE, "profiling is off");
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaEventSynchronize(h->ev[6]));
+  for (int k = 0; k < n; ++k) CK(h, cudaEventElapsedTime(&out[k], h->ev[k], h->ev[k + 1]));
+  return MOP_OK;
+}
+
+mop_status mop_count_pairs(mop_handle* h, int32_t path_id, int64_t* unique, int64_t* listed) {
+  if (!h) return MOP_ERR_ARG;
+  if (!unique || !listed) return fail(h, MOP_ERR_ARG, "NULL output");
+  int k = -1;
+  for (size_t i = 0; i < h->last_ids.size(); ++i)
+    if (h->last_ids[i] == path_id) k = (int)i;
+  if (k < 0) return fail(h, MOP_ERR_STATE, "path %d was not in the last evaluation", path_id);
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaDeviceSynchronize());
+  PathDev D = h->last_pd[k];
+  D.unit_off = 0;
+  CK(h, h->d_one.ensure(1));
+  CK(h, h->counts.ensure(2));
+  CK(h, cudaMemcpy(h->d_one.p, &D, sizeof(D), cudaMemcpyHostToDevice));
+  int dummy = 0;
+  Launch L{nullptr, &dummy};
+  CK(h, launch_count_pairs(h->sc, h->d_one.p, 1, (long long)D.n_force * D.n_clu, h->counts.p, h->num_sms, L));
+  unsigned long long c[2];
+  CK(h, cudaMemcpy(c, h->counts.p, sizeof(c), cudaMemcpyDeviceToHost));
+  *unique = (int64_t)(c[0] / 2);
+  *listed = (int64_t)c[1];
+  return MOP_OK;
+}
 
 const char* mop_last_error(const mop_handle* h) { return h ? h->err.c_str() : "null handle"; }
 

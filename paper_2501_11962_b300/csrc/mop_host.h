@@ -95,6 +95,9 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
                         int mode, int num_sms, Launch L);
 
+cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
+                               unsigned long long* counts, int num_sms, Launch L);
+
 // --- mop_path.cu: bonded terms, eta, path gradient, bias, reductions, integrator ----------
 cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
                       double* e_bond, int e_bond_stride);

@@ -271,7 +271,72 @@ cudaError_t launch_one(const SysConsts& sc, const PathDev* d_paths, int n_paths,
   return cudaGetLastError();
 }
 
+// in-cutoff, non-excluded ordered pairs of every force unit (instrumentation)
+__global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, int n_paths, long long n_units,
+                              unsigned long long* counts) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long inside = 0, listed = 0;
+  for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nw) {
+    int p = 0;
+    while (p + 1 < n_paths && paths[p + 1].unit_off <= u) ++p;
+    const PathDev& P = paths[p];
+    const long long v = u - P.unit_off;
+    const int n = (int)(v % P.n_force), ci = (int)(v / P.n_force);
+    const int i = lane & 7, jj = lane >> 3;
+    const size_t bo = (size_t)n * P.Qpad;
+    const bool vi = P.perm[ci * kCL + i] >= 0;
+    for (int e = P.loff[ci]; e < P.loff[ci + 1]; ++e) {
+      const int4 en = P.ent[e];
+      const unsigned long long m = (en.x < 0) ? P.emask[e] : 0ull;
+      const int cj = en.x & 0x7fffffff;
+      double D[3];
+      if (P.ent64) {
+        D[0] = P.ent64[e].x; D[1] = P.ent64[e].y; D[2] = P.ent64[e].z;
+      } else {
+        D[0] = __int_as_float(en.y); D[1] = __int_as_float(en.z); D[2] = __int_as_float(en.w);
+      }
+      for (int h = 0; h < 2; ++h) {
+        const int jl = jj + 4 * h, sj = cj * kCL + jl;
+        double a[3], b[3];
+        if (P.xq64) {
+          const double4_32a x = P.xq64[bo + ci * kCL + i], y = P.xq64[bo + sj];
+          a[0] = x.x; a[1] = x.y; a[2] = x.z; b[0] = y.x; b[1] = y.y; b[2] = y.z;
+        } else {
+          const float4 x = P.xq[bo + ci * kCL + i], y = P.xq[bo + sj];
+          a[0] = x.x; a[1] = x.y; a[2] = x.z; b[0] = y.x; b[1] = y.y; b[2] = y.z;
+        }
+        double r2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          const double d = a[c] + D[c] - b[c];
+          r2 += d * d;
+        }
+        const bool vj = P.perm[sj] >= 0;
+        listed += 1;
+        inside += (vi && vj && r2 < sc.rc2 && !((m >> (i * kCL + jl)) & 1ull)) ? 1 : 0;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    inside += __shfl_xor_sync(0xffffffffu, inside, o);
+    listed += __shfl_xor_sync(0xffffffffu, listed, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&counts[0], inside);
+    atomicAdd(&counts[1], listed);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
+                               unsigned long long* counts, int num_sms, Launch L) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), L.st);
+  if (e != cudaSuccess) return e;
+  k_count_pairs<<<num_sms * 4, 128, 0, L.st>>>(sc, d_paths, n_paths, n_units, counts);
+  ++*L.counter;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
                         int num_sms, Launch L) {

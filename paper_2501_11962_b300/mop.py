@@ -23,7 +23,7 @@ MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 
 EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_veff_and_grad", "mop_get_field",
            "mop_get_energies", "mop_add_bias", "mop_step", "mop_kinetic_energy", "mop_last_launch_count",
-           "mop_last_error")
+           "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -78,6 +78,9 @@ def load(build_if_needed: bool = True):
     L.mop_kinetic_energy.argtypes = [p, i32, p]
     L.mop_last_launch_count.argtypes = [p]
     L.mop_last_launch_count.restype = i32
+    L.mop_set_profiling.argtypes = [p, i32]
+    L.mop_last_pass_ms.argtypes = [p, p, i32]
+    L.mop_count_pairs.argtypes = [p, i32, p, p]
     L.mop_last_error.argtypes = [p]
     L.mop_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -225,6 +228,21 @@ class Engine:
 
     def last_launch_count(self) -> int:
         return int(self.L.mop_last_launch_count(self.h))
+
+    PASSES = ("prep", "pair_force", "bonded_eta", "pair_hvp", "bonded_hvp_grad", "bias_reduce")
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.L.mop_set_profiling(self.h, int(on)), "mop_set_profiling")
+
+    def pass_ms(self) -> dict:
+        out = np.zeros(6, np.float32)
+        self._check(self.L.mop_last_pass_ms(self.h, _np_ptr(out), 6), "mop_last_pass_ms")
+        return dict(zip(self.PASSES, out.astype(float).tolist()))
+
+    def count_pairs(self, path_id: int):
+        u, l = np.zeros(1, np.int64), np.zeros(1, np.int64)
+        self._check(self.L.mop_count_pairs(self.h, path_id, _np_ptr(u), _np_ptr(l)), "mop_count_pairs")
+        return int(u[0]), int(l[0])
 
 
 def _autograd_function():

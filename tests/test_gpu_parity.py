@@ -1,0 +1,213 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (relative 2-norms over all beads and atoms, the spec bar):
+  forces F^n <= 1e-5, H eta <= 1e-4, V_eff <= 1e-6 (mixed precision);
+  FP64 mode: 1e-9.
+The gradient G, eta and the energy parts are reported and held to the same bars as the
+quantity that dominates them (F for eta and G, V_eff for the energies).
+"""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_11962_b300 import mop
+from tests.conftest import workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_F, TOL_H, TOL_V = 1e-5, 1e-4, 1e-6
+TOL_F64 = 1e-9
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def gpu_eval(w, path=0, **kw):
+    eng = mop.Engine(w.system, **kw)
+    eng.set_path(path, w.paths[0])
+    v, G = eng.veff_and_grad(path)
+    out = dict(veff=v[0], G=G, F=eng.get_field(path, mop.MOP_FIELD_FORCE),
+               eta=eng.get_field(path, mop.MOP_FIELD_ETA), Heta=eng.get_field(path, mop.MOP_FIELD_HETA))
+    out.update(eng.energies(path))
+    out["launches"] = eng.last_launch_count()
+    return eng, out
+
+
+def test_cfg1_fp64_matches_oracle():
+    w = workload(1)
+    X = w.paths[0]
+    eng, g = gpu_eval(w, precision=mop.MOP_PREC_FP64)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "eta", "Heta"))
+    N = X.shape[0]
+    errs = dict(F=rel(g["F"][:N - 1], r["F"][:N - 1]), eta=rel(g["eta"][:N - 1], r["eta"][:N - 1]),
+                Heta=rel(g["Heta"][:N - 1], r["Heta"][:N - 1]), G=rel(g["G"], r["G"]),
+                V=abs(g["veff"] - r["veff"]) / abs(r["veff"]), U1=abs(g["U1"] - r["U1"]) / abs(r["U1"]))
+    print("cfg1 fp64 errors", errs)
+    for k, e in errs.items():
+        assert e < TOL_F64, (k, e)
+    assert g["launches"] > 0
+
+
+def test_cfg2_mixed_matches_oracle():
+    w = workload(2)
+    X = w.paths[0]
+    eng, g = gpu_eval(w)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "eta", "Heta"))
+    N = X.shape[0]
+    errs = dict(F=rel(g["F"][:N - 1], r["F"][:N - 1]), eta=rel(g["eta"][:N - 1], r["eta"][:N - 1]),
+                Heta=rel(g["Heta"][:N - 1], r["Heta"][:N - 1]), G=rel(g["G"], r["G"]),
+                V=abs(g["veff"] - r["veff"]) / abs(r["veff"]), U1=abs(g["U1"] - r["U1"]) / abs(r["U1"]),
+                Es=abs(g["Espring"] - r["Espring"]) / abs(r["Espring"]))
+    print("cfg2 mixed errors", errs)
+    assert errs["F"] < TOL_F and errs["eta"] < TOL_F and errs["G"] < TOL_F
+    assert errs["Heta"] < TOL_H
+    assert errs["V"] < TOL_V and errs["Es"] < TOL_V and errs["U1"] < TOL_V
+
+
+def test_cfg2_small_path_edge_cases():
+    """N = 1 (V = U, G = -F) and N = 2 (one spring, no interior bead)."""
+    w = workload(2)
+    o = oracle.Oracle(w.system)
+    eng = mop.Engine(w.system)
+    for N in (1, 2):
+        X = w.paths[0][:N]
+        eng.set_path(0, X)
+        v, G = eng.veff_and_grad(0)
+        r = o.veff(X.astype(np.float64))
+        assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V
+        assert rel(G, r["G"]) < TOL_F
+
+
+def test_fd_mode_fp64_matches_oracle_eq5():
+    w = workload(1)
+    X = w.paths[0]
+    eng, g = gpu_eval(w, precision=mop.MOP_PREC_FP64, hvp_mode=mop.MOP_HVP_FD, fd_h=1e-4)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), hvp_mode=oracle.HVP_FD_EQ5, fd_h=1e-4,
+                                     want=("G", "Heta"))
+    N = X.shape[0]
+    assert rel(g["Heta"][:N - 1], r["Heta"][:N - 1]) < 1e-6
+    assert rel(g["G"], r["G"]) < 1e-8
+
+
+def test_fd_mode_mixed_accuracy_is_reported():
+    w = workload(2)
+    X = w.paths[0]
+    exact = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "Heta"))
+    N = X.shape[0]
+    for h in (1e-5, 1e-4, 1e-3):
+        eng, g = gpu_eval(w, hvp_mode=mop.MOP_HVP_FD, fd_h=h)
+        e = rel(g["Heta"][:N - 1], exact["Heta"][:N - 1])
+        print(f"FD h={h:g}: H eta error vs exact {e:.3e}, G error {rel(g['G'], exact['G']):.3e}")
+        assert np.isfinite(e) and e < 1.0
+
+
+def test_deterministic_and_batch_invariant():
+    w = workload(4, n_beads=8)
+    eng = mop.Engine(w.system)
+    for p in range(3):
+        eng.set_path(p, w.paths[p])
+    v_all, G_all = eng.veff_and_grad(-1)
+    v_again, G_again = eng.veff_and_grad(-1)
+    assert np.array_equal(v_all, v_again) and np.array_equal(G_all, G_again)
+    off = 0
+    for p in range(3):
+        v1, G1 = eng.veff_and_grad(p)
+        n = w.paths[p].shape[0]
+        assert v1[0] == v_all[p]
+        assert np.array_equal(G1, G_all[off:off + n])
+        off += n
+
+
+def test_nonfinite_input_rejected():
+    w = workload(2, n_beads=2)
+    eng = mop.Engine(w.system)
+    X = w.paths[0].copy()
+    X[1, 5, 2] = np.nan
+    with pytest.raises(mop.MopError) as ei:
+        eng.set_path(0, X)
+    assert ei.value.status == mop.MOP_ERR_NONFINITE
+    with pytest.raises(mop.MopError) as ei:
+        eng.veff_and_grad(3)
+    assert ei.value.status == mop.MOP_ERR_STATE
+
+
+@pytest.mark.slow
+def test_cfg3_autograd_matches_oracle():
+    import torch
+    w = workload(3)
+    X = w.paths[0]
+    eng = mop.Engine(w.system)
+    coords = torch.tensor(X, device="cuda", requires_grad=True)
+    V = mop.veff(coords, eng, 0)
+    V.backward()
+    torch.cuda.synchronize()
+    G = coords.grad.double().cpu().numpy()
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64))
+    assert abs(V.item() - r["veff"]) / abs(r["veff"]) < TOL_V
+    # float32 gradient from backward: bounded by its own rounding and the FP64 bar
+    assert rel(G, r["G"]) < TOL_F
+
+
+@pytest.mark.slow
+def test_cfg4_uneven_batch_with_bias():
+    w = workload(4)
+    o = oracle.Oracle(w.system)
+    eng = mop.Engine(w.system)
+    ga, gb = w.cv_groups
+    for p, X in enumerate(w.paths):
+        eng.set_path(p, X)
+        s0, _ = o.cv_distance(X[-1].astype(np.float64), ga, gb)
+        eng.add_bias(p, s0 + 0.02, w.bias["height"], w.bias["width"], groups=(ga, gb))
+    v, G = eng.veff_and_grad(-1)
+    offs = np.cumsum([0] + [X.shape[0] for X in w.paths])
+    for p in (0, 1, 4):
+        X = w.paths[p].astype(np.float64)
+        r = o.veff(X)
+        s0, _ = o.cv_distance(X[-1], ga, gb)
+        Vb, Gb, S = o.bias(X, ga, gb, [s0 + 0.02], [w.bias["height"]], [w.bias["width"]])
+        ref_v = r["veff"] + Vb
+        ref_G = r["G"] + Gb
+        assert abs(v[p] - ref_v) / abs(ref_v) < TOL_V
+        assert rel(G[offs[p]:offs[p + 1]], ref_G) < TOL_F
+        e = eng.energies(p)
+        assert e["Ebias"] == pytest.approx(Vb, rel=1e-6, abs=1e-9)
+        assert e["cv"] == pytest.approx(S, rel=1e-9)
+
+
+@pytest.mark.slow
+def test_cfg5_sampled_beads_match_oracle():
+    w = workload(5)
+    X = w.paths[0]
+    N = X.shape[0]
+    eng, g = gpu_eval(w)
+    o = oracle.Oracle(w.system)
+    Xd = X.astype(np.float64)
+    beads = list(range(N - 1))
+    with ThreadPoolExecutor(max_workers=max(1, oracle.num_threads())) as ex:
+        res = list(ex.map(lambda n: o.forces(Xd[n]), beads))
+    F = np.stack([r[0] for r in res])
+    U1 = res[0][1]
+    m = w.system.mass
+    K = m * w.system.nu_path / (2 * w.system.dt_path)
+    c = w.system.dt_path / (m * w.system.nu_path)
+    eta = Xd[1:] - Xd[:-1] - c[None, :, None] * F
+    Es = 0.5 * np.sum(K[None, :, None] * eta ** 2)
+    errs = dict(F=rel(g["F"][:N - 1], F), eta=rel(g["eta"][:N - 1], eta), U1=abs(g["U1"] - U1) / abs(U1),
+                V=abs(g["veff"] - (U1 + Es)) / abs(U1 + Es))
+    sample = [0, N // 2, N - 2]
+    with ThreadPoolExecutor(max_workers=3) as ex:
+        H = list(ex.map(lambda n: o.hvp(Xd[n], eta[n]), sample))
+    errs["Heta"] = rel(g["Heta"][sample], np.stack(H))
+    # gradient on beads 1, N/2 + 1 and N from the sampled pieces
+    n = N // 2
+    Gn = K[:, None] * eta[n - 1] - K[:, None] * eta[n] + 0.5 * H[1]
+    G0 = -F[0] - K[:, None] * eta[0] + 0.5 * H[0]
+    GN = K[:, None] * eta[N - 2]
+    errs["G"] = rel(np.stack([g["G"][0], g["G"][n], g["G"][N - 1]]), np.stack([G0, Gn, GN]))
+    print("cfg5 errors", errs)
+    assert errs["F"] < TOL_F and errs["eta"] < TOL_F and errs["G"] < TOL_F
+    assert errs["Heta"] < TOL_H
+    assert errs["V"] < TOL_V and errs["U1"] < TOL_V
