@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the MoP effective-potential path (V_eff of Eq. 3 and its gradient) on B300.
+
+One step = one full evaluation of V_eff and dV_eff/dR of a Q = 150,000-atom, N = 64-bead path
+(synthetic chains + water system) through the C ABI: mop_set_path (device copy of the step's
+coordinates) + mop_veff_and_grad.  value = N * Q * evaluations / s (bead-atoms/s), summed over
+ranks.  Inputs are larger than L2 (coordinates 115 MB per step, fields > 1 GB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "path-gradient evals/s (bead·atoms/s) at Q=150k, N=64; adjoint vs FD-HVP at tol"
+UNIT = "bead*atoms/s"
+# canonical flop counts per unique in-cutoff pair (FADD/FMUL = 1, FFMA = 2, rsqrt not counted)
+FLOPS_FORCE = 36
+FLOPS_HVP = 59
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+FD_SWEEP = (1e-5, 3e-5, 1e-4, 3e-4, 1e-3)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--config", type=int, default=5)
+    ap.add_argument("--beads", type=int, default=None)
+    ap.add_argument("--no-fd", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(cfg, N, Q):
+    names = {5: "chains+water membrane-sized synthetic system", 4: "water+ion", 3: "water", 2: "water", 1: "LJ fcc"}
+    return f"cfg{cfg} {names.get(cfg, '')}: Q={Q}, N={N}"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline arm and the cpu_baseline leg)
+
+
+def oracle_sample_time(w, n_beads_sample: int):
+    """Time one oracle V_eff + gradient (analytic HVP, OpenMP over beads) of a sub-path."""
+    import oracle
+    o = oracle.Oracle(w.system)
+    X = np.ascontiguousarray(w.paths[0][:n_beads_sample].astype(np.float64))
+    t0 = time.perf_counter()
+    o.veff(X)
+    dt = time.perf_counter() - t0
+    return dt, oracle.num_threads()
+
+
+def cpu_sample_beads(w):
+    import oracle
+    return int(min(w.paths[0].shape[0], oracle.num_threads() + 1))
+
+
+def run_reference(args, world, rank):
+    from paper_2501_11962_b300 import synth
+    if rank != 0:
+        return
+    w = synth.config(args.config, n_beads=args.beads)
+    N, Q = w.paths[0].shape[:2]
+    ns = cpu_sample_beads(w)
+    times = []
+    for k in range(args.warmup + args.steps):
+        dt, cores = oracle_sample_time(w, ns)
+        if k >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = ns * Q / t
+    sample = (f"oracle V_eff+gradient (analytic HVP) of a {ns}-bead sub-path of the workload, "
+              f"OpenMP over beads; value = {ns}*Q/time")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.config, N, Q), "Q": Q, "N": N, "paths": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
+# CUDA path
+
+
+def run_ours(args, world, rank, local):
+    import ctypes as C
+    import torch
+    from paper_2501_11962_b300 import mop, synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.config(args.config, n_beads=args.beads)
+    X = w.paths[0]
+    N, Q = X.shape[:2]
+    prec = mop.MOP_PREC_FP64 if w.precision == "fp64" else mop.MOP_PREC_MIXED
+    eng = mop.Engine(w.system, precision=prec, device=local)
+    eng.set_profiling(True)
+    Xd = torch.tensor(X, device=dev)
+    veff = torch.empty(1, dtype=torch.float64, device=dev)
+    grad = torch.empty((N, Q, 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        eng.set_path(0, Xd, stream=stream.cuda_stream)
+        eng.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+
+    passes = []
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = eng.last_launch_count() + 1   # + the conversion kernel of mop_set_path
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+            passes.append(eng.pass_ms())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    value = world * N * Q / (ms * 1e-3)
+    mean_pass = {k: float(np.mean([p[k] for p in passes])) for k in passes[0]}
+
+    # roofline of the dominant pair kernel (FP32 ALU bound)
+    unique, listed = eng.count_pairs(0)
+    n_force = N - 1 if N > 1 else 1
+    flops = {"pair_force": unique * FLOPS_FORCE, "pair_hvp": unique * FLOPS_HVP}
+    dom = max(("pair_force", "pair_hvp"), key=lambda k: mean_pass[k])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops[dom] / (mean_pass[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_pair<float," + ("0>" if dom == "pair_force" else "1>"),
+                "unique_pairs_per_launch": unique, "listed_pairs_per_launch": listed,
+                "flops_per_unique_pair": FLOPS_FORCE if dom == "pair_force" else FLOPS_HVP,
+                "peak_note": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {SM_MAX_MHZ:.0f} MHz"}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    xh = torch.tensor(X).pin_memory()
+    gh = torch.empty((N, Q, 3), dtype=torch.float64).pin_memory()
+    vh = np.zeros(1)
+    L = eng.L
+
+    def e2e_step():
+        st = L.mop_set_path(eng.h, 0, N, C.c_void_p(xh.data_ptr()), 0, C.c_void_p(stream.cuda_stream))
+        eng._check(st, "mop_set_path")
+        st = L.mop_veff_and_grad(eng.h, 0, vh.ctypes.data_as(C.c_void_p), C.c_void_p(gh.data_ptr()), 0,
+                                 C.c_void_p(stream.cuda_stream))
+        eng._check(st, "mop_veff_and_grad")
+
+    for _ in range(2):
+        e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    e2e = {"value": world * N * Q / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * Q * 3 * 4),
+           "d2h_bytes_per_step": int(N * Q * 3 * 8 + 8), "ms_per_step": e2e_s * 1e3}
+
+    # FD-HVP comparison path (paper Eq. 5) at the same workload
+    fd = None
+    if not args.no_fd and rank == 0:
+        ref_H = eng.get_field(0, mop.MOP_FIELD_HETA)[:N - 1]
+        errs, vals = {}, {}
+        for h in FD_SWEEP:
+            ef = mop.Engine(w.system, precision=prec, hvp_mode=mop.MOP_HVP_FD, fd_h=h, device=local)
+            ef.set_path(0, Xd, stream=stream.cuda_stream)
+            ef.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            H = ef.get_field(0, mop.MOP_FIELD_HETA)[:N - 1]
+            errs[h] = float(np.linalg.norm(H - ref_H) / np.linalg.norm(ref_H))
+            if h == FD_SWEEP[0] or errs[h] <= min(errs.values()):
+                k = max(3, args.steps // 2)
+                ef.set_path(0, Xd, stream=stream.cuda_stream)
+                ef.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(k):
+                    ef.set_path(0, Xd, stream=stream.cuda_stream)
+                    ef.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                vals[h] = N * Q / (a.elapsed_time(b) / k * 1e-3)
+            ef.close()
+        best = min(errs, key=errs.get)
+        fd = {"value": vals.get(best), "unit": UNIT, "best_h_nm": best, "hvp_rel_err_best": errs[best],
+              "hvp_rel_err_by_h": {f"{h:g}": e for h, e in errs.items()},
+              "reaches_1e-4": bool(errs[best] <= 1e-4),
+              "adjoint_over_fd_speed": value / world / vals[best] if vals.get(best) else None}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        ns = cpu_sample_beads(w)
+        dt, cores = oracle_sample_time(w, ns)
+        cpu = {"value": ns * Q / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one oracle V_eff+gradient (analytic HVP) of a {ns}-bead sub-path of the workload "
+                         f"({dt:.1f} s, OpenMP over beads); value = {ns}*Q/time"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pair math, f64 accumulation" if prec == 0 else "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.config, N, Q), "Q": Q, "N": N, "paths": 1,
+                       "hvp": "adjoint", "l2": "inputs larger than L2 (115 MB coordinates per step, >1 GB fields)",
+                       "parallelism": f"{world} independent replica(s), one per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fd_hvp": fd,
+            "pass_ms": mean_pass, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

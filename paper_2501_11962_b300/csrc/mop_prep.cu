@@ -60,8 +60,9 @@ __global__ void k_ref_columns(SysConsts sc, const float* x32, const double* x64,
     r[d] = w;
     ref[3 * i + d] = w;
   }
-  const int cx = min((int)(r[0] / wx), ncx - 1);
-  const int cy = min((int)(r[1] / wy), ncy - 1);
+  // fmax/fmin also map a NaN coordinate to a valid column (the result is then rejected later)
+  const int cx = (int)fmin(fmax(r[0] / wx, 0.0), (double)(ncx - 1));
+  const int cy = (int)fmin(fmax(r[1] / wy, 0.0), (double)(ncy - 1));
   const int col = cx * ncy + cy;
   colid[i] = col;
   atomicAdd(&colcnt[col], 1);
@@ -210,7 +211,7 @@ __global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const
     if (w >= sc.L[d]) w -= sc.L[d];
     if (w < 0.0) w = 0.0;
     cwrap[3 * c + d] = w;
-    bidx[d] = min((int)(w / bw[d]), nb[d] - 1);
+    bidx[d] = (int)fmin(fmax(w / bw[d], 0.0), (double)(nb[d] - 1));
   }
   const int bin = (bidx[0] * nb1 + bidx[1]) * nb2 + bidx[2];
   cbin[c] = bin;
@@ -285,7 +286,8 @@ __global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const do
     wi[d] = cwrap[3 * ci + d];
     ei[d] = hext[3 * ci + d];
     const double em = __uint_as_float(emax[d]);
-    R[d] = (int)floor((sc.rc + ei[d] + em) / bw[d] + 1e-6) + 1;
+    const double reach = fmin(fmax((sc.rc + ei[d] + em) / bw[d] + 1e-6, 0.0), 3.0 * nb[d] + 1.0);
+    R[d] = (int)floor(reach) + 1;
   }
   const int mi0 = molr[2 * ci], mi1 = molr[2 * ci + 1];
   long long out = FILL ? loff[ci] : 0;
