@@ -184,10 +184,11 @@ class Engine:
     def veff_and_grad(self, path_id: int = -1, want_grad: bool = True):
         """Host call: returns (veff array [P], grad array [sum N, Q, 3] or None)."""
         ids = [path_id] if path_id >= 0 else sorted(self.n_beads)
-        nb = sum(self.n_beads[i] for i in ids)
+        nb = sum(self.n_beads.get(i, 0) for i in ids)
         v = np.empty(len(ids))
         g = np.empty((nb, self.Q, 3)) if want_grad else None
-        st = self.L.mop_veff_and_grad(self.h, path_id, _np_ptr(v), _np_ptr(g) if want_grad else None, 0, None)
+        st = self.L.mop_veff_and_grad(self.h, path_id, _np_ptr(v), _np_ptr(g) if (want_grad and nb) else None, 0,
+                                      None)
         self._check(st, "mop_veff_and_grad")
         return v, g
 
