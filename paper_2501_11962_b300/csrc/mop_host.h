@@ -46,7 +46,8 @@ struct PathHost {
   bool set = false;
   int N = 0;
   int n_clu = 0;
-  long long n_ent = 0;
+  int cap = 256;          // list entries reserved per i-cluster
+  int max_count = 0;      // largest list of the last build
   // state
   DevBuf<float> x32;      // [N][Q][3]
   DevBuf<double> x64;     // [N][Q][3] master positions (FP64)
@@ -61,7 +62,9 @@ struct PathHost {
   DevBuf<unsigned> emax;  // [3] float bits
   DevBuf<int> cbin, bincnt, binstart, bincur, binlist;
   DevBuf<double> cwrap;   // [max_clu][3]
-  DevBuf<int> lcnt, loff;
+  DevBuf<int> lcnt;
+  DevBuf<float4> abox;    // [max_slots] union sphere of each atom over the beads
+  DevBuf<unsigned> ctype; // [max_clu] packed LJ types
   DevBuf<int> meta;       // [4]: n_clu, n_ent, overflow, spare
   DevBuf<float4> xq;
   DevBuf<double4_32a> xq64;

@@ -60,8 +60,10 @@ struct PathDev {
   const float4* xq;
   const double4_32a* xq64;
   const int* ts;
-  const int* loff;
-  const int4* ent;
+  const int* lcnt;          // list length of each i-cluster
+  int cap;                  // entries of cluster ci start at ci * cap
+  const unsigned* ctype;    // packed LJ types of each cluster (4 bits per atom)
+  const int4* ent;          // x = cj | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
   const double4_32a* ent64;
   const unsigned long long* emask;
   double* Fnb;

@@ -23,9 +23,10 @@ template <class R> struct Tr;
 
 template <> struct Tr<float> {
   using V4 = float4;
+  using E4 = float4;   // eta as stored for the pair kernels
   static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-  static __device__ __forceinline__ V4 xq(const PathDev& P, size_t k) { return __ldg(&P.xq[k]); }
-  static __device__ __forceinline__ void delta(const PathDev&, long long, const int4& en, float* D) {
+  static __device__ __forceinline__ const V4* xq(const PathDev& P) { return P.xq; }
+  static __device__ __forceinline__ void delta(const PathDev&, size_t, const int4& en, float* D) {
     D[0] = __int_as_float(en.y);
     D[1] = __int_as_float(en.z);
     D[2] = __int_as_float(en.w);
@@ -42,8 +43,8 @@ template <> struct Tr<float> {
 template <> struct Tr<double> {
   using V4 = double4_32a;
   static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-  static __device__ __forceinline__ V4 xq(const PathDev& P, size_t k) { return P.xq64[k]; }
-  static __device__ __forceinline__ void delta(const PathDev& P, long long e, const int4&, double* D) {
+  static __device__ __forceinline__ const V4* xq(const PathDev& P) { return P.xq64; }
+  static __device__ __forceinline__ void delta(const PathDev& P, size_t e, const int4&, double* D) {
     const double4_32a v = P.ent64[e];
     D[0] = v.x;
     D[1] = v.y;
@@ -102,6 +103,69 @@ __device__ __forceinline__ R pair_g(R rinv, R rinv2, R rinv6, const V4& p, R qq,
   return rinv6 * fma(p.x, rinv6, -p.y) * rinv2 + qq * fma(rinv, rinv2, -k2rf) + sh * rinv;
 }
 
+// One pair of the unit: i-atom of this lane against j-atom xj (type row p), cutoff test against
+// rc2e (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or
+// F(+) - F(-) (MODE 2) into acc and the pair energy into eacc (ENERGY).
+template <class R, int MODE, bool ENERGY, class V4>
+__device__ __forceinline__ void pair_one(const Cst<R>& k, const V4& xi, R xs, R ys, R zs, const V4& xj, const V4& p,
+                                         R rc2e, const R* ei, const R* ej, R eps, Acc3<R>& acc, Acc1<R>& eacc) {
+  const R qq = xi.w * xj.w;
+  const R sh = fma(qq, k.drf, p.z);   // phi'(rc) of this pair (0 for the potential-shift modifier)
+  const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
+  if (MODE == 0) {
+    const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const bool in = r2 < rc2e;
+    const R rinv = Tr<R>::rsq(r2);
+    const R rinv2 = rinv * rinv;
+    const R rinv6 = rinv2 * rinv2 * rinv2;
+    R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+    g = in ? g : R(0);
+    acc.a[0] = fma(g, dx, acc.a[0]);
+    acc.a[1] = fma(g, dy, acc.a[1]);
+    acc.a[2] = fma(g, dz, acc.a[2]);
+    if (ENERGY) {
+      // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
+      const R r = r2 * rinv;
+      const R elj = rinv6 * fma(p.x * R(1.0 / 12.0), rinv6, -p.y * R(1.0 / 6.0));
+      const R erf = qq * (rinv + fma(k.krf, r2, -k.crf));
+      const R E = elj + erf - p.w - (r - k.rc) * sh;
+      eacc.a += in ? E : R(0);
+    }
+  } else if (MODE == 1) {
+    const R ux = ei[0] - ej[0], uy = ei[1] - ej[1], uz = ei[2] - ej[2];
+    const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const bool in = r2 < rc2e;
+    const R rinv = Tr<R>::rsq(r2);
+    const R rinv2 = rinv * rinv;
+    const R rinv3 = rinv * rinv2;
+    const R rinv6 = rinv2 * rinv2 * rinv2;
+    R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+    const R b = rinv6 * fma(R(14) * p.x, rinv6, R(-8) * p.y) * rinv2 * rinv2 + fma(R(3) * qq, rinv2, sh) * rinv3;
+    const R s = fma(dx, ux, fma(dy, uy, dz * uz));
+    const R t = in ? b * s : R(0);
+    g = in ? g : R(0);
+    acc.a[0] += fma(t, dx, -g * ux);
+    acc.a[1] += fma(t, dy, -g * uy);
+    acc.a[2] += fma(t, dz, -g * uz);
+  } else {
+    const R ux = eps * (ei[0] - ej[0]), uy = eps * (ei[1] - ej[1]), uz = eps * (ei[2] - ej[2]);
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const R px = sgn ? dx - ux : dx + ux, py = sgn ? dy - uy : dy + uy, pz = sgn ? dz - uz : dz + uz;
+      const R r2 = fma(px, px, fma(py, py, pz * pz));
+      const bool in = r2 < rc2e;
+      const R rinv = Tr<R>::rsq(r2);
+      const R rinv2 = rinv * rinv;
+      const R rinv6 = rinv2 * rinv2 * rinv2;
+      R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+      g = in ? (sgn ? -g : g) : R(0);
+      acc.a[0] = fma(g, px, acc.a[0]);
+      acc.a[1] = fma(g, py, acc.a[1]);
+      acc.a[2] = fma(g, pz, acc.a[2]);
+    }
+  }
+}
+
 template <class R, int MODE, bool ENERGY>
 __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab,
                                           const PathDev& P, int n, int ci, int lane) {
@@ -110,8 +174,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   const int i = lane & 7, jj = lane >> 3;
   const size_t bo = (size_t)n * P.Qpad;
   const int si = ci * kCL + i;
-  const V4 xi = Tr<R>::xq(P, bo + si);
-  const int ti = __ldg(&P.ts[si]) * sc.n_types;
+  const V4* __restrict__ xqb = Tr<R>::xq(P) + bo;
+  const V4 xi = xqb[si];
+  const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * sc.n_types;
   R ei[3] = {R(0), R(0), R(0)};
   R eps = R(0);
   if (MODE >= 1) Tr<R>::eta(P, bo + si, ei);
@@ -121,88 +186,39 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   }
   Acc3<R> acc;
   Acc1<R> eacc;
-  const int e0 = __ldg(&P.loff[ci]), e1 = __ldg(&P.loff[ci + 1]);
-  int chunk = 0;
-  for (int e = e0; e < e1; ++e) {
-    const int4 en = __ldg(&P.ent[e]);
-    const unsigned long long m = (en.x < 0) ? __ldg(&P.emask[e]) : 0ull;
-    const int cj = en.x & 0x7fffffff;
-    R D[3];
-    Tr<R>::delta(P, e, en, D);
-    const R xs = xi.x + D[0], ys = xi.y + D[1], zs = xi.z + D[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int jl = jj + 4 * h;
-      const int sj = cj * kCL + jl;
-      const V4 xj = Tr<R>::xq(P, bo + sj);
-      const int tj = __ldg(&P.ts[sj]);
-      const V4 p = tab[ti + tj];
-      const bool ex = (m >> (i * kCL + jl)) & 1ull;
-      const R qq = xi.w * xj.w;
-      const R sh = fma(qq, k.drf, p.z);
-      const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
-      if (MODE == 0) {
-        const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const bool in = (r2 < k.rc2) && !ex;
-        const R rinv = Tr<R>::rsq(r2);
-        const R rinv2 = rinv * rinv;
-        const R rinv6 = rinv2 * rinv2 * rinv2;
-        R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
-        g = in ? g : R(0);
-        acc.a[0] = fma(g, dx, acc.a[0]);
-        acc.a[1] = fma(g, dy, acc.a[1]);
-        acc.a[2] = fma(g, dz, acc.a[2]);
-        if (ENERGY) {
-          // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
-          const R r = r2 * rinv;
-          const R elj = rinv6 * fma(p.x * R(1.0 / 12.0), rinv6, -p.y * R(1.0 / 6.0));
-          const R erf = qq * (rinv + fma(k.krf, r2, -k.crf));
-          const R E = elj + erf - p.w - (r - k.rc) * sh;
-          eacc.a += in ? E : R(0);
-        }
-      } else if (MODE == 1) {
-        R ej[3];
-        Tr<R>::eta(P, bo + sj, ej);
-        const R ux = ei[0] - ej[0], uy = ei[1] - ej[1], uz = ei[2] - ej[2];
-        const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const bool in = (r2 < k.rc2) && !ex;
-        const R rinv = Tr<R>::rsq(r2);
-        const R rinv2 = rinv * rinv;
-        const R rinv3 = rinv * rinv2;
-        const R rinv6 = rinv2 * rinv2 * rinv2;
-        R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
-        const R b = rinv6 * fma(R(14) * p.x, rinv6, R(-8) * p.y) * rinv2 * rinv2 + fma(R(3) * qq, rinv2, sh) * rinv3;
-        const R s = fma(dx, ux, fma(dy, uy, dz * uz));
-        const R t = in ? b * s : R(0);
-        g = in ? g : R(0);
-        acc.a[0] += fma(t, dx, -g * ux);
-        acc.a[1] += fma(t, dy, -g * uy);
-        acc.a[2] += fma(t, dz, -g * uz);
-      } else {
-        R ej[3];
-        Tr<R>::eta(P, bo + sj, ej);
-        const R ux = eps * (ei[0] - ej[0]), uy = eps * (ei[1] - ej[1]), uz = eps * (ei[2] - ej[2]);
-#pragma unroll
-        for (int sgn = 0; sgn < 2; ++sgn) {
-          const R px = sgn ? dx - ux : dx + ux, py = sgn ? dy - uy : dy + uy, pz = sgn ? dz - uz : dz + uz;
-          const R r2 = fma(px, px, fma(py, py, pz * pz));
-          const bool in = (r2 < k.rc2) && !ex;
-          const R rinv = Tr<R>::rsq(r2);
-          const R rinv2 = rinv * rinv;
-          const R rinv6 = rinv2 * rinv2 * rinv2;
-          R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
-          g = in ? (sgn ? -g : g) : R(0);
-          acc.a[0] = fma(g, px, acc.a[0]);
-          acc.a[1] = fma(g, py, acc.a[1]);
-          acc.a[2] = fma(g, pz, acc.a[2]);
-        }
+  const int cnt = __ldg(&P.lcnt[ci]);
+  const size_t eb = (size_t)ci * P.cap;
+  const int4* __restrict__ entp = P.ent + eb;
+  const int mshift = i * kCL + jj;
+  for (int e0 = 0; e0 < cnt; e0 += 16) {
+    const int e1 = min(cnt, e0 + 16);
+    for (int e = e0; e < e1; ++e) {
+      const int4 en = __ldg(&entp[e]);
+      const int cj = en.x & 0x1fffffff;
+      R rcA = k.rc2, rcB = k.rc2;
+      if (en.x < 0) {
+        const unsigned long long m = __ldg(&P.emask[eb + e]) >> mshift;
+        rcA = (m & 1ull) ? R(-1) : k.rc2;
+        rcB = ((m >> 4) & 1ull) ? R(-1) : k.rc2;
+      }
+      R D[3];
+      Tr<R>::delta(P, eb + e, en, D);
+      const R xs = xi.x + D[0], ys = xi.y + D[1], zs = xi.z + D[2];
+      const unsigned ct = __ldg(&P.ctype[cj]) >> (4 * jj);
+      const V4* __restrict__ xj = xqb + cj * kCL + jj;
+      R ejA[3] = {R(0), R(0), R(0)}, ejB[3] = {R(0), R(0), R(0)};
+      if (en.x & (1 << 29)) {
+        if (MODE >= 1) Tr<R>::eta(P, bo + cj * kCL + jj, ejA);
+        pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, xj[0], tabrow[ct & 15u], rcA, ei, ejA, eps, acc, eacc);
+      }
+      if (en.x & (1 << 30)) {
+        if (MODE >= 1) Tr<R>::eta(P, bo + cj * kCL + jj + 4, ejB);
+        pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, xj[4], tabrow[(ct >> 16) & 15u], rcB, ei, ejB, eps, acc,
+                                      eacc);
       }
     }
-    if (++chunk == 16) {
-      acc.fold();
-      if (ENERGY) eacc.fold();
-      chunk = 0;
-    }
+    acc.fold();
+    if (ENERGY) eacc.fold();
   }
   const bool valid = __ldg(&P.perm[si]) >= 0;
   double out[3];
@@ -271,7 +287,8 @@ cudaError_t launch_one(const SysConsts& sc, const PathDev* d_paths, int n_paths,
   return cudaGetLastError();
 }
 
-// in-cutoff, non-excluded ordered pairs of every force unit (instrumentation)
+// in-cutoff, non-excluded ordered pairs of every force unit, and the pairs the list makes the
+// force kernel evaluate (instrumentation)
 __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, int n_paths, long long n_units,
                               unsigned long long* counts) {
   const int lane = threadIdx.x & 31;
@@ -286,17 +303,19 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
     const int i = lane & 7, jj = lane >> 3;
     const size_t bo = (size_t)n * P.Qpad;
     const bool vi = P.perm[ci * kCL + i] >= 0;
-    for (int e = P.loff[ci]; e < P.loff[ci + 1]; ++e) {
-      const int4 en = P.ent[e];
-      const unsigned long long m = (en.x < 0) ? P.emask[e] : 0ull;
-      const int cj = en.x & 0x7fffffff;
+    const size_t eb = (size_t)ci * P.cap;
+    for (int e = 0; e < P.lcnt[ci]; ++e) {
+      const int4 en = P.ent[eb + e];
+      const unsigned long long m = (en.x < 0) ? P.emask[eb + e] : 0ull;
+      const int cj = en.x & 0x1fffffff;
       double D[3];
       if (P.ent64) {
-        D[0] = P.ent64[e].x; D[1] = P.ent64[e].y; D[2] = P.ent64[e].z;
+        D[0] = P.ent64[eb + e].x; D[1] = P.ent64[eb + e].y; D[2] = P.ent64[eb + e].z;
       } else {
         D[0] = __int_as_float(en.y); D[1] = __int_as_float(en.z); D[2] = __int_as_float(en.w);
       }
       for (int h = 0; h < 2; ++h) {
+        if (!(en.x & (1 << (29 + h)))) continue;
         const int jl = jj + 4 * h, sj = cj * kCL + jl;
         double a[3], b[3];
         if (P.xq64) {

@@ -262,18 +262,69 @@ __global__ void k_sort_bins(int nbins, const int* binstart, int* binlist) {
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-// cluster-pair list of one i-cluster: count pass (FILL = false) or fill pass
-template <bool FILL, bool F64>
-__global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const double* cwrap, const float* hext,
-                            const unsigned* emax, const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
-                            double bw2, const int* binstart, const int* binlist, const int* perm, const int* molr,
-                            int* lcnt, const int* loff, int4* ent, double4_32a* ent64, unsigned long long* emask) {
-  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ci >= max_clu) return;
-  if (ci >= meta[0]) {
-    if (!FILL) lcnt[ci] = 0;
+// Union over beads of each atom's aligned position, as a sphere (centre relative to the
+// cluster centre, radius) used by the exact pruning of cluster pairs.
+__global__ void k_atom_box(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
+                           const int* perm, const int* meta, const double* center, double margin, float4* abox) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= meta[0] * kCL) return;
+  const int a = perm[s];
+  if (a < 0) {
+    abox[s] = make_float4(kDummyCoord, kDummyCoord, kDummyCoord, -1.0f);
     return;
   }
+  const int c = s / kCL;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  const size_t Q3 = 3 * (size_t)sc.Q;
+  for (int b = 0; b < N; ++b)
+    for (int d = 0; d < 3; ++d) {
+      const double v = aligned_coord(coord(x32, x64, b * Q3 + 3 * (size_t)a + d), ref[3 * a + d], sc.L[d], sc.invL[d]);
+      lo[d] = fmin(lo[d], v);
+      hi[d] = fmax(hi[d], v);
+    }
+  float cf[3];
+  double r2 = 0.0, e2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double cen = 0.5 * (lo[d] + hi[d]) - center[3 * c + d];
+    cf[d] = (float)cen;
+    const double h = 0.5 * (hi[d] - lo[d]);
+    r2 += h * h;
+    const double er = fabs((double)cf[d] - cen);
+    e2 += er * er;
+  }
+  const float r = __double2float_ru(sqrt(r2) + sqrt(e2) + margin + 1e-6);
+  abox[s] = make_float4(cf[0], cf[1], cf[2], r);
+}
+
+// LJ types of the 8 atoms of each cluster, 4 bits each
+__global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= meta[0]) return;
+  unsigned v = 0;
+  for (int k = 0; k < kCL; ++k) v |= ((unsigned)ts[c * kCL + k] & 15u) << (4 * k);
+  ctype[c] = v;
+}
+
+// Cluster-pair list of one i-cluster per warp.  Candidates come from the bins around the
+// i-cluster (every periodic image), pass the union-bounding-box test, then the exact test on
+// the atoms' union spheres; bit 29 / bit 30 of an entry mark the j-half-clusters (atoms 0-3 /
+// 4-7) that hold at least one pair that can come within rc in some bead.  Entries of cluster ci
+// go to ent[ci * cap ...] in bin order (deterministic); lcnt[ci] = their number; meta[2] =
+// largest count (a count above cap means the list must be rebuilt with a larger cap).
+template <bool F64>
+__global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta_in, int max_clu,
+                                                   const double* cwrap, const float* hext, const unsigned* emax,
+                                                   const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
+                                                   double bw2, const int* binstart, const int* binlist,
+                                                   const int* perm, const int* molr, const float4* abox, int cap,
+                                                   int* lcnt, int4* ent, double4_32a* ent64,
+                                                   unsigned long long* emask, int* meta) {
+  __shared__ float4 ibox[4][kCL];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ci = blockIdx.x * 4 + warp;
+  if (ci >= max_clu || ci >= meta_in[0]) return;   // warp-uniform
+  if (lane < kCL) ibox[warp][lane] = abox[ci * kCL + lane];
+  __syncwarp();
   const int nb[3] = {nb0, nb1, nb2};
   const double bw[3] = {bw0, bw1, bw2};
   double wi[3], ei[3];
@@ -290,7 +341,8 @@ __global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const do
     R[d] = (int)floor(reach) + 1;
   }
   const int mi0 = molr[2 * ci], mi1 = molr[2 * ci + 1];
-  long long out = FILL ? loff[ci] : 0;
+  const float rcf = (float)sc.rc + 1e-5f;
+  const size_t base = (size_t)ci * cap;
   int count = 0;
   for (int dx = -R[0]; dx <= R[0]; ++dx) {
     const int Bx = bi[0] + dx, kx = floor_div(Bx, nb[0]), wx = Bx - kx * nb[0];
@@ -299,43 +351,75 @@ __global__ void k_pair_list(SysConsts sc, const int* meta, int max_clu, const do
       for (int dz = -R[2]; dz <= R[2]; ++dz) {
         const int Bz = bi[2] + dz, kz = floor_div(Bz, nb[2]), wz = Bz - kz * nb[2];
         const int bin = (wx * nb1 + wy) * nb2 + wz;
+        const int s0 = binstart[bin], nbin = binstart[bin + 1] - s0;
         const int kk[3] = {kx, ky, kz};
-        for (int t = binstart[bin]; t < binstart[bin + 1]; ++t) {
-          const int cj = binlist[t];
-          double D[3], g2 = 0.0;
-          for (int d = 0; d < 3; ++d) {
-            D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
-            const double gap = fmax(0.0, fabs(D[d]) - ei[d] - (double)hext[3 * cj + d]);
-            g2 += gap * gap;
-          }
-          if (!(g2 < sc.rc2)) continue;
-          if (FILL) {
-            unsigned long long m = 0ull;
-            const int mj0 = molr[2 * cj], mj1 = molr[2 * cj + 1];
-            if (mi0 <= mj1 && mj0 <= mi1) {
-              for (int i = 0; i < kCL; ++i) {
-                const int a = perm[ci * kCL + i];
-                if (a < 0) continue;
-                for (int j = 0; j < kCL; ++j) {
-                  const int b = perm[cj * kCL + j];
-                  if (b < 0) continue;
-                  if (sc.mol[a] == sc.mol[b] && abs(sc.loc[a] - sc.loc[b]) <= 2) m |= 1ull << (i * kCL + j);
+        for (int t0 = 0; t0 < nbin; t0 += 32) {
+          const int t = t0 + lane;
+          unsigned hm = 0;
+          int cj = 0;
+          double D[3] = {0.0, 0.0, 0.0};
+          if (t < nbin) {
+            cj = binlist[s0 + t];
+            double g2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
+              const double gap = fmax(0.0, fabs(D[d]) - ei[d] - (double)hext[3 * cj + d]);
+              g2 += gap * gap;
+            }
+            if (g2 < sc.rc2) {
+              const float Dx = (float)D[0], Dy = (float)D[1], Dz = (float)D[2];
+              for (int j = 0; j < kCL && hm != 3u; ++j) {
+                const float4 bj = abox[cj * kCL + j];
+                if (bj.w < 0.f) continue;
+                const unsigned bit = j < 4 ? 1u : 2u;
+                if (hm & bit) continue;
+                for (int i = 0; i < kCL; ++i) {
+                  const float4 bi4 = ibox[warp][i];
+                  if (bi4.w < 0.f) continue;
+                  const float ux = bi4.x + Dx - bj.x, uy = bi4.y + Dy - bj.y, uz = bi4.z + Dz - bj.z;
+                  const float lim = rcf + bi4.w + bj.w;
+                  if (ux * ux + uy * uy + uz * uz < lim * lim) {
+                    hm |= bit;
+                    break;
+                  }
                 }
               }
             }
-            const float fx = (float)D[0], fy = (float)D[1], fz = (float)D[2];
-            ent[out] = make_int4(cj | (m ? (int)0x80000000 : 0), __float_as_int(fx), __float_as_int(fy),
-                                 __float_as_int(fz));
-            if (F64) ent64[out] = make_double4_32a(D[0], D[1], D[2], 0.0);
-            emask[out] = m;
-            ++out;
           }
-          ++count;
+          const bool pass = hm != 0u;
+          const unsigned bal = __ballot_sync(0xffffffffu, pass);
+          if (pass) {
+            const int pos = count + __popc(bal & ((1u << lane) - 1u));
+            if (pos < cap) {
+              unsigned long long m = 0ull;
+              const int mj0 = molr[2 * cj], mj1 = molr[2 * cj + 1];
+              if (mi0 <= mj1 && mj0 <= mi1) {
+                for (int i = 0; i < kCL; ++i) {
+                  const int a = perm[ci * kCL + i];
+                  if (a < 0) continue;
+                  for (int j = 0; j < kCL; ++j) {
+                    const int b = perm[cj * kCL + j];
+                    if (b < 0) continue;
+                    if (sc.mol[a] == sc.mol[b] && abs(sc.loc[a] - sc.loc[b]) <= 2) m |= 1ull << (i * kCL + j);
+                  }
+                }
+              }
+              const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0);
+              ent[base + pos] = make_int4(cj | flags, __float_as_int((float)D[0]), __float_as_int((float)D[1]),
+                                          __float_as_int((float)D[2]));
+              if (F64) ent64[base + pos] = make_double4_32a(D[0], D[1], D[2], 0.0);
+              emask[base + pos] = m;
+            }
+          }
+          count += __popc(bal);
         }
       }
     }
   }
-  if (!FILL) lcnt[ci] = count;
+  if (lane == 0) {
+    lcnt[ci] = min(count, cap);
+    atomicMax(&meta[2], count);
+  }
 }
 
 inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
@@ -386,7 +470,8 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_CK(P.bincur.ensure(nbins));
   MOP_CK(P.binlist.ensure(max_clu));
   MOP_CK(P.lcnt.ensure(max_clu));
-  MOP_CK(P.loff.ensure(max_clu + 1));
+  MOP_CK(P.abox.ensure(max_slots));
+  MOP_CK(P.ctype.ensure(max_clu));
   MOP_CK(P.meta.ensure(4));
   if (f64) MOP_CK(P.xq64.ensure((size_t)N * max_slots));
   else MOP_CK(P.xq.ensure((size_t)N * max_slots));
@@ -427,33 +512,42 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_KL();
   k_sort_bins<<<nblk(nbins, bs), bs, 0, st>>>(nbins, P.binstart.p, P.binlist.p);
   MOP_KL();
-  k_pair_list<false, false><<<nblk(max_clu, 128), 128, 0, st>>>(
-      sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1],
-      g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.lcnt.p, nullptr, nullptr, nullptr, nullptr);
+  k_atom_box<<<nblk(max_slots, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, P.center.p, margin,
+                                                  P.abox.p);
   MOP_KL();
-  k_scan<<<1, 1024, 0, st>>>(P.lcnt.p, max_clu, P.loff.p, nullptr, P.meta.p + 1);
+  k_cluster_types<<<nblk(max_clu, bs), bs, 0, st>>>(P.meta.p, P.ts.p, P.ctype.p);
   MOP_KL();
-  int meta[4];
-  MOP_CK(cudaMemcpyAsync(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost, st));
-  MOP_CK(cudaStreamSynchronize(st));
-  P.n_clu = meta[0];
-  P.n_ent = meta[1];
-  const size_t ne = (size_t)P.n_ent;
-  MOP_CK(P.ent.ensure(ne + ne / 8 + 64));
-  MOP_CK(P.emask.ensure(ne + ne / 8 + 64));
-  if (f64) MOP_CK(P.ent64.ensure(ne + ne / 8 + 64));
-  if (f64)
-    k_pair_list<true, true><<<nblk(max_clu, 128), 128, 0, st>>>(
-        sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0],
-        g.bw[1], g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.lcnt.p, P.loff.p, P.ent.p, P.ent64.p,
-        P.emask.p);
-  else
-    k_pair_list<true, false><<<nblk(max_clu, 128), 128, 0, st>>>(
-        sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0],
-        g.bw[1], g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.lcnt.p, P.loff.p, P.ent.p, nullptr,
-        P.emask.p);
-  MOP_KL();
-  return cudaSuccess;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    const size_t cap_total = (size_t)max_clu * P.cap;
+    MOP_CK(P.ent.ensure(cap_total));
+    MOP_CK(P.emask.ensure(cap_total));
+    if (f64) MOP_CK(P.ent64.ensure(cap_total));
+    MOP_CK(cudaMemsetAsync(P.meta.p + 2, 0, sizeof(int), st));
+    const int blocks = nblk(max_clu, 4);
+    if (f64)
+      k_pair_list<true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
+                                                g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
+                                                P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cap, P.lcnt.p, P.ent.p,
+                                                P.ent64.p, P.emask.p, P.meta.p);
+    else
+      k_pair_list<false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
+                                                 g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
+                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cap, P.lcnt.p, P.ent.p,
+                                                 nullptr, P.emask.p, P.meta.p);
+    MOP_KL();
+    int meta[4];
+    MOP_CK(cudaMemcpyAsync(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost, st));
+    MOP_CK(cudaStreamSynchronize(st));
+    P.n_clu = meta[0];
+    if (meta[2] <= P.cap) {
+      P.max_count = meta[2];
+      return cudaSuccess;
+    }
+    P.cap = (meta[2] + meta[2] / 4 + 31) / 32 * 32;   // grow and rebuild
+  }
+  if (err) *err = "pair list did not fit after growing its capacity";
+  return cudaErrorMemoryAllocation;
 }
 
 }  // namespace mop
+
