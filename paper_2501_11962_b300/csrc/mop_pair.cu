@@ -166,9 +166,30 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const V4& xi, R xs, R 
   }
 }
 
+// Warp-private staging area: one chunk of up to 32 list entries, and the 32 j-atoms (4 entries
+// x 8 atoms) of the block being processed.
+template <class R> struct Stage {
+  using V4 = typename Tr<R>::V4;
+  V4 x[32];                  // j coordinates + charge
+  V4 e[32];                  // j eta (HVP / FD)
+  V4 d[32];                  // Delta of each staged entry
+  int4 ent[32];              // entries of the chunk
+  unsigned long long m[32];  // exclusion masks of the chunk
+  int t[32];                 // j types
+};
+
+template <class R, class V4>
+__device__ __forceinline__ V4 load_eta4(const PathDev& P, size_t k);
+template <> __device__ __forceinline__ float4 load_eta4<float, float4>(const PathDev& P, size_t k) {
+  return __ldg(&P.eta32[k]);
+}
+template <> __device__ __forceinline__ double4_32a load_eta4<double, double4_32a>(const PathDev& P, size_t k) {
+  return make_double4_32a(P.eta[3 * k], P.eta[3 * k + 1], P.eta[3 * k + 2], 0.0);
+}
+
 template <class R, int MODE, bool ENERGY>
 __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab,
-                                          const PathDev& P, int n, int ci, int lane) {
+                                          Stage<R>& S, const PathDev& P, int n, int ci, int lane) {
   using V4 = typename Tr<R>::V4;
   const Cst<R> k(sc);
   const int i = lane & 7, jj = lane >> 3;
@@ -188,33 +209,86 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   Acc1<R> eacc;
   const int cnt = __ldg(&P.lcnt[ci]);
   const size_t eb = (size_t)ci * P.cap;
-  const int4* __restrict__ entp = P.ent + eb;
   const int mshift = i * kCL + jj;
-  for (int e0 = 0; e0 < cnt; e0 += 16) {
-    const int e1 = min(cnt, e0 + 16);
-    for (int e = e0; e < e1; ++e) {
-      const int4 en = __ldg(&entp[e]);
-      const int cj = en.x & 0x1fffffff;
-      R rcA = k.rc2, rcB = k.rc2;
-      if (en.x < 0) {
-        const unsigned long long m = __ldg(&P.emask[eb + e]) >> mshift;
-        rcA = (m & 1ull) ? R(-1) : k.rc2;
-        rcB = ((m >> 4) & 1ull) ? R(-1) : k.rc2;
+  const int sa = lane & 7, sk = lane >> 3;   // staging role: atom sa of block entry sk
+  for (int c0 = 0; c0 < cnt; c0 += 32) {
+    const int nc = min(32, cnt - c0);
+    __syncwarp();
+    {
+      int4 en = make_int4(0, 0, 0, 0);
+      unsigned long long m = 0ull;
+      V4 dv;
+      if (lane < nc) {
+        en = __ldg(&P.ent[eb + c0 + lane]);
+        if (en.x < 0) m = __ldg(&P.emask[eb + c0 + lane]);
+        R D[3];
+        Tr<R>::delta(P, eb + c0 + lane, en, D);
+        dv.x = D[0];
+        dv.y = D[1];
+        dv.z = D[2];
+        dv.w = R(0);
       }
-      R D[3];
-      Tr<R>::delta(P, eb + e, en, D);
-      const R xs = xi.x + D[0], ys = xi.y + D[1], zs = xi.z + D[2];
-      const unsigned ct = __ldg(&P.ctype[cj]) >> (4 * jj);
-      const V4* __restrict__ xj = xqb + cj * kCL + jj;
-      R ejA[3] = {R(0), R(0), R(0)}, ejB[3] = {R(0), R(0), R(0)};
-      if (en.x & (1 << 29)) {
-        if (MODE >= 1) Tr<R>::eta(P, bo + cj * kCL + jj, ejA);
-        pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, xj[0], tabrow[ct & 15u], rcA, ei, ejA, eps, acc, eacc);
+      S.ent[lane] = en;
+      S.m[lane] = m;
+      S.d[lane] = dv;
+    }
+    __syncwarp();
+    // fetch block 0 of the chunk into registers
+    V4 fx, fe;
+    int ft = 0;
+    auto fetch = [&](int b) {
+      const int e = 4 * b + sk;
+      if (e < nc) {
+        const int cj = S.ent[e].x & 0x1fffffff;
+        const int sj = cj * kCL + sa;
+        fx = xqb[sj];
+        ft = __ldg(&P.ts[sj]);
+        if (MODE >= 1) fe = load_eta4<R, V4>(P, bo + sj);
       }
-      if (en.x & (1 << 30)) {
-        if (MODE >= 1) Tr<R>::eta(P, bo + cj * kCL + jj + 4, ejB);
-        pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, xj[4], tabrow[(ct >> 16) & 15u], rcB, ei, ejB, eps, acc,
-                                      eacc);
+    };
+    fetch(0);
+    const int nb = (nc + 3) >> 2;
+    for (int b = 0; b < nb; ++b) {
+      __syncwarp();
+      S.x[lane] = fx;
+      S.t[lane] = ft;
+      if (MODE >= 1) S.e[lane] = fe;
+      __syncwarp();
+      if (b + 1 < nb) fetch(b + 1);
+      const int kmax = min(4, nc - 4 * b);
+      for (int q = 0; q < kmax; ++q) {
+        const int e = 4 * b + q;
+        const int fl = S.ent[e].x;
+        R rcA = k.rc2, rcB = k.rc2;
+        if (fl < 0) {
+          const unsigned long long m = S.m[e] >> mshift;
+          rcA = (m & 1ull) ? R(-1) : k.rc2;
+          rcB = ((m >> 4) & 1ull) ? R(-1) : k.rc2;
+        }
+        const V4 D = S.d[e];
+        const R xs = xi.x + D.x, ys = xi.y + D.y, zs = xi.z + D.z;
+        const int so = q * kCL + jj;
+        if (fl & (1 << 29)) {
+          R ej[3] = {R(0), R(0), R(0)};
+          if (MODE >= 1) {
+            const V4 v = S.e[so];
+            ej[0] = v.x; ej[1] = v.y; ej[2] = v.z;
+          }
+          pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, S.x[so], tabrow[S.t[so]], rcA, ei, ej, eps, acc, eacc);
+        }
+        if (fl & (1 << 30)) {
+          R ej[3] = {R(0), R(0), R(0)};
+          if (MODE >= 1) {
+            const V4 v = S.e[so + 4];
+            ej[0] = v.x; ej[1] = v.y; ej[2] = v.z;
+          }
+          pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, S.x[so + 4], tabrow[S.t[so + 4]], rcB, ei, ej, eps, acc,
+                                        eacc);
+        }
+      }
+      if ((b & 3) == 3) {
+        acc.fold();
+        if (ENERGY) eacc.fold();
       }
     }
     acc.fold();
@@ -244,14 +318,16 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
 }
 
 template <class R, int MODE>
-__global__ void __launch_bounds__(128) k_pair(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
                                               long long n_units) {
   using V4 = typename Tr<R>::V4;
   __shared__ V4 tab[kMaxTypes * kMaxTypes];
+  __shared__ Stage<R> stage[4];
   const int nt2 = sc.n_types * sc.n_types;
   for (int k = threadIdx.x; k < nt2; k += blockDim.x) tab[k] = Tr<R>::tab(sc, k);
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  Stage<R>& S = stage[threadIdx.x >> 5];
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nw) {
     int p = 0;
@@ -265,8 +341,8 @@ __global__ void __launch_bounds__(128) k_pair(SysConsts sc, const PathDev* __res
     const long long v = u - (MODE == 0 ? P.unit_off : P.unit_off_h);
     const int n = (int)(v % nb);
     const int ci = (int)(v / nb);
-    if (MODE == 0 && n == 0) pair_unit<R, 0, true>(sc, tab, P, n, ci, lane);
-    else pair_unit<R, MODE, false>(sc, tab, P, n, ci, lane);
+    if (MODE == 0 && n == 0) pair_unit<R, 0, true>(sc, tab, S, P, n, ci, lane);
+    else pair_unit<R, MODE, false>(sc, tab, S, P, n, ci, lane);
   }
 }
 

@@ -348,10 +348,15 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
     const int Bx = bi[0] + dx, kx = floor_div(Bx, nb[0]), wx = Bx - kx * nb[0];
     for (int dy = -R[1]; dy <= R[1]; ++dy) {
       const int By = bi[1] + dy, ky = floor_div(By, nb[1]), wy = By - ky * nb[1];
-      for (int dz = -R[2]; dz <= R[2]; ++dz) {
-        const int Bz = bi[2] + dz, kz = floor_div(Bz, nb[2]), wz = Bz - kz * nb[2];
-        const int bin = (wx * nb1 + wy) * nb2 + wz;
-        const int s0 = binstart[bin], nbin = binstart[bin + 1] - s0;
+      const int binbase = (wx * nb1 + wy) * nb2;
+      // the z window, cut where it crosses a periodic image: each piece is one contiguous
+      // range of binlist (bins are ordered with z fastest)
+      for (int z0 = bi[2] - R[2]; z0 <= bi[2] + R[2];) {
+        const int kz = floor_div(z0, nb[2]);
+        const int zl = min(bi[2] + R[2], (kz + 1) * nb[2] - 1);
+        const int s0 = binstart[binbase + (z0 - kz * nb[2])];
+        const int nbin = binstart[binbase + (zl - kz * nb[2]) + 1] - s0;
+        z0 = zl + 1;
         const int kk[3] = {kx, ky, kz};
         for (int t0 = 0; t0 < nbin; t0 += 32) {
           const int t = t0 + lane;
