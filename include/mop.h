@@ -178,6 +178,22 @@ mop_status mop_last_pass_ms(mop_handle* h, float* out, int32_t n);
  * included).  Synchronous. */
 mop_status mop_count_pairs(mop_handle* h, int32_t path_id, int64_t* unique, int64_t* listed);
 
+/* Spring energy without any device allocation.  No counterpart in the paper: this is a service
+ * for callers that cannot allocate device memory, for example code that runs inside a CUDA
+ * graph that another framework captures and replays, or a plug-in whose host application owns
+ * every allocation.  Returns, in *out (device pointer, one double), the spring energy
+ *     sum_{n < n_springs} sum_i K_i/2 |eta^n_i|^2,   K_i = mass_i nu_path / (2 dt_path),
+ * of eta [n_springs][n_atoms][3] (device, FP64, as mop_get_field returns it) and mass
+ * [n_atoms] (device, FP64), with the same deterministic two-stage reduction as
+ * mop_veff_and_grad.  No handle is needed and nothing is allocated: the block partial sums live
+ * in a fixed array of 65,536 doubles (512 KiB) that every GPU loading the library keeps until
+ * the process exits.  n_springs * ceil(n_atoms / 256) must not exceed 65,536 (MOP_ERR_ARG
+ * otherwise).  Work is enqueued on cuda_stream on the current device; the first call on a
+ * device looks up the array's device address, so make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race.  Errors: MOP_ERR_ARG, MOP_ERR_CUDA. */
+mop_status mop_spring_energy_noalloc(const double* eta, const double* mass, int32_t n_springs, int32_t n_atoms,
+                                     double dt_path, double nu_path, double* out, void* cuda_stream);
+
 /* Text of the last error of the handle ("" if none); valid until the next call. */
 const char* mop_last_error(const mop_handle* h);
 
