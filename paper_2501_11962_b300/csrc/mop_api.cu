@@ -27,6 +27,8 @@ struct mop_handle {
   uint64_t step_count = 0;
   // device copies of the system
   DevBuf<double> mass, Kspr, cL, qs;
+  DevBuf<float2> c_df;
+  DevBuf<float> Kf;
   DevBuf<int> type, mol, loc, inc_off;
   DevBuf<int4> inc;
   DevBuf<double2> incp;
@@ -83,13 +85,28 @@ __global__ void k_d2f(const double* in, float* out, long long n) {
   if (t < n) out[t] = (float)in[t];
 }
 
-// slot-ordered field -> caller-ordered [N][Q][3], zero rows outside [0, n_rows)
-__global__ void k_gather_field(const double* f, const int* slot, int Q, int Qpad, int N, int n_rows, double* out) {
+// slot-ordered field -> caller-ordered [N][Q][3], zero rows outside [0, n_rows).
+// fmt 0: FP64 x 3; 1: double-float (hi, lo) x 3; 2: float4
+__global__ void k_gather_field(const void* f, int fmt, const int* slot, int Q, int Qpad, int N, int n_rows,
+                               double* out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)N * Q) return;
   const int a = (int)(t % Q), n = (int)(t / Q);
-  for (int c = 0; c < 3; ++c)
-    out[3 * t + c] = n < n_rows ? f[3 * ((size_t)n * Qpad + slot[a]) + c] : 0.0;
+  const size_t k = (size_t)n * Qpad + slot[a];
+  for (int c = 0; c < 3; ++c) {
+    double v = 0.0;
+    if (n < n_rows) {
+      if (fmt == 0) v = ((const double*)f)[3 * k + c];
+      else if (fmt == 1) {
+        const float2 w = ((const float2*)f)[3 * k + c];
+        v = (double)w.x + (double)w.y;
+      } else {
+        const float4 w = ((const float4*)f)[k];
+        v = c == 0 ? w.x : (c == 1 ? w.y : w.z);
+      }
+    }
+    out[3 * t + c] = v;
+  }
 }
 
 inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
@@ -309,11 +326,16 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.fd_h = d->fd_h;
 
   std::vector<double> Kspr(Q), cL(Q), qs(Q);
+  std::vector<float2> c_df(Q);
+  std::vector<float> Kf(Q);
   const double sqf = std::sqrt(kCoulombF);
   for (int i = 0; i < Q; ++i) {
     Kspr[i] = d->mass[i] * d->nu_path / (2.0 * d->dt_path);
     cL[i] = d->dt_path / (d->mass[i] * d->nu_path);
     qs[i] = d->charge[i] * sqf;
+    const float ch = (float)cL[i];
+    c_df[i] = make_float2(ch, (float)(cL[i] - (double)ch));
+    Kf[i] = (float)Kspr[i];
   }
   // type-pair table (Lorentz-Berthelot)
   std::vector<float4> tab(kMaxTypes * kMaxTypes);
@@ -358,6 +380,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   mop_status s;
   if ((s = upload(h, h->mass, d->mass, Q)) || (s = upload(h, h->Kspr, Kspr.data(), Q)) ||
       (s = upload(h, h->cL, cL.data(), Q)) || (s = upload(h, h->qs, qs.data(), Q)) ||
+      (s = upload(h, h->c_df, c_df.data(), Q)) || (s = upload(h, h->Kf, Kf.data(), Q)) ||
       (s = upload(h, h->type, d->type, Q)) || (s = upload(h, h->mol, d->mol_id, Q)) ||
       (s = upload(h, h->loc, d->mol_local, Q)) || (s = upload(h, h->inc_off, off.data(), Q + 1)) ||
       (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
@@ -369,6 +392,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.Kspr = h->Kspr.p;
   sc.cL = h->cL.p;
   sc.qs = h->qs.p;
+  sc.c_df = h->c_df.p;
+  sc.Kf = h->Kf.p;
   sc.type = h->type.p;
   sc.mol = h->mol.p;
   sc.loc = h->loc.p;
@@ -398,7 +423,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
 mop_status mop_destroy(mop_handle* h) {
   if (!h) return MOP_OK;
   cudaSetDevice(h->device);
-  h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release();
+  h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release(); h->c_df.release(); h->Kf.release();
   h->type.release(); h->mol.release(); h->loc.release(); h->inc_off.release();
   h->inc.release(); h->incp.release(); h->tab.release(); h->tab64.release();
   for (auto& e : h->ev)
@@ -410,7 +435,7 @@ mop_status mop_destroy(mop_handle* h) {
     P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();
     P.ts.release(); P.center.release(); P.hext.release(); P.molr.release(); P.emax.release();
     P.cbin.release(); P.bincnt.release(); P.binstart.release(); P.bincur.release(); P.binlist.release();
-    P.cwrap.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
+    P.cwrap.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
     P.eta32.release(); P.etamax.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
@@ -519,12 +544,13 @@ mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* 
   CK(h, cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int N = P.N, Qpad = P.n_clu * kCL;
-  const double* f;
-  int rows;
+  const void* f;
+  int rows, fmt;
+  const bool mixed = h->precision == MOP_PREC_MIXED;
   switch (field) {
-    case MOP_FIELD_FORCE: f = P.F.p; rows = N == 1 ? 1 : N - 1; break;
-    case MOP_FIELD_ETA: f = P.eta.p; rows = N - 1; break;
-    case MOP_FIELD_HETA: f = P.Heta.p; rows = N - 1; break;
+    case MOP_FIELD_FORCE: f = P.F.p; rows = N == 1 ? 1 : N - 1; fmt = mixed ? 1 : 0; break;
+    case MOP_FIELD_ETA: f = mixed ? (const void*)P.eta32.p : P.eta.p; rows = N - 1; fmt = mixed ? 2 : 0; break;
+    case MOP_FIELD_HETA: f = P.Heta.p; rows = N - 1; fmt = mixed ? 2 : 0; break;
     default: return fail(h, MOP_ERR_ARG, "unknown field %d", field);
   }
   const size_t n = 3 * (size_t)N * h->sc.Q;
@@ -533,7 +559,7 @@ mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* 
     CK(h, h->scratch.ensure(n));
     dst = h->scratch.p;
   }
-  k_gather_field<<<nblk((long long)N * h->sc.Q, 256), 256, 0, st>>>(f, P.slot.p, h->sc.Q, Qpad, N, rows, dst);
+  k_gather_field<<<nblk((long long)N * h->sc.Q, 256), 256, 0, st>>>(f, fmt, P.slot.p, h->sc.Q, Qpad, N, rows, dst);
   CK(h, cudaGetLastError());
   if (!(flags & MOP_DEVPTR)) {
     CK(h, cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -35,6 +35,8 @@ struct SysConsts {
   const double* Kspr;   // m nu / (2 dt)
   const double* cL;     // dt / (m nu)
   const double* qs;     // q sqrt(f)
+  const float2* c_df;   // c_i as a double-float (hi, lo) pair
+  const float* Kf;      // K_i rounded to FP32
   const int* type;
   const int* mol;
   const int* loc;
@@ -66,6 +68,8 @@ struct PathDev {
   const int4* ent;          // x = cj | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
   const double4_32a* ent64;
   const unsigned long long* emask;
+  // FP64 mode: [N][Qpad][3] doubles.  Mixed mode views of the same buffers: Fnb and F as
+  // double-float (hi, lo) x 3 (float2 [N][Qpad][3]), Hnb and Heta as float4 [N][Qpad].
   double* Fnb;
   double* F;
   double* eta;
@@ -118,6 +122,52 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float a) {
   const float err = (hi - (s - bp)) + (a - bp);
   hi = s;
   lo += err;
+}
+
+// Double-float (hi + lo, |lo| <= ulp(hi)/2) helpers: FP64-class accuracy on the FP32 pipes.
+// B300 issues FP64 at a small fraction of the FP32 rate, so the mixed-precision path keeps
+// its extended-precision steps in this form (error-free transformations: Knuth's TwoSum,
+// Dekker's FastTwoSum, and TwoProd through a fused multiply-add).
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = a + b;
+  const float bp = s - a;
+  return {s, (a - (s - bp)) + (b - bp)};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ df df_add_f(df x, float b) {
+  df s = two_sum(x.hi, b);
+  return fast_two_sum(s.hi, s.lo + x.lo);
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+__host__ __device__ __forceinline__ df df_from_double(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+// warp sum of a double-float value (fixed butterfly order)
+__device__ __forceinline__ df df_warp_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, w);
+  }
+  return v;
 }
 
 __device__ __forceinline__ double aligned_coord(double v, double ref, double L, double invL) {

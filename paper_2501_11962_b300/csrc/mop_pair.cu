@@ -255,8 +255,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       if (MODE >= 1) S.e[lane] = fe;
       __syncwarp();
       if (b + 1 < nb) fetch(b + 1);
-      const int kmax = min(4, nc - 4 * b);
-      for (int q = 0; q < kmax; ++q) {
+      // entries past the end of the chunk were staged with no half bits, so all 4 are safe
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
         const int e = 4 * b + q;
         const int fl = S.ent[e].x;
         R rcA = k.rc2, rcB = k.rc2;
@@ -295,25 +296,57 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
     if (ENERGY) eacc.fold();
   }
   const bool valid = __ldg(&P.perm[si]) >= 0;
-  double out[3];
+  if constexpr (sizeof(R) == 4) {
+    // mixed mode: sum the four lanes of each i-atom as double-floats, no FP64 instructions
+    df v[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    double v = acc.get(c);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    out[c] = valid ? v : 0.0;
-  }
-  if (jj == 0) {
-    double* dst = (MODE == 0 ? P.Fnb : P.Hnb) + 3 * (bo + si);
-    const double scale = (MODE == 2) ? -0.5 / (double)eps : 1.0;
-    dst[0] = out[0] * scale;
-    dst[1] = out[1] * scale;
-    dst[2] = out[2] * scale;
-  }
-  if (ENERGY) {
-    double ev = valid ? eacc.get() : 0.0;
-    ev = warp_sum(ev);
-    if (lane == 0) P.e_pair[ci] = 0.5 * ev;   // full list: every pair seen twice
+    for (int c = 0; c < 3; ++c) {
+      v[c] = df{acc.h[c], acc.l[c]};
+#pragma unroll
+      for (int o = 8; o <= 16; o <<= 1) {
+        const df w{__shfl_xor_sync(0xffffffffu, v[c].hi, o), __shfl_xor_sync(0xffffffffu, v[c].lo, o)};
+        v[c] = df_add(v[c], w);
+      }
+      if (!valid) v[c] = df{0.f, 0.f};
+    }
+    if (jj == 0) {
+      if (MODE == 0) {
+        float2* dst = reinterpret_cast<float2*>(P.Fnb) + 3 * (bo + si);
+        dst[0] = make_float2(v[0].hi, v[0].lo);
+        dst[1] = make_float2(v[1].hi, v[1].lo);
+        dst[2] = make_float2(v[2].hi, v[2].lo);
+      } else {
+        const float scale = (MODE == 2) ? -0.5f / (float)eps : 1.0f;
+        reinterpret_cast<float4*>(P.Hnb)[bo + si] =
+            make_float4((v[0].hi + v[0].lo) * scale, (v[1].hi + v[1].lo) * scale, (v[2].hi + v[2].lo) * scale, 0.f);
+      }
+    }
+    if (ENERGY) {
+      df ev = valid ? df{eacc.h, eacc.l} : df{0.f, 0.f};
+      ev = df_warp_sum(ev);
+      if (lane == 0) P.e_pair[ci] = 0.5 * ((double)ev.hi + (double)ev.lo);   // full list: pairs seen twice
+    }
+  } else {
+    double out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = acc.get(c);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      out[c] = valid ? v : 0.0;
+    }
+    if (jj == 0) {
+      double* dst = (MODE == 0 ? P.Fnb : P.Hnb) + 3 * (bo + si);
+      const double scale = (MODE == 2) ? -0.5 / (double)eps : 1.0;
+      dst[0] = out[0] * scale;
+      dst[1] = out[1] * scale;
+      dst[2] = out[2] * scale;
+    }
+    if (ENERGY) {
+      double ev = valid ? eacc.get() : 0.0;
+      ev = warp_sum(ev);
+      if (lane == 0) P.e_pair[ci] = 0.5 * ev;   // full list: every pair seen twice
+    }
   }
 }
 

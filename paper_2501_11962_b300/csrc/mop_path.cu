@@ -131,8 +131,8 @@ __device__ __forceinline__ void eta_of(const PathDev& P, int n, int atom, R* e) 
 
 // Bonded force on atom a at bead n, accumulated in FP64; U (if non-NULL) gets the energy of
 // the terms for which a has role 0 (so that every term is counted once).
-template <class R>
-__device__ void bonded_force(const SysConsts& sc, const PathDev& P, int a, int n, double* F, double* U) {
+template <class R, class A>
+__device__ void bonded_force(const SysConsts& sc, const PathDev& P, int a, int n, A* F, double* U) {
   for (int t = sc.inc_off[a]; t < sc.inc_off[a + 1]; ++t) {
     const int4 in = sc.inc[t];
     const double2 pr = sc.incp[t];
@@ -149,16 +149,16 @@ __device__ void bonded_force(const SysConsts& sc, const PathDev& P, int a, int n
       mi_diff<R>(sc, P, n, in.w, in.z, q);
       angle_force<R, R>(p, q, (R)pr.x, (R)pr.y, role, f, U && role == 0 ? &u : nullptr);
     }
-    F[0] += (double)f[0];
-    F[1] += (double)f[1];
-    F[2] += (double)f[2];
+    F[0] += (A)f[0];
+    F[1] += (A)f[1];
+    F[2] += (A)f[2];
     if (U && role == 0) *U += (double)u;
   }
 }
 
 // Bonded H eta on atom a at bead n: adjoint (dual numbers) or central difference with eps.
-template <class R, bool FD>
-__device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, double eps, double* H) {
+template <class R, bool FD, class A>
+__device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, double eps, A* H) {
   for (int t = sc.inc_off[a]; t < sc.inc_off[a + 1]; ++t) {
     const int4 in = sc.inc[t];
     const double2 pr = sc.incp[t];
@@ -183,7 +183,7 @@ __device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, 
       }
       if (kind == 0) bond_force<Dl<R>, R>(d1, (R)pr.x, (R)pr.y, role, f, nullptr);
       else angle_force<Dl<R>, R>(d1, d2, (R)pr.x, (R)pr.y, role, f, nullptr);
-      for (int c = 0; c < 3; ++c) H[c] -= (double)f[c].d;   // H eta = -d/dt F(x + t eta)
+      for (int c = 0; c < 3; ++c) H[c] -= (A)f[c].d;   // H eta = -d/dt F(x + t eta)
     } else {
       R fp[3], fm[3], a1[3], a2[3];
       const R e = (R)eps;
@@ -197,7 +197,12 @@ __device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, 
         if (kind == 0) bond_force<R, R>(a1, (R)pr.x, (R)pr.y, role, f, nullptr);
         else angle_force<R, R>(a1, a2, (R)pr.x, (R)pr.y, role, f, nullptr);
       }
-      for (int c = 0; c < 3; ++c) H[c] -= ((double)fp[c] - (double)fm[c]) / (2.0 * eps);
+      if (sizeof(A) == 4) {
+        const R inv2e = R(0.5) / (R)eps;
+        for (int c = 0; c < 3; ++c) H[c] -= (A)((fp[c] - fm[c]) * inv2e);
+      } else {
+        for (int c = 0; c < 3; ++c) H[c] -= (A)(((double)fp[c] - (double)fm[c]) / (2.0 * eps));
+      }
     }
   }
 }
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* _
       F[0] = P.Fnb[3 * k];
       F[1] = P.Fnb[3 * k + 1];
       F[2] = P.Fnb[3 * k + 2];
-      bonded_force<R>(sc, P, a, n, F, n == 0 ? &eb : nullptr);
+      bonded_force<R, double>(sc, P, a, n, F, n == 0 ? &eb : nullptr);
       if (P.N > 1) {
         const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
         const double c = sc.cL[a];
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
           // the pair kernel used the same eps rounded to the pair precision
           eps = (double)(R)eps;
         }
-        bonded_hvp<R, FD>(sc, P, a, n, eps, H);
+        bonded_hvp<R, FD, double>(sc, P, a, n, eps, H);
         double e2 = 0.0;
         for (int c = 0; c < 3; ++c) {
           const double e = P.eta[3 * k + c];
@@ -302,6 +307,128 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
   }
   const double tot = block_sum<kRedBlock>(es, sh);
   if (threadIdx.x == 0) e_spring[(size_t)p * stride + blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------------------------------
+// mixed precision (MOP_PREC_MIXED): FP32 arithmetic with double-float where cancellation needs
+// more than FP32.  F^n = F_nonbonded (double-float from the pair kernel) + F_bonded;
+// eta^n = (R^{n+1} - R^n) - c F^n in double-float (the difference of nearly equal terms when
+// the path is close to a solution of Eq. 1), stored rounded to FP32; bonded energy of bead 1.
+__global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+                                                        double* e_bond, int stride) {
+  __shared__ double sh[32];
+  const int p = blockIdx.y;
+  if (p >= n_paths) return;
+  const PathDev& P = paths[p];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)P.n_force * P.Qpad;
+  double eb = 0.0;
+  int bead = -1;            // bead of this thread, for the per-warp |eta| maximum (FD mode)
+  unsigned nbits = 0u;
+  if (t < total) {
+    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+    bead = n;
+    const size_t k = (size_t)n * P.Qpad + s;
+    const int a = P.perm[s];
+    const float2* Fnb = reinterpret_cast<const float2*>(P.Fnb) + 3 * k;
+    float2* Fo = reinterpret_cast<float2*>(P.F) + 3 * k;
+    df F[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    float4 ef = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a >= 0) {
+      float Fb[3] = {0.f, 0.f, 0.f};
+      bonded_force<float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
+      for (int c = 0; c < 3; ++c) F[c] = df_add_f(df{Fnb[c].x, Fnb[c].y}, Fb[c]);
+      if (P.N > 1) {
+        const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
+        const float2 cc = sc.c_df[a];
+        float e[3];
+        for (int c = 0; c < 3; ++c) {
+          const df d = two_sum(P.x32[b1 + c], -P.x32[b0 + c]);   // exact R^{n+1} - R^n
+          const df cf = df_mul(df{cc.x, cc.y}, F[c]);
+          const df et = df_add(d, df_neg(cf));
+          e[c] = et.hi + et.lo;
+        }
+        ef = make_float4(e[0], e[1], e[2], 0.f);
+        if (sc.hvp_mode == 1) nbits = __float_as_uint(sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) * 1.000001f);
+      }
+    }
+    for (int c = 0; c < 3; ++c) Fo[c] = make_float2(F[c].hi, F[c].lo);
+    if (P.N > 1) P.eta32[k] = ef;
+  }
+  if (sc.hvp_mode == 1) {
+    // one atomic per (warp, bead): lanes of the same bead take their maximum first
+    const unsigned same = __match_any_sync(0xffffffffu, bead);
+    const unsigned mx = __reduce_max_sync(same, nbits);
+    if (bead >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicMax(&P.etamax[bead], mx);
+  }
+  // only blocks that hold bead-1 slots have bonded energy to sum
+  if ((long long)blockIdx.x * blockDim.x < P.Qpad) {
+    const double tot = block_sum<kRedBlock>(eb, sh);
+    if (threadIdx.x == 0) e_bond[(size_t)p * stride + blockIdx.x] = tot;
+  } else if (threadIdx.x == 0) {
+    e_bond[(size_t)p * stride + blockIdx.x] = 0.0;
+  }
+}
+
+// H eta (pair part from the HVP kernel + bonded part), the gradient of Eqs. 5-7 in FP32 from the
+// FP32-rounded eta, spring energy summed as double-floats per warp and in FP64 per block.
+template <bool FD>
+__global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+                                                        double* e_spring, int stride) {
+  __shared__ double shw[kRedBlock / 32];
+  const int p = blockIdx.y;
+  if (p >= n_paths) return;
+  const PathDev& P = paths[p];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)P.N * P.Qpad;
+  float es = 0.f;
+  if (t < total) {
+    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+    const int a = P.perm[s];
+    const size_t k = (size_t)n * P.Qpad + s;
+    if (a >= 0) {
+      const float K = sc.Kf[a];
+      float g[3] = {0.f, 0.f, 0.f};
+      if (n == 0) {
+        const float2* F1 = reinterpret_cast<const float2*>(P.F) + 3 * (size_t)s;
+        for (int c = 0; c < 3; ++c) g[c] = -(F1[c].x + F1[c].y);
+      }
+      if (n > 0) {
+        const float4 ep = P.eta32[k - P.Qpad];
+        g[0] += K * ep.x;
+        g[1] += K * ep.y;
+        g[2] += K * ep.z;
+      }
+      if (n < P.N - 1) {
+        const float4 hn = reinterpret_cast<const float4*>(P.Hnb)[k];
+        float H[3] = {hn.x, hn.y, hn.z};
+        double eps = 0.0;
+        if (FD) {
+          const float mx = __uint_as_float(P.etamax[n]);
+          eps = (double)(float)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
+        }
+        bonded_hvp<float, FD, float>(sc, P, a, n, eps, H);
+        reinterpret_cast<float4*>(P.Heta)[k] = make_float4(H[0], H[1], H[2], 0.f);
+        const float4 e = P.eta32[k];
+        g[0] += fmaf(-K, e.x, 0.5f * H[0]);
+        g[1] += fmaf(-K, e.y, 0.5f * H[1]);
+        g[2] += fmaf(-K, e.z, 0.5f * H[2]);
+        es = 0.5f * K * (e.x * e.x + e.y * e.y + e.z * e.z);
+      }
+      double* G = P.grad + 3 * ((size_t)n * P.Q + a);
+      G[0] = (double)g[0];
+      G[1] = (double)g[1];
+      G[2] = (double)g[2];
+    }
+  }
+  const df w = df_warp_sum(df{es, 0.f});
+  if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = (double)w.hi + (double)w.lo;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < kRedBlock / 32; ++k) tot += shw[k];
+    e_spring[(size_t)p * stride + blockIdx.x] = tot;
+  }
 }
 
 // centroid of a group at bead n, each atom unwrapped relative to the group's first atom
@@ -477,7 +604,7 @@ cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
                       double* e_bond, int stride) {
   dim3 grid(nblk(max_threads, kRedBlock), n_paths);
   if (sc.precision == 1) k_e1<double><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
-  else k_e1<float><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
+  else k_e1_mixed<<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
   ++*L.counter;
   return cudaGetLastError();
 }
@@ -490,8 +617,8 @@ cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
     if (fd) k_e2<double, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
     else k_e2<double, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
   } else {
-    if (fd) k_e2<float, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
-    else k_e2<float, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+    if (fd) k_e2_mixed<true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+    else k_e2_mixed<false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
   }
   ++*L.counter;
   return cudaGetLastError();

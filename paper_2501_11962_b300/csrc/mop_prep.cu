@@ -199,8 +199,9 @@ __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64
   if (b == 0) ts[s] = sc.type[a];
 }
 
-__global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const double* center, int nb0, int nb1,
-                               int nb2, double bw0, double bw1, double bw2, double* cwrap, int* cbin, int* bincnt) {
+__global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const double* center, const float* hext,
+                               int nb0, int nb1, int nb2, double bw0, double bw1, double bw2, double* cwrap,
+                               float4* cbox, int* cbin, int* bincnt) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= max_clu || c >= meta[0]) return;
   int bidx[3];
@@ -214,6 +215,8 @@ __global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const
     bidx[d] = (int)fmin(fmax(w / bw[d], 0.0), (double)(nb[d] - 1));
   }
   const int bin = (bidx[0] * nb1 + bidx[1]) * nb2 + bidx[2];
+  cbox[2 * c] = make_float4((float)cwrap[3 * c], (float)cwrap[3 * c + 1], (float)cwrap[3 * c + 2], 0.f);
+  cbox[2 * c + 1] = make_float4(hext[3 * c], hext[3 * c + 1], hext[3 * c + 2], 0.f);
   cbin[c] = bin;
   atomicAdd(&bincnt[bin], 1);
 }
@@ -316,7 +319,8 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
                                                    const double* cwrap, const float* hext, const unsigned* emax,
                                                    const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
                                                    double bw2, const int* binstart, const int* binlist,
-                                                   const int* perm, const int* molr, const float4* abox, int cap,
+                                                   const int* perm, const int* molr, const float4* abox,
+                                                   const float4* cbox, int cap,
                                                    int* lcnt, int4* ent, double4_32a* ent64,
                                                    unsigned long long* emask, int* meta) {
   __shared__ float4 ibox[4][kCL];
@@ -342,6 +346,10 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
   }
   const int mi0 = molr[2 * ci], mi1 = molr[2 * ci + 1];
   const float rcf = (float)sc.rc + 1e-5f;
+  const float rcs = (float)sc.rc + 1e-4f, rcs2 = rcs * rcs;
+  const float wif[3] = {(float)wi[0], (float)wi[1], (float)wi[2]};
+  const float eif[3] = {(float)ei[0], (float)ei[1], (float)ei[2]};
+  const float Lf[3] = {sc.Lf[0], sc.Lf[1], sc.Lf[2]};
   const size_t base = (size_t)ci * cap;
   int count = 0;
   for (int dx = -R[0]; dx <= R[0]; ++dx) {
@@ -365,13 +373,14 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
           double D[3] = {0.0, 0.0, 0.0};
           if (t < nbin) {
             cj = binlist[s0 + t];
-            double g2 = 0.0;
-            for (int d = 0; d < 3; ++d) {
-              D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
-              const double gap = fmax(0.0, fabs(D[d]) - ei[d] - (double)hext[3 * cj + d]);
-              g2 += gap * gap;
-            }
-            if (g2 < sc.rc2) {
+            // FP32 pre-test of the union boxes (slack covers the FP32 rounding of the centres)
+            const float4 cw = cbox[2 * cj], ce = cbox[2 * cj + 1];
+            const float gx = fmaxf(0.f, fabsf(wif[0] - (cw.x + kk[0] * Lf[0])) - eif[0] - ce.x);
+            const float gy = fmaxf(0.f, fabsf(wif[1] - (cw.y + kk[1] * Lf[1])) - eif[1] - ce.y);
+            const float gz = fmaxf(0.f, fabsf(wif[2] - (cw.z + kk[2] * Lf[2])) - eif[2] - ce.z);
+            const float g2 = gx * gx + gy * gy + gz * gz;
+            if (g2 < rcs2) {
+              for (int d = 0; d < 3; ++d) D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
               const float Dx = (float)D[0], Dy = (float)D[1], Dz = (float)D[2];
               for (int j = 0; j < kCL && hm != 3u; ++j) {
                 const float4 bj = abox[cj * kCL + j];
@@ -470,6 +479,7 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_CK(P.emax.ensure(3));
   MOP_CK(P.cbin.ensure(max_clu));
   MOP_CK(P.cwrap.ensure(3 * (size_t)max_clu));
+  MOP_CK(P.cbox.ensure(2 * (size_t)max_clu));
   MOP_CK(P.bincnt.ensure(nbins));
   MOP_CK(P.binstart.ensure(nbins + 1));
   MOP_CK(P.bincur.ensure(nbins));
@@ -508,8 +518,9 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
     k_local_coords<false><<<nblk((long long)N * max_slots, bs), bs, 0, st>>>(
         sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, P.xq.p, nullptr, P.ts.p);
   MOP_KL();
-  k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, g.nb[0], g.nb[1], g.nb[2],
-                                                   g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cbin.p, P.bincnt.p);
+  k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, P.hext.p, g.nb[0], g.nb[1],
+                                                   g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cbox.p,
+                                                   P.cbin.p, P.bincnt.p);
   MOP_KL();
   k_scan<<<1, 1024, 0, st>>>(P.bincnt.p, nbins, P.binstart.p, P.bincur.p, nullptr);
   MOP_KL();
@@ -532,13 +543,13 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
     if (f64)
       k_pair_list<true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
                                                 g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
-                                                P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cap, P.lcnt.p, P.ent.p,
-                                                P.ent64.p, P.emask.p, P.meta.p);
+                                                P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
+                                                P.ent.p, P.ent64.p, P.emask.p, P.meta.p);
     else
       k_pair_list<false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
                                                  g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
-                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cap, P.lcnt.p, P.ent.p,
-                                                 nullptr, P.emask.p, P.meta.p);
+                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
+                                                 P.ent.p, nullptr, P.emask.p, P.meta.p);
     MOP_KL();
     int meta[4];
     MOP_CK(cudaMemcpyAsync(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost, st));
