@@ -32,6 +32,7 @@ struct mop_handle {
   DevBuf<int> type, mol, loc, inc_off;
   DevBuf<int4> inc;
   DevBuf<double2> incp;
+  DevBuf<float2> incpf;
   DevBuf<float4> tab;
   DevBuf<double4_32a> tab64;
   // paths
@@ -162,8 +163,9 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.n_clu = P.n_clu;
     D.unit_off = units;
     D.unit_off_h = units_h;
-    units += (long long)n_force * P.n_clu;
-    units_h += (long long)n_hvp * P.n_clu;
+    const int bpu = pair_beads_per_unit(h->precision);
+    units += (long long)((n_force + bpu - 1) / bpu) * P.n_clu;
+    units_h += (long long)((n_hvp + bpu - 1) / bpu) * P.n_clu;
     max_e1 = std::max(max_e1, (long long)n_force * Qpad);
     max_e2 = std::max(max_e2, (long long)N * Qpad);
     D.x32 = h->precision == MOP_PREC_FP64 ? nullptr : P.x32.p;
@@ -360,6 +362,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   for (int i = 0; i < Q; ++i) off[i + 1] = off[i] + cnt[i];
   std::vector<int4> inc(std::max(off[Q], 1));
   std::vector<double2> incp(std::max(off[Q], 1));
+  std::vector<float2> incpf(std::max(off[Q], 1));
   std::vector<int> cur(off.begin(), off.end() - 1);
   for (int b = 0; b < d->n_bonds; ++b) {
     const int i = d->bond_ij[2 * b], j = d->bond_ij[2 * b + 1];
@@ -377,6 +380,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
       incp[cur[a]++] = make_double2(d->angle_th0[t], d->angle_k[t]);
     }
   }
+  for (size_t k = 0; k < incp.size(); ++k) incpf[k] = make_float2((float)incp[k].x, (float)incp[k].y);
   mop_status s;
   if ((s = upload(h, h->mass, d->mass, Q)) || (s = upload(h, h->Kspr, Kspr.data(), Q)) ||
       (s = upload(h, h->cL, cL.data(), Q)) || (s = upload(h, h->qs, qs.data(), Q)) ||
@@ -384,6 +388,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
       (s = upload(h, h->type, d->type, Q)) || (s = upload(h, h->mol, d->mol_id, Q)) ||
       (s = upload(h, h->loc, d->mol_local, Q)) || (s = upload(h, h->inc_off, off.data(), Q + 1)) ||
       (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
+      (s = upload(h, h->incpf, incpf.data(), incpf.size())) ||
       (s = upload(h, h->tab, tab.data(), tab.size())) || (s = upload(h, h->tab64, tab64.data(), tab64.size()))) {
     mop_destroy(h);
     return s;
@@ -400,6 +405,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.inc_off = h->inc_off.p;
   sc.inc = h->inc.p;
   sc.incp = h->incp.p;
+  sc.incpf = h->incpf.p;
   sc.tab = h->tab.p;
   sc.tab64 = h->tab64.p;
 
@@ -425,7 +431,7 @@ mop_status mop_destroy(mop_handle* h) {
   cudaSetDevice(h->device);
   h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release(); h->c_df.release(); h->Kf.release();
   h->type.release(); h->mol.release(); h->loc.release(); h->inc_off.release();
-  h->inc.release(); h->incp.release(); h->tab.release(); h->tab64.release();
+  h->inc.release(); h->incp.release(); h->incpf.release(); h->tab.release(); h->tab64.release();
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   h->d_one.release(); h->counts.release();

@@ -95,7 +95,9 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                       std::string* err);
 
 // --- mop_pair.cu: pair kernels over every unit of every path -------------------------------
-// mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP
+// mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP.  A unit is one i-cluster for
+// pair_beads_per_unit(precision) consecutive beads.
+int pair_beads_per_unit(int precision);
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
                         int mode, int num_sms, Launch L);
 

@@ -44,6 +44,7 @@ struct SysConsts {
   const int* inc_off;
   const int4* inc;      // x = kind (0 bond, 1 angle) | role << 2, y,z,w = atoms (w = -1 for bonds)
   const double2* incp;  // (r0 or theta0, k)
+  const float2* incpf;  // the same in FP32 (mixed precision)
   // type-pair tables: (12 c12, 6 c6, phi'_LJ(rc) if shifted else 0, phi_LJ(rc))
   const float4* tab;
   const double4_32a* tab64;
@@ -168,6 +169,26 @@ __device__ __forceinline__ df df_warp_sum(df v) {
     v = df_add(v, w);
   }
   return v;
+}
+
+// float -> double widening on the integer pipes (exact for normal numbers, zero, inf and NaN;
+// FP32 subnormals are flushed to zero, as -ftz does).  B300 runs F2F conversions on its slow
+// FP64 path, which made them the bottleneck of the elementwise kernels.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (ex == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else if (ex == 0xffu) {
+    hi = sign | 0x7ff00000u | (man >> 3);
+    lo = man << 29;
+  } else {
+    hi = sign | ((ex + 896u) << 20) | (man >> 3);
+    lo = man << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ double aligned_coord(double v, double ref, double L, double invL) {

@@ -103,14 +103,13 @@ __device__ __forceinline__ R pair_g(R rinv, R rinv2, R rinv6, const V4& p, R qq,
   return rinv6 * fma(p.x, rinv6, -p.y) * rinv2 + qq * fma(rinv, rinv2, -k2rf) + sh * rinv;
 }
 
-// One pair of the unit: i-atom of this lane against j-atom xj (type row p), cutoff test against
-// rc2e (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or
-// F(+) - F(-) (MODE 2) into acc and the pair energy into eacc (ENERGY).
+// One pair for one bead: i-atom of this lane against j-atom xj, type-pair row p, qq = f q_i q_j,
+// sh = phi'(rc) of the pair; cutoff test against rc2e (negative for an excluded pair).
+// Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-) (MODE 2) into a[3] and the pair energy
+// into e (ENERGY).
 template <class R, int MODE, bool ENERGY, class V4>
-__device__ __forceinline__ void pair_one(const Cst<R>& k, const V4& xi, R xs, R ys, R zs, const V4& xj, const V4& p,
-                                         R rc2e, const R* ei, const R* ej, R eps, Acc3<R>& acc, Acc1<R>& eacc) {
-  const R qq = xi.w * xj.w;
-  const R sh = fma(qq, k.drf, p.z);   // phi'(rc) of this pair (0 for the potential-shift modifier)
+__device__ __forceinline__ void pair_one(const Cst<R>& k, R xs, R ys, R zs, const V4& xj, const V4& p, R qq, R sh,
+                                         R rc2e, const R* ei, const R* ej, R eps, R* a, R& e) {
   const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
   if (MODE == 0) {
     const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
@@ -120,16 +119,16 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const V4& xi, R xs, R 
     const R rinv6 = rinv2 * rinv2 * rinv2;
     R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
     g = in ? g : R(0);
-    acc.a[0] = fma(g, dx, acc.a[0]);
-    acc.a[1] = fma(g, dy, acc.a[1]);
-    acc.a[2] = fma(g, dz, acc.a[2]);
+    a[0] = fma(g, dx, a[0]);
+    a[1] = fma(g, dy, a[1]);
+    a[2] = fma(g, dz, a[2]);
     if (ENERGY) {
       // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
       const R r = r2 * rinv;
       const R elj = rinv6 * fma(p.x * R(1.0 / 12.0), rinv6, -p.y * R(1.0 / 6.0));
       const R erf = qq * (rinv + fma(k.krf, r2, -k.crf));
       const R E = elj + erf - p.w - (r - k.rc) * sh;
-      eacc.a += in ? E : R(0);
+      e += in ? E : R(0);
     }
   } else if (MODE == 1) {
     const R ux = ei[0] - ej[0], uy = ei[1] - ej[1], uz = ei[2] - ej[2];
@@ -139,14 +138,14 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const V4& xi, R xs, R 
     const R rinv2 = rinv * rinv;
     const R rinv3 = rinv * rinv2;
     const R rinv6 = rinv2 * rinv2 * rinv2;
-    R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+    const R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
     const R b = rinv6 * fma(R(14) * p.x, rinv6, R(-8) * p.y) * rinv2 * rinv2 + fma(R(3) * qq, rinv2, sh) * rinv3;
     const R s = fma(dx, ux, fma(dy, uy, dz * uz));
     const R t = in ? b * s : R(0);
-    g = in ? g : R(0);
-    acc.a[0] += fma(t, dx, -g * ux);
-    acc.a[1] += fma(t, dy, -g * uy);
-    acc.a[2] += fma(t, dz, -g * uz);
+    const R ng = in ? -g : R(0);
+    a[0] = fma(ng, ux, fma(t, dx, a[0]));
+    a[1] = fma(ng, uy, fma(t, dy, a[1]));
+    a[2] = fma(ng, uz, fma(t, dz, a[2]));
   } else {
     const R ux = eps * (ei[0] - ej[0]), uy = eps * (ei[1] - ej[1]), uz = eps * (ei[2] - ej[2]);
 #pragma unroll
@@ -159,23 +158,25 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const V4& xi, R xs, R 
       const R rinv6 = rinv2 * rinv2 * rinv2;
       R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
       g = in ? (sgn ? -g : g) : R(0);
-      acc.a[0] = fma(g, px, acc.a[0]);
-      acc.a[1] = fma(g, py, acc.a[1]);
-      acc.a[2] = fma(g, pz, acc.a[2]);
+      a[0] = fma(g, px, a[0]);
+      a[1] = fma(g, py, a[1]);
+      a[2] = fma(g, pz, a[2]);
     }
   }
 }
 
-// Warp-private staging area: one chunk of up to 32 list entries, and the 32 j-atoms (4 entries
-// x 8 atoms) of the block being processed.
-template <class R> struct Stage {
+// Warp-private staging area: one chunk of up to 32 list entries, the 32 j-atoms (4 entries x 8
+// atoms) of the block being processed for each of the B beads, and the double-float partial
+// sums (hi, lo) of every lane.
+template <class R, int B> struct Stage {
   using V4 = typename Tr<R>::V4;
-  V4 x[32];                  // j coordinates + charge
-  V4 e[32];                  // j eta (HVP / FD)
+  V4 x[B][32];               // j coordinates + charge
+  V4 e[B][32];               // j eta (HVP / FD)
   V4 d[32];                  // Delta of each staged entry
   int4 ent[32];              // entries of the chunk
   unsigned long long m[32];  // exclusion masks of the chunk
   int t[32];                 // j types
+  R hl[B][6][32];            // folded sums: hi x 3, lo x 3 (FP32 mode)
 };
 
 template <class R, class V4>
@@ -187,25 +188,61 @@ template <> __device__ __forceinline__ double4_32a load_eta4<double, double4_32a
   return make_double4_32a(P.eta[3 * k], P.eta[3 * k + 1], P.eta[3 * k + 2], 0.0);
 }
 
-template <class R, int MODE, bool ENERGY>
+// fold the FP32 chunk sums a[b][3] of this lane into its (hi, lo) pairs in shared memory
+template <class R, int B>
+__device__ __forceinline__ void fold_into(Stage<R, B>& S, R (&a)[B][3], int lane) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float h = S.hl[b][c][lane], l = S.hl[b][3 + c][lane];
+        two_sum_add(h, l, a[b][c]);
+        S.hl[b][c][lane] = h;
+        S.hl[b][3 + c][lane] = l;
+        a[b][c] = 0.f;
+      }
+  }
+}
+
+// One work unit: the i-cluster ci against its whole list, for the B beads n0 .. n0 + B - 1
+// (bead n0 + 1 of a unit past the last bead repeats bead n0 and is not written).
+template <class R, int MODE, bool ENERGY, int B>
 __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab,
-                                          Stage<R>& S, const PathDev& P, int n, int ci, int lane) {
+                                          Stage<R, B>& S, const PathDev& P, int n0, int n_pass, int ci, int lane) {
   using V4 = typename Tr<R>::V4;
   const Cst<R> k(sc);
   const int i = lane & 7, jj = lane >> 3;
-  const size_t bo = (size_t)n * P.Qpad;
   const int si = ci * kCL + i;
-  const V4* __restrict__ xqb = Tr<R>::xq(P) + bo;
-  const V4 xi = xqb[si];
-  const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * sc.n_types;
-  R ei[3] = {R(0), R(0), R(0)};
-  R eps = R(0);
-  if (MODE >= 1) Tr<R>::eta(P, bo + si, ei);
-  if (MODE == 2) {
-    const float mx = __uint_as_float(P.etamax[n]);
-    eps = (R)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
+  int nb[B];
+  const V4* __restrict__ xqb[B];
+  V4 xi[B];
+  R ei[B][3], eps[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    nb[b] = min(n0 + b, n_pass - 1);
+    xqb[b] = Tr<R>::xq(P) + (size_t)nb[b] * P.Qpad;
+    xi[b] = xqb[b][si];
+    ei[b][0] = ei[b][1] = ei[b][2] = R(0);
+    eps[b] = R(0);
+    if (MODE >= 1) Tr<R>::eta(P, (size_t)nb[b] * P.Qpad + si, ei[b]);
+    if (MODE == 2) {
+      const float mx = __uint_as_float(P.etamax[nb[b]]);
+      eps[b] = (R)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
+    }
   }
-  Acc3<R> acc;
+  const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * sc.n_types;
+  const R qi = xi[0].w;
+  R a[B][3];
+  Acc3<R> accd;   // FP64 mode accumulates directly (B == 1)
+#pragma unroll
+  for (int b = 0; b < B; ++b) a[b][0] = a[b][1] = a[b][2] = R(0);
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) S.hl[b][c][lane] = 0.f;
+  }
   Acc1<R> eacc;
   const int cnt = __ldg(&P.lcnt[ci]);
   const size_t eb = (size_t)ci * P.cap;
@@ -233,32 +270,36 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       S.d[lane] = dv;
     }
     __syncwarp();
-    // fetch block 0 of the chunk into registers
-    V4 fx, fe;
+    V4 fx[B], fe[B];
     int ft = 0;
-    auto fetch = [&](int b) {
-      const int e = 4 * b + sk;
+    auto fetch = [&](int blk) {
+      const int e = 4 * blk + sk;
       if (e < nc) {
-        const int cj = S.ent[e].x & 0x1fffffff;
-        const int sj = cj * kCL + sa;
-        fx = xqb[sj];
+        const int sj = (S.ent[e].x & 0x1fffffff) * kCL + sa;
         ft = __ldg(&P.ts[sj]);
-        if (MODE >= 1) fe = load_eta4<R, V4>(P, bo + sj);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          fx[b] = xqb[b][sj];
+          if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, (size_t)nb[b] * P.Qpad + sj);
+        }
       }
     };
     fetch(0);
-    const int nb = (nc + 3) >> 2;
-    for (int b = 0; b < nb; ++b) {
+    const int nblk = (nc + 3) >> 2;
+    for (int blk = 0; blk < nblk; ++blk) {
       __syncwarp();
-      S.x[lane] = fx;
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        S.x[b][lane] = fx[b];
+        if (MODE >= 1) S.e[b][lane] = fe[b];
+      }
       S.t[lane] = ft;
-      if (MODE >= 1) S.e[lane] = fe;
       __syncwarp();
-      if (b + 1 < nb) fetch(b + 1);
-      // entries past the end of the chunk were staged with no half bits, so all 4 are safe
+      if (blk + 1 < nblk) fetch(blk + 1);
+      // entries past the end of the chunk were staged with no half bits
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int e = 4 * b + q;
+        const int e = 4 * blk + q;
         const int fl = S.ent[e].x;
         R rcA = k.rc2, rcB = k.rc2;
         if (fl < 0) {
@@ -267,58 +308,71 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           rcB = ((m >> 4) & 1ull) ? R(-1) : k.rc2;
         }
         const V4 D = S.d[e];
-        const R xs = xi.x + D.x, ys = xi.y + D.y, zs = xi.z + D.z;
         const int so = q * kCL + jj;
-        if (fl & (1 << 29)) {
-          R ej[3] = {R(0), R(0), R(0)};
-          if (MODE >= 1) {
-            const V4 v = S.e[so];
-            ej[0] = v.x; ej[1] = v.y; ej[2] = v.z;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!(fl & (1 << (29 + h)))) continue;
+          const int sj = so + 4 * h;
+          const V4 p = tabrow[S.t[sj]];
+          const R qq = qi * S.x[0][sj].w;
+          const R sh = fma(qq, k.drf, p.z);
+          const R rce = h ? rcB : rcA;
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            R ej[3] = {R(0), R(0), R(0)};
+            if (MODE >= 1) {
+              const V4 v = S.e[b][sj];
+              ej[0] = v.x;
+              ej[1] = v.y;
+              ej[2] = v.z;
+            }
+            R* acc = (sizeof(R) == 4) ? a[b] : accd.a;
+            if (ENERGY && b == 0)
+              pair_one<R, MODE, true, V4>(k, xi[b].x + D.x, xi[b].y + D.y, xi[b].z + D.z, S.x[b][sj], p, qq, sh,
+                                          rce, ei[b], ej, eps[b], acc, eacc.a);
+            else
+              pair_one<R, MODE, false, V4>(k, xi[b].x + D.x, xi[b].y + D.y, xi[b].z + D.z, S.x[b][sj], p, qq, sh,
+                                           rce, ei[b], ej, eps[b], acc, eacc.a);
           }
-          pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, S.x[so], tabrow[S.t[so]], rcA, ei, ej, eps, acc, eacc);
-        }
-        if (fl & (1 << 30)) {
-          R ej[3] = {R(0), R(0), R(0)};
-          if (MODE >= 1) {
-            const V4 v = S.e[so + 4];
-            ej[0] = v.x; ej[1] = v.y; ej[2] = v.z;
-          }
-          pair_one<R, MODE, ENERGY, V4>(k, xi, xs, ys, zs, S.x[so + 4], tabrow[S.t[so + 4]], rcB, ei, ej, eps, acc,
-                                        eacc);
         }
       }
-      if ((b & 3) == 3) {
-        acc.fold();
+      if ((blk & 3) == 3) {
+        fold_into<R, B>(S, a, lane);
         if (ENERGY) eacc.fold();
       }
     }
-    acc.fold();
-    if (ENERGY) eacc.fold();
   }
+  fold_into<R, B>(S, a, lane);
+  if (ENERGY) eacc.fold();
   const bool valid = __ldg(&P.perm[si]) >= 0;
   if constexpr (sizeof(R) == 4) {
-    // mixed mode: sum the four lanes of each i-atom as double-floats, no FP64 instructions
-    df v[3];
+    // sum the four lanes of each i-atom as double-floats, no FP64 instructions
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      v[c] = df{acc.h[c], acc.l[c]};
+    for (int b = 0; b < B; ++b) {
+      df v[3];
 #pragma unroll
-      for (int o = 8; o <= 16; o <<= 1) {
-        const df w{__shfl_xor_sync(0xffffffffu, v[c].hi, o), __shfl_xor_sync(0xffffffffu, v[c].lo, o)};
-        v[c] = df_add(v[c], w);
+      for (int c = 0; c < 3; ++c) {
+        v[c] = df{S.hl[b][c][lane], S.hl[b][3 + c][lane]};
+#pragma unroll
+        for (int o = 8; o <= 16; o <<= 1) {
+          const df w{__shfl_xor_sync(0xffffffffu, v[c].hi, o), __shfl_xor_sync(0xffffffffu, v[c].lo, o)};
+          v[c] = df_add(v[c], w);
+        }
+        if (!valid) v[c] = df{0.f, 0.f};
       }
-      if (!valid) v[c] = df{0.f, 0.f};
-    }
-    if (jj == 0) {
-      if (MODE == 0) {
-        float2* dst = reinterpret_cast<float2*>(P.Fnb) + 3 * (bo + si);
-        dst[0] = make_float2(v[0].hi, v[0].lo);
-        dst[1] = make_float2(v[1].hi, v[1].lo);
-        dst[2] = make_float2(v[2].hi, v[2].lo);
-      } else {
-        const float scale = (MODE == 2) ? -0.5f / (float)eps : 1.0f;
-        reinterpret_cast<float4*>(P.Hnb)[bo + si] =
-            make_float4((v[0].hi + v[0].lo) * scale, (v[1].hi + v[1].lo) * scale, (v[2].hi + v[2].lo) * scale, 0.f);
+      if (jj == 0 && (b == 0 || n0 + b < n_pass)) {
+        const size_t k2 = (size_t)nb[b] * P.Qpad + si;
+        if (MODE == 0) {
+          float2* dst = reinterpret_cast<float2*>(P.Fnb) + 3 * k2;
+          dst[0] = make_float2(v[0].hi, v[0].lo);
+          dst[1] = make_float2(v[1].hi, v[1].lo);
+          dst[2] = make_float2(v[2].hi, v[2].lo);
+        } else {
+          const float scale = (MODE == 2) ? -0.5f / (float)eps[b] : 1.0f;
+          reinterpret_cast<float4*>(P.Hnb)[k2] = make_float4((v[0].hi + v[0].lo) * scale,
+                                                             (v[1].hi + v[1].lo) * scale,
+                                                             (v[2].hi + v[2].lo) * scale, 0.f);
+        }
       }
     }
     if (ENERGY) {
@@ -330,14 +384,14 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
     double out[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double v = acc.get(c);
+      double v = accd.get(c);
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
       out[c] = valid ? v : 0.0;
     }
     if (jj == 0) {
-      double* dst = (MODE == 0 ? P.Fnb : P.Hnb) + 3 * (bo + si);
-      const double scale = (MODE == 2) ? -0.5 / (double)eps : 1.0;
+      double* dst = (MODE == 0 ? P.Fnb : P.Hnb) + 3 * ((size_t)nb[0] * P.Qpad + si);
+      const double scale = (MODE == 2) ? -0.5 / (double)eps[0] : 1.0;
       dst[0] = out[0] * scale;
       dst[1] = out[1] * scale;
       dst[2] = out[2] * scale;
@@ -350,17 +404,20 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   }
 }
 
+template <class R> struct BeadsPerUnit { static constexpr int value = sizeof(R) == 4 ? 2 : 1; };
+
 template <class R, int MODE>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                              long long n_units) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths,
+                                                                      int n_paths, long long n_units) {
   using V4 = typename Tr<R>::V4;
+  constexpr int B = BeadsPerUnit<R>::value;
   __shared__ V4 tab[kMaxTypes * kMaxTypes];
-  __shared__ Stage<R> stage[4];
+  __shared__ Stage<R, B> stage[4];
   const int nt2 = sc.n_types * sc.n_types;
   for (int k = threadIdx.x; k < nt2; k += blockDim.x) tab[k] = Tr<R>::tab(sc, k);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  Stage<R>& S = stage[threadIdx.x >> 5];
+  Stage<R, B>& S = stage[threadIdx.x >> 5];
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nw) {
     int p = 0;
@@ -370,12 +427,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 2) k_pair(SysConsts 
       while (p + 1 < n_paths && paths[p + 1].unit_off_h <= u) ++p;
     }
     const PathDev& P = paths[p];
-    const int nb = MODE == 0 ? P.n_force : P.n_hvp;
+    const int n_pass = MODE == 0 ? P.n_force : P.n_hvp;
+    const int ngrp = (n_pass + B - 1) / B;
     const long long v = u - (MODE == 0 ? P.unit_off : P.unit_off_h);
-    const int n = (int)(v % nb);
-    const int ci = (int)(v / nb);
-    if (MODE == 0 && n == 0) pair_unit<R, 0, true>(sc, tab, S, P, n, ci, lane);
-    else pair_unit<R, MODE, false>(sc, tab, S, P, n, ci, lane);
+    const int n0 = (int)(v % ngrp) * B;
+    const int ci = (int)(v / ngrp);
+    if (MODE == 0 && n0 == 0) pair_unit<R, 0, true, B>(sc, tab, S, P, n0, n_pass, ci, lane);
+    else pair_unit<R, MODE, false, B>(sc, tab, S, P, n0, n_pass, ci, lane);
   }
 }
 
@@ -465,6 +523,8 @@ cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int 
   ++*L.counter;
   return cudaGetLastError();
 }
+
+int pair_beads_per_unit(int precision) { return precision == 1 ? 1 : 2; }
 
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
                         int num_sms, Launch L) {

@@ -131,28 +131,41 @@ __device__ __forceinline__ void eta_of(const PathDev& P, int n, int atom, R* e) 
 
 // Bonded force on atom a at bead n, accumulated in FP64; U (if non-NULL) gets the energy of
 // the terms for which a has role 0 (so that every term is counted once).
-template <class R, class A>
-__device__ void bonded_force(const SysConsts& sc, const PathDev& P, int a, int n, A* F, double* U) {
+template <class R> __device__ __forceinline__ void term_params(const SysConsts& sc, int t, R* a, R* b);
+template <> __device__ __forceinline__ void term_params<float>(const SysConsts& sc, int t, float* a, float* b) {
+  const float2 v = sc.incpf[t];
+  *a = v.x;
+  *b = v.y;
+}
+template <> __device__ __forceinline__ void term_params<double>(const SysConsts& sc, int t, double* a, double* b) {
+  const double2 v = sc.incp[t];
+  *a = v.x;
+  *b = v.y;
+}
+
+template <class R, class A, class U_t>
+__device__ void bonded_force(const SysConsts& sc, const PathDev& P, int a, int n, A* F, U_t* U) {
   for (int t = sc.inc_off[a]; t < sc.inc_off[a + 1]; ++t) {
     const int4 in = sc.inc[t];
-    const double2 pr = sc.incp[t];
+    R pr0, pr1;
+    term_params<R>(sc, t, &pr0, &pr1);
     const int kind = in.x & 3, role = in.x >> 2;
     R f[3];
     R u = R(0);
     if (kind == 0) {
       R d[3];
       mi_diff<R>(sc, P, n, in.y, in.z, d);
-      bond_force<R, R>(d, (R)pr.x, (R)pr.y, role, f, U && role == 0 ? &u : nullptr);
+      bond_force<R, R>(d, pr0, pr1, role, f, U && role == 0 ? &u : nullptr);
     } else {
       R p[3], q[3];
       mi_diff<R>(sc, P, n, in.y, in.z, p);
       mi_diff<R>(sc, P, n, in.w, in.z, q);
-      angle_force<R, R>(p, q, (R)pr.x, (R)pr.y, role, f, U && role == 0 ? &u : nullptr);
+      angle_force<R, R>(p, q, pr0, pr1, role, f, U && role == 0 ? &u : nullptr);
     }
     F[0] += (A)f[0];
     F[1] += (A)f[1];
     F[2] += (A)f[2];
-    if (U && role == 0) *U += (double)u;
+    if (U && role == 0) *U += u;
   }
 }
 
@@ -161,7 +174,8 @@ template <class R, bool FD, class A>
 __device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, double eps, A* H) {
   for (int t = sc.inc_off[a]; t < sc.inc_off[a + 1]; ++t) {
     const int4 in = sc.inc[t];
-    const double2 pr = sc.incp[t];
+    R pr0, pr1;
+    term_params<R>(sc, t, &pr0, &pr1);
     const int kind = in.x & 3, role = in.x >> 2;
     // relative vectors and their tangents (differences of eta)
     R v1[3], v2[3], t1[3], t2[3];
@@ -181,8 +195,8 @@ __device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, 
         d1[c] = {v1[c], t1[c]};
         d2[c] = {kind == 1 ? v2[c] : R(0), kind == 1 ? t2[c] : R(0)};
       }
-      if (kind == 0) bond_force<Dl<R>, R>(d1, (R)pr.x, (R)pr.y, role, f, nullptr);
-      else angle_force<Dl<R>, R>(d1, d2, (R)pr.x, (R)pr.y, role, f, nullptr);
+      if (kind == 0) bond_force<Dl<R>, R>(d1, pr0, pr1, role, f, nullptr);
+      else angle_force<Dl<R>, R>(d1, d2, pr0, pr1, role, f, nullptr);
       for (int c = 0; c < 3; ++c) H[c] -= (A)f[c].d;   // H eta = -d/dt F(x + t eta)
     } else {
       R fp[3], fm[3], a1[3], a2[3];
@@ -194,8 +208,8 @@ __device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, 
           a2[c] = kind == 1 ? v2[c] + sg * t2[c] : R(0);
         }
         R* f = s == 0 ? fp : fm;
-        if (kind == 0) bond_force<R, R>(a1, (R)pr.x, (R)pr.y, role, f, nullptr);
-        else angle_force<R, R>(a1, a2, (R)pr.x, (R)pr.y, role, f, nullptr);
+        if (kind == 0) bond_force<R, R>(a1, pr0, pr1, role, f, nullptr);
+        else angle_force<R, R>(a1, a2, pr0, pr1, role, f, nullptr);
       }
       if (sizeof(A) == 4) {
         const R inv2e = R(0.5) / (R)eps;
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* _
       F[0] = P.Fnb[3 * k];
       F[1] = P.Fnb[3 * k + 1];
       F[2] = P.Fnb[3 * k + 2];
-      bonded_force<R, double>(sc, P, a, n, F, n == 0 ? &eb : nullptr);
+      bonded_force<R, double, double>(sc, P, a, n, F, n == 0 ? &eb : nullptr);
       if (P.N > 1) {
         const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
         const double c = sc.cL[a];
@@ -316,13 +330,13 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
 // the path is close to a solution of Eq. 1), stored rounded to FP32; bonded energy of bead 1.
 __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
                                                         double* e_bond, int stride) {
-  __shared__ double sh[32];
+  __shared__ double shw[kRedBlock / 32];
   const int p = blockIdx.y;
   if (p >= n_paths) return;
   const PathDev& P = paths[p];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)P.n_force * P.Qpad;
-  double eb = 0.0;
+  float eb = 0.f;
   int bead = -1;            // bead of this thread, for the per-warp |eta| maximum (FD mode)
   unsigned nbits = 0u;
   if (t < total) {
@@ -336,7 +350,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
     float4 ef = make_float4(0.f, 0.f, 0.f, 0.f);
     if (a >= 0) {
       float Fb[3] = {0.f, 0.f, 0.f};
-      bonded_force<float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
+      bonded_force<float, float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
       for (int c = 0; c < 3; ++c) F[c] = df_add_f(df{Fnb[c].x, Fnb[c].y}, Fb[c]);
       if (P.N > 1) {
         const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
@@ -363,8 +377,14 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
   }
   // only blocks that hold bead-1 slots have bonded energy to sum
   if ((long long)blockIdx.x * blockDim.x < P.Qpad) {
-    const double tot = block_sum<kRedBlock>(eb, sh);
-    if (threadIdx.x == 0) e_bond[(size_t)p * stride + blockIdx.x] = tot;
+    const df w = df_warp_sum(df{eb, 0.f});
+    if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = widen(w.hi) + widen(w.lo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int k = 0; k < kRedBlock / 32; ++k) tot += shw[k];
+      e_bond[(size_t)p * stride + blockIdx.x] = tot;
+    }
   } else if (threadIdx.x == 0) {
     e_bond[(size_t)p * stride + blockIdx.x] = 0.0;
   }
@@ -416,13 +436,13 @@ __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const Path
         es = 0.5f * K * (e.x * e.x + e.y * e.y + e.z * e.z);
       }
       double* G = P.grad + 3 * ((size_t)n * P.Q + a);
-      G[0] = (double)g[0];
-      G[1] = (double)g[1];
-      G[2] = (double)g[2];
+      G[0] = widen(g[0]);
+      G[1] = widen(g[1]);
+      G[2] = widen(g[2]);
     }
   }
   const df w = df_warp_sum(df{es, 0.f});
-  if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = (double)w.hi + (double)w.lo;
+  if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = widen(w.hi) + widen(w.lo);
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
