@@ -90,9 +90,10 @@ __global__ void k_d2f(const double* in, float* out, long long n) {
 // fmt 0: FP64 x 3; 1: double-float (hi, lo) x 3; 2: float4
 __global__ void k_gather_field(const void* f, int fmt, const int* slot, int Q, int Qpad, int N, int n_rows,
                                double* out) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)N * Q) return;
-  const int a = (int)(t % Q), n = (int)(t / Q);
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (atoms, beads)
+  if (a >= Q) return;
+  const int n = blockIdx.y;
+  const size_t t = (size_t)n * Q + a;
   const size_t k = (size_t)n * Qpad + slot[a];
   for (int c = 0; c < 3; ++c) {
     double v = 0.0;
@@ -131,7 +132,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   std::vector<PathDev> pd(ids.size());
   if (h->profiling) CK(h, cudaEventRecord(h->ev[0], st));
   long long units = 0, units_h = 0;
-  long long max_e1 = 0, max_e2 = 0;
+  int max_qpad = 0, max_nf = 0, max_n = 0;
   size_t goff = 0;
   for (size_t k = 0; k < ids.size(); ++k) {
     PathHost& P = h->paths[ids[k]];
@@ -166,8 +167,9 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     const int bpu = pair_beads_per_unit(h->precision);
     units += (long long)((n_force + bpu - 1) / bpu) * P.n_clu;
     units_h += (long long)((n_hvp + bpu - 1) / bpu) * P.n_clu;
-    max_e1 = std::max(max_e1, (long long)n_force * Qpad);
-    max_e2 = std::max(max_e2, (long long)N * Qpad);
+    max_qpad = std::max(max_qpad, Qpad);
+    max_nf = std::max(max_nf, n_force);
+    max_n = std::max(max_n, N);
     D.x32 = h->precision == MOP_PREC_FP64 ? nullptr : P.x32.p;
     D.x64 = h->precision == MOP_PREC_FP64 ? P.x64.p : nullptr;
     D.perm = P.perm.p;
@@ -204,7 +206,8 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.veff_out = dev_veff ? dev_veff + k : P.veff_int.p;
   }
   const int np = (int)ids.size();
-  const int sb = nblk(max_e1, kRedBlock), ss = nblk(max_e2, kRedBlock);
+  const int nbx = nblk(max_qpad, kRedBlock);
+  const int sb = nbx, ss = max_n * nbx;
   CK(h, h->e_bond.ensure((size_t)np * sb));
   CK(h, h->e_spring.ensure((size_t)np * ss));
   CK(h, h->d_paths.ensure(np));
@@ -213,11 +216,11 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, mark(1));
   CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
   CK(h, mark(2));
-  CK(h, launch_e1(sc, h->d_paths.p, np, (int)max_e1, L, h->e_bond.p, sb));
+  CK(h, launch_e1(sc, h->d_paths.p, np, max_qpad, max_nf, L, h->e_bond.p, nbx));
   CK(h, mark(3));
   if (units_h > 0) CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
   CK(h, mark(4));
-  CK(h, launch_e2(sc, h->d_paths.p, np, (int)max_e2, L, h->e_spring.p, ss));
+  CK(h, launch_e2(sc, h->d_paths.p, np, max_qpad, max_n, L, h->e_spring.p, nbx));
   CK(h, mark(5));
   CK(h, launch_bias(sc, h->d_paths.p, np, L));
   CK(h, launch_reduce(sc, h->d_paths.p, np, L, h->e_bond.p, sb, sb, h->e_spring.p, ss, ss));
@@ -565,7 +568,7 @@ mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* 
     CK(h, h->scratch.ensure(n));
     dst = h->scratch.p;
   }
-  k_gather_field<<<nblk((long long)N * h->sc.Q, 256), 256, 0, st>>>(f, fmt, P.slot.p, h->sc.Q, Qpad, N, rows, dst);
+  k_gather_field<<<dim3(nblk(h->sc.Q, 256), N), 256, 0, st>>>(f, fmt, P.slot.p, h->sc.Q, Qpad, N, rows, dst);
   CK(h, cudaGetLastError());
   if (!(flags & MOP_DEVPTR)) {
     CK(h, cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -105,10 +105,12 @@ cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int 
                                unsigned long long* counts, int num_sms, Launch L);
 
 // --- mop_path.cu: bonded terms, eta, path gradient, bias, reductions, integrator ----------
-cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
-                      double* e_bond, int e_bond_stride);
-cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
-                      double* e_spring, int e_spring_stride);
+// grids: (slot blocks of 256, beads, paths); e_bond gets nbx partials per path, e_spring
+// max_beads * nbx partials per path
+cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
+                      double* e_bond, int nbx);
+cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
+                      double* e_spring, int nbx);
 cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L);
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L,
                           const double* e_bond, int e_bond_stride, int n_e1_blocks,

@@ -224,16 +224,14 @@ __device__ void bonded_hvp(const SysConsts& sc, const PathDev& P, int a, int n, 
 // E1: F^n = F_nonbonded + F_bonded, eta^n = R^{n+1} - R^n - c F^n (FP64), bonded energy of bead 1
 template <class R>
 __global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                                  double* e_bond, int stride) {
+                                                  double* e_bond, int nbx) {
   __shared__ double sh[32];
-  const int p = blockIdx.y;
-  if (p >= n_paths) return;
+  const int p = blockIdx.z, n = blockIdx.y;
   const PathDev& P = paths[p];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)P.n_force * P.Qpad;
+  if (n >= P.n_force) return;   // whole block; only bead-1 blocks write energy partials
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double eb = 0.0;
-  if (t < total) {
-    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+  if (s < P.Qpad) {
     const size_t k = (size_t)n * P.Qpad + s;
     const int a = P.perm[s];
     double F[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
@@ -266,23 +264,27 @@ __global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* _
       P.eta32[k] = make_float4((float)e[0], (float)e[1], (float)e[2], 0.f);
     }
   }
-  const double tot = block_sum<kRedBlock>(eb, sh);
-  if (threadIdx.x == 0) e_bond[(size_t)p * stride + blockIdx.x] = tot;
+  if (n == 0) {
+    const double tot = block_sum<kRedBlock>(eb, sh);
+    if (threadIdx.x == 0) e_bond[(size_t)p * nbx + blockIdx.x] = tot;
+  }
 }
 
 // E2: bonded H eta, H eta total, path gradient (caller order), spring energy
 template <class R, bool FD>
 __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                                  double* e_spring, int stride) {
+                                                  double* e_spring, int nbx, int maxN) {
   __shared__ double sh[32];
-  const int p = blockIdx.y;
-  if (p >= n_paths) return;
+  const int p = blockIdx.z, n = blockIdx.y;
   const PathDev& P = paths[p];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)P.N * P.Qpad;
+  double* part = e_spring + ((size_t)p * maxN + n) * nbx + blockIdx.x;
+  if (n >= P.N) {
+    if (threadIdx.x == 0) *part = 0.0;
+    return;
+  }
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double es = 0.0;
-  if (t < total) {
-    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+  if (s < P.Qpad) {
     const int a = P.perm[s];
     const size_t k = (size_t)n * P.Qpad + s;
     if (a >= 0) {
@@ -300,8 +302,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
         if (FD) {
           const float mx = __uint_as_float(P.etamax[n]);
           eps = mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h;
-          // the pair kernel used the same eps rounded to the pair precision
-          eps = (double)(R)eps;
+          eps = (double)(R)eps;   // the pair kernel used the same eps in its own precision
         }
         bonded_hvp<R, FD, double>(sc, P, a, n, eps, H);
         double e2 = 0.0;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
     }
   }
   const double tot = block_sum<kRedBlock>(es, sh);
-  if (threadIdx.x == 0) e_spring[(size_t)p * stride + blockIdx.x] = tot;
+  if (threadIdx.x == 0) *part = tot;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -329,19 +330,15 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
 // eta^n = (R^{n+1} - R^n) - c F^n in double-float (the difference of nearly equal terms when
 // the path is close to a solution of Eq. 1), stored rounded to FP32; bonded energy of bead 1.
 __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                                        double* e_bond, int stride) {
+                                                        double* e_bond, int nbx) {
   __shared__ double shw[kRedBlock / 32];
-  const int p = blockIdx.y;
-  if (p >= n_paths) return;
+  const int p = blockIdx.z, n = blockIdx.y;
   const PathDev& P = paths[p];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)P.n_force * P.Qpad;
+  if (n >= P.n_force) return;   // whole block; only bead-1 blocks write energy partials
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   float eb = 0.f;
-  int bead = -1;            // bead of this thread, for the per-warp |eta| maximum (FD mode)
   unsigned nbits = 0u;
-  if (t < total) {
-    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
-    bead = n;
+  if (s < P.Qpad) {
     const size_t k = (size_t)n * P.Qpad + s;
     const int a = P.perm[s];
     const float2* Fnb = reinterpret_cast<const float2*>(P.Fnb) + 3 * k;
@@ -370,23 +367,19 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
     if (P.N > 1) P.eta32[k] = ef;
   }
   if (sc.hvp_mode == 1) {
-    // one atomic per (warp, bead): lanes of the same bead take their maximum first
-    const unsigned same = __match_any_sync(0xffffffffu, bead);
-    const unsigned mx = __reduce_max_sync(same, nbits);
-    if (bead >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicMax(&P.etamax[bead], mx);
+    // one atomic per warp (all lanes belong to bead n)
+    const unsigned mx = __reduce_max_sync(0xffffffffu, nbits);
+    if ((threadIdx.x & 31) == 0) atomicMax(&P.etamax[n], mx);
   }
-  // only blocks that hold bead-1 slots have bonded energy to sum
-  if ((long long)blockIdx.x * blockDim.x < P.Qpad) {
+  if (n == 0) {
     const df w = df_warp_sum(df{eb, 0.f});
     if ((threadIdx.x & 31) == 0) shw[threadIdx.x >> 5] = widen(w.hi) + widen(w.lo);
     __syncthreads();
     if (threadIdx.x == 0) {
       double tot = 0.0;
       for (int k = 0; k < kRedBlock / 32; ++k) tot += shw[k];
-      e_bond[(size_t)p * stride + blockIdx.x] = tot;
+      e_bond[(size_t)p * nbx + blockIdx.x] = tot;
     }
-  } else if (threadIdx.x == 0) {
-    e_bond[(size_t)p * stride + blockIdx.x] = 0.0;
   }
 }
 
@@ -394,16 +387,18 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
 // FP32-rounded eta, spring energy summed as double-floats per warp and in FP64 per block.
 template <bool FD>
 __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                                        double* e_spring, int stride) {
+                                                        double* e_spring, int nbx, int maxN) {
   __shared__ double shw[kRedBlock / 32];
-  const int p = blockIdx.y;
-  if (p >= n_paths) return;
+  const int p = blockIdx.z, n = blockIdx.y;
   const PathDev& P = paths[p];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)P.N * P.Qpad;
+  double* part = e_spring + ((size_t)p * maxN + n) * nbx + blockIdx.x;
+  if (n >= P.N) {
+    if (threadIdx.x == 0) *part = 0.0;
+    return;
+  }
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   float es = 0.f;
-  if (t < total) {
-    const int n = (int)(t / P.Qpad), s = (int)(t % P.Qpad);
+  if (s < P.Qpad) {
     const int a = P.perm[s];
     const size_t k = (size_t)n * P.Qpad + s;
     if (a >= 0) {
@@ -447,7 +442,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const Path
   if (threadIdx.x == 0) {
     double tot = 0.0;
     for (int k = 0; k < kRedBlock / 32; ++k) tot += shw[k];
-    e_spring[(size_t)p * stride + blockIdx.x] = tot;
+    *part = tot;
   }
 }
 
@@ -532,6 +527,7 @@ __global__ void k_bias(SysConsts sc, const PathDev* __restrict__ paths, int n_pa
 // fixed-order sums of the partial energies -> V_eff (one block per path)
 __global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const double* e_bond, int sb, int nb1,
                          const double* e_spring, int ss, int nb2) {
+  // e_bond: nb1 partials per path (stride sb); e_spring: nb2 partials per path (stride ss)
   __shared__ double sh[32];
   const int p = blockIdx.x;
   const PathDev& P = paths[p];
@@ -570,18 +566,20 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
-__global__ void k_kick(int n3Q, int Q, int N, const double* mass, double* vel, const double* grad, double half_dt) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)N * n3Q) return;
-  const int a = (int)((t % n3Q) / 3);
-  vel[t] -= half_dt * grad[t] / mass[a];
+__global__ void k_kick(int Q, const double* mass, double* vel, const double* grad, double half_dt) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (atoms, beads)
+  if (a >= Q) return;
+  const size_t t = 3 * ((size_t)blockIdx.y * Q + a);
+  const double s = half_dt / mass[a];
+  for (int d = 0; d < 3; ++d) vel[t + d] -= s * grad[t + d];
 }
 
 __global__ void k_drift(int Q, int N, const double* mass, double* x64, double* vel, float* x32, double dt, double c1,
                         double c2, double kT, uint64_t seed, uint64_t step) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)N * Q) return;
-  const int a = (int)(t % Q), n = (int)(t / Q);
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (atoms, beads)
+  if (a >= Q) return;
+  const int n = blockIdx.y;
+  const size_t t = (size_t)n * Q + a;
   double* x = x64 + 3 * t;
   double* v = vel + 3 * t;
   for (int d = 0; d < 3; ++d) x[d] += 0.5 * dt * v[d];
@@ -608,10 +606,11 @@ __global__ void k_drift(int Q, int N, const double* mass, double* x64, double* v
 __global__ void k_kinetic(int Q, int N, const double* mass, const double* vel, double* out) {
   __shared__ double sh[32];
   double s = 0.0;
-  for (long long t = threadIdx.x; t < (long long)N * Q; t += blockDim.x) {
-    const double* v = vel + 3 * t;
-    s += 0.5 * mass[t % Q] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  }
+  for (int n = 0; n < N; ++n)
+    for (int a = threadIdx.x; a < Q; a += blockDim.x) {
+      const double* v = vel + 3 * ((size_t)n * Q + a);
+      s += 0.5 * mass[a] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
   s = block_sum<kRedBlock>(s, sh);
   if (threadIdx.x == 0) *out = s;
 }
@@ -620,25 +619,27 @@ inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
 }  // namespace
 
-cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
-                      double* e_bond, int stride) {
-  dim3 grid(nblk(max_threads, kRedBlock), n_paths);
-  if (sc.precision == 1) k_e1<double><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
-  else k_e1_mixed<<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, stride);
+cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
+                      double* e_bond, int nbx) {
+  dim3 grid(nbx, max_beads, n_paths);
+  if (sc.precision == 1) k_e1<double><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, nbx);
+  else k_e1_mixed<<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_bond, nbx);
+  (void)max_qpad;
   ++*L.counter;
   return cudaGetLastError();
 }
 
-cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_threads, Launch L,
-                      double* e_spring, int stride) {
-  dim3 grid(nblk(max_threads, kRedBlock), n_paths);
+cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
+                      double* e_spring, int nbx) {
+  dim3 grid(nbx, max_beads, n_paths);
   const bool fd = sc.hvp_mode == 1;
+  (void)max_qpad;
   if (sc.precision == 1) {
-    if (fd) k_e2<double, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
-    else k_e2<double, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+    if (fd) k_e2<double, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
+    else k_e2<double, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
   } else {
-    if (fd) k_e2_mixed<true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
-    else k_e2_mixed<false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, stride);
+    if (fd) k_e2_mixed<true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
+    else k_e2_mixed<false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
   }
   ++*L.counter;
   return cudaGetLastError();
@@ -659,8 +660,7 @@ cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_pat
 }
 
 cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, int N, double half_dt, Launch L) {
-  const long long n = (long long)N * 3 * sc.Q;
-  k_kick<<<nblk(n, kRedBlock), kRedBlock, 0, L.st>>>(3 * sc.Q, sc.Q, N, sc.mass, vel, grad, half_dt);
+  k_kick<<<dim3(nblk(sc.Q, kRedBlock), N), kRedBlock, 0, L.st>>>(sc.Q, sc.mass, vel, grad, half_dt);
   ++*L.counter;
   return cudaGetLastError();
 }
@@ -669,8 +669,8 @@ cudaError_t launch_drift(const SysConsts& sc, double* x64, double* vel, float* x
                          double kT, uint64_t seed, uint64_t step, int, Launch L) {
   const double c1 = gamma > 0.0 ? exp(-gamma * dt) : 1.0;
   const double c2 = gamma > 0.0 ? sqrt(1.0 - c1 * c1) : 0.0;
-  const long long n = (long long)N * sc.Q;
-  k_drift<<<nblk(n, kRedBlock), kRedBlock, 0, L.st>>>(sc.Q, N, sc.mass, x64, vel, x32, dt, c1, c2, kT, seed, step);
+  k_drift<<<dim3(nblk(sc.Q, kRedBlock), N), kRedBlock, 0, L.st>>>(sc.Q, N, sc.mass, x64, vel, x32, dt, c1, c2, kT,
+                                                                  seed, step);
   ++*L.counter;
   return cudaGetLastError();
 }

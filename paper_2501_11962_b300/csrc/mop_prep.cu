@@ -174,11 +174,10 @@ template <bool F64>
 __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
                                const int* perm, const int* meta, int max_slots, const double* center, float4* xq,
                                double4_32a* xq64, int* ts) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int Qpad = meta[0] * kCL;
-  const int s = (int)(t % max_slots);
-  const int b = (int)(t / max_slots);
-  if (b >= N || s >= Qpad) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (slots, beads)
+  const int b = blockIdx.y;
+  if (s >= Qpad) return;
   const int a = perm[s];
   const size_t o = (size_t)b * Qpad + s;
   if (a < 0) {
@@ -512,10 +511,10 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                                                                    P.emax.p);
   MOP_KL();
   if (f64)
-    k_local_coords<true><<<nblk((long long)N * max_slots, bs), bs, 0, st>>>(
+    k_local_coords<true><<<dim3(nblk(max_slots, bs), N), bs, 0, st>>>(
         sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, nullptr, P.xq64.p, P.ts.p);
   else
-    k_local_coords<false><<<nblk((long long)N * max_slots, bs), bs, 0, st>>>(
+    k_local_coords<false><<<dim3(nblk(max_slots, bs), N), bs, 0, st>>>(
         sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, P.xq.p, nullptr, P.ts.p);
   MOP_KL();
   k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, P.hext.p, g.nb[0], g.nb[1],

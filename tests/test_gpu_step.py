@@ -1,0 +1,65 @@
+"""mop_step (path dynamics of Eq. 4) against the oracle's integrator.
+
+Both sides draw the Langevin noise from their own Philox-4x32-10 implementation with the same
+(seed, step, bead, atom) counters, so BAOAB trajectories agree to rounding; velocity Verlet
+conserves V_eff + kinetic energy (the paper's NVE check, Sec. 2.3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_11962_b300 import mop
+from tests.conftest import workload
+
+pytestmark = pytest.mark.gpu
+
+
+def run_both(gamma, n_steps=5, dt=2e-4, seed=11):
+    w = workload(1, n_beads=4)
+    X0 = w.paths[0]
+    eng = mop.Engine(w.system, precision=mop.MOP_PREC_FP64)
+    eng.set_path(0, X0)
+    eng.step(n_steps, dt, gamma, seed)
+    Xg = eng.get_path(0).astype(np.float64)
+    keg = eng.kinetic_energy(0)
+    o = oracle.Oracle(w.system)
+    X = X0.astype(np.float64).copy()
+    V = np.zeros_like(X)
+    G = o.veff(X)["G"]
+    for k in range(n_steps):
+        o.step(X, V, G, dt, gamma, w.system.temperature, seed, k, round_f32=False)
+    ke = 0.5 * np.sum(w.system.mass[None, :, None] * V ** 2)
+    return Xg, X, keg, ke
+
+
+def test_velocity_verlet_matches_oracle():
+    Xg, X, keg, ke = run_both(gamma=0.0)
+    disp = np.abs(X - workload(1, n_beads=4).paths[0]).max()
+    assert disp > 1e-6                                  # the atoms did move
+    assert np.abs(Xg - X).max() < 1e-6                  # float32 readback of FP64 positions
+    assert keg == pytest.approx(ke, rel=1e-9)
+
+
+def test_baoab_matches_oracle_noise():
+    Xg, X, keg, ke = run_both(gamma=5.0)
+    assert np.abs(Xg - X).max() < 1e-6
+    assert keg == pytest.approx(ke, rel=1e-8)
+
+
+def test_nve_energy_conserved():
+    w = workload(1, n_beads=4)
+    eng = mop.Engine(w.system, precision=mop.MOP_PREC_FP64)
+    eng.set_path(0, w.paths[0])
+    v0, _ = eng.veff_and_grad(0)
+    E0 = v0[0]
+    drift = []
+    for dt in (2e-4, 1e-4):
+        eng.set_path(0, w.paths[0])
+        errs = []
+        for k in range(int(round(0.004 / dt))):
+            eng.step(1, dt, 0.0, 1)
+            v, _ = eng.veff_and_grad(0)
+            errs.append(abs(v[0] + eng.kinetic_energy(0) - E0))
+        drift.append(max(errs))
+    assert drift[1] < drift[0]
+    assert 2.5 < drift[0] / drift[1] < 5.5           # second-order integrator
