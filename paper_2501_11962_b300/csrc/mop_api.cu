@@ -206,7 +206,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.veff_out = dev_veff ? dev_veff + k : P.veff_int.p;
   }
   const int np = (int)ids.size();
-  const int nbx = nblk(max_qpad, kRedBlock);
+  const int nbx = nblk(sc.Q, kRedBlock);   // E1/E2 blocks run over atoms in caller order
   const int sb = nbx, ss = max_n * nbx;
   CK(h, h->e_bond.ensure((size_t)np * sb));
   CK(h, h->e_spring.ensure((size_t)np * ss));

@@ -229,13 +229,13 @@ __global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* _
   const int p = blockIdx.z, n = blockIdx.y;
   const PathDev& P = paths[p];
   if (n >= P.n_force) return;   // whole block; only bead-1 blocks write energy partials
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // caller order: molecules are contiguous
   double eb = 0.0;
-  if (s < P.Qpad) {
+  if (a < P.Q) {
+    const int s = P.slot[a];
     const size_t k = (size_t)n * P.Qpad + s;
-    const int a = P.perm[s];
     double F[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
-    if (a >= 0) {
+    {
       F[0] = P.Fnb[3 * k];
       F[1] = P.Fnb[3 * k + 1];
       F[2] = P.Fnb[3 * k + 2];
@@ -282,12 +282,12 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
     if (threadIdx.x == 0) *part = 0.0;
     return;
   }
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // caller order
   double es = 0.0;
-  if (s < P.Qpad) {
-    const int a = P.perm[s];
+  if (a < P.Q) {
+    const int s = P.slot[a];
     const size_t k = (size_t)n * P.Qpad + s;
-    if (a >= 0) {
+    {
       const double K = sc.Kspr[a];
       double g[3] = {0.0, 0.0, 0.0};
       if (n == 0)
@@ -335,17 +335,17 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
   const int p = blockIdx.z, n = blockIdx.y;
   const PathDev& P = paths[p];
   if (n >= P.n_force) return;   // whole block; only bead-1 blocks write energy partials
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // caller order: molecules are contiguous
   float eb = 0.f;
   unsigned nbits = 0u;
-  if (s < P.Qpad) {
+  if (a < P.Q) {
+    const int s = P.slot[a];
     const size_t k = (size_t)n * P.Qpad + s;
-    const int a = P.perm[s];
     const float2* Fnb = reinterpret_cast<const float2*>(P.Fnb) + 3 * k;
     float2* Fo = reinterpret_cast<float2*>(P.F) + 3 * k;
     df F[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     float4 ef = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (a >= 0) {
+    {
       float Fb[3] = {0.f, 0.f, 0.f};
       bonded_force<float, float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
       for (int c = 0; c < 3; ++c) F[c] = df_add_f(df{Fnb[c].x, Fnb[c].y}, Fb[c]);
@@ -396,12 +396,12 @@ __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const Path
     if (threadIdx.x == 0) *part = 0.0;
     return;
   }
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;   // caller order
   float es = 0.f;
-  if (s < P.Qpad) {
-    const int a = P.perm[s];
+  if (a < P.Q) {
+    const int s = P.slot[a];
     const size_t k = (size_t)n * P.Qpad + s;
-    if (a >= 0) {
+    {
       const float K = sc.Kf[a];
       float g[3] = {0.f, 0.f, 0.f};
       if (n == 0) {

@@ -173,7 +173,7 @@ __global__ void k_cluster_bbox(SysConsts sc, const float* x32, const double* x64
 template <bool F64>
 __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
                                const int* perm, const int* meta, int max_slots, const double* center, float4* xq,
-                               double4_32a* xq64, int* ts) {
+                               double4_32a* xq64, int* ts, float4* eta32, double* eta64) {
   const int Qpad = meta[0] * kCL;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (slots, beads)
   const int b = blockIdx.y;
@@ -184,6 +184,9 @@ __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64
     const double dmy = (double)kDummyCoord + 3.0 * (s & (kCL - 1));
     if (F64) xq64[o] = make_double4_32a(dmy, dmy, dmy, 0.0);
     else xq[o] = make_float4((float)dmy, (float)dmy, (float)dmy, 0.0f);
+    // padding slots have no eta; the pair HVP kernels read it as j-atoms
+    eta32[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (F64) eta64[3 * o] = eta64[3 * o + 1] = eta64[3 * o + 2] = 0.0;
     if (b == 0) ts[s] = 0;
     return;
   }
@@ -489,6 +492,8 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_CK(P.meta.ensure(4));
   if (f64) MOP_CK(P.xq64.ensure((size_t)N * max_slots));
   else MOP_CK(P.xq.ensure((size_t)N * max_slots));
+  MOP_CK(P.eta32.ensure((size_t)N * max_slots));
+  if (f64) MOP_CK(P.eta.ensure(3 * (size_t)N * max_slots));
 
   MOP_CK(cudaMemsetAsync(P.colcnt.p, 0, sizeof(int) * ncol, st));
   MOP_CK(cudaMemsetAsync(P.perm.p, 0xff, sizeof(int) * max_slots, st));
@@ -512,10 +517,12 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_KL();
   if (f64)
     k_local_coords<true><<<dim3(nblk(max_slots, bs), N), bs, 0, st>>>(
-        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, nullptr, P.xq64.p, P.ts.p);
+        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, nullptr, P.xq64.p, P.ts.p, P.eta32.p,
+        P.eta.p);
   else
     k_local_coords<false><<<dim3(nblk(max_slots, bs), N), bs, 0, st>>>(
-        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, P.xq.p, nullptr, P.ts.p);
+        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, P.xq.p, nullptr, P.ts.p, P.eta32.p,
+        nullptr);
   MOP_KL();
   k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, P.hext.p, g.nb[0], g.nb[1],
                                                    g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cbox.p,
