@@ -16,6 +16,11 @@
 //   b  = (phi''(r) + g) / r^2              H block A = b d d^T - g I,  A u with u = eta_i - eta_j
 #include "mop_host.h"
 
+// resident 128-thread blocks per SM requested for the FP32 pair kernels (register budget)
+#ifndef MOP_PAIR_MINB
+#define MOP_PAIR_MINB 4
+#endif
+
 namespace mop {
 namespace {
 
@@ -103,13 +108,47 @@ __device__ __forceinline__ R pair_g(R rinv, R rinv2, R rinv6, const V4& p, R qq,
   return rinv6 * fma(p.x, rinv6, -p.y) * rinv2 + qq * fma(rinv, rinv2, -k2rf) + sh * rinv;
 }
 
-// One pair for one bead: i-atom of this lane against j-atom xj, type-pair row p, qq = f q_i q_j,
-// sh = phi'(rc) of the pair; cutoff test against rc2e (negative for an excluded pair).
-// Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-) (MODE 2) into a[3] and the pair energy
-// into e (ENERGY).
+// Per (entry, half) constants shared by all beads of a unit: type-pair row p = (12 c12, 6 c6,
+// phi'_LJ(rc), phi_LJ(rc)), qq = f q_i q_j, sh = phi'(rc), and derived factors.
+template <class R> struct PairK {
+  R A, B;      // 12 c12, 6 c6
+  R qq, sh;    // f q_i q_j, phi'(rc) of the pair
+  R qk;        // qq * 2 k_rf
+  R A14, B8;   // 14 * 12 c12, 8 * 6 c6   (HVP)
+  R q3;        // 3 qq                    (HVP)
+  R Ew;        // phi_LJ(rc)              (energy)
+};
+
+template <class R, int MODE, class V4>
+__device__ __forceinline__ PairK<R> pair_consts(const Cst<R>& k, const V4& p, R qq) {
+  PairK<R> c;
+  c.A = p.x;
+  c.B = p.y;
+  c.qq = qq;
+  c.sh = fma(qq, k.drf, p.z);
+  c.qk = qq * k.k2rf;
+  if (MODE == 1) {
+    c.A14 = R(14) * p.x;
+    c.B8 = R(8) * p.y;
+    c.q3 = R(3) * qq;
+  }
+  c.Ew = p.w;
+  return c;
+}
+
+// g = -phi'_sf(r) / r = r^-2 [r^-6 (A r^-6 - B) + qq r^-1] + (sh r^-1 - qq 2 k_rf)
+template <class R>
+__device__ __forceinline__ R pair_g2(const PairK<R>& c, R rinv, R rinv2, R rinv6) {
+  const R t = fma(c.qq, rinv, rinv6 * fma(c.A, rinv6, -c.B));
+  return fma(rinv2, t, fma(c.sh, rinv, -c.qk));
+}
+
+// One pair for one bead (i-atom of this lane at xs, j-atom xj); cutoff test against rc2e
+// (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-)
+// (MODE 2) into a[3] and the pair energy into e (ENERGY).
 template <class R, int MODE, bool ENERGY, class V4>
-__device__ __forceinline__ void pair_one(const Cst<R>& k, R xs, R ys, R zs, const V4& xj, const V4& p, R qq, R sh,
-                                         R rc2e, const R* ei, const R* ej, R eps, R* a, R& e) {
+__device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R xs, R ys, R zs, const V4& xj, R rc2e,
+                                         const R* ei, const R* ej, R eps, R* a, R& e) {
   const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
   if (MODE == 0) {
     const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
@@ -117,7 +156,7 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, R xs, R ys, R zs, cons
     const R rinv = Tr<R>::rsq(r2);
     const R rinv2 = rinv * rinv;
     const R rinv6 = rinv2 * rinv2 * rinv2;
-    R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+    R g = pair_g2<R>(c, rinv, rinv2, rinv6);
     g = in ? g : R(0);
     a[0] = fma(g, dx, a[0]);
     a[1] = fma(g, dy, a[1]);
@@ -125,9 +164,9 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, R xs, R ys, R zs, cons
     if (ENERGY) {
       // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
       const R r = r2 * rinv;
-      const R elj = rinv6 * fma(p.x * R(1.0 / 12.0), rinv6, -p.y * R(1.0 / 6.0));
-      const R erf = qq * (rinv + fma(k.krf, r2, -k.crf));
-      const R E = elj + erf - p.w - (r - k.rc) * sh;
+      const R elj = rinv6 * fma(c.A * R(1.0 / 12.0), rinv6, -c.B * R(1.0 / 6.0));
+      const R erf = c.qq * (rinv + fma(k.krf, r2, -k.crf));
+      const R E = elj + erf - c.Ew - (r - k.rc) * c.sh;
       e += in ? E : R(0);
     }
   } else if (MODE == 1) {
@@ -138,8 +177,9 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, R xs, R ys, R zs, cons
     const R rinv2 = rinv * rinv;
     const R rinv3 = rinv * rinv2;
     const R rinv6 = rinv2 * rinv2 * rinv2;
-    const R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
-    const R b = rinv6 * fma(R(14) * p.x, rinv6, R(-8) * p.y) * rinv2 * rinv2 + fma(R(3) * qq, rinv2, sh) * rinv3;
+    const R g = pair_g2<R>(c, rinv, rinv2, rinv6);
+    // b = (phi'' + g) / r^2 = r^-4 r^-6 (14 A r^-6 - 8 B) + r^-3 (3 qq r^-2 + sh)
+    const R b = fma(rinv2 * rinv2, rinv6 * fma(c.A14, rinv6, -c.B8), rinv3 * fma(c.q3, rinv2, c.sh));
     const R s = fma(dx, ux, fma(dy, uy, dz * uz));
     const R t = in ? b * s : R(0);
     const R ng = in ? -g : R(0);
@@ -156,7 +196,7 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, R xs, R ys, R zs, cons
       const R rinv = Tr<R>::rsq(r2);
       const R rinv2 = rinv * rinv;
       const R rinv6 = rinv2 * rinv2 * rinv2;
-      R g = pair_g<R, V4>(rinv, rinv2, rinv6, p, qq, sh, k.k2rf);
+      R g = pair_g2<R>(c, rinv, rinv2, rinv6);
       g = in ? (sgn ? -g : g) : R(0);
       a[0] = fma(g, px, a[0]);
       a[1] = fma(g, py, a[1]);
@@ -309,13 +349,18 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         }
         const V4 D = S.d[e];
         const int so = q * kCL + jj;
+        R xs[B][3];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          xs[b][0] = xi[b].x + D.x;
+          xs[b][1] = xi[b].y + D.y;
+          xs[b][2] = xi[b].z + D.z;
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (!(fl & (1 << (29 + h)))) continue;
           const int sj = so + 4 * h;
-          const V4 p = tabrow[S.t[sj]];
-          const R qq = qi * S.x[0][sj].w;
-          const R sh = fma(qq, k.drf, p.z);
+          const PairK<R> pc = pair_consts<R, MODE, V4>(k, tabrow[S.t[sj]], qi * S.x[0][sj].w);
           const R rce = h ? rcB : rcA;
 #pragma unroll
           for (int b = 0; b < B; ++b) {
@@ -328,11 +373,11 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
             }
             R* acc = (sizeof(R) == 4) ? a[b] : accd.a;
             if (ENERGY && b == 0)
-              pair_one<R, MODE, true, V4>(k, xi[b].x + D.x, xi[b].y + D.y, xi[b].z + D.z, S.x[b][sj], p, qq, sh,
-                                          rce, ei[b], ej, eps[b], acc, eacc.a);
+              pair_one<R, MODE, true, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej, eps[b],
+                                          acc, eacc.a);
             else
-              pair_one<R, MODE, false, V4>(k, xi[b].x + D.x, xi[b].y + D.y, xi[b].z + D.z, S.x[b][sj], p, qq, sh,
-                                           rce, ei[b], ej, eps[b], acc, eacc.a);
+              pair_one<R, MODE, false, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej, eps[b],
+                                           acc, eacc.a);
           }
         }
       }
@@ -407,7 +452,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
 template <class R> struct BeadsPerUnit { static constexpr int value = sizeof(R) == 4 ? 2 : 1; };
 
 template <class R, int MODE>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths,
                                                                       int n_paths, long long n_units) {
   using V4 = typename Tr<R>::V4;
   constexpr int B = BeadsPerUnit<R>::value;
