@@ -21,6 +21,7 @@
 #define MOP_PAIR_MINB 4
 #endif
 
+
 namespace mop {
 namespace {
 
@@ -170,9 +171,9 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
       e += in ? E : R(0);
     }
   } else if (MODE == 1) {
-    const R ux = ei[0] - ej[0], uy = ei[1] - ej[1], uz = ei[2] - ej[2];
     const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
     const bool in = r2 < rc2e;
+    const R ux = ei[0] - ej[0], uy = ei[1] - ej[1], uz = ei[2] - ej[2];
     const R rinv = Tr<R>::rsq(r2);
     const R rinv2 = rinv * rinv;
     const R rinv3 = rinv * rinv2;
