@@ -159,6 +159,15 @@ mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const in
 mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed,
                     void* cuda_stream);
 
+/* Graph mode of mop_step (off by default).  When on, mop_step captures one MD step of all set
+ * paths (integrator kernels plus a full V_eff + gradient evaluation, with no host
+ * synchronisation inside) into a CUDA graph on a stream of the handle, and replays it n_steps
+ * times.  The graph is captured again when the set of paths, dt, gamma or seed changes.  The
+ * pair lists keep the capacity sized by the last synchronous evaluation (with 25% headroom); if a
+ * list outgrows it during the replays, mop_step returns MOP_ERR_STATE and the steps since the
+ * last synchronous call are invalid. */
+mop_status mop_set_graph_mode(mop_handle* h, int32_t on);
+
 /* Kinetic energy sum_i m_i |v_i|^2 / 2 over all beads of `path_id` (synchronous). */
 mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke);
 

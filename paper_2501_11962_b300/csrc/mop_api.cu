@@ -45,6 +45,15 @@ struct mop_handle {
   // instrumentation
   bool profiling = false;
   cudaEvent_t ev[7] = {};
+  // CUDA-graph mode of mop_step
+  bool graph_mode = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  std::vector<int> graph_ids;
+  double graph_dt = 0.0, graph_gamma = -1.0;
+  uint64_t graph_seed = 0;
+  DevBuf<unsigned long long> step_dev;   // Philox step counter read by the integrator
+  bool step_ready = false;
 };
 
 namespace {
@@ -123,8 +132,11 @@ mop_status upload(mop_handle* h, DevBuf<T>& b, const T* src, size_t n) {
 // Evaluates the listed paths.  dev_veff/dev_grad: caller device pointers (or NULL for the
 // handle's buffers).  Enqueues everything on st; the only host synchronisation is the read of
 // the cluster and pair counts in prep_path.
+// sync = false makes the call stream-capture safe: no host synchronisation, no allocation (the
+// buffers must already have their size from an earlier synchronous call) and no host-to-device
+// copy of the path table (it must already be on the device).
 mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff, double* dev_grad,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool sync = true) {
   SysConsts& sc = h->sc;
   Launch L{st, &h->launches};
   const bool fd = h->hvp_mode == MOP_HVP_FD;
@@ -137,19 +149,19 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   for (size_t k = 0; k < ids.size(); ++k) {
     PathHost& P = h->paths[ids[k]];
     std::string err;
-    cudaError_t e = prep_path(sc, h->grid, P, margin, L, &err);
+    cudaError_t e = prep_path(sc, h->grid, P, margin, L, &err, sync);
     if (e != cudaSuccess) return fail(h, e == cudaErrorMemoryAllocation ? MOP_ERR_OOM : MOP_ERR_CUDA, "%s", err.c_str());
-    const int N = P.N, Qpad = P.n_clu * kCL;
+    const int N = P.N, Qpad = h->grid.max_clu * kCL;   // fixed slot stride (capture safe)
     const int n_force = N == 1 ? 1 : N - 1, n_hvp = N - 1;
     const size_t nq3 = 3 * (size_t)N * Qpad;
     CK(h, P.Fnb.ensure(3 * (size_t)n_force * Qpad));
     CK(h, P.F.ensure(nq3));
-    CK(h, P.eta.ensure(nq3));
+    if (h->precision == MOP_PREC_FP64) CK(h, P.eta.ensure(nq3));
     CK(h, P.eta32.ensure((size_t)N * Qpad));
     CK(h, P.Hnb.ensure(nq3));
     CK(h, P.Heta.ensure(nq3));
     CK(h, P.etamax.ensure(N));
-    CK(h, P.e_pair.ensure(P.n_clu));
+    CK(h, P.e_pair.ensure(h->grid.max_clu));
     CK(h, P.diag.ensure(8));
     CK(h, P.veff_int.ensure(1));
     CK(h, P.grad_int.ensure(3 * (size_t)N * sc.Q));
@@ -161,12 +173,13 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.n_hvp = n_hvp;
     D.Q = sc.Q;
     D.Qpad = Qpad;
-    D.n_clu = P.n_clu;
+    D.n_clu = h->grid.max_clu;
+    D.meta = P.meta.p;
     D.unit_off = units;
     D.unit_off_h = units_h;
     const int bpu = pair_beads_per_unit(h->precision);
-    units += (long long)((n_force + bpu - 1) / bpu) * P.n_clu;
-    units_h += (long long)((n_hvp + bpu - 1) / bpu) * P.n_clu;
+    units += (long long)((n_force + bpu - 1) / bpu) * h->grid.max_clu;
+    units_h += (long long)((n_hvp + bpu - 1) / bpu) * h->grid.max_clu;
     max_qpad = std::max(max_qpad, Qpad);
     max_nf = std::max(max_nf, n_force);
     max_n = std::max(max_n, N);
@@ -211,7 +224,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, h->e_bond.ensure((size_t)np * sb));
   CK(h, h->e_spring.ensure((size_t)np * ss));
   CK(h, h->d_paths.ensure(np));
-  CK(h, cudaMemcpyAsync(h->d_paths.p, pd.data(), sizeof(PathDev) * np, cudaMemcpyHostToDevice, st));
+  if (sync) CK(h, cudaMemcpyAsync(h->d_paths.p, pd.data(), sizeof(PathDev) * np, cudaMemcpyHostToDevice, st));
   auto mark = [&](int k) { return h->profiling ? cudaEventRecord(h->ev[k], st) : cudaSuccess; };
   CK(h, mark(1));
   CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
@@ -230,6 +243,8 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   h->last_pd = pd;
   return MOP_OK;
 }
+
+void drop_graph(mop_handle* h);
 
 mop_status select_paths(mop_handle* h, int32_t path_id, std::vector<int>* ids) {
   ids->clear();
@@ -437,6 +452,9 @@ mop_status mop_destroy(mop_handle* h) {
   h->inc.release(); h->incp.release(); h->incpf.release(); h->tab.release(); h->tab64.release();
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+  h->step_dev.release();
   h->d_one.release(); h->counts.release();
   h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release();
   for (auto& P : h->paths) {
@@ -489,6 +507,7 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
   CK(h, cudaGetLastError());
   CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
   if (!dev) CK(h, cudaStreamSynchronize(st));
+  if (P.N != n_beads) drop_graph(h);
   P.N = n_beads;
   P.set = true;
   P.have_grad = false;
@@ -552,7 +571,7 @@ mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* 
   if (!P.set || P.n_clu == 0 || !P.F.p) return fail(h, MOP_ERR_STATE, "path %d has no evaluation", path_id);
   CK(h, cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const int N = P.N, Qpad = P.n_clu * kCL;
+  const int N = P.N, Qpad = h->grid.max_clu * kCL;
   const void* f;
   int rows, fmt;
   const bool mixed = h->precision == MOP_PREC_MIXED;
@@ -627,6 +646,40 @@ mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const in
   return MOP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// one MD step of every listed path: B (half kick), A O A (drift with Langevin noise), evaluation
+// of dV_eff/dR at the new positions, B; then the Philox step counter advances
+mop_status step_body(mop_handle* h, const std::vector<int>& ids, double dt_md, double gamma, uint64_t seed,
+                     cudaStream_t st, bool sync) {
+  Launch L{st, &h->launches};
+  const double kT = kBoltz * h->temperature;
+  for (int id : ids) {
+    PathHost& P = h->paths[id];
+    CK(h, launch_kick(h->sc, P.vel.p, P.grad_int.p, P.N, 0.5 * dt_md, L));
+    CK(h, launch_drift(h->sc, P.x64.p, P.vel.p, P.x32.p, P.N, dt_md, gamma, kT, seed, h->step_dev.p, L));
+  }
+  mop_status s = evaluate(h, ids, nullptr, nullptr, st, sync);
+  if (s) return s;
+  for (int id : ids) {
+    PathHost& P = h->paths[id];
+    CK(h, launch_kick(h->sc, P.vel.p, P.grad_int.p, P.N, 0.5 * dt_md, L));
+  }
+  CK(h, launch_step_inc(h->step_dev.p, L));
+  return MOP_OK;
+}
+
+void drop_graph(mop_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
 mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed, void* cuda_stream) {
   if (!h) return MOP_ERR_ARG;
   h->err.clear();
@@ -637,25 +690,70 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
   if (s) return s;
   CK(h, cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  Launch L{st, &h->launches};
+  CK(h, h->step_dev.ensure(1));
+  if (!h->step_ready) {
+    CK(h, cudaMemsetAsync(h->step_dev.p, 0, sizeof(unsigned long long), st));
+    h->step_ready = true;
+  }
+  // the first evaluation at the current positions is synchronous: it sizes the pair lists
   bool need = false;
   for (int id : ids) need |= !h->paths[id].have_grad;
   if (need && (s = evaluate(h, ids, nullptr, nullptr, st))) return s;
-  const double kT = kBoltz * h->temperature;
-  for (int k = 0; k < n_steps; ++k) {
-    for (int id : ids) {
-      PathHost& P = h->paths[id];
-      CK(h, launch_kick(h->sc, P.vel.p, P.grad_int.p, P.N, 0.5 * dt_md, L));
-      CK(h, launch_drift(h->sc, P.x64.p, P.vel.p, P.x32.p, P.N, dt_md, gamma, kT, seed, h->step_count, 0, L));
-    }
-    if ((s = evaluate(h, ids, nullptr, nullptr, st))) return s;
-    for (int id : ids) {
-      PathHost& P = h->paths[id];
-      CK(h, launch_kick(h->sc, P.vel.p, P.grad_int.p, P.N, 0.5 * dt_md, L));
-    }
-    ++h->step_count;
+  if (!h->graph_mode) {
+    for (int k = 0; k < n_steps; ++k)
+      if ((s = step_body(h, ids, dt_md, gamma, seed, st, true))) return s;
+    CK(h, cudaStreamSynchronize(st));
+    return MOP_OK;
   }
+  // graph mode: capture one step (on a stream of the handle; capture is not allowed on the
+  // legacy default stream) and replay it n_steps times
+  if (!h->graph_stream) CK(h, cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
   CK(h, cudaStreamSynchronize(st));
+  cudaStream_t gs = h->graph_stream;
+  if (!h->graph_exec || ids != h->graph_ids || dt_md != h->graph_dt || gamma != h->graph_gamma ||
+      seed != h->graph_seed) {
+    drop_graph(h);
+    // a synchronous evaluation uploads the path table the captured step reuses
+    if ((s = evaluate(h, ids, nullptr, nullptr, gs))) return s;
+    CK(h, cudaStreamSynchronize(gs));
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    s = step_body(h, ids, dt_md, gamma, seed, gs, false);
+    cudaError_t ce = cudaStreamEndCapture(gs, &g);
+    if (s) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    CK(h, ce);
+    ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, ce);
+    h->graph_ids = ids;
+    h->graph_dt = dt_md;
+    h->graph_gamma = gamma;
+    h->graph_seed = seed;
+  }
+  for (int k = 0; k < n_steps; ++k) CK(h, cudaGraphLaunch(h->graph_exec, gs));
+  CK(h, cudaStreamSynchronize(gs));
+  // a list that outgrew its capacity during the replays invalidates those steps
+  for (int id : ids) {
+    int flag = 0;
+    CK(h, cudaMemcpy(&flag, h->paths[id].meta.p + 3, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      drop_graph(h);
+      h->paths[id].sized = false;
+      return fail(h, MOP_ERR_STATE,
+                  "pair list of path %d outgrew its capacity during graph replay; steps since the last "
+                  "synchronous call are invalid (set the path again)", id);
+    }
+  }
+  return MOP_OK;
+}
+
+mop_status mop_set_graph_mode(mop_handle* h, int32_t on) {
+  if (!h) return MOP_ERR_ARG;
+  h->graph_mode = on != 0;
+  if (!h->graph_mode) drop_graph(h);
   return MOP_OK;
 }
 
@@ -712,6 +810,7 @@ mop_status mop_count_pairs(mop_handle* h, int32_t path_id, int64_t* unique, int6
   int dummy = 0;
   Launch L{nullptr, &dummy};
   CK(h, launch_count_pairs(h->sc, h->d_one.p, 1, (long long)D.n_force * D.n_clu, h->counts.p, h->num_sms, L));
+  (void)0;
   unsigned long long c[2];
   CK(h, cudaMemcpy(c, h->counts.p, sizeof(c), cudaMemcpyDeviceToHost));
   *unique = (int64_t)(c[0] / 2);

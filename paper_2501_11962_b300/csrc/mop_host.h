@@ -47,7 +47,8 @@ struct PathHost {
   int N = 0;
   int n_clu = 0;
   int cap = 256;          // list entries reserved per i-cluster
-  int max_count = 0;      // largest list of the last build
+  int max_count = 0;      // largest list of the last synchronous build
+  bool sized = false;     // cap has been checked on the host at least once
   // state
   DevBuf<float> x32;      // [N][Q][3]
   DevBuf<double> x64;     // [N][Q][3] master positions (FP64)
@@ -66,7 +67,7 @@ struct PathHost {
   DevBuf<int> lcnt;
   DevBuf<float4> abox;    // [max_slots] union sphere of each atom over the beads
   DevBuf<unsigned> ctype; // [max_clu] packed LJ types
-  DevBuf<int> meta;       // [4]: n_clu, n_ent, overflow, spare
+  DevBuf<int> meta;       // [4]: clusters, (scan total), largest list, sticky overflow flag
   DevBuf<float4> xq;
   DevBuf<double4_32a> xq64;
   DevBuf<int4> ent;
@@ -91,8 +92,10 @@ struct Launch {
 };
 
 // --- mop_prep.cu: spatial sort, clusters, local coordinates, cluster-pair list ------------
+// sync = false: no host synchronisation (stream-capture safe); reuses the capacity of the last
+// synchronous build and records an overflow in meta[3].
 cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L,
-                      std::string* err);
+                      std::string* err, bool sync);
 
 // --- mop_pair.cu: pair kernels over every unit of every path -------------------------------
 // mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP.  A unit is one i-cluster for
@@ -116,8 +119,10 @@ cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_pat
                           const double* e_bond, int e_bond_stride, int n_e1_blocks,
                           const double* e_spring, int e_spring_stride, int n_e2_blocks);
 cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, int N, double half_dt, Launch L);
+// the Philox step counter is read from device memory (*step), so a captured step can be replayed
 cudaError_t launch_drift(const SysConsts& sc, double* x64, double* vel, float* x32, int N, double dt,
-                         double gamma, double kT, uint64_t seed, uint64_t step, int path_bead0, Launch L);
+                         double gamma, double kT, uint64_t seed, const unsigned long long* step, Launch L);
+cudaError_t launch_step_inc(unsigned long long* step, Launch L);
 cudaError_t launch_kinetic(const SysConsts& sc, const double* vel, int N, double* out, Launch L);
 
 }  // namespace mop

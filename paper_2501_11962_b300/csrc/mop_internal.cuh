@@ -52,7 +52,10 @@ struct SysConsts {
 
 // Device view of one path of a multi-path launch.
 struct PathDev {
+  // Qpad is the slot stride of every [bead][slot] array (8 x the cluster-count upper bound);
+  // n_clu is that upper bound; the clusters of the current sort are meta[0] <= n_clu.
   int N, n_force, n_hvp, Q, Qpad, n_clu;
+  const int* meta;
   long long unit_off;      // first force-kernel unit of this path
   long long unit_off_h;    // first HVP-kernel unit of this path
   int blk_off_e1, blk_off_e2;

@@ -478,6 +478,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pai
     const long long v = u - (MODE == 0 ? P.unit_off : P.unit_off_h);
     const int n0 = (int)(v % ngrp) * B;
     const int ci = (int)(v / ngrp);
+    if (ci >= __ldg(&P.meta[0])) continue;   // past the clusters of the current sort
     if (MODE == 0 && n0 == 0) pair_unit<R, 0, true, B>(sc, tab, S, P, n0, n_pass, ci, lane);
     else pair_unit<R, MODE, false, B>(sc, tab, S, P, n0, n_pass, ci, lane);
   }
@@ -513,6 +514,7 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
     const PathDev& P = paths[p];
     const long long v = u - P.unit_off;
     const int n = (int)(v % P.n_force), ci = (int)(v / P.n_force);
+    if (ci >= P.meta[0]) continue;
     const int i = lane & 7, jj = lane >> 3;
     const size_t bo = (size_t)n * P.Qpad;
     const bool vi = P.perm[ci * kCL + i] >= 0;

@@ -532,7 +532,7 @@ __global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const d
   const int p = blockIdx.x;
   const PathDev& P = paths[p];
   double up = 0.0, ub = 0.0, es = 0.0;
-  for (int k = threadIdx.x; k < P.n_clu; k += blockDim.x) up += P.e_pair[k];
+  for (int k = threadIdx.x; k < P.meta[0]; k += blockDim.x) up += P.e_pair[k];
   for (int k = threadIdx.x; k < nb1; k += blockDim.x) ub += e_bond[(size_t)p * sb + k];
   for (int k = threadIdx.x; k < nb2; k += blockDim.x) es += e_spring[(size_t)p * ss + k];
   up = block_sum<kRedBlock>(up, sh);
@@ -575,9 +575,10 @@ __global__ void k_kick(int Q, const double* mass, double* vel, const double* gra
 }
 
 __global__ void k_drift(int Q, int N, const double* mass, double* x64, double* vel, float* x32, double dt, double c1,
-                        double c2, double kT, uint64_t seed, uint64_t step) {
+                        double c2, double kT, uint64_t seed, const unsigned long long* step_ptr) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (atoms, beads)
   if (a >= Q) return;
+  const unsigned long long step = *step_ptr;
   const int n = blockIdx.y;
   const size_t t = (size_t)n * Q + a;
   double* x = x64 + 3 * t;
@@ -665,8 +666,16 @@ cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, in
   return cudaGetLastError();
 }
 
+__global__ void k_step_inc(unsigned long long* step) { *step += 1ull; }
+
+cudaError_t launch_step_inc(unsigned long long* step, Launch L) {
+  k_step_inc<<<1, 1, 0, L.st>>>(step);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_drift(const SysConsts& sc, double* x64, double* vel, float* x32, int N, double dt, double gamma,
-                         double kT, uint64_t seed, uint64_t step, int, Launch L) {
+                         double kT, uint64_t seed, const unsigned long long* step, Launch L) {
   const double c1 = gamma > 0.0 ? exp(-gamma * dt) : 1.0;
   const double c2 = gamma > 0.0 ? sqrt(1.0 - c1 * c1) : 0.0;
   k_drift<<<dim3(nblk(sc.Q, kRedBlock), N), kRedBlock, 0, L.st>>>(sc.Q, N, sc.mass, x64, vel, x32, dt, c1, c2, kT,

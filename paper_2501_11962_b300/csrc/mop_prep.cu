@@ -174,12 +174,11 @@ template <bool F64>
 __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
                                const int* perm, const int* meta, int max_slots, const double* center, float4* xq,
                                double4_32a* xq64, int* ts, float4* eta32, double* eta64) {
-  const int Qpad = meta[0] * kCL;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (slots, beads)
   const int b = blockIdx.y;
-  if (s >= Qpad) return;
+  if (s >= meta[0] * kCL) return;
   const int a = perm[s];
-  const size_t o = (size_t)b * Qpad + s;
+  const size_t o = (size_t)b * max_slots + s;            // fixed slot stride
   if (a < 0) {
     const double dmy = (double)kDummyCoord + 3.0 * (s & (kCL - 1));
     if (F64) xq64[o] = make_double4_32a(dmy, dmy, dmy, 0.0);
@@ -435,6 +434,7 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
   if (lane == 0) {
     lcnt[ci] = min(count, cap);
     atomicMax(&meta[2], count);
+    if (count > cap) atomicOr(&meta[3], 1);   // sticky: cleared only by a synchronous rebuild
   }
 }
 
@@ -456,7 +456,8 @@ inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
     MOP_CK(cudaGetLastError());                           \
   } while (0)
 
-cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L, std::string* err) {
+cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L, std::string* err,
+                      bool sync) {
   const int Q = sc.Q, N = P.N;
   const int ncol = g.ncx * g.ncy;
   const int max_clu = g.max_clu;
@@ -499,7 +500,7 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_CK(cudaMemsetAsync(P.perm.p, 0xff, sizeof(int) * max_slots, st));
   MOP_CK(cudaMemsetAsync(P.emax.p, 0, sizeof(unsigned) * 3, st));
   MOP_CK(cudaMemsetAsync(P.bincnt.p, 0, sizeof(int) * nbins, st));
-  MOP_CK(cudaMemsetAsync(P.meta.p, 0, sizeof(int) * 4, st));
+  MOP_CK(cudaMemsetAsync(P.meta.p, 0, sizeof(int) * 3, st));   // meta[3] (overflow) is sticky
 
   const int bs = 256;
   k_ref_columns<<<nblk(Q, bs), bs, 0, st>>>(sc, x32, x64, g.ncx, g.ncy, g.wx, g.wy, P.ref.p, P.colid.p, P.colcnt.p);
@@ -539,12 +540,13 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_KL();
   k_cluster_types<<<nblk(max_clu, bs), bs, 0, st>>>(P.meta.p, P.ts.p, P.ctype.p);
   MOP_KL();
+  if (!sync && !P.sized) sync = true;   // the first build must size the list on the host
   for (int attempt = 0; attempt < 3; ++attempt) {
     const size_t cap_total = (size_t)max_clu * P.cap;
     MOP_CK(P.ent.ensure(cap_total));
     MOP_CK(P.emask.ensure(cap_total));
     if (f64) MOP_CK(P.ent64.ensure(cap_total));
-    MOP_CK(cudaMemsetAsync(P.meta.p + 2, 0, sizeof(int), st));
+    if (sync) MOP_CK(cudaMemsetAsync(P.meta.p + 2, 0, 2 * sizeof(int), st));
     const int blocks = nblk(max_clu, 4);
     if (f64)
       k_pair_list<true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
@@ -557,15 +559,22 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                                                  P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
                                                  P.ent.p, nullptr, P.emask.p, P.meta.p);
     MOP_KL();
+    if (!sync) return cudaSuccess;   // capture-safe: an overflow shows up in the sticky flag
     int meta[4];
     MOP_CK(cudaMemcpyAsync(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost, st));
     MOP_CK(cudaStreamSynchronize(st));
     P.n_clu = meta[0];
     if (meta[2] <= P.cap) {
       P.max_count = meta[2];
-      return cudaSuccess;
+      // keep a quarter of headroom so that later steps (graph replays) rarely overflow
+      if (P.max_count + P.max_count / 4 > P.cap) P.cap = (P.max_count + P.max_count / 4 + 31) / 32 * 32;
+      else {
+        P.sized = true;
+        return cudaSuccess;
+      }
+    } else {
+      P.cap = (meta[2] + meta[2] / 4 + 31) / 32 * 32;   // grow and rebuild
     }
-    P.cap = (meta[2] + meta[2] / 4 + 31) / 32 * 32;   // grow and rebuild
   }
   if (err) *err = "pair list did not fit after growing its capacity";
   return cudaErrorMemoryAllocation;

@@ -24,7 +24,7 @@ MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_veff_and_grad", "mop_get_field",
            "mop_get_energies", "mop_add_bias", "mop_step", "mop_kinetic_energy", "mop_last_launch_count",
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
-           "mop_last_error")
+           "mop_set_graph_mode", "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -83,6 +83,7 @@ def load(build_if_needed: bool = True):
     L.mop_last_pass_ms.argtypes = [p, p, i32]
     L.mop_count_pairs.argtypes = [p, i32, p, p]
     L.mop_spring_energy_noalloc.argtypes = [p, p, i32, i32, d, d, p, p]
+    L.mop_set_graph_mode.argtypes = [p, i32]
     L.mop_last_error.argtypes = [p]
     L.mop_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -220,6 +221,9 @@ class Engine:
         else:
             st = self.L.mop_add_bias(self.h, None, 0, None, 0, s_center, height, width, path_id, 0)
         self._check(st, "mop_add_bias")
+
+    def set_graph_mode(self, on: bool = True):
+        self._check(self.L.mop_set_graph_mode(self.h, int(on)), "mop_set_graph_mode")
 
     def step(self, n_steps: int, dt: float, gamma: float = 0.0, seed: int = 1):
         self._check(self.L.mop_step(self.h, n_steps, dt, gamma, seed, None), "mop_step")
