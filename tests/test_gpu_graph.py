@@ -25,9 +25,9 @@ def make_engine(graph):
 def test_graph_step_matches_eager_steps():
     eager = make_engine(False)
     graph = make_engine(True)
-    eager.step(6, 5e-4, 2.0, seed=9)
-    graph.step(4, 5e-4, 2.0, seed=9)
-    graph.step(2, 5e-4, 2.0, seed=9)       # same graph, counter continues on the device
+    eager.step(6, 2e-5, 2.0, seed=9)
+    graph.step(4, 2e-5, 2.0, seed=9)
+    graph.step(2, 2e-5, 2.0, seed=9)       # same graph, counter continues on the device
     for p in (0, 1, 2):
         a, b = eager.get_path(p), graph.get_path(p)
         assert np.array_equal(a, b), p
@@ -39,9 +39,19 @@ def test_graph_step_matches_eager_steps():
 
 def test_graph_recaptures_on_new_parameters():
     eng = make_engine(True)
-    eng.step(2, 5e-4, 2.0, seed=9)
+    eng.step(2, 2e-5, 2.0, seed=9)
     x1 = eng.get_path(1)
-    eng.step(2, 2.5e-4, 0.0, seed=9)       # new dt and gamma: a new graph
+    eng.step(2, 1e-5, 0.0, seed=9)       # new dt and gamma: a new graph
     x2 = eng.get_path(1)
     assert not np.array_equal(x1, x2)
     assert np.isfinite(x2).all()
+
+
+def test_graph_replay_reports_list_overflow():
+    # from these unrelaxed structures a large step moves atoms far enough that the lists outgrow
+    # the capacity sized before the capture; mop_step must say so rather than return bad steps
+    eng = make_engine(True)
+    with pytest.raises(mop.MopError) as ei:
+        for _ in range(20):
+            eng.step(5, 5e-4, 2.0, seed=9)
+    assert ei.value.status == mop.MOP_ERR_STATE
