@@ -168,6 +168,24 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
  * last synchronous call are invalid. */
 mop_status mop_set_graph_mode(mop_handle* h, int32_t on);
 
+/* Geometry of the neighbour search, chosen by the autotuner.  col_factor scales the x-y width of
+ * the columns that are cut into 8-atom clusters (1 = near-cubic clusters); bin_factor sets the
+ * bin edge of the cluster-pair search in units of rc.  Neither changes any result, only the
+ * number of pairs the kernels evaluate and the cost of the list build. */
+typedef struct {
+  double col_factor;  /* default 1.0 */
+  double bin_factor;  /* default 0.5 */
+} mop_tuning;
+
+mop_status mop_set_tuning(mop_handle* h, const mop_tuning* t);
+mop_status mop_get_tuning(const mop_handle* h, mop_tuning* t);
+
+/* Times full evaluations of path `path_id` for col_factor in {0.85, 1, 1.2} and bin_factor in
+ * {0.5, 1} (CUDA events, a warm-up call and two timed calls each), keeps the fastest setting on
+ * the handle and returns it with its time per evaluation in ms (either output may be NULL).
+ * Synchronous.  Errors: MOP_ERR_STATE (path not set), MOP_ERR_CUDA. */
+mop_status mop_autotune(mop_handle* h, int32_t path_id, mop_tuning* best, double* best_ms);
+
 /* Kinetic energy sum_i m_i |v_i|^2 / 2 over all beads of `path_id` (synchronous). */
 mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke);
 

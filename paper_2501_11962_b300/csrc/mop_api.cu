@@ -40,6 +40,8 @@ struct mop_handle {
   DevBuf<PathDev> d_paths, d_one;
   DevBuf<double> e_bond, e_spring, scratch;
   DevBuf<unsigned long long> counts;
+  mop_tuning tuning{1.0, 0.5};
+  double box[3] = {0.0, 0.0, 0.0};
   std::vector<int> last_ids;
   std::vector<PathDev> last_pd;
   // instrumentation
@@ -246,6 +248,24 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
 
 void drop_graph(mop_handle* h);
 
+// column grid of the cluster sort and bins of the pair search for the current tuning
+void make_grid(mop_handle* h) {
+  Grid& g = h->grid;
+  const double* box = h->box;
+  const int Q = h->sc.Q;
+  const double vol = box[0] * box[1] * box[2];
+  const double w = h->tuning.col_factor * std::cbrt(kCL * vol / Q);
+  g.ncx = std::max(1, (int)std::lround(box[0] / w));
+  g.ncy = std::max(1, (int)std::lround(box[1] / w));
+  g.wx = box[0] / g.ncx;
+  g.wy = box[1] / g.ncy;
+  g.max_clu = (Q + kCL - 1) / kCL + g.ncx * g.ncy;
+  for (int k = 0; k < 3; ++k) {
+    g.nb[k] = std::max(1, (int)std::floor(box[k] / (h->tuning.bin_factor * h->sc.rc)));
+    g.bw[k] = box[k] / g.nb[k];
+  }
+}
+
 mop_status select_paths(mop_handle* h, int32_t path_id, std::vector<int>* ids) {
   ids->clear();
   if (path_id >= 0) {
@@ -427,19 +447,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.tab = h->tab.p;
   sc.tab64 = h->tab64.p;
 
-  // column grid of the cluster sort (near-cubic clusters of 8) and bins of the pair search
-  Grid& g = h->grid;
-  const double vol = d->box[0] * d->box[1] * d->box[2];
-  const double w = std::cbrt(kCL * vol / Q);
-  g.ncx = std::max(1, (int)std::lround(d->box[0] / w));
-  g.ncy = std::max(1, (int)std::lround(d->box[1] / w));
-  g.wx = d->box[0] / g.ncx;
-  g.wy = d->box[1] / g.ncy;
-  g.max_clu = (Q + kCL - 1) / kCL + g.ncx * g.ncy;
-  for (int k = 0; k < 3; ++k) {
-    g.nb[k] = std::max(1, (int)std::floor(d->box[k] / (0.5 * rc)));
-    g.bw[k] = d->box[k] / g.nb[k];
-  }
+  for (int k = 0; k < 3; ++k) h->box[k] = d->box[k];
+  make_grid(h);
   *out = h;
   return MOP_OK;
 }
@@ -747,6 +756,67 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
                   "synchronous call are invalid (set the path again)", id);
     }
   }
+  return MOP_OK;
+}
+
+mop_status mop_set_tuning(mop_handle* h, const mop_tuning* t) {
+  if (!h || !t) return MOP_ERR_ARG;
+  if (!(t->col_factor >= 0.25 && t->col_factor <= 4.0) || !(t->bin_factor >= 0.2 && t->bin_factor <= 4.0))
+    return fail(h, MOP_ERR_ARG, "tuning factors out of range");
+  h->tuning = *t;
+  make_grid(h);
+  drop_graph(h);
+  for (auto& P : h->paths) {
+    P.sized = false;     // strides and list shapes change: rebuild synchronously
+    P.have_grad = false;
+  }
+  return MOP_OK;
+}
+
+mop_status mop_get_tuning(const mop_handle* h, mop_tuning* t) {
+  if (!h || !t) return MOP_ERR_ARG;
+  *t = h->tuning;
+  return MOP_OK;
+}
+
+mop_status mop_autotune(mop_handle* h, int32_t path_id, mop_tuning* best, double* best_ms) {
+  if (!h) return MOP_ERR_ARG;
+  std::vector<int> ids;
+  mop_status s = select_paths(h, path_id, &ids);
+  if (s) return s;
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0, e1;
+  CK(h, cudaEventCreate(&e0));
+  CK(h, cudaEventCreate(&e1));
+  const double cols[] = {0.85, 1.0, 1.2};
+  const double bins[] = {0.5, 1.0};
+  mop_tuning keep = h->tuning, win = h->tuning;
+  double win_ms = 1e300;
+  for (double c : cols)
+    for (double b : bins) {
+      const mop_tuning t{c, b};
+      if ((s = mop_set_tuning(h, &t))) break;
+      if ((s = evaluate(h, ids, nullptr, nullptr, st))) break;   // warm-up, sizes the lists
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && !s; ++r) s = evaluate(h, ids, nullptr, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (s) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 2.0 < win_ms) {
+        win_ms = ms / 2.0;
+        win = t;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  mop_status s2 = mop_set_tuning(h, s ? &keep : &win);
+  if (s) return s;
+  if (s2) return s2;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
   return MOP_OK;
 }
 

@@ -24,7 +24,7 @@ MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_veff_and_grad", "mop_get_field",
            "mop_get_energies", "mop_add_bias", "mop_step", "mop_kinetic_energy", "mop_last_launch_count",
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
-           "mop_set_graph_mode", "mop_last_error")
+           "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -32,6 +32,10 @@ class MopError(RuntimeError):
         self.status = status
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
         super().__init__(f"{name}: {msg}")
+
+
+class mop_tuning(C.Structure):
+    _fields_ = [("col_factor", C.c_double), ("bin_factor", C.c_double)]
 
 
 class mop_system_desc(C.Structure):
@@ -84,6 +88,9 @@ def load(build_if_needed: bool = True):
     L.mop_count_pairs.argtypes = [p, i32, p, p]
     L.mop_spring_energy_noalloc.argtypes = [p, p, i32, i32, d, d, p, p]
     L.mop_set_graph_mode.argtypes = [p, i32]
+    L.mop_set_tuning.argtypes = [p, p]
+    L.mop_get_tuning.argtypes = [p, p]
+    L.mop_autotune.argtypes = [p, i32, p, p]
     L.mop_last_error.argtypes = [p]
     L.mop_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -221,6 +228,21 @@ class Engine:
         else:
             st = self.L.mop_add_bias(self.h, None, 0, None, 0, s_center, height, width, path_id, 0)
         self._check(st, "mop_add_bias")
+
+    def tuning(self) -> dict:
+        t = mop_tuning()
+        self._check(self.L.mop_get_tuning(self.h, C.byref(t)), "mop_get_tuning")
+        return dict(col_factor=t.col_factor, bin_factor=t.bin_factor)
+
+    def set_tuning(self, col_factor: float, bin_factor: float):
+        t = mop_tuning(col_factor, bin_factor)
+        self._check(self.L.mop_set_tuning(self.h, C.byref(t)), "mop_set_tuning")
+
+    def autotune(self, path_id: int = 0):
+        """Runs mop_autotune; returns (tuning dict, ms per evaluation)."""
+        t, ms = mop_tuning(), C.c_double()
+        self._check(self.L.mop_autotune(self.h, path_id, C.byref(t), C.byref(ms)), "mop_autotune")
+        return dict(col_factor=t.col_factor, bin_factor=t.bin_factor), ms.value
 
     def set_graph_mode(self, on: bool = True):
         self._check(self.L.mop_set_graph_mode(self.h, int(on)), "mop_set_graph_mode")

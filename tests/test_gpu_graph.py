@@ -55,3 +55,18 @@ def test_graph_replay_reports_list_overflow():
         for _ in range(20):
             eng.step(5, 5e-4, 2.0, seed=9)
     assert ei.value.status == mop.MOP_ERR_STATE
+
+
+def test_autotune_keeps_results():
+    w = workload(2, n_beads=8)
+    eng = mop.Engine(w.system)
+    eng.set_path(0, w.paths[0])
+    v0, g0 = eng.veff_and_grad(0)
+    best, ms = eng.autotune(0)
+    assert best["col_factor"] in (0.85, 1.0, 1.2) and best["bin_factor"] in (0.5, 1.0) and ms > 0
+    assert eng.tuning() == best
+    for c, b in ((0.85, 1.0), (1.2, 0.5)):
+        eng.set_tuning(c, b)
+        v, g = eng.veff_and_grad(0)
+        assert abs(v[0] - v0[0]) / abs(v0[0]) < 1e-6
+        assert np.linalg.norm(g - g0) / np.linalg.norm(g0) < 1e-5
