@@ -205,6 +205,13 @@ mop_status mop_last_pass_ms(mop_handle* h, float* out, int32_t n);
  * included).  Synchronous. */
 mop_status mop_count_pairs(mop_handle* h, int32_t path_id, int64_t* unique, int64_t* listed);
 
+/* Measured FP32 throughput of `device` in TFLOP/s (FFMA = 2 flops): a kernel of independent
+ * dependent-FMA chains over a grid of SMs x resident blocks, best of three timed launches after
+ * a warm-up.  No counterpart in the paper; the pair kernels' roofline is quoted against it
+ * beside the nominal lanes x maximum clock figure.  Synchronous; allocates and frees a small
+ * buffer.  Errors: MOP_ERR_ARG (NULL output), MOP_ERR_OOM, MOP_ERR_CUDA. */
+mop_status mop_measure_fp32_peak(int32_t device, double* tflops);
+
 /* Spring energy without any device allocation.  No counterpart in the paper: this is a service
  * for callers that cannot allocate device memory, for example code that runs inside a CUDA
  * graph that another framework captures and replays, or a plug-in whose host application owns

@@ -24,7 +24,8 @@ MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_veff_and_grad", "mop_get_field",
            "mop_get_energies", "mop_add_bias", "mop_step", "mop_kinetic_energy", "mop_last_launch_count",
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
-           "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_last_error")
+           "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_measure_fp32_peak",
+           "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -272,6 +273,16 @@ class Engine:
         u, l = np.zeros(1, np.int64), np.zeros(1, np.int64)
         self._check(self.L.mop_count_pairs(self.h, path_id, _np_ptr(u), _np_ptr(l)), "mop_count_pairs")
         return int(u[0]), int(l[0])
+
+
+def measure_fp32_peak(device: int = 0) -> float:
+    """Measured FP32 FMA throughput of `device` in TFLOP/s (mop_measure_fp32_peak)."""
+    L = load()
+    t = np.zeros(1, np.float64)
+    st = L.mop_measure_fp32_peak(int(device), _np_ptr(t))
+    if st != 0:
+        raise MopError(st, "mop_measure_fp32_peak")
+    return float(t[0])
 
 
 def _autograd_function():
