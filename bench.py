@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--beads", type=int, default=None)
     ap.add_argument("--no-fd", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default neighbour-search geometry")
     return ap.parse_args()
 
 
@@ -203,7 +204,9 @@ def run_ours(args, world, rank, local):
     eng = mop.Engine(w.system, precision=prec, device=local)
     Xd = torch.tensor(X, device=dev)
     eng.set_path(0, Xd)
-    tuned, tuned_ms = eng.autotune(0)           # neighbour-search geometry (not timed)
+    tuned = eng.tuning()
+    if not args.no_tune:
+        tuned, _ = eng.autotune(0)              # neighbour-search geometry (not timed)
     eng.set_profiling(True)
     veff = torch.empty(1, dtype=torch.float64, device=dev)
     grad = torch.empty((N, Q, 3), dtype=torch.float64, device=dev)

@@ -163,6 +163,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.Hnb.ensure(nq3));
     CK(h, P.Heta.ensure(nq3));
     CK(h, P.etamax.ensure(N));
+    if (h->precision == MOP_PREC_MIXED) CK(h, P.jacc.ensure(nq3));
     CK(h, P.e_pair.ensure(h->grid.max_clu));
     CK(h, P.diag.ensure(8));
     CK(h, P.veff_int.ensure(1));
@@ -205,6 +206,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.Hnb = P.Hnb.p;
     D.Heta = P.Heta.p;
     D.etamax = P.etamax.p;
+    D.jacc = h->precision == MOP_PREC_MIXED ? P.jacc.p : nullptr;
     D.e_pair = P.e_pair.p;
     D.grad = dev_grad ? dev_grad + goff : P.grad_int.p;
     goff += 3 * (size_t)N * sc.Q;
@@ -228,12 +230,27 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, h->d_paths.ensure(np));
   if (sync) CK(h, cudaMemcpyAsync(h->d_paths.p, pd.data(), sizeof(PathDev) * np, cudaMemcpyHostToDevice, st));
   auto mark = [&](int k) { return h->profiling ? cudaEventRecord(h->ev[k], st) : cudaSuccess; };
+  // the half-list pair kernels add j-side sums into zeroed fixed-point accumulators
+  auto clear_jacc = [&](bool hvp) -> cudaError_t {
+    for (const PathDev& D : pd) {
+      if (!D.jacc) continue;
+      const size_t rows = hvp ? (size_t)D.n_hvp : (size_t)D.n_force;
+      if (rows == 0) continue;
+      cudaError_t e = cudaMemsetAsync(D.jacc, 0, sizeof(unsigned long long) * 3 * rows * D.Qpad, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
   CK(h, mark(1));
+  CK(h, clear_jacc(false));
   CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
   CK(h, mark(2));
   CK(h, launch_e1(sc, h->d_paths.p, np, max_qpad, max_nf, L, h->e_bond.p, nbx));
   CK(h, mark(3));
-  if (units_h > 0) CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+  if (units_h > 0) {
+    CK(h, clear_jacc(true));
+    CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+  }
   CK(h, mark(4));
   CK(h, launch_e2(sc, h->d_paths.p, np, max_qpad, max_n, L, h->e_spring.p, nbx));
   CK(h, mark(5));
@@ -474,7 +491,7 @@ mop_status mop_destroy(mop_handle* h) {
     P.cwrap.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
-    P.eta32.release(); P.etamax.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
+    P.eta32.release(); P.etamax.release(); P.jacc.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
     P.gA.release(); P.gB.release(); P.gc.release(); P.gh.release(); P.gw.release();
   }
   delete h;

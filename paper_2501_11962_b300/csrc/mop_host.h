@@ -77,6 +77,7 @@ struct PathHost {
   DevBuf<double> Fnb, F, eta, Hnb, Heta, grad_int;
   DevBuf<float4> eta32;
   DevBuf<unsigned> etamax;
+  DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
   // bias
   std::vector<int> hA, hB;

@@ -21,6 +21,13 @@ constexpr int kRedBlock = 256;    // threads of the elementwise kernels
 constexpr double kCoulombF = 138.935458;   // kJ mol^-1 nm e^-2
 constexpr double kBoltz = 0.0083144626;    // kJ mol^-1 K^-1
 constexpr float kDummyCoord = 1.0e5f;      // padding slots sit far outside every cutoff
+// list entry word x: j-cluster index | self-entry flag << 28 | half mask << 29 | exclusions << 31
+constexpr int kCluMask = 0x0fffffff;
+constexpr int kSelfFlag = 1 << 28;
+// j-side sums of the half-list pair kernels are fixed point with 23 fractional bits in int64:
+// integer addition makes the atomics order-independent, so results stay bitwise reproducible
+constexpr float kFixScale = 8388608.0f;           // 2^23
+constexpr float kFixInv = 1.0f / 8388608.0f;
 
 // System-wide constants, passed by value to kernels.
 struct SysConsts {
@@ -69,7 +76,7 @@ struct PathDev {
   const int* lcnt;          // list length of each i-cluster
   int cap;                  // entries of cluster ci start at ci * cap
   const unsigned* ctype;    // packed LJ types of each cluster (4 bits per atom)
-  const int4* ent;          // x = cj | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
+  const int4* ent;          // x = cj | self << 28 | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
   const double4_32a* ent64;
   const unsigned long long* emask;
   // FP64 mode: [N][Qpad][3] doubles.  Mixed mode views of the same buffers: Fnb and F as
@@ -81,6 +88,9 @@ struct PathDev {
   double* Hnb;
   double* Heta;
   unsigned* etamax;        // [N] float bits of max_i |eta_i|
+  // mixed mode: the list holds each cluster pair once and the pair kernels add the j-side sums
+  // here, fixed point (kFixScale), [n_pass][Qpad][3]; NULL in FP64 mode (full list)
+  unsigned long long* jacc;
   double* e_pair;          // [n_clu]
   double* grad;            // [N][Q][3] caller order
   // bias
@@ -196,6 +206,14 @@ __device__ __forceinline__ double widen(float x) {
 
 __device__ __forceinline__ double aligned_coord(double v, double ref, double L, double invL) {
   return v - L * rint((v - ref) * invL);
+}
+
+// fixed-point j-side sum (kFixScale units) as a double-float: hi is the value rounded to FP32,
+// lo the exact integer remainder rounded to FP32
+__device__ __forceinline__ df fix_to_df(long long v) {
+  const float hi = __ll2float_rn(v);
+  const long long r = v - __float2ll_rn(hi);
+  return df{hi * kFixInv, __ll2float_rn(r) * kFixInv};
 }
 
 }  // namespace mop

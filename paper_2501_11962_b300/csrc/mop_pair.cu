@@ -147,9 +147,10 @@ __device__ __forceinline__ R pair_g2(const PairK<R>& c, R rinv, R rinv2, R rinv6
 // One pair for one bead (i-atom of this lane at xs, j-atom xj); cutoff test against rc2e
 // (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-)
 // (MODE 2) into a[3] and the pair energy into e (ENERGY).
-template <class R, int MODE, bool ENERGY, class V4>
+// HALF: the pair's contribution to atom i is also returned in f (atom j receives -f).
+template <class R, int MODE, bool ENERGY, bool HALF, class V4>
 __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R xs, R ys, R zs, const V4& xj, R rc2e,
-                                         const R* ei, const R* ej, R eps, R* a, R& e) {
+                                         const R* ei, const R* ej, R eps, R ew, R* a, R& e, R* f) {
   const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
   if (MODE == 0) {
     const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
@@ -159,16 +160,25 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
     const R rinv6 = rinv2 * rinv2 * rinv2;
     R g = pair_g2<R>(c, rinv, rinv2, rinv6);
     g = in ? g : R(0);
-    a[0] = fma(g, dx, a[0]);
-    a[1] = fma(g, dy, a[1]);
-    a[2] = fma(g, dz, a[2]);
+    if (HALF) {
+      f[0] = g * dx;
+      f[1] = g * dy;
+      f[2] = g * dz;
+      a[0] += f[0];
+      a[1] += f[1];
+      a[2] += f[2];
+    } else {
+      a[0] = fma(g, dx, a[0]);
+      a[1] = fma(g, dy, a[1]);
+      a[2] = fma(g, dz, a[2]);
+    }
     if (ENERGY) {
       // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
       const R r = r2 * rinv;
       const R elj = rinv6 * fma(c.A * R(1.0 / 12.0), rinv6, -c.B * R(1.0 / 6.0));
       const R erf = c.qq * (rinv + fma(k.krf, r2, -k.crf));
       const R E = elj + erf - c.Ew - (r - k.rc) * c.sh;
-      e += in ? E : R(0);
+      e = in ? fma(ew, E, e) : e;
     }
   } else if (MODE == 1) {
     const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
@@ -184,9 +194,18 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
     const R s = fma(dx, ux, fma(dy, uy, dz * uz));
     const R t = in ? b * s : R(0);
     const R ng = in ? -g : R(0);
-    a[0] = fma(ng, ux, fma(t, dx, a[0]));
-    a[1] = fma(ng, uy, fma(t, dy, a[1]));
-    a[2] = fma(ng, uz, fma(t, dz, a[2]));
+    if (HALF) {
+      f[0] = fma(ng, ux, t * dx);
+      f[1] = fma(ng, uy, t * dy);
+      f[2] = fma(ng, uz, t * dz);
+      a[0] += f[0];
+      a[1] += f[1];
+      a[2] += f[2];
+    } else {
+      a[0] = fma(ng, ux, fma(t, dx, a[0]));
+      a[1] = fma(ng, uy, fma(t, dy, a[1]));
+      a[2] = fma(ng, uz, fma(t, dz, a[2]));
+    }
   } else {
     const R ux = eps * (ei[0] - ej[0]), uy = eps * (ei[1] - ej[1]), uz = eps * (ei[2] - ej[2]);
 #pragma unroll
@@ -199,12 +218,30 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
       const R rinv6 = rinv2 * rinv2 * rinv2;
       R g = pair_g2<R>(c, rinv, rinv2, rinv6);
       g = in ? (sgn ? -g : g) : R(0);
-      a[0] = fma(g, px, a[0]);
-      a[1] = fma(g, py, a[1]);
-      a[2] = fma(g, pz, a[2]);
+      if (HALF) {
+        f[0] = sgn ? fma(g, px, f[0]) : g * px;
+        f[1] = sgn ? fma(g, py, f[1]) : g * py;
+        f[2] = sgn ? fma(g, pz, f[2]) : g * pz;
+      } else {
+        a[0] = fma(g, px, a[0]);
+        a[1] = fma(g, py, a[1]);
+        a[2] = fma(g, pz, a[2]);
+      }
+    }
+    if (HALF) {
+      a[0] += f[0];
+      a[1] += f[1];
+      a[2] += f[2];
     }
   }
 }
+
+// floats per jq row of the j-partial staging (8 i-lanes x 12 values + 16 padding, so that the
+// 24 reading lanes hit every bank at most twice)
+constexpr int kJpStride = 112;
+// entries whose j-side partials are staged before one flush (divides the 4 entries of a block;
+// more would take the warp staging past the static shared-memory limit)
+constexpr int kJBatch = 2;
 
 // Warp-private staging area: one chunk of up to 32 list entries, the 32 j-atoms (4 entries x 8
 // atoms) of the block being processed for each of the B beads, and the double-float partial
@@ -218,6 +255,8 @@ template <class R, int B> struct Stage {
   unsigned long long m[32];  // exclusion masks of the chunk
   int t[32];                 // j types
   R hl[B][6][32];            // folded sums: hi x 3, lo x 3 (FP32 mode)
+  // half list (FP32 mode): j-side partials of kJBatch entries, [slot][jq][i][12]
+  float jp[kJBatch][4 * kJpStride];
 };
 
 template <class R, class V4>
@@ -246,24 +285,81 @@ __device__ __forceinline__ void fold_into(Stage<R, B>& S, R (&a)[B][3], int lane
   }
 }
 
+// round(s * kFixScale) as int64 (saturating beyond 2^40 in magnitude).  One conversion; the
+// FP32-only splits measured slower in this latency-bound loop.
+__device__ __forceinline__ unsigned long long to_fix(float s) {
+  return (unsigned long long)__float2ll_rn(s * kFixScale);
+}
+
+// Per-lane constants of the half-list j-side flush, fixed for a whole unit.
+struct JFlush {
+  int w;         // float offset of this lane's 12 j-partials in a staging slot
+  int r;         // reading lanes: float offset of the column this lane sums
+  int o1;        // offset of the second bead's j-side sums from the first's
+  int oc;        // offset of j-atom a, component c within a j-cluster's 24 sums
+  int hbit;      // half-mask bit of the j-atom this lane reads (0: lane does not read)
+  bool second;   // the unit's second bead is real
+};
+
+// Stores this lane's j-side contributions of one entry: jf[h][c][b] belongs to j-atom
+// (lane >> 3) + 4h, component c, bead b (value k = 6h + 2c + b of the lane's 12).
+template <int B>
+__device__ __forceinline__ void j_stage(float* slot, const JFlush& J, const float (&jf)[2][3][B]) {
+  static_assert(B == 2, "the j-partial layout holds two beads");
+  float4* w = reinterpret_cast<float4*>(slot + J.w);
+  w[0] = make_float4(jf[0][0][0], jf[0][0][1], jf[0][1][0], jf[0][1][1]);
+  w[1] = make_float4(jf[0][2][0], jf[0][2][1], jf[1][0][0], jf[1][0][1]);
+  w[2] = make_float4(jf[1][1][0], jf[1][1][1], jf[1][2][0], jf[1][2][1]);
+}
+
+// Half list: sums the staged j-side contributions of kJBatch entries (the first is entry e0 of
+// the chunk) over the 8 i-lanes in a fixed order and adds them, fixed point, to each
+// j-cluster's atoms of both beads.  Lane < 24 reads j-atom a = lane / 3, component lane % 3.
+// The self entry and entries past the end of the chunk add nothing.  jscale[b] maps a sum to
+// the value added (sign and FD scale).
+template <int B>
+__device__ __forceinline__ void j_flush(const JFlush& J, Stage<float, B>& S, int e0, unsigned long long* jacc,
+                                        const float* jscale) {
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < kJBatch; ++q) {
+    const int fl = S.ent[e0 + q].x;
+    if ((fl & J.hbit) && !(fl & kSelfFlag)) {
+      const float* r = &S.jp[q][J.r];
+      float2 t[kCL];
+#pragma unroll
+      for (int ii = 0; ii < kCL; ++ii) t[ii] = *reinterpret_cast<const float2*>(r + ii * 12);
+      const float s0 = ((t[0].x + t[1].x) + (t[2].x + t[3].x)) + ((t[4].x + t[5].x) + (t[6].x + t[7].x));
+      const float s1 = ((t[0].y + t[1].y) + (t[2].y + t[3].y)) + ((t[4].y + t[5].y) + (t[6].y + t[7].y));
+      unsigned long long* dst = jacc + (size_t)(fl & kCluMask) * (kCL * 3) + J.oc;
+      atomicAdd(dst, to_fix(s0 * jscale[0]));
+      if (J.second) atomicAdd(dst + J.o1, to_fix(s1 * jscale[1]));
+    }
+  }
+  __syncwarp();
+}
+
 // One work unit: the i-cluster ci against its whole list, for the B beads n0 .. n0 + B - 1
-// (bead n0 + 1 of a unit past the last bead repeats bead n0 and is not written).
+// (bead n0 + 1 of a unit past the last bead repeats bead n0 and is not written).  FP32 mode runs
+// on the half list (each cluster pair once, j-side sums to P.jacc), FP64 mode on the full list.
 template <class R, int MODE, bool ENERGY, int B>
-__device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab,
+__device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab, int tstr,
                                           Stage<R, B>& S, const PathDev& P, int n0, int n_pass, int ci, int lane) {
   using V4 = typename Tr<R>::V4;
+  constexpr bool HALF = sizeof(R) == 4;
+  static_assert(!HALF || B == 2, "the half-list flush pairs two beads");
   const Cst<R> k(sc);
   const int i = lane & 7, jj = lane >> 3;
   const int si = ci * kCL + i;
   int nb[B];
-  const V4* __restrict__ xqb[B];
+  bool bval[B];
   V4 xi[B];
   R ei[B][3], eps[B];
 #pragma unroll
   for (int b = 0; b < B; ++b) {
+    bval[b] = n0 + b < n_pass;
     nb[b] = min(n0 + b, n_pass - 1);
-    xqb[b] = Tr<R>::xq(P) + (size_t)nb[b] * P.Qpad;
-    xi[b] = xqb[b][si];
+    xi[b] = Tr<R>::xq(P)[(size_t)nb[b] * P.Qpad + si];
     ei[b][0] = ei[b][1] = ei[b][2] = R(0);
     eps[b] = R(0);
     if (MODE >= 1) Tr<R>::eta(P, (size_t)nb[b] * P.Qpad + si, ei[b]);
@@ -272,7 +368,30 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       eps[b] = (R)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
     }
   }
-  const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * sc.n_types;
+  const V4* __restrict__ xqs[B];
+  size_t eos[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    eos[b] = (size_t)nb[b] * P.Qpad;
+    xqs[b] = Tr<R>::xq(P) + eos[b];
+  }
+  // half list: j-side flush constants; atom j gets -f, or +f / (2 eps) in FD mode
+  float jscale[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) jscale[b] = (MODE == 2) ? 0.5f / (float)eps[b] : -1.f;
+  JFlush J{};
+  unsigned long long* jacc = nullptr;
+  if constexpr (HALF) {
+    const int ra = lane / 3, rc = lane - 3 * ra;   // reading lane: j-atom of the entry, component
+    J.w = jj * kJpStride + i * 12;
+    J.r = (ra & 3) * kJpStride + (ra >> 2) * 6 + rc * 2;
+    J.hbit = lane < 24 ? 1 << (29 + (ra >> 2)) : 0;
+    J.oc = ra * 3 + rc;
+    J.o1 = (nb[B - 1] - nb[0]) * P.Qpad * 3;
+    J.second = bval[B - 1] && B > 1;
+    jacc = P.jacc + (size_t)nb[0] * P.Qpad * 3;
+  }
+  const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * tstr;
   const R qi = xi[0].w;
   R a[B][3];
   Acc3<R> accd;   // FP64 mode accumulates directly (B == 1)
@@ -316,12 +435,12 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
     auto fetch = [&](int blk) {
       const int e = 4 * blk + sk;
       if (e < nc) {
-        const int sj = (S.ent[e].x & 0x1fffffff) * kCL + sa;
+        const int sj = (S.ent[e].x & kCluMask) * kCL + sa;
         ft = __ldg(&P.ts[sj]);
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-          fx[b] = xqb[b][sj];
-          if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, (size_t)nb[b] * P.Qpad + sj);
+          fx[b] = xqs[b][sj];
+          if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, eos[b] + sj);
         }
       }
     };
@@ -350,6 +469,14 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         }
         const V4 D = S.d[e];
         const int so = q * kCL + jj;
+        const R ew = (fl & kSelfFlag) ? R(0.5) : R(1);   // the self entry sees each pair twice
+        R jf[2][3][B];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < B; ++b) jf[h][c][b] = R(0);
         R xs[B][3];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -373,13 +500,22 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
               ej[2] = v.z;
             }
             R* acc = (sizeof(R) == 4) ? a[b] : accd.a;
-            if (ENERGY && b == 0)
-              pair_one<R, MODE, true, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej, eps[b],
-                                          acc, eacc.a);
+            R f[3];
+            if (ENERGY && b == 0)   // energy of bead n0 (= bead 1) only
+              pair_one<R, MODE, true, HALF, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej,
+                                                eps[b], ew, acc, eacc.a, f);
             else
-              pair_one<R, MODE, false, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej, eps[b],
-                                           acc, eacc.a);
+              pair_one<R, MODE, false, HALF, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej,
+                                                 eps[b], ew, acc, eacc.a, f);
+            if (HALF) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) jf[h][c][b] = f[c];
+            }
           }
+        }
+        if constexpr (HALF) {
+          j_stage<B>(S.jp[q % kJBatch], J, jf);
+          if (q % kJBatch == kJBatch - 1) j_flush<B>(J, S, e - (kJBatch - 1), jacc, jscale);
         }
       }
       if ((blk & 3) == 3) {
@@ -406,7 +542,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         }
         if (!valid) v[c] = df{0.f, 0.f};
       }
-      if (jj == 0 && (b == 0 || n0 + b < n_pass)) {
+      if (jj == 0 && bval[b]) {
         const size_t k2 = (size_t)nb[b] * P.Qpad + si;
         if (MODE == 0) {
           float2* dst = reinterpret_cast<float2*>(P.Fnb) + 3 * k2;
@@ -424,7 +560,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
     if (ENERGY) {
       df ev = valid ? df{eacc.h, eacc.l} : df{0.f, 0.f};
       ev = df_warp_sum(ev);
-      if (lane == 0) P.e_pair[ci] = 0.5 * ((double)ev.hi + (double)ev.lo);   // full list: pairs seen twice
+      if (lane == 0) P.e_pair[ci] = (double)ev.hi + (double)ev.lo;   // half list: each pair once
     }
   } else {
     double out[3];
@@ -457,10 +593,15 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pai
                                                                       int n_paths, long long n_units) {
   using V4 = typename Tr<R>::V4;
   constexpr int B = BeadsPerUnit<R>::value;
-  __shared__ V4 tab[kMaxTypes * kMaxTypes];
+  // type-pair table with an odd row stride: the 8 i-lanes of a quarter-warp (one j type, up to
+  // 8 i types) then read distinct banks
+  __shared__ V4 tab[kMaxTypes * (kMaxTypes + 1)];
   __shared__ Stage<R, B> stage[4];
-  const int nt2 = sc.n_types * sc.n_types;
-  for (int k = threadIdx.x; k < nt2; k += blockDim.x) tab[k] = Tr<R>::tab(sc, k);
+  const int tstr = sc.n_types | 1;
+  for (int k = threadIdx.x; k < sc.n_types * tstr; k += blockDim.x) {
+    const int ti = k / tstr, tj = k - ti * tstr;
+    tab[k] = tj < sc.n_types ? Tr<R>::tab(sc, ti * sc.n_types + tj) : V4{};
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   Stage<R, B>& S = stage[threadIdx.x >> 5];
@@ -474,13 +615,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pai
     }
     const PathDev& P = paths[p];
     const int n_pass = MODE == 0 ? P.n_force : P.n_hvp;
-    const int ngrp = (n_pass + B - 1) / B;
+    // bead-major: the warps in flight share a few beads, so their coordinates and j-side sums
+    // stay in L2
     const long long v = u - (MODE == 0 ? P.unit_off : P.unit_off_h);
-    const int n0 = (int)(v % ngrp) * B;
-    const int ci = (int)(v / ngrp);
+    const int n0 = (int)(v / P.n_clu) * B;
+    const int ci = (int)(v % P.n_clu);
     if (ci >= __ldg(&P.meta[0])) continue;   // past the clusters of the current sort
-    if (MODE == 0 && n0 == 0) pair_unit<R, 0, true, B>(sc, tab, S, P, n0, n_pass, ci, lane);
-    else pair_unit<R, MODE, false, B>(sc, tab, S, P, n0, n_pass, ci, lane);
+    if (MODE == 0 && n0 == 0) pair_unit<R, 0, true, B>(sc, tab, tstr, S, P, n0, n_pass, ci, lane);
+    else pair_unit<R, MODE, false, B>(sc, tab, tstr, S, P, n0, n_pass, ci, lane);
   }
 }
 
@@ -522,7 +664,7 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
     for (int e = 0; e < P.lcnt[ci]; ++e) {
       const int4 en = P.ent[eb + e];
       const unsigned long long m = (en.x < 0) ? P.emask[eb + e] : 0ull;
-      const int cj = en.x & 0x1fffffff;
+      const int cj = en.x & kCluMask;
       double D[3];
       if (P.ent64) {
         D[0] = P.ent64[eb + e].x; D[1] = P.ent64[eb + e].y; D[2] = P.ent64[eb + e].z;
@@ -546,8 +688,11 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
           r2 += d * d;
         }
         const bool vj = P.perm[sj] >= 0;
+        // a half-list entry holds each unordered pair once, the self entry (and the full list)
+        // each pair in both orders
+        const int wgt = (P.jacc && !(en.x & kSelfFlag)) ? 2 : 1;
         listed += 1;
-        inside += (vi && vj && r2 < sc.rc2 && !((m >> (i * kCL + jl)) & 1ull)) ? 1 : 0;
+        inside += (vi && vj && r2 < sc.rc2 && !((m >> (i * kCL + jl)) & 1ull)) ? wgt : 0;
       }
     }
   }

@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
     {
       float Fb[3] = {0.f, 0.f, 0.f};
       bonded_force<float, float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
-      for (int c = 0; c < 3; ++c) F[c] = df_add_f(df{Fnb[c].x, Fnb[c].y}, Fb[c]);
+      for (int c = 0; c < 3; ++c) {
+        F[c] = df_add_f(df{Fnb[c].x, Fnb[c].y}, Fb[c]);
+        F[c] = df_add(F[c], fix_to_df((long long)P.jacc[3 * k + c]));   // j-side sums of the half list
+      }
       if (P.N > 1) {
         const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
         const float2 cc = sc.c_df[a];
@@ -416,7 +419,9 @@ __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const Path
       }
       if (n < P.N - 1) {
         const float4 hn = reinterpret_cast<const float4*>(P.Hnb)[k];
-        float H[3] = {hn.x, hn.y, hn.z};
+        const unsigned long long* J = P.jacc + 3 * k;   // j-side sums of the half list
+        float H[3] = {hn.x + __ll2float_rn((long long)J[0]) * kFixInv, hn.y + __ll2float_rn((long long)J[1]) * kFixInv,
+                      hn.z + __ll2float_rn((long long)J[2]) * kFixInv};
         double eps = 0.0;
         if (FD) {
           const float mx = __uint_as_float(P.etamax[n]);

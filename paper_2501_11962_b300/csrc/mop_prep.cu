@@ -372,8 +372,17 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
           unsigned hm = 0;
           int cj = 0;
           double D[3] = {0.0, 0.0, 0.0};
-          if (t < nbin) {
-            cj = binlist[s0 + t];
+          bool self = false;
+          if (t < nbin) cj = binlist[s0 + t];
+          if (!F64 && t < nbin) {
+            // half list: every unordered cluster pair (with its image) once; the parity rule
+            // gives each cluster about half of its neighbours
+            self = cj == ci && kk[0] == 0 && kk[1] == 0 && kk[2] == 0;
+            const bool keep = cj != ci ? (((ci ^ cj) & 1) ? ci < cj : ci > cj)
+                                       : (kk[0] > 0 || (kk[0] == 0 && (kk[1] > 0 || (kk[1] == 0 && kk[2] >= 0))));
+            if (!keep) cj = -1;
+          }
+          if (t < nbin && cj >= 0) {
             // FP32 pre-test of the union boxes (slack covers the FP32 rounding of the centres)
             const float4 cw = cbox[2 * cj], ce = cbox[2 * cj + 1];
             const float gx = fmaxf(0.f, fabsf(wif[0] - (cw.x + kk[0] * Lf[0])) - eif[0] - ce.x);
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
                   }
                 }
               }
-              const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0);
+              const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0) | (self ? kSelfFlag : 0);
               ent[base + pos] = make_int4(cj | flags, __float_as_int((float)D[0]), __float_as_int((float)D[1]),
                                           __float_as_int((float)D[2]));
               if (F64) ent64[base + pos] = make_double4_32a(D[0], D[1], D[2], 0.0);
