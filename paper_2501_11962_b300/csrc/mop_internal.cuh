@@ -78,7 +78,7 @@ struct PathDev {
   const unsigned* ctype;    // packed LJ types of each cluster (4 bits per atom)
   const int4* ent;          // x = cj | self << 28 | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
   const double4_32a* ent64;
-  const unsigned long long* emask;
+  const unsigned long long* emask;   // excluded atom pairs of an entry: bit j * 8 + i
   // FP64 mode: [N][Qpad][3] doubles.  Mixed mode views of the same buffers: Fnb and F as
   // double-float (hi, lo) x 3 (float2 [N][Qpad][3]), Hnb and Heta as float4 [N][Qpad].
   double* Fnb;

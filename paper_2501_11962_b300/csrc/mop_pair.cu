@@ -242,6 +242,11 @@ constexpr int kJpStride = 112;
 // entries whose j-side partials are staged before one flush (divides the 4 entries of a block;
 // more would take the warp staging past the static shared-memory limit)
 constexpr int kJBatch = 2;
+// unrolling of the 4-entry loop of a staged block
+#ifndef MOP_Q_UNROLL
+#define MOP_Q_UNROLL 4
+#endif
+constexpr int kQUnroll = MOP_Q_UNROLL;
 
 // Warp-private staging area: one chunk of up to 32 list entries, the 32 j-atoms (4 entries x 8
 // atoms) of the block being processed for each of the B beads, and the double-float partial
@@ -406,7 +411,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   Acc1<R> eacc;
   const int cnt = __ldg(&P.lcnt[ci]);
   const size_t eb = (size_t)ci * P.cap;
-  const int mshift = i * kCL + jj;
+  const int mshift = jj * kCL + i;   // exclusion bit of pair (i, jj); pair (i, jj + 4) is 32 higher
   const int sa = lane & 7, sk = lane >> 3;   // staging role: atom sa of block entry sk
   for (int c0 = 0; c0 < cnt; c0 += 32) {
     const int nc = min(32, cnt - c0);
@@ -457,7 +462,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       __syncwarp();
       if (blk + 1 < nblk) fetch(blk + 1);
       // entries past the end of the chunk were staged with no half bits
-#pragma unroll
+#pragma unroll kQUnroll
       for (int q = 0; q < 4; ++q) {
         const int e = 4 * blk + q;
         const int fl = S.ent[e].x;
@@ -465,7 +470,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         if (fl < 0) {
           const unsigned long long m = S.m[e] >> mshift;
           rcA = (m & 1ull) ? R(-1) : k.rc2;
-          rcB = ((m >> 4) & 1ull) ? R(-1) : k.rc2;
+          rcB = ((m >> 32) & 1ull) ? R(-1) : k.rc2;
         }
         const V4 D = S.d[e];
         const int so = q * kCL + jj;
@@ -692,7 +697,7 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
         // each pair in both orders
         const int wgt = (P.jacc && !(en.x & kSelfFlag)) ? 2 : 1;
         listed += 1;
-        inside += (vi && vj && r2 < sc.rc2 && !((m >> (i * kCL + jl)) & 1ull)) ? wgt : 0;
+        inside += (vi && vj && r2 < sc.rc2 && !((m >> (jl * kCL + i)) & 1ull)) ? wgt : 0;
       }
     }
   }

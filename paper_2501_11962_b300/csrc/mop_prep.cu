@@ -312,7 +312,9 @@ __global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype)
 // Cluster-pair list of one i-cluster per warp.  Candidates come from the bins around the
 // i-cluster (every periodic image), pass the union-bounding-box test, then the exact test on
 // the atoms' union spheres; bit 29 / bit 30 of an entry mark the j-half-clusters (atoms 0-3 /
-// 4-7) that hold at least one pair that can come within rc in some bead.  Entries of cluster ci
+// 4-7) that hold at least one pair that can come within rc in some bead.  The union-box test
+// runs one candidate per lane; the exact test runs one candidate at a time over the whole warp
+// (two atom pairs per lane), and so does the exclusion mask (bit j * 8 + i).  Entries of cluster ci
 // go to ent[ci * cap ...] in bin order (deterministic); lcnt[ci] = their number; meta[2] =
 // largest count (a count above cap means the list must be rebuilt with a larger cap).
 template <bool F64>
@@ -324,12 +326,14 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
                                                    const float4* cbox, int cap,
                                                    int* lcnt, int4* ent, double4_32a* ent64,
                                                    unsigned long long* emask, int* meta) {
-  __shared__ float4 ibox[4][kCL];
+  __shared__ float4 jbox[4][32][kCL];   // per warp: the atom spheres of each lane's candidate
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ci = blockIdx.x * 4 + warp;
   if (ci >= max_clu || ci >= meta_in[0]) return;   // warp-uniform
-  if (lane < kCL) ibox[warp][lane] = abox[ci * kCL + lane];
-  __syncwarp();
+  const int iq = lane & 7, jq = lane >> 3;
+  const float4 bi4 = abox[ci * kCL + iq];          // this lane's i-atom sphere
+  const int ai = perm[ci * kCL + iq];
+  const int mol_i = ai >= 0 ? sc.mol[ai] : -1, loc_i = ai >= 0 ? sc.loc[ai] : 0;
   const int nb[3] = {nb0, nb1, nb2};
   const double bw[3] = {bw0, bw1, bw2};
   double wi[3], ei[3];
@@ -369,73 +373,89 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
         const int kk[3] = {kx, ky, kz};
         for (int t0 = 0; t0 < nbin; t0 += 32) {
           const int t = t0 + lane;
-          unsigned hm = 0;
-          int cj = 0;
-          double D[3] = {0.0, 0.0, 0.0};
+          int cj = -1;
           bool self = false;
-          if (t < nbin) cj = binlist[s0 + t];
-          if (!F64 && t < nbin) {
-            // half list: every unordered cluster pair (with its image) once; the parity rule
-            // gives each cluster about half of its neighbours
-            self = cj == ci && kk[0] == 0 && kk[1] == 0 && kk[2] == 0;
-            const bool keep = cj != ci ? (((ci ^ cj) & 1) ? ci < cj : ci > cj)
-                                       : (kk[0] > 0 || (kk[0] == 0 && (kk[1] > 0 || (kk[1] == 0 && kk[2] >= 0))));
-            if (!keep) cj = -1;
+          double D[3] = {0.0, 0.0, 0.0};
+          if (t < nbin) {
+            cj = binlist[s0 + t];
+            if (!F64) {
+              // half list: every unordered cluster pair (with its image) once; the parity rule
+              // gives each cluster about half of its neighbours
+              self = cj == ci && kk[0] == 0 && kk[1] == 0 && kk[2] == 0;
+              const bool keep = cj != ci ? (((ci ^ cj) & 1) ? ci < cj : ci > cj)
+                                         : (kk[0] > 0 || (kk[0] == 0 && (kk[1] > 0 || (kk[1] == 0 && kk[2] >= 0))));
+              if (!keep) cj = -1;
+            }
           }
-          if (t < nbin && cj >= 0) {
+          bool box = false;
+          if (cj >= 0) {
             // FP32 pre-test of the union boxes (slack covers the FP32 rounding of the centres)
             const float4 cw = cbox[2 * cj], ce = cbox[2 * cj + 1];
             const float gx = fmaxf(0.f, fabsf(wif[0] - (cw.x + kk[0] * Lf[0])) - eif[0] - ce.x);
             const float gy = fmaxf(0.f, fabsf(wif[1] - (cw.y + kk[1] * Lf[1])) - eif[1] - ce.y);
             const float gz = fmaxf(0.f, fabsf(wif[2] - (cw.z + kk[2] * Lf[2])) - eif[2] - ce.z);
-            const float g2 = gx * gx + gy * gy + gz * gz;
-            if (g2 < rcs2) {
-              for (int d = 0; d < 3; ++d) D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
-              const float Dx = (float)D[0], Dy = (float)D[1], Dz = (float)D[2];
-              for (int j = 0; j < kCL && hm != 3u; ++j) {
-                const float4 bj = abox[cj * kCL + j];
-                if (bj.w < 0.f) continue;
-                const unsigned bit = j < 4 ? 1u : 2u;
-                if (hm & bit) continue;
-                for (int i = 0; i < kCL; ++i) {
-                  const float4 bi4 = ibox[warp][i];
-                  if (bi4.w < 0.f) continue;
-                  const float ux = bi4.x + Dx - bj.x, uy = bi4.y + Dy - bj.y, uz = bi4.z + Dz - bj.z;
-                  const float lim = rcf + bi4.w + bj.w;
-                  if (ux * ux + uy * uy + uz * uz < lim * lim) {
-                    hm |= bit;
-                    break;
-                  }
-                }
+            box = gx * gx + gy * gy + gz * gz < rcs2;
+          }
+          if (box) {
+            for (int d = 0; d < 3; ++d) D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
+            // the atom spheres of this lane's candidate, read by the whole warp below
+#pragma unroll
+            for (int j = 0; j < kCL; ++j) jbox[warp][lane][j] = abox[cj * kCL + j];
+          }
+          __syncwarp();
+          // exact test of each surviving candidate by the whole warp, in bin order: lane
+          // (i = lane & 7, jq = lane >> 3) tests atom pairs (i, jq) and (i, jq + 4)
+          unsigned pend = __ballot_sync(0xffffffffu, box);
+          while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int cs = __shfl_sync(0xffffffffu, cj, src);
+            const float Dx = __shfl_sync(0xffffffffu, (float)D[0], src);
+            const float Dy = __shfl_sync(0xffffffffu, (float)D[1], src);
+            const float Dz = __shfl_sync(0xffffffffu, (float)D[2], src);
+            const float4 bj0 = jbox[warp][src][jq], bj1 = jbox[warp][src][jq + 4];
+            bool in0 = false, in1 = false;
+            if (bi4.w >= 0.f) {
+              if (bj0.w >= 0.f) {
+                const float ux = bi4.x + Dx - bj0.x, uy = bi4.y + Dy - bj0.y, uz = bi4.z + Dz - bj0.z;
+                const float lim = rcf + bi4.w + bj0.w;
+                in0 = ux * ux + uy * uy + uz * uz < lim * lim;
+              }
+              if (bj1.w >= 0.f) {
+                const float ux = bi4.x + Dx - bj1.x, uy = bi4.y + Dy - bj1.y, uz = bi4.z + Dz - bj1.z;
+                const float lim = rcf + bi4.w + bj1.w;
+                in1 = ux * ux + uy * uy + uz * uz < lim * lim;
               }
             }
-          }
-          const bool pass = hm != 0u;
-          const unsigned bal = __ballot_sync(0xffffffffu, pass);
-          if (pass) {
-            const int pos = count + __popc(bal & ((1u << lane) - 1u));
-            if (pos < cap) {
+            const unsigned hm = (__ballot_sync(0xffffffffu, in0) ? 1u : 0u) | (__ballot_sync(0xffffffffu, in1) ? 2u : 0u);
+            if (!hm) continue;   // warp-uniform
+            if (count < cap) {
+              // exclusions, bit j * 8 + i (the lane index for j < 4, + 32 for j >= 4); only
+              // clusters whose molecule ranges overlap can hold excluded pairs
               unsigned long long m = 0ull;
-              const int mj0 = molr[2 * cj], mj1 = molr[2 * cj + 1];
+              const int mj0 = molr[2 * cs], mj1 = molr[2 * cs + 1];
               if (mi0 <= mj1 && mj0 <= mi1) {
-                for (int i = 0; i < kCL; ++i) {
-                  const int a = perm[ci * kCL + i];
-                  if (a < 0) continue;
-                  for (int j = 0; j < kCL; ++j) {
-                    const int b = perm[cj * kCL + j];
-                    if (b < 0) continue;
-                    if (sc.mol[a] == sc.mol[b] && abs(sc.loc[a] - sc.loc[b]) <= 2) m |= 1ull << (i * kCL + j);
-                  }
+                bool x0 = false, x1 = false;
+                if (ai >= 0) {
+                  const int b0 = perm[cs * kCL + jq], b1 = perm[cs * kCL + jq + 4];
+                  x0 = b0 >= 0 && sc.mol[b0] == mol_i && abs(sc.loc[b0] - loc_i) <= 2;
+                  x1 = b1 >= 0 && sc.mol[b1] == mol_i && abs(sc.loc[b1] - loc_i) <= 2;
                 }
+                m = (unsigned long long)__ballot_sync(0xffffffffu, x0) |
+                    ((unsigned long long)__ballot_sync(0xffffffffu, x1) << 32);
               }
-              const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0) | (self ? kSelfFlag : 0);
-              ent[base + pos] = make_int4(cj | flags, __float_as_int((float)D[0]), __float_as_int((float)D[1]),
-                                          __float_as_int((float)D[2]));
-              if (F64) ent64[base + pos] = make_double4_32a(D[0], D[1], D[2], 0.0);
-              emask[base + pos] = m;
+              if (lane == src) {
+                const bool slf = self;
+                const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0) | (slf ? kSelfFlag : 0);
+                ent[base + count] = make_int4(cj | flags, __float_as_int((float)D[0]), __float_as_int((float)D[1]),
+                                              __float_as_int((float)D[2]));
+                if (F64) ent64[base + count] = make_double4_32a(D[0], D[1], D[2], 0.0);
+                emask[base + count] = m;
+              }
             }
+            ++count;
           }
-          count += __popc(bal);
+          __syncwarp();
         }
       }
     }
