@@ -365,6 +365,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     sc.invL[k] = 1.0 / d->box[k];
     sc.Lf[k] = (float)d->box[k];
     sc.halfLf[k] = (float)(0.5 * d->box[k]);
+    sc.invLf[k] = (float)(1.0 / d->box[k]);
+    sc.Llo[k] = (float)(d->box[k] - (double)sc.Lf[k]);
   }
   const double rc = d->rc;
   const bool shifted = d->cutoff_mode == MOP_SHIFTED_FORCE;

@@ -34,6 +34,8 @@ struct SysConsts {
   int Q, n_types, cutoff_mode, precision, hvp_mode;
   double L[3], invL[3];
   float Lf[3], halfLf[3];
+  float invLf[3];
+  float Llo[3];   // L - Lf: the box as a double-float (Lf, Llo)
   double rc, rc2, krf, crf, k2rf, drf;   // RF constants; drf = phi'_RF(rc) / (f qi qj) if shifted
   float rcf, rc2f, krff, crff, k2rff, drff;
   double fd_h;

@@ -106,9 +106,14 @@ __device__ __forceinline__ void mi_diff(const SysConsts& sc, const PathDev& P, i
     const float xa = P.x32[base + 3 * (size_t)a + c], xb = P.x32[base + 3 * (size_t)b + c];
     float v = xa - xb;   // exact when both lie in the same periodic image
     if (fabsf(v) > sc.halfLf[c]) {
-      double w = (double)xa - (double)xb;
-      w -= sc.L[c] * rint(w * sc.invL[c]);
-      v = (float)w;
+      // across images, in FP32 only (the FP64 pipe is slow and a warp takes this branch
+      // whenever any lane does): the exact difference w = xa - xb as a double-float, minus
+      // k L with L = (Lf, Llo) and k Lf formed exactly by an FMA
+      const df w = two_sum(xa, -xb);
+      const float k = rintf(w.hi * sc.invLf[c]);
+      const float p = k * sc.Lf[c];
+      const df r = df_add(w, df{-p, -fmaf(k, sc.Lf[c], -p)});
+      v = r.hi + (r.lo - k * sc.Llo[c]);
     }
     d[c] = (R)v;
   }
