@@ -486,7 +486,7 @@ mop_status mop_destroy(mop_handle* h) {
   h->d_one.release(); h->counts.release();
   h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release();
   for (auto& P : h->paths) {
-    P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.colid.release();
+    P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.reff.release(); P.colid.release();
     P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();
     P.ts.release(); P.center.release(); P.hext.release(); P.molr.release(); P.emax.release();
     P.cbin.release(); P.bincnt.release(); P.binstart.release(); P.bincur.release(); P.binlist.release();

@@ -56,6 +56,7 @@ struct PathHost {
   bool have_grad = false; // grad_int holds dV/dR at the current positions
   // sort and clusters
   DevBuf<double> ref;     // [Q][3]
+  DevBuf<float> reff;     // [Q][3] the same rounded to FP32 (mixed precision)
   DevBuf<int> colid, colcnt, colinfo, colatoms, perm, slot, ts;
   DevBuf<double> center;  // [max_clu][3]
   DevBuf<float> hext;     // [max_clu][3]

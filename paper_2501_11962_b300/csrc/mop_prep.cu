@@ -48,7 +48,7 @@ __device__ int block_excl_scan(int v, int* sh, int* total) {
 
 // reference wrap of bead 1, column index and column counts
 __global__ void k_ref_columns(SysConsts sc, const float* x32, const double* x64, int ncx, int ncy, double wx,
-                              double wy, double* ref, int* colid, int* colcnt) {
+                              double wy, double* ref, float* reff, int* colid, int* colcnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= sc.Q) return;
   double r[3];
@@ -59,6 +59,7 @@ __global__ void k_ref_columns(SysConsts sc, const float* x32, const double* x64,
     if (w < 0.0) w = 0.0;
     r[d] = w;
     ref[3 * i + d] = w;
+    if (reff) reff[3 * i + d] = (float)w;
   }
   // fmax/fmin also map a NaN coordinate to a valid column (the result is then rejected later)
   const int cx = (int)fmin(fmax(r[0] / wx, 0.0), (double)(ncx - 1));
@@ -115,6 +116,129 @@ __global__ void k_rank(int Q, const double* ref, const int* colid, const int* co
   const int s = colinfo[3 * col + 1] + rank;
   perm[s] = i;
   slot[i] = s;
+}
+
+// Mixed precision: the caller's FP32 coordinate x taken at the periodic image nearest its
+// reference r, x - k L, as an exact double-float (FP32 pipes only; k L with L = (Lf, Llo) and
+// k Lf formed exactly by an FMA).  Every FP32-path kernel picks k by the same FP32 formula.
+__device__ __forceinline__ df aligned_df(const SysConsts& sc, float x, float r, int d) {
+  const float k = rintf((x - r) * sc.invLf[d]);
+  const float p = k * sc.Lf[d];
+  const float pe = fmaf(k, sc.Lf[d], -p);
+  const df t = two_sum(x, -p);
+  return fast_two_sum(t.hi, (t.lo - pe) - k * sc.Llo[d]);
+}
+
+// union bounding box of each cluster over all beads (mixed precision); one warp per cluster,
+// lanes over beads.  Coordinates are rounded to FP32 after alignment, so the half extents get
+// a slack of a few units in the last place of the box size.
+__global__ void k_cluster_bbox32(SysConsts sc, const float* x32, int N, const float* reff, const int* perm,
+                                 const int* meta, int max_clu, double margin, double* center, float* hext, int* molr,
+                                 unsigned* emax) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= max_clu || c >= meta[0]) return;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int atoms[kCL];
+#pragma unroll
+  for (int k = 0; k < kCL; ++k) atoms[k] = perm[c * kCL + k];
+  const size_t Q3 = 3 * (size_t)sc.Q;
+  for (int b = lane; b < N; b += 32) {
+#pragma unroll
+    for (int k = 0; k < kCL; ++k) {
+      const int a = atoms[k];
+      if (a < 0) continue;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const df v = aligned_df(sc, x32[b * Q3 + 3 * (size_t)a + d], reff[3 * a + d], d);
+        const float f = v.hi + v.lo;
+        lo[d] = fminf(lo[d], f);
+        hi[d] = fmaxf(hi[d], f);
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+  }
+  if (lane == 0) {
+    int m0 = 0x7fffffff, m1 = -0x7fffffff;
+    for (int k = 0; k < kCL; ++k)
+      if (atoms[k] >= 0) {
+        m0 = min(m0, sc.mol[atoms[k]]);
+        m1 = max(m1, sc.mol[atoms[k]]);
+      }
+    molr[2 * c] = m0;
+    molr[2 * c + 1] = m1;
+    for (int d = 0; d < 3; ++d) {
+      const float cen = 0.5f * (lo[d] + hi[d]);
+      const float ext = fmaxf(hi[d] - cen, cen - lo[d]);
+      // |coordinate| < 2^k: the FP32 roundings above stay below 4 ulps of that size
+      const float e = ext + (fabsf(cen) + ext) * 4.8e-7f + (float)margin + 1e-6f;
+      center[3 * c + d] = widen(cen);
+      hext[3 * c + d] = e;
+      atomicMax(&emax[d], __float_as_uint(e));
+    }
+  }
+}
+
+// Mixed precision: cluster-local coordinates x - C of every bead (xq, with q sqrt(f) in w) and
+// each atom's union sphere over the beads (abox), one thread per slot looping over the beads.
+// Padding slots get far-away dummy coordinates, zero eta and an empty sphere.
+__global__ void k_local_box32(SysConsts sc, const float* x32, int N, const float* reff, const int* perm,
+                              const int* meta, int max_slots, const double* center, double margin, float4* xq, int* ts,
+                              float4* eta32, float4* abox) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= meta[0] * kCL) return;
+  const int a = perm[s];
+  if (a < 0) {
+    const float dmy = kDummyCoord + 3.0f * (float)(s & (kCL - 1));
+    for (int b = 0; b < N; ++b) {
+      const size_t o = (size_t)b * max_slots + s;
+      xq[o] = make_float4(dmy, dmy, dmy, 0.0f);
+      eta32[o] = make_float4(0.f, 0.f, 0.f, 0.f);   // read as j-atoms by the HVP kernels
+    }
+    ts[s] = 0;
+    abox[s] = make_float4(kDummyCoord, kDummyCoord, kDummyCoord, -1.0f);
+    return;
+  }
+  const int c = s / kCL;
+  float cen[3], r[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    cen[d] = (float)center[3 * c + d];   // exactly representable
+    r[d] = reff[3 * a + d];
+  }
+  const float q = (float)sc.qs[a];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  const size_t Q3 = 3 * (size_t)sc.Q;
+#pragma unroll 4
+  for (int b = 0; b < N; ++b) {
+    float v[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const df A = aligned_df(sc, x32[b * Q3 + 3 * (size_t)a + d], r[d], d);
+      const df t = two_sum(A.hi, -cen[d]);
+      v[d] = t.hi + (t.lo + A.lo);
+      lo[d] = fminf(lo[d], v[d]);
+      hi[d] = fmaxf(hi[d], v[d]);
+    }
+    xq[(size_t)b * max_slots + s] = make_float4(v[0], v[1], v[2], q);
+  }
+  ts[s] = sc.type[a];
+  float cf[3], h2 = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    cf[d] = 0.5f * (lo[d] + hi[d]);
+    const float h = fmaxf(hi[d] - cf[d], cf[d] - lo[d]);
+    h2 = fmaf(h, h, h2);
+  }
+  // local coordinates are below a few nm: 1e-6 nm covers every FP32 rounding here
+  abox[s] = make_float4(cf[0], cf[1], cf[2], sqrtf(h2) * 1.000001f + (float)margin + 1e-6f);
 }
 
 // union bounding box of each cluster over all beads; one warp per cluster, lanes over beads
@@ -532,7 +656,9 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_CK(cudaMemsetAsync(P.meta.p, 0, sizeof(int) * 3, st));   // meta[3] (overflow) is sticky
 
   const int bs = 256;
-  k_ref_columns<<<nblk(Q, bs), bs, 0, st>>>(sc, x32, x64, g.ncx, g.ncy, g.wx, g.wy, P.ref.p, P.colid.p, P.colcnt.p);
+  if (!f64) MOP_CK(P.reff.ensure(3 * (size_t)Q));
+  k_ref_columns<<<nblk(Q, bs), bs, 0, st>>>(sc, x32, x64, g.ncx, g.ncy, g.wx, g.wy, P.ref.p, f64 ? nullptr : P.reff.p,
+                                            P.colid.p, P.colcnt.p);
   MOP_KL();
   k_scan_columns<<<1, 1024, 0, st>>>(P.colcnt.p, ncol, P.colinfo.p, P.meta.p);
   MOP_KL();
@@ -541,19 +667,24 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   k_rank<<<nblk(Q, bs), bs, 0, st>>>(Q, P.ref.p, P.colid.p, P.colcnt.p, P.colinfo.p, P.colatoms.p, P.perm.p,
                                      P.slot.p);
   MOP_KL();
-  k_cluster_bbox<<<nblk((long long)max_clu * 32, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p,
-                                                                   max_clu, margin, P.center.p, P.hext.p, P.molr.p,
-                                                                   P.emax.p);
-  MOP_KL();
-  if (f64)
+  if (f64) {
+    k_cluster_bbox<<<nblk((long long)max_clu * 32, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p,
+                                                                     max_clu, margin, P.center.p, P.hext.p, P.molr.p,
+                                                                     P.emax.p);
+    MOP_KL();
     k_local_coords<true><<<dim3(nblk(max_slots, bs), N), bs, 0, st>>>(
         sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, nullptr, P.xq64.p, P.ts.p, P.eta32.p,
         P.eta.p);
-  else
-    k_local_coords<false><<<dim3(nblk(max_slots, bs), N), bs, 0, st>>>(
-        sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, max_slots, P.center.p, P.xq.p, nullptr, P.ts.p, P.eta32.p,
-        nullptr);
-  MOP_KL();
+    MOP_KL();
+  } else {
+    k_cluster_bbox32<<<nblk((long long)max_clu * 32, bs), bs, 0, st>>>(sc, x32, N, P.reff.p, P.perm.p, P.meta.p,
+                                                                       max_clu, margin, P.center.p, P.hext.p,
+                                                                       P.molr.p, P.emax.p);
+    MOP_KL();
+    k_local_box32<<<nblk(max_slots, bs), bs, 0, st>>>(sc, x32, N, P.reff.p, P.perm.p, P.meta.p, max_slots,
+                                                      P.center.p, margin, P.xq.p, P.ts.p, P.eta32.p, P.abox.p);
+    MOP_KL();
+  }
   k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, P.hext.p, g.nb[0], g.nb[1],
                                                    g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cbox.p,
                                                    P.cbin.p, P.bincnt.p);
@@ -564,9 +695,11 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_KL();
   k_sort_bins<<<nblk(nbins, bs), bs, 0, st>>>(nbins, P.binstart.p, P.binlist.p);
   MOP_KL();
-  k_atom_box<<<nblk(max_slots, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, P.center.p, margin,
-                                                  P.abox.p);
-  MOP_KL();
+  if (f64) {
+    k_atom_box<<<nblk(max_slots, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p, P.center.p, margin,
+                                                    P.abox.p);
+    MOP_KL();
+  }
   k_cluster_types<<<nblk(max_clu, bs), bs, 0, st>>>(P.meta.p, P.ts.p, P.ctype.p);
   MOP_KL();
   if (!sync && !P.sized) sync = true;   // the first build must size the list on the host
