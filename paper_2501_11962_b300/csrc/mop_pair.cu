@@ -236,9 +236,10 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
   }
 }
 
-// floats per jq row of the j-partial staging (8 i-lanes x 12 values + 16 padding, so that the
-// 24 reading lanes hit every bank at most twice)
-constexpr int kJpStride = 112;
+// j-partial staging of one entry: value (h, c, b) of i-lane ii and j-atom jq at
+// ii * kJpRow + jq * 6 + h * 24 + 2c + b.  Both the 64-bit stores (16 lanes per phase: 8 ii x
+// 2 jq) and the 64-bit loads of the 24 summing lanes then hit every bank once per phase.
+constexpr int kJpRow = 52;
 // entries whose j-side partials are staged before one flush (divides the 4 entries of a block;
 // more would take the warp staging past the static shared-memory limit)
 constexpr int kJBatch = 2;
@@ -260,8 +261,8 @@ template <class R, int B> struct Stage {
   unsigned long long m[32];  // exclusion masks of the chunk
   int t[32];                 // j types
   R hl[B][6][32];            // folded sums: hi x 3, lo x 3 (FP32 mode)
-  // half list (FP32 mode): j-side partials of kJBatch entries, [slot][jq][i][12]
-  float jp[kJBatch][4 * kJpStride];
+  // half list (FP32 mode): j-side partials of kJBatch entries
+  float jp[kJBatch][kCL * kJpRow];
 };
 
 template <class R, class V4>
@@ -307,14 +308,15 @@ struct JFlush {
 };
 
 // Stores this lane's j-side contributions of one entry: jf[h][c][b] belongs to j-atom
-// (lane >> 3) + 4h, component c, bead b (value k = 6h + 2c + b of the lane's 12).
+// (lane >> 3) + 4h, component c, bead b.
 template <int B>
 __device__ __forceinline__ void j_stage(float* slot, const JFlush& J, const float (&jf)[2][3][B]) {
   static_assert(B == 2, "the j-partial layout holds two beads");
-  float4* w = reinterpret_cast<float4*>(slot + J.w);
-  w[0] = make_float4(jf[0][0][0], jf[0][0][1], jf[0][1][0], jf[0][1][1]);
-  w[1] = make_float4(jf[0][2][0], jf[0][2][1], jf[1][0][0], jf[1][0][1]);
-  w[2] = make_float4(jf[1][1][0], jf[1][1][1], jf[1][2][0], jf[1][2][1]);
+  float2* w = reinterpret_cast<float2*>(slot + J.w);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[h * 12 + c] = make_float2(jf[h][c][0], jf[h][c][1]);
 }
 
 // Half list: sums the staged j-side contributions of kJBatch entries (the first is entry e0 of
@@ -333,7 +335,7 @@ __device__ __forceinline__ void j_flush(const JFlush& J, Stage<float, B>& S, int
       const float* r = &S.jp[q][J.r];
       float2 t[kCL];
 #pragma unroll
-      for (int ii = 0; ii < kCL; ++ii) t[ii] = *reinterpret_cast<const float2*>(r + ii * 12);
+      for (int ii = 0; ii < kCL; ++ii) t[ii] = *reinterpret_cast<const float2*>(r + ii * kJpRow);
       const float s0 = ((t[0].x + t[1].x) + (t[2].x + t[3].x)) + ((t[4].x + t[5].x) + (t[6].x + t[7].x));
       const float s1 = ((t[0].y + t[1].y) + (t[2].y + t[3].y)) + ((t[4].y + t[5].y) + (t[6].y + t[7].y));
       unsigned long long* dst = jacc + (size_t)(fl & kCluMask) * (kCL * 3) + J.oc;
@@ -388,8 +390,8 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   unsigned long long* jacc = nullptr;
   if constexpr (HALF) {
     const int ra = lane / 3, rc = lane - 3 * ra;   // reading lane: j-atom of the entry, component
-    J.w = jj * kJpStride + i * 12;
-    J.r = (ra & 3) * kJpStride + (ra >> 2) * 6 + rc * 2;
+    J.w = i * kJpRow + jj * 6;
+    J.r = (ra & 3) * 6 + (ra >> 2) * 24 + rc * 2;
     J.hbit = lane < 24 ? 1 << (29 + (ra >> 2)) : 0;
     J.oc = ra * 3 + rc;
     J.o1 = (nb[B - 1] - nb[0]) * P.Qpad * 3;
