@@ -32,6 +32,17 @@ FLOPS_HVP = 59
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 FD_SWEEP = (1e-5, 3e-5, 1e-4, 3e-4, 1e-3)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels on
+# this workload, from the ncu launch list in profiles/launches_cfg5_Q150k_N64.md.  Valid only
+# for the kernel sources they were measured on: any change to them makes `traffic` null.
+PAIR_TRAFFIC = {"sources_sha256_16": "0d70d3b2d2d164ed", "k_pair<float,0>": 1016.8e6, "k_pair<float,1>": 1802.9e6}
+PAIR_SOURCES = ("mop_pair.cu", "mop_prep.cu", "mop_internal.cuh")
+
+
+def pair_sources_sha() -> str:
+    import hashlib
+    csrc = ROOT / "paper_2501_11962_b300" / "csrc"
+    return hashlib.sha256(b"".join((csrc / f).read_bytes() for f in PAIR_SOURCES)).hexdigest()[:16]
 
 
 def parse():
@@ -247,8 +258,11 @@ def run_ours(args, world, rank, local):
     achieved = flops[dom] / (mean_pass[dom] * 1e-3) / 1e12
     fma_peak = mop.measure_fp32_peak(local)      # dependent-FMA microkernel on this GPU, now
     ach_force = flops["pair_force"] / (mean_pass["pair_force"] * 1e-3) / 1e12
+    kname = "k_pair<float," + ("0>" if dom == "pair_force" else "1>")
+    traffic = PAIR_TRAFFIC.get(kname) if (args.config == 5 and N == 64 and
+                                          pair_sources_sha() == PAIR_TRAFFIC["sources_sha256_16"]) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_pair<float," + ("0>" if dom == "pair_force" else "1>"),
+                "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname,
                 "unique_pairs_per_launch": unique, "listed_pairs_per_launch": listed,
                 "flops_per_unique_pair": FLOPS_FORCE if dom == "pair_force" else FLOPS_HVP,
                 "peak_note": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {SM_MAX_MHZ:.0f} MHz",

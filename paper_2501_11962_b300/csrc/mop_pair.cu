@@ -242,7 +242,10 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
 constexpr int kJpRow = 52;
 // entries whose j-side partials are staged before one flush (divides the 4 entries of a block;
 // more would take the warp staging past the static shared-memory limit)
-constexpr int kJBatch = 2;
+#ifndef MOP_JBATCH
+#define MOP_JBATCH 2
+#endif
+constexpr int kJBatch = MOP_JBATCH;
 // unrolling of the 4-entry loop of a staged block
 #ifndef MOP_Q_UNROLL
 #define MOP_Q_UNROLL 4
