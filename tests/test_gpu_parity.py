@@ -67,6 +67,27 @@ def test_cfg2_mixed_matches_oracle():
     assert errs["V"] < TOL_V and errs["Es"] < TOL_V and errs["U1"] < TOL_V
 
 
+@pytest.mark.parametrize("prec", [mop.MOP_PREC_MIXED, mop.MOP_PREC_FP64])
+def test_bonds_across_the_box_edge(prec):
+    # every 7th atom moved by whole box vectors in all beads: its bonds and angles cross the box
+    # edge in the caller's coordinates, which takes the minimum-image branch of the bonded terms
+    from tests.test_oracle_pins import lattice_shift
+    w = workload(2, n_beads=6)
+    X = (w.paths[0].astype(np.float64) + lattice_shift(w.system)[None]).astype(np.float32)
+    eng = mop.Engine(w.system, precision=prec)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    F = eng.get_field(0, mop.MOP_FIELD_FORCE)
+    H = eng.get_field(0, mop.MOP_FIELD_HETA)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "Heta"))
+    N = X.shape[0]
+    errs = dict(F=rel(F[:N - 1], r["F"][:N - 1]), Heta=rel(H[:N - 1], r["Heta"][:N - 1]), G=rel(G, r["G"]),
+                V=abs(v[0] - r["veff"]) / abs(r["veff"]))
+    print("shifted atoms", prec, errs)
+    tf, th, tv = (TOL_F, TOL_H, TOL_V) if prec == mop.MOP_PREC_MIXED else (TOL_F64, TOL_F64, TOL_F64)
+    assert errs["F"] < tf and errs["G"] < tf and errs["Heta"] < th and errs["V"] < tv, errs
+
+
 def test_cfg2_small_path_edge_cases():
     """N = 1 (V = U, G = -F) and N = 2 (one spring, no interior bead)."""
     w = workload(2)

@@ -195,6 +195,27 @@ def test_newton_third_law_and_translation():
     assert np.abs(F2 - F).max() < 1e-9 * np.abs(F).max()
 
 
+def lattice_shift(system, every=7):
+    """Whole-box shifts for atoms a % every == 0 (the same in every bead): the path and every
+    difference R^{n+1} - R^n are unchanged, while their bonds and pairs now reach across the box
+    edge in the caller's coordinates."""
+    shift = np.zeros((system.n_atoms, 3))
+    shift[::every] = np.asarray(system.box) * np.array([1.0, -1.0, 2.0])
+    return shift
+
+
+def test_periodic_images_of_single_atoms_leave_veff_unchanged():
+    # U and the spring term depend on positions only through minimum images (bonded terms, pair
+    # terms) and through R^{n+1} - R^n, which a per-atom lattice shift keeps
+    w = workload(2, n_beads=3)
+    o = oracle.Oracle(w.system)
+    X = w.paths[0].astype(float)
+    r0 = o.veff(X)
+    r1 = o.veff(X + lattice_shift(w.system)[None])
+    assert r1["veff"] == pytest.approx(r0["veff"], rel=1e-12)
+    assert np.abs(r1["G"] - r0["G"]).max() < 1e-9 * np.abs(r0["G"]).max()
+
+
 def test_force_is_minus_gradient_of_U(rng):
     w = workload(2, n_beads=2)
     o = oracle.Oracle(w.system)
