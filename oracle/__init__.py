@@ -65,6 +65,13 @@ def lib():
         _lib.orc_bias.restype = d
         _lib.orc_step.argtypes = [p, i, p, p, p, d, d, d, C.c_uint64, C.c_uint64, i]
         _lib.orc_step.restype = d
+        _lib.orc_cv_com.argtypes = [p, p, p, i, p, i, i, p, d]
+        _lib.orc_cv_com.restype = d
+        _lib.orc_bias_com.argtypes = [p, i, p, p, i, p, i, i, i, i, p, p, p, p, p]
+        _lib.orc_bias_com.restype = d
+        _lib.orc_metad.argtypes = [p, i, p, p, d, d, d, C.c_uint64, C.c_uint64, i, i, p, i, p, i, i, i, d, d, i,
+                                   p, p, p, i]
+        _lib.orc_metad.restype = d
         _lib.orc_num_threads.restype = i
     return _lib
 
@@ -184,6 +191,47 @@ class Oracle:
         V = self.L.orc_bias(self._sp, X.shape[0], _ptr(X), _ptr(ga), len(ga), _ptr(gb), len(gb), int(e2e),
                             len(c), _ptr(c), _ptr(h), _ptr(w), _ptr(G), _ptr(cv))
         return V, G, float(cv[0])
+
+    def cv_com(self, x, ga, gb, com: bool):
+        """CV with optional mass weighting (orc_cv_com): s and ds/dx [Q][3]."""
+        x = np.ascontiguousarray(x, np.float64)
+        ga = np.ascontiguousarray(ga, np.int32)
+        gb = np.ascontiguousarray(gb, np.int32)
+        ds = np.zeros((self.Q, 3))
+        s = self.L.orc_cv_com(self._sp, _ptr(x), _ptr(ga), len(ga), _ptr(gb), len(gb), int(com), _ptr(ds), 1.0)
+        return s, ds
+
+    def bias_com(self, X, ga, gb, centers, heights, widths, e2e: bool = False, com: bool = False):
+        X = np.ascontiguousarray(X, np.float64)
+        ga = np.ascontiguousarray(ga, np.int32)
+        gb = np.ascontiguousarray(gb, np.int32)
+        c = np.ascontiguousarray(centers, np.float64)
+        h = np.ascontiguousarray(heights, np.float64)
+        w = np.ascontiguousarray(widths, np.float64)
+        G = np.zeros(X.shape)
+        cv = np.zeros(1)
+        V = self.L.orc_bias_com(self._sp, X.shape[0], _ptr(X), _ptr(ga), len(ga), _ptr(gb), len(gb), int(e2e),
+                                int(com), len(c), _ptr(c), _ptr(h), _ptr(w), _ptr(G), _ptr(cv))
+        return V, G, float(cv[0])
+
+    def metad(self, X, Vel, dt, gamma, temperature, seed, step0, n_deposits, stride, ga, gb, height, width,
+              e2e=False, com=False, gaussians=None, round_f32=True):
+        """Metadynamics of paths (orc_metad), X and Vel updated in place.  Returns V_eff + V_bias
+        at the final positions and the Gaussians (centers, heights, widths) after the run."""
+        ga = np.ascontiguousarray(ga, np.int32)
+        gb = np.ascontiguousarray(gb, np.int32)
+        g0 = [] if gaussians is None else list(zip(*gaussians))
+        n0 = len(g0)
+        c = np.zeros(n0 + n_deposits)
+        h = np.zeros(n0 + n_deposits)
+        w = np.zeros(n0 + n_deposits)
+        for k, (ck, hk, wk) in enumerate(g0):
+            c[k], h[k], w[k] = ck, hk, wk
+        V = self.L.orc_metad(self._sp, X.shape[0], _ptr(X), _ptr(Vel), float(dt), float(gamma), float(temperature),
+                             int(seed), int(step0), int(n_deposits), int(stride), _ptr(ga), len(ga), _ptr(gb),
+                             len(gb), int(e2e), int(com), float(height), float(width), n0, _ptr(c), _ptr(h),
+                             _ptr(w), int(round_f32))
+        return V, (c, h, w)
 
     def step(self, X, V, G, dt, gamma, temperature, seed, step, round_f32=True):
         """One BAOAB / velocity-Verlet step in place; returns V_eff at the new positions."""

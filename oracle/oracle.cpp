@@ -33,6 +33,7 @@
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -607,13 +608,77 @@ double orc_bias(const orc_system* s, int N, const double* X, const int32_t* ga, 
   return V;
 }
 
+// Collective variable with optional mass weighting: s = |C_A - C_B| (minimum image), where
+// C = sum_k w_k x_k / sum_k w_k over a group, w_k = m_k when com != 0 (the centre-of-mass
+// distance the paper biases, Sec. 3) and 1 otherwise (the geometric centroid); each atom is
+// unwrapped relative to its group's first atom.  Adds w * ds/dx into dsdx[Q][3] (if non-NULL);
+// returns s.
+double orc_cv_com(const orc_system* s, const double* x, const int32_t* ga, int na, const int32_t* gb,
+                  int nb, int com, double* dsdx, double w) {
+  auto centre = [&](const int32_t* g, int n, double* c, double* W) {
+    double acc[3] = {0, 0, 0}, wt = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double d[3];
+      min_image(*s, x + 3 * g[k], x + 3 * g[0], d);
+      const double m = com ? s->mass[g[k]] : 1.0;
+      for (int c2 = 0; c2 < 3; ++c2) acc[c2] += m * (x[3 * g[0] + c2] + d[c2]);
+      wt += m;
+    }
+    for (int c2 = 0; c2 < 3; ++c2) c[c2] = acc[c2] / wt;
+    *W = wt;
+  };
+  double ca[3], cb[3], Wa, Wb;
+  centre(ga, na, ca, &Wa);
+  centre(gb, nb, cb, &Wb);
+  double d[3];
+  min_image(*s, ca, cb, d);
+  const double sv = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (dsdx) {
+    for (int k = 0; k < na; ++k) {
+      const double m = com ? s->mass[ga[k]] : 1.0;
+      for (int c = 0; c < 3; ++c) dsdx[3 * ga[k] + c] += w * d[c] / sv * m / Wa;
+    }
+    for (int k = 0; k < nb; ++k) {
+      const double m = com ? s->mass[gb[k]] : 1.0;
+      for (int c = 0; c < 3; ++c) dsdx[3 * gb[k] + c] -= w * d[c] / sv * m / Wb;
+    }
+  }
+  return sv;
+}
+
+// Bias of orc_bias on the CV of orc_cv_com (com selects the mass weighting).
+double orc_bias_com(const orc_system* s, int N, const double* X, const int32_t* ga, int na,
+                    const int32_t* gb, int nb, int e2e, int com, int n_gauss, const double* centers,
+                    const double* heights, const double* widths, double* G, double* cv) {
+  const size_t n3 = 3 * (size_t)s->Q;
+  std::vector<double> dS((size_t)N * n3, 0.0);
+  double S = orc_cv_com(s, X + (size_t)(N - 1) * n3, ga, na, gb, nb, com, dS.data() + (size_t)(N - 1) * n3, 1.0);
+  if (e2e) S -= orc_cv_com(s, X, ga, na, gb, nb, com, dS.data(), -1.0);
+  double V = 0.0, dV = 0.0;
+  for (int k = 0; k < n_gauss; ++k) {
+    const double z = (S - centers[k]) / widths[k];
+    const double e = heights[k] * std::exp(-0.5 * z * z);
+    V += e;
+    dV += -e * z / widths[k];
+  }
+  if (G)
+    for (size_t k = 0; k < dS.size(); ++k) G[k] += dV * dS[k];
+  if (cv) *cv = S;
+  return V;
+}
+
+}  // extern "C"
+
+namespace {
+
 // One BAOAB step (gamma > 0) or velocity-Verlet step (gamma = 0) of the path dynamics
-// M d2R^n/dt2 = -dV_eff/dR^n (Eq. 4) with fictitious masses equal to the physical ones.
-// X, Vel: [N][Q][3] FP64 state, updated in place; G: gradient at X on entry, at the new X on
-// exit.  The gradient is evaluated at the float32-rounded positions when round_f32 != 0.
-// Returns V_eff at the new positions.
-double orc_step(const orc_system* s, int N, double* X, double* Vel, double* G, double dt, double gamma,
-                double temperature, uint64_t seed, uint64_t step, int round_f32) {
+// M d2R^n/dt2 = -dU_tot/dR^n (Eq. 4) with fictitious masses equal to the physical ones: half
+// kick, half drift, Ornstein-Uhlenbeck velocity update with Philox noise keyed by (seed, step,
+// bead, atom), half drift, new gradient, half kick.  grad(Xe, G) returns U_tot at Xe and writes
+// its gradient; Xe is X rounded to float32 when round_f32 != 0.
+double baoab_step(const orc_system* s, int N, double* X, double* Vel, double* G, double dt, double gamma,
+                  double temperature, uint64_t seed, uint64_t step, int round_f32,
+                  const std::function<double(const double*, double*)>& grad) {
   const int Q = s->Q;
   const size_t n3 = 3 * (size_t)Q, tot = (size_t)N * n3;
   const double kT = kBoltzmann * temperature;
@@ -637,9 +702,68 @@ double orc_step(const orc_system* s, int N, double* X, double* Vel, double* G, d
   std::vector<double> Xe(X, X + tot);
   if (round_f32)
     for (auto& v : Xe) v = (double)(float)v;
-  double V;
-  orc_veff(s, N, Xe.data(), 0, 0.0, &V, G, nullptr, nullptr, nullptr, nullptr);
+  const double V = grad(Xe.data(), G);
   for (size_t k = 0; k < tot; ++k) Vel[k] -= 0.5 * dt * G[k] / s->mass[(k % n3) / 3];
+  return V;
+}
+
+}  // namespace
+
+extern "C" {
+
+// One step of the path dynamics on V_eff alone (see baoab_step).  X, Vel: [N][Q][3] FP64 state,
+// updated in place; G: gradient at X on entry, at the new X on exit.  Returns V_eff at the new
+// positions.
+double orc_step(const orc_system* s, int N, double* X, double* Vel, double* G, double dt, double gamma,
+                double temperature, uint64_t seed, uint64_t step, int round_f32) {
+  return baoab_step(s, N, X, Vel, G, dt, gamma, temperature, seed, step, round_f32,
+                    [&](const double* Xe, double* Gout) {
+                      double V;
+                      orc_veff(s, N, Xe, 0, 0.0, &V, Gout, nullptr, nullptr, nullptr, nullptr);
+                      return V;
+                    });
+}
+
+// Metadynamics of paths (Sec. 1.2 with the deposition of Sec. 3, a new Gaussian every `stride`
+// MD steps): n_deposits rounds of `stride` steps of the path dynamics on V_eff + V_bias, each
+// round ending with one Gaussian of the given height and width centred at the CV's value at the
+// current (float32-rounded when round_f32) positions.  After each deposit the gradient is
+// evaluated again, so the next step starts from the new bias.  Step k of the run draws its
+// noise with counter step0 + k.  centers/heights/widths hold n_gauss0 Gaussians on entry and
+// n_gauss0 + n_deposits on exit.  Vel holds the velocities (zero for a fresh start).  Returns
+// V_eff + V_bias at the final positions.
+double orc_metad(const orc_system* s, int N, double* X, double* Vel, double dt, double gamma, double temperature,
+                 uint64_t seed, uint64_t step0, int n_deposits, int stride, const int32_t* ga, int na,
+                 const int32_t* gb, int nb, int e2e, int com, double height, double width, int n_gauss0,
+                 double* centers, double* heights, double* widths, int round_f32) {
+  const size_t tot = (size_t)N * 3 * (size_t)s->Q;
+  int ng = n_gauss0;
+  auto total = [&](const double* Xe, double* Gout) {
+    double V;
+    orc_veff(s, N, Xe, 0, 0.0, &V, Gout, nullptr, nullptr, nullptr, nullptr);
+    return V + orc_bias_com(s, N, Xe, ga, na, gb, nb, e2e, com, ng, centers, heights, widths, Gout, nullptr);
+  };
+  auto rounded = [&](const double* x) {
+    std::vector<double> Xe(x, x + tot);
+    if (round_f32)
+      for (auto& v : Xe) v = (double)(float)v;
+    return Xe;
+  };
+  std::vector<double> G(tot);
+  double V = total(rounded(X).data(), G.data());
+  uint64_t step = step0;
+  for (int d = 0; d < n_deposits; ++d) {
+    for (int k = 0; k < stride; ++k)
+      V = baoab_step(s, N, X, Vel, G.data(), dt, gamma, temperature, seed, step++, round_f32, total);
+    const std::vector<double> Xe = rounded(X);
+    double S = 0.0;
+    orc_bias_com(s, N, Xe.data(), ga, na, gb, nb, e2e, com, 0, nullptr, nullptr, nullptr, nullptr, &S);
+    centers[ng] = S;
+    heights[ng] = height;
+    widths[ng] = width;
+    ++ng;
+    V = total(Xe.data(), G.data());
+  }
   return V;
 }
 

@@ -452,3 +452,84 @@ def test_nve_energy_error_scales_as_dt_squared():
             err = max(err, abs(Ve + 0.5 * np.sum(m * V ** 2) - E0))
         drift.append(err)
     assert 3.0 < drift[0] / drift[1] < 5.0
+
+
+def test_com_cv_reduces_to_centroid_and_matches_two_atom_closed_form():
+    # with unit weights the CV is the geometric-centroid distance of the existing pin
+    w = workload(4, n_beads=2)
+    o = oracle.Oracle(w.system)
+    x = w.paths[0][-1].astype(float)
+    ga, gb = w.cv_groups
+    s0, d0 = o.cv_distance(x, ga, gb)
+    s1, d1 = o.cv_com(x, ga, gb, com=False)
+    assert s1 == pytest.approx(s0, rel=1e-14)
+    np.testing.assert_allclose(d1, d0, rtol=1e-12, atol=1e-15)
+    # mass-weighted centres of two two-atom groups, written out by hand
+    pos = np.array([[1.0, 2.0, 3.0], [1.4, 2.0, 3.3], [4.0, 4.5, 2.0], [4.2, 4.1, 2.6]])
+    m = np.array([1.0, 3.0, 2.0, 6.0])
+    sys = small_system(pos, [0, 0, 0, 0], [0.3], [0.0], mass=m, box=20.0)
+    o2 = oracle.Oracle(sys)
+    ca = (1.0 * pos[0] + 3.0 * pos[1]) / 4.0
+    cb = (2.0 * pos[2] + 6.0 * pos[3]) / 8.0
+    s, ds = o2.cv_com(pos, [0, 1], [2, 3], com=True)
+    assert s == pytest.approx(np.linalg.norm(ca - cb), rel=1e-14)
+    u = (ca - cb) / np.linalg.norm(ca - cb)
+    np.testing.assert_allclose(ds[1], 3.0 / 4.0 * u, rtol=1e-12)
+    np.testing.assert_allclose(ds[3], -6.0 / 8.0 * u, rtol=1e-12)
+    # and its derivative by central differences
+    h = 1e-6
+    for a in range(4):
+        for c in range(3):
+            xp, xm = pos.copy(), pos.copy()
+            xp[a, c] += h
+            xm[a, c] -= h
+            fd = (o2.cv_com(xp, [0, 1], [2, 3], True)[0] - o2.cv_com(xm, [0, 1], [2, 3], True)[0]) / (2 * h)
+            assert fd == pytest.approx(ds[a, c], rel=1e-6, abs=1e-9)
+
+
+def _metad_setup():
+    sys, pos = synth.lj_fcc()
+    X0 = synth.make_path(pos, 3, 91, std=0.005).astype(np.float64)
+    ga, gb = np.arange(0, 4), np.arange(100, 104)
+    return sys, X0, ga, gb
+
+
+def test_metad_with_zero_height_is_plain_dynamics_and_deposits_track_the_cv():
+    sys, X0, ga, gb = _metad_setup()
+    o = oracle.Oracle(sys)
+    dt, gamma, T = 2e-4, 5.0, 300.0
+    X, V = X0.copy(), np.zeros_like(X0)
+    _, (c, h, w) = o.metad(X, V, dt, gamma, T, 7, 0, 2, 3, ga, gb, 0.0, 0.1, com=True)
+    # the same six steps without any bias, and the CV after each block of three
+    Y, U = X0.copy(), np.zeros_like(X0)
+    G = o.veff(Y.astype(np.float32).astype(np.float64))["G"]
+    centres = []
+    for k in range(6):
+        o.step(Y, U, G, dt, gamma, T, 7, k)
+        if k % 3 == 2:
+            centres.append(o.cv_com(Y[-1].astype(np.float32).astype(np.float64), ga, gb, True)[0])
+    assert np.array_equal(X, Y) and np.array_equal(V, U)
+    np.testing.assert_allclose(c, centres, rtol=1e-14)
+    assert np.all(h == 0.0) and np.all(w == 0.1)
+
+
+def test_metad_energy_with_a_static_bias_is_conserved_to_second_order():
+    # velocity Verlet on V_eff + V_bias + kinetic energy: a bias force inconsistent with the bias
+    # energy would show up as a first-order drift
+    sys, X0, ga, gb = _metad_setup()
+    o = oracle.Oracle(sys)
+    m = sys.mass[None, :, None]
+    s0 = o.cv_com(X0[-1], ga, gb, True)[0]
+    g = ([s0 + 0.02], [500.0], [0.05])          # a steep Gaussian just past the start
+    drift = []
+    for dt in (2e-4, 1e-4):
+        X = X0.copy()
+        V = np.random.default_rng(3).normal(0, 1, X.shape) * np.sqrt(0.0083144626 * 30 / m)
+        Vb0, _, _ = o.bias_com(X, ga, gb, *g, com=True)
+        E0 = o.veff(X, want=())["veff"] + Vb0 + 0.5 * np.sum(m * V ** 2)
+        n = int(round(0.01 / dt))
+        # one round of n steps; its deposit has zero height, so it does not change the energy
+        Vt, _ = o.metad(X, V, dt, 0.0, 300.0, 1, 0, 1, n, ga, gb, 0.0, 0.05, com=True, gaussians=g,
+                        round_f32=False)
+        drift.append(abs(Vt + 0.5 * np.sum(m * V ** 2) - E0))
+    assert drift[1] > 0 and 3.0 < drift[0] / drift[1] < 5.0
