@@ -65,6 +65,7 @@ enum { MOP_PREC_MIXED = 0, /* FP32 pair arithmetic, FP64 accumulation and path t
 #define MOP_DEVPTR 1       /* pointer arguments are device pointers; call is asynchronous */
 #define MOP_INPUT_F64 2    /* mop_set_path: xyz is double* instead of float* */
 #define MOP_E2E 4          /* mop_add_bias: CV = s(R^N) - s(R^1) (Eq. 8) instead of s(R^N) */
+#define MOP_COM 8          /* mop_add_bias: mass-weighted group centres (centres of mass) */
 
 /* fields for mop_get_field, each [N][Q][3] FP64 in the caller's atom order */
 enum { MOP_FIELD_FORCE = 0, /* F^n = -grad U(R^n) on the beads that need it */
@@ -142,8 +143,9 @@ mop_status mop_get_energies(mop_handle* h, int32_t path_id, double out[4]);
 
 /* Metadynamics bias (Sec. 1.2): defines the CV of path `path_id` as the distance between the
  * centroids of atom groups A and B (minimum image; each centroid taken with its group
- * unwrapped relative to the group's first atom) at the last bead, or, with MOP_E2E, its
- * difference between the last and the first bead (Eq. 8); then appends one Gaussian
+ * unwrapped relative to the group's first atom; mass-weighted, i.e. centres of mass as in
+ * Sec. 3, with MOP_COM) at the last bead, or, with MOP_E2E, its difference between the last
+ * and the first bead (Eq. 8); then appends one Gaussian
  * height * exp(-(S - s_center)^2 / (2 width^2)).  grpA/grpB may be NULL to keep the groups of
  * the previous call.  Groups hold 1..1024 atom indices (host pointers); at most 4096
  * Gaussians per path.  Errors: MOP_ERR_ARG, MOP_ERR_STATE (no groups yet), MOP_ERR_CUDA. */
@@ -158,6 +160,25 @@ mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const in
  * rounding (MOP_PREC_MIXED).  Errors: MOP_ERR_STATE, MOP_ERR_ARG, MOP_ERR_CUDA. */
 mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed,
                     void* cuda_stream);
+
+/* Metadynamics of paths (Sec. 1.2, with the deposition rule of Sec. 3: a new Gaussian every
+ * `stride` MD steps, 500 in the paper).  Runs n_deposits rounds; each round is mop_step(stride,
+ * dt_md, gamma, seed) on V_eff plus the bias deposited so far, then appends to every path with
+ * CV groups (mop_add_bias) one Gaussian height * exp(-(S - S_now)^2 / (2 width^2)) centred at
+ * the CV's value S_now at the current positions, computed on the device.  The gradient is then
+ * evaluated again before the next round, so its first half kick sees the new Gaussian.  Works
+ * in graph mode (the rounds replay the captured step).  Synchronous.  Errors: MOP_ERR_ARG
+ * (n_deposits < 0, stride < 1, non-finite height, width <= 0, more than 4096 Gaussians),
+ * MOP_ERR_STATE (no path has CV groups), and those of mop_step. */
+mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, double dt_md, double gamma,
+                            uint64_t seed, double height, double width, void* cuda_stream);
+
+/* Copies the Gaussians of path `path_id` (those of mop_add_bias and mop_metadynamics, in the
+ * order they were added) into centers/heights/widths (host arrays of `cap` doubles each; any may
+ * be NULL) and their number into *n (may exceed cap; then only cap are copied).  Synchronous.
+ * Errors: MOP_ERR_ARG, MOP_ERR_CUDA. */
+mop_status mop_get_gaussians(mop_handle* h, int32_t path_id, double* centers, double* heights, double* widths,
+                             int32_t cap, int32_t* n);
 
 /* Graph mode of mop_step (off by default).  When on, mop_step captures one MD step of all set
  * paths (integrator kernels plus a full V_eff + gradient evaluation, with no host

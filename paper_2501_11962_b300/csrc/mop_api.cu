@@ -212,7 +212,8 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     goff += 3 * (size_t)N * sc.Q;
     D.nA = (int)P.hA.size();
     D.nB = (int)P.hB.size();
-    D.n_gauss = (int)P.hc.size();
+    D.n_gauss = P.n_gauss;
+    D.com = P.com;
     D.e2e = P.e2e;
     D.gA = P.gA.p;
     D.gB = P.gB.p;
@@ -656,20 +657,23 @@ mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const in
     P.hA.assign(grpA, grpA + nA);
     P.hB.assign(grpB, grpB + nB);
     P.e2e = (flags & MOP_E2E) ? 1 : 0;
+    P.com = (flags & MOP_COM) ? 1 : 0;
     mop_status s;
     if ((s = upload(h, P.gA, P.hA.data(), P.hA.size())) || (s = upload(h, P.gB, P.hB.data(), P.hB.size())))
       return s;
   } else if (P.hA.empty()) {
     return fail(h, MOP_ERR_STATE, "no CV groups defined for path %d", path_id);
   }
-  if ((int)P.hc.size() >= kMaxGauss) return fail(h, MOP_ERR_ARG, "more than %d Gaussians", kMaxGauss);
-  P.hc.push_back(s_center);
-  P.hh.push_back(height);
-  P.hw.push_back(width);
-  mop_status s;
-  if ((s = upload(h, P.gc, P.hc.data(), P.hc.size())) || (s = upload(h, P.gh, P.hh.data(), P.hh.size())) ||
-      (s = upload(h, P.gw, P.hw.data(), P.hw.size())))
-    return s;
+  if (P.n_gauss >= kMaxGauss) return fail(h, MOP_ERR_ARG, "more than %d Gaussians", kMaxGauss);
+  // the Gaussians live on the device only (mop_metadynamics deposits there): append in place
+  CK(h, P.gc.ensure(kMaxGauss));
+  CK(h, P.gh.ensure(kMaxGauss));
+  CK(h, P.gw.ensure(kMaxGauss));
+  CK(h, cudaDeviceSynchronize());
+  CK(h, cudaMemcpy(P.gc.p + P.n_gauss, &s_center, sizeof(double), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(P.gh.p + P.n_gauss, &height, sizeof(double), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(P.gw.p + P.n_gauss, &width, sizeof(double), cudaMemcpyHostToDevice));
+  ++P.n_gauss;
   P.have_grad = false;
   return MOP_OK;
 }
@@ -836,6 +840,68 @@ mop_status mop_autotune(mop_handle* h, int32_t path_id, mop_tuning* best, double
   if (s2) return s2;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
+  return MOP_OK;
+}
+
+mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, double dt_md, double gamma,
+                            uint64_t seed, double height, double width, void* cuda_stream) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (n_deposits < 0 || stride < 1) return fail(h, MOP_ERR_ARG, "need n_deposits >= 0 and stride >= 1");
+  if (!std::isfinite(height) || !std::isfinite(width) || !(width > 0))
+    return fail(h, MOP_ERR_ARG, "invalid Gaussian height or width");
+  std::vector<int> ids;
+  mop_status s = select_paths(h, -1, &ids);
+  if (s) return s;
+  bool any = false;
+  for (int id : ids) {
+    const PathHost& P = h->paths[id];
+    if (P.hA.empty()) continue;
+    any = true;
+    if (P.n_gauss + n_deposits > kMaxGauss)
+      return fail(h, MOP_ERR_ARG, "path %d would hold more than %d Gaussians", id, kMaxGauss);
+  }
+  if (!any) return fail(h, MOP_ERR_STATE, "no path has CV groups (mop_add_bias)");
+  CK(h, cudaSetDevice(h->device));
+  for (int id : ids) {
+    PathHost& P = h->paths[id];
+    if (P.hA.empty()) continue;
+    CK(h, P.gc.ensure(kMaxGauss));
+    CK(h, P.gh.ensure(kMaxGauss));
+    CK(h, P.gw.ensure(kMaxGauss));
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (int d = 0; d < n_deposits; ++d) {
+    if ((s = mop_step(h, stride, dt_md, gamma, seed, cuda_stream))) return s;
+    // mop_step's last evaluation (eager or before the replays) left the table of all set paths,
+    // with their current Gaussian counts, in d_paths; positions are current on the device
+    Launch L{st, &h->launches};
+    CK(h, launch_deposit(h->sc, h->d_paths.p, (int)ids.size(), height, width, L));
+    for (int id : ids) {
+      PathHost& P = h->paths[id];
+      if (P.hA.empty()) continue;
+      ++P.n_gauss;
+      P.have_grad = false;   // the next round starts from a gradient with the new Gaussian
+    }
+    CK(h, cudaStreamSynchronize(st));
+  }
+  return MOP_OK;
+}
+
+mop_status mop_get_gaussians(mop_handle* h, int32_t path_id, double* centers, double* heights, double* widths,
+                             int32_t cap, int32_t* n) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (path_id < 0 || path_id >= kMaxPaths || cap < 0 || !n) return fail(h, MOP_ERR_ARG, "invalid argument");
+  const PathHost& P = h->paths[path_id];
+  *n = P.n_gauss;
+  const int k = std::min(cap, P.n_gauss);
+  if (k == 0) return MOP_OK;
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaDeviceSynchronize());
+  if (centers) CK(h, cudaMemcpy(centers, P.gc.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
+  if (heights) CK(h, cudaMemcpy(heights, P.gh.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
+  if (widths) CK(h, cudaMemcpy(widths, P.gw.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
   return MOP_OK;
 }
 

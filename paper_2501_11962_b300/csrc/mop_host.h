@@ -82,8 +82,8 @@ struct PathHost {
   DevBuf<double> e_pair, diag, veff_int;
   // bias
   std::vector<int> hA, hB;
-  std::vector<double> hc, hh, hw;
-  int e2e = 0;
+  int n_gauss = 0;          // Gaussians in gc/gh/gw (capacity kMaxGauss)
+  int e2e = 0, com = 0;
   DevBuf<int> gA, gB;
   DevBuf<double> gc, gh, gw;
 };
@@ -116,6 +116,8 @@ cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
                       double* e_bond, int nbx);
 cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
                       double* e_spring, int nbx);
+cudaError_t launch_deposit(const SysConsts& sc, const PathDev* d_paths, int n_paths, double height, double width,
+                           Launch L);
 cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L);
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L,
                           const double* e_bond, int e_bond_stride, int n_e1_blocks,

@@ -96,12 +96,12 @@ struct PathDev {
   double* e_pair;          // [n_clu]
   double* grad;            // [N][Q][3] caller order
   // bias
-  int nA, nB, n_gauss, e2e;
+  int nA, nB, n_gauss, e2e, com;   // com: mass-weighted group centres
   const int* gA;
   const int* gB;
-  const double* gc;        // centres, heights, widths [n_gauss]
-  const double* gh;
-  const double* gw;
+  double* gc;              // centres, heights, widths [kMaxGauss], n_gauss in use
+  double* gh;
+  double* gw;
   double* diag;            // [8]: U1, E_spring, E_bias, CV, V_eff, U_pair, U_bonded
   double* veff_out;        // one double
 };

@@ -456,26 +456,36 @@ __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const Path
   }
 }
 
-// centroid of a group at bead n, each atom unwrapped relative to the group's first atom
-__device__ void centroid(const SysConsts& sc, const PathDev& P, int n, const int* g, int ng, double* c) {
+// weight of atom a in a group centre: its mass with MOP_COM (centre of mass), else 1
+__device__ __forceinline__ double group_weight(const SysConsts& sc, const PathDev& P, int a) {
+  return P.com ? sc.mass[a] : 1.0;
+}
+
+// weighted centre of a group at bead n, each atom unwrapped relative to the group's first atom;
+// *W gets the total weight
+__device__ void centroid(const SysConsts& sc, const PathDev& P, int n, const int* g, int ng, double* c, double* W) {
   const size_t base = (size_t)n * 3 * P.Q;
-  double x0[3], acc[3] = {0.0, 0.0, 0.0};
+  double x0[3], acc[3] = {0.0, 0.0, 0.0}, wt = 0.0;
   for (int d = 0; d < 3; ++d) x0[d] = P.x64 ? P.x64[base + 3 * (size_t)g[0] + d] : (double)P.x32[base + 3 * (size_t)g[0] + d];
-  for (int k = 0; k < ng; ++k)
+  for (int k = 0; k < ng; ++k) {
+    const double m = group_weight(sc, P, g[k]);
     for (int d = 0; d < 3; ++d) {
       const double v = P.x64 ? P.x64[base + 3 * (size_t)g[k] + d] : (double)P.x32[base + 3 * (size_t)g[k] + d];
       double w = v - x0[d];
       w -= sc.L[d] * rint(w * sc.invL[d]);
-      acc[d] += w;
+      acc[d] += m * w;
     }
-  for (int d = 0; d < 3; ++d) c[d] = x0[d] + acc[d] / ng;
+    wt += m;
+  }
+  for (int d = 0; d < 3; ++d) c[d] = x0[d] + acc[d] / wt;
+  *W = wt;
 }
 
 // distance CV s = |c_A - c_B| (minimum image) at bead n; u = (c_A - c_B) / s
-__device__ double cv_at(const SysConsts& sc, const PathDev& P, int n, double* u) {
+__device__ double cv_at(const SysConsts& sc, const PathDev& P, int n, double* u, double* Wa, double* Wb) {
   double ca[3], cb[3];
-  centroid(sc, P, n, P.gA, P.nA, ca);
-  centroid(sc, P, n, P.gB, P.nB, cb);
+  centroid(sc, P, n, P.gA, P.nA, ca, Wa);
+  centroid(sc, P, n, P.gB, P.nB, cb, Wb);
   double s2 = 0.0;
   for (int d = 0; d < 3; ++d) {
     double w = ca[d] - cb[d];
@@ -494,12 +504,12 @@ __global__ void k_bias(SysConsts sc, const PathDev* __restrict__ paths, int n_pa
   __shared__ double sS;
   const PathDev& P = paths[blockIdx.x];
   const bool on = P.n_gauss > 0 && P.nA > 0 && P.nB > 0;
-  double uN[3], u1[3];
+  double uN[3], u1[3], Wa = 1.0, Wb = 1.0;
   if (threadIdx.x == 0) {
     double S = 0.0;
     if (on) {
-      S = cv_at(sc, P, P.N - 1, uN);
-      if (P.e2e) S -= cv_at(sc, P, 0, u1);
+      S = cv_at(sc, P, P.N - 1, uN, &Wa, &Wb);
+      if (P.e2e) S -= cv_at(sc, P, 0, u1, &Wa, &Wb);
     }
     sS = S;
   }
@@ -518,20 +528,37 @@ __global__ void k_bias(SysConsts sc, const PathDev* __restrict__ paths, int n_pa
   if (threadIdx.x == 0) {
     if (on && P.grad) {
       const int nl = P.N - 1;
-      for (int k = 0; k < P.nA; ++k)
-        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gA[k]) + d] += dV * uN[d] / P.nA;
-      for (int k = 0; k < P.nB; ++k)
-        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gB[k]) + d] -= dV * uN[d] / P.nB;
-      if (P.e2e) {
-        for (int k = 0; k < P.nA; ++k)
-          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gA[k]) + d] -= dV * u1[d] / P.nA;
-        for (int k = 0; k < P.nB; ++k)
-          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gB[k]) + d] += dV * u1[d] / P.nB;
+      // ds/dx_k = +-(w_k / W) u for the atoms of group A / B (the total weights are the same
+      // at both beads)
+      for (int k = 0; k < P.nA; ++k) {
+        const double f = dV * group_weight(sc, P, P.gA[k]) / Wa;
+        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gA[k]) + d] += f * uN[d];
+        if (P.e2e)
+          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gA[k]) + d] -= f * u1[d];
+      }
+      for (int k = 0; k < P.nB; ++k) {
+        const double f = dV * group_weight(sc, P, P.gB[k]) / Wb;
+        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gB[k]) + d] -= f * uN[d];
+        if (P.e2e)
+          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gB[k]) + d] += f * u1[d];
       }
     }
     P.diag[2] = on ? V : 0.0;
     P.diag[3] = S;
   }
+}
+
+// metadynamics deposition (one block per path): a Gaussian centred at the current CV value
+// goes to slot n_gauss of every path with CV groups (the host counts the deposits)
+__global__ void k_deposit(SysConsts sc, const PathDev* __restrict__ paths, double height, double width) {
+  const PathDev& P = paths[blockIdx.x];
+  if (threadIdx.x != 0 || P.nA < 1 || P.nB < 1 || P.n_gauss >= kMaxGauss) return;
+  double u[3], Wa, Wb;
+  double S = cv_at(sc, P, P.N - 1, u, &Wa, &Wb);
+  if (P.e2e) S -= cv_at(sc, P, 0, u, &Wa, &Wb);
+  P.gc[P.n_gauss] = S;
+  P.gh[P.n_gauss] = height;
+  P.gw[P.n_gauss] = width;
 }
 
 // fixed-order sums of the partial energies -> V_eff (one block per path)
@@ -652,6 +679,13 @@ cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
     if (fd) k_e2_mixed<true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
     else k_e2_mixed<false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
   }
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deposit(const SysConsts& sc, const PathDev* d_paths, int n_paths, double height, double width,
+                           Launch L) {
+  k_deposit<<<n_paths, 32, 0, L.st>>>(sc, d_paths, height, width);
   ++*L.counter;
   return cudaGetLastError();
 }

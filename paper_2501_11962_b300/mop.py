@@ -18,13 +18,14 @@ STATUS_NAMES = ["MOP_OK", "MOP_ERR_ARG", "MOP_ERR_CUDA", "MOP_ERR_OOM", "MOP_ERR
 MOP_SHIFTED_FORCE, MOP_POT_SHIFT = 0, 1
 MOP_HVP_ADJOINT, MOP_HVP_FD = 0, 1
 MOP_PREC_MIXED, MOP_PREC_FP64 = 0, 1
-MOP_DEVPTR, MOP_INPUT_F64, MOP_E2E = 1, 2, 4
+MOP_DEVPTR, MOP_INPUT_F64, MOP_E2E, MOP_COM = 1, 2, 4, 8
 MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 
 EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_veff_and_grad", "mop_get_field",
            "mop_get_energies", "mop_add_bias", "mop_step", "mop_kinetic_energy", "mop_last_launch_count",
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
            "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_measure_fp32_peak",
+           "mop_metadynamics", "mop_get_gaussians",
            "mop_last_error")
 
 
@@ -81,6 +82,8 @@ def load(build_if_needed: bool = True):
     L.mop_get_energies.argtypes = [p, i32, p]
     L.mop_add_bias.argtypes = [p, p, i32, p, i32, d, d, d, i32, i32]
     L.mop_step.argtypes = [p, i32, d, d, C.c_uint64, p]
+    L.mop_metadynamics.argtypes = [p, i32, i32, d, d, C.c_uint64, d, d, p]
+    L.mop_get_gaussians.argtypes = [p, i32, p, p, p, i32, p]
     L.mop_kinetic_energy.argtypes = [p, i32, p]
     L.mop_last_launch_count.argtypes = [p]
     L.mop_last_launch_count.restype = i32
@@ -220,12 +223,14 @@ class Engine:
         self._check(self.L.mop_get_energies(self.h, path_id, _np_ptr(out)), "mop_get_energies")
         return dict(U1=out[0], Espring=out[1], Ebias=out[2], cv=out[3])
 
-    def add_bias(self, path_id: int, s_center: float, height: float, width: float, groups=None, e2e=False):
+    def add_bias(self, path_id: int, s_center: float, height: float, width: float, groups=None, e2e=False,
+                 com=False):
         if groups is not None:
             ga = np.ascontiguousarray(groups[0], np.int32)
             gb = np.ascontiguousarray(groups[1], np.int32)
+            flags = (MOP_E2E if e2e else 0) | (MOP_COM if com else 0)
             st = self.L.mop_add_bias(self.h, _np_ptr(ga), len(ga), _np_ptr(gb), len(gb), s_center, height, width,
-                                     path_id, MOP_E2E if e2e else 0)
+                                     path_id, flags)
         else:
             st = self.L.mop_add_bias(self.h, None, 0, None, 0, s_center, height, width, path_id, 0)
         self._check(st, "mop_add_bias")
@@ -250,6 +255,22 @@ class Engine:
 
     def step(self, n_steps: int, dt: float, gamma: float = 0.0, seed: int = 1):
         self._check(self.L.mop_step(self.h, n_steps, dt, gamma, seed, None), "mop_step")
+
+    def gaussians(self, path_id: int):
+        """(centers, heights, widths) of the Gaussians of a path, in the order they were added."""
+        n = np.zeros(1, np.int32)
+        self._check(self.L.mop_get_gaussians(self.h, path_id, None, None, None, 0, _np_ptr(n)), "mop_get_gaussians")
+        c, hh, w = np.zeros(int(n[0])), np.zeros(int(n[0])), np.zeros(int(n[0]))
+        self._check(self.L.mop_get_gaussians(self.h, path_id, _np_ptr(c), _np_ptr(hh), _np_ptr(w), int(n[0]),
+                                             _np_ptr(n)), "mop_get_gaussians")
+        return c, hh, w
+
+    def metadynamics(self, n_deposits: int, stride: int, dt: float, gamma: float, seed: int, height: float,
+                     width: float):
+        """n_deposits rounds of `stride` MD steps, each followed by one Gaussian at the current CV
+        of every path with CV groups (mop_metadynamics)."""
+        self._check(self.L.mop_metadynamics(self.h, n_deposits, stride, dt, gamma, seed, height, width, None),
+                    "mop_metadynamics")
 
     def kinetic_energy(self, path_id: int) -> float:
         out = np.zeros(1)

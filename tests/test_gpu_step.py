@@ -63,3 +63,29 @@ def test_nve_energy_conserved():
         drift.append(max(errs))
     assert drift[1] < drift[0]
     assert 2.5 < drift[0] / drift[1] < 5.5           # second-order integrator
+
+
+@pytest.mark.parametrize("com,graph", [(False, False), (True, False), (True, True)])
+def test_metadynamics_matches_oracle(com, graph):
+    # three rounds of two BAOAB steps, a Gaussian deposited on the CV after each round, on top of
+    # one Gaussian placed by hand; the oracle runs the same loop (same Philox counters)
+    w = workload(1, n_beads=4)
+    X0 = w.paths[0]
+    ga, gb = np.arange(0, 4), np.arange(100, 104)
+    o = oracle.Oracle(w.system)
+    s0 = o.cv_com(X0[-1].astype(np.float64), ga, gb, com)[0]
+    eng = mop.Engine(w.system, precision=mop.MOP_PREC_FP64)
+    eng.set_path(0, X0)
+    eng.add_bias(0, s0 + 0.02, 20.0, 0.05, groups=(ga, gb), com=com)
+    eng.set_graph_mode(graph)
+    eng.metadynamics(3, 2, 2e-4, 5.0, 11, 10.0, 0.05)
+    Xg = eng.get_path(0).astype(np.float64)
+    c, h, wd = eng.gaussians(0)
+    X = X0.astype(np.float64).copy()
+    V = np.zeros_like(X)
+    _, (co, ho, wo) = o.metad(X, V, 2e-4, 5.0, w.system.temperature, 11, 0, 3, 2, ga, gb, 10.0, 0.05, com=com,
+                              gaussians=([s0 + 0.02], [20.0], [0.05]), round_f32=False)
+    assert len(c) == 4 and np.abs(X - X0).max() > 1e-6
+    assert np.abs(Xg - X).max() < 1e-6                  # float32 readback of FP64 positions
+    np.testing.assert_allclose(c, co, rtol=1e-10)
+    assert np.array_equal(h, ho) and np.array_equal(wd, wo)
