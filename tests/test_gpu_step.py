@@ -89,3 +89,21 @@ def test_metadynamics_matches_oracle(com, graph):
     assert np.abs(Xg - X).max() < 1e-6                  # float32 readback of FP64 positions
     np.testing.assert_allclose(c, co, rtol=1e-10)
     assert np.array_equal(h, ho) and np.array_equal(wd, wo)
+
+
+def test_baoab_thermostat_holds_the_temperature():
+    # NVT check of the path dynamics (the paper's Sec. 2.3 validation): with strong Langevin
+    # coupling the kinetic temperature of all beads settles at the bath temperature
+    # (equipartition, 3 degrees of freedom per atom and bead)
+    w = workload(1, n_beads=4)
+    eng = mop.Engine(w.system, precision=mop.MOP_PREC_FP64)
+    eng.set_path(0, w.paths[0])
+    T, dt, gamma = w.system.temperature, 2e-4, 50.0
+    eng.step(200, dt, gamma, 5)                      # about 10 / gamma to equilibrate
+    kin = []
+    for _ in range(40):
+        eng.step(5, dt, gamma, 5)
+        kin.append(eng.kinetic_energy(0))
+    dof = 3 * w.system.n_atoms * w.paths[0].shape[0]
+    T_kin = 2.0 * np.mean(kin) / (dof * 0.0083144626)
+    assert abs(T_kin - T) / T < 0.05, T_kin
