@@ -55,6 +55,7 @@ struct mop_handle {
   double graph_dt = 0.0, graph_gamma = -1.0;
   uint64_t graph_seed = 0;
   DevBuf<unsigned long long> step_dev;   // Philox step counter read by the integrator
+  DevBuf<int> flag;                       // non-finite input flag of mop_set_path
   bool step_ready = false;
 };
 
@@ -88,13 +89,22 @@ bool finite_all(const double* p, size_t n) {
   return true;
 }
 
-__global__ void k_f2d(const float* in, double* out, long long n) {
+// precision copies of a path; *bad (if non-NULL) is set when a coordinate is not finite
+__global__ void k_f2d(const float* in, double* out, long long n, int* bad) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = (double)in[t];
+  if (t < n) {
+    const float v = in[t];
+    out[t] = widen(v);
+    if (bad && !isfinite(v)) atomicOr(bad, 1);
+  }
 }
-__global__ void k_d2f(const double* in, float* out, long long n) {
+__global__ void k_d2f(const double* in, float* out, long long n, int* bad) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = (float)in[t];
+  if (t < n) {
+    const double v = in[t];
+    out[t] = (float)v;
+    if (bad && !isfinite(v)) atomicOr(bad, 1);
+  }
 }
 
 // slot-ordered field -> caller-ordered [N][Q][3], zero rows outside [0, n_rows).
@@ -513,29 +523,36 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
   PathHost& P = h->paths[path_id];
   const size_t n = 3 * (size_t)n_beads * h->sc.Q;
   const bool dev = flags & MOP_DEVPTR, f64 = flags & MOP_INPUT_F64;
-  if (!dev) {
-    if (f64) {
-      if (!finite_all((const double*)xyz, n)) return fail(h, MOP_ERR_NONFINITE, "non-finite coordinate");
-    } else {
-      const float* x = (const float*)xyz;
-      for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(x[i])) return fail(h, MOP_ERR_NONFINITE, "non-finite coordinate");
-    }
-  }
   CK(h, P.x32.ensure(n));
   CK(h, P.x64.ensure(n));
   CK(h, P.vel.ensure(n));
+  // host input is checked for non-finite values on the device, during the precision copy
+  int* bad = nullptr;
+  if (!dev) {
+    CK(h, h->flag.ensure(1));
+    CK(h, cudaMemsetAsync(h->flag.p, 0, sizeof(int), st));
+    bad = h->flag.p;
+  }
   const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (f64) {
     CK(h, cudaMemcpyAsync(P.x64.p, xyz, n * sizeof(double), kind, st));
-    k_d2f<<<nblk(n, 256), 256, 0, st>>>(P.x64.p, P.x32.p, (long long)n);
+    k_d2f<<<nblk(n, 256), 256, 0, st>>>(P.x64.p, P.x32.p, (long long)n, bad);
   } else {
     CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), kind, st));
-    k_f2d<<<nblk(n, 256), 256, 0, st>>>(P.x32.p, P.x64.p, (long long)n);
+    k_f2d<<<nblk(n, 256), 256, 0, st>>>(P.x32.p, P.x64.p, (long long)n, bad);
   }
   CK(h, cudaGetLastError());
   CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
-  if (!dev) CK(h, cudaStreamSynchronize(st));
+  if (!dev) {
+    int flag = 0;
+    CK(h, cudaMemcpyAsync(&flag, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    if (flag) {
+      P.set = false;
+      drop_graph(h);
+      return fail(h, MOP_ERR_NONFINITE, "non-finite coordinate");
+    }
+  }
   if (P.N != n_beads) drop_graph(h);
   P.N = n_beads;
   P.set = true;
