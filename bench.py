@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default neighbour-search geometry")
     ap.add_argument("--no-metad", action="store_true", help="skip the metadynamics production-loop timing")
+    ap.add_argument("--no-batch", action="store_true", help="skip the multi-path batching timing")
     return ap.parse_args()
 
 
@@ -354,6 +355,35 @@ def run_ours(args, world, rank, local):
                  "note": "host wall clock over the rounds, including one synchronous re-evaluation per deposit"}
         em.close()
 
+    # batching: the 8 paths of uneven length of the water + ion workload (config 4, 968 beads)
+    # in one call, every pass one launch over all paths, against the same paths one call each
+    batch = None
+    if not args.no_batch and rank == 0:
+        w4 = synth.config(4)
+        eb = mop.Engine(w4.system, precision=mop.MOP_PREC_MIXED, device=local)
+        nbeads = 0
+        for pid, Xp in enumerate(w4.paths):
+            eb.set_path(pid, Xp)
+            nbeads += Xp.shape[0]
+        Q4 = w4.system.n_atoms
+
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / reps
+
+        t_all = timed(lambda: eb.veff_and_grad(-1, want_grad=False))
+        t_one = timed(lambda: [eb.veff_and_grad(pid, want_grad=False) for pid in range(len(w4.paths))])
+        batch = {"workload": f"config 4: {len(w4.paths)} paths, N = {[p.shape[0] for p in w4.paths]}, Q = {Q4}",
+                 "value": nbeads * Q4 / t_all, "unit": UNIT, "ms_per_call": t_all * 1e3,
+                 "one_call_per_path_ms": t_one * 1e3, "speedup_over_one_call_per_path": t_one / t_all,
+                 "note": "host wall clock of the synchronous C-ABI call (V_eff only read back)"}
+        eb.close()
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         ns = cpu_sample_beads(w)
@@ -371,7 +401,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": workload_name(args.config, N, Q), "Q": Q, "N": N, "paths": 1,
                        "hvp": "adjoint", "l2": "inputs larger than L2 (115 MB coordinates per step, >1 GB fields)",
                        "parallelism": f"{world} independent replica(s), one per GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fd_hvp": fd, "metad": metad,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fd_hvp": fd, "metad": metad, "batch": batch,
             "pass_ms": mean_pass, "tuning": tuned, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
         }
