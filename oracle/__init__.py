@@ -72,6 +72,11 @@ def lib():
         _lib.orc_metad.argtypes = [p, i, p, p, d, d, d, C.c_uint64, C.c_uint64, i, i, p, i, p, i, i, i, d, d, i,
                                    p, p, p, i]
         _lib.orc_metad.restype = d
+        _lib.orc_bias_multi.argtypes = [p, i, p, i, p, p, p, p, p, p, i, p, p, p, p, p]
+        _lib.orc_bias_multi.restype = d
+        _lib.orc_metad_multi.argtypes = [p, i, p, p, d, d, d, C.c_uint64, C.c_uint64, i, i, i, p, p, p, p, p, p,
+                                         d, p, i, p, p, p, i]
+        _lib.orc_metad_multi.restype = d
         _lib.orc_num_threads.restype = i
     return _lib
 
@@ -232,6 +237,50 @@ class Oracle:
                              len(gb), int(e2e), int(com), float(height), float(width), n0, _ptr(c), _ptr(h),
                              _ptr(w), int(round_f32))
         return V, (c, h, w)
+
+    @staticmethod
+    def _cv_arrays(cvs):
+        """cvs: [(group A, group B, e2e, com), ...] -> concatenated groups, offsets and flags."""
+        ga = np.concatenate([np.asarray(c[0], np.int32) for c in cvs]).astype(np.int32)
+        gb = np.concatenate([np.asarray(c[1], np.int32) for c in cvs]).astype(np.int32)
+        ga_off = np.concatenate([[0], np.cumsum([len(c[0]) for c in cvs])]).astype(np.int32)
+        gb_off = np.concatenate([[0], np.cumsum([len(c[1]) for c in cvs])]).astype(np.int32)
+        e2e = np.asarray([int(bool(c[2])) for c in cvs], np.int32)
+        com = np.asarray([int(bool(c[3])) for c in cvs], np.int32)
+        return ga, ga_off, gb, gb_off, e2e, com
+
+    def bias_multi(self, X, cvs, centers, widths, heights):
+        """Multi-CV bias (orc_bias_multi): returns V_b, dV_b/dX and the CV values."""
+        X = np.ascontiguousarray(X, np.float64)
+        arrs = self._cv_arrays(cvs)
+        n = len(cvs)
+        c = np.ascontiguousarray(np.reshape(centers, (-1, n)), np.float64)
+        w = np.ascontiguousarray(np.reshape(widths, (-1, n)), np.float64)
+        h = np.ascontiguousarray(heights, np.float64)
+        G = np.zeros(X.shape)
+        cv = np.zeros(n)
+        V = self.L.orc_bias_multi(self._sp, X.shape[0], _ptr(X), n, *[_ptr(a) for a in arrs], len(h), _ptr(c),
+                                  _ptr(w), _ptr(h), _ptr(G), _ptr(cv))
+        return V, G, cv
+
+    def metad_multi(self, X, Vel, dt, gamma, temperature, seed, step0, n_deposits, stride, cvs, height, dep_widths,
+                    gaussians=None, round_f32=True):
+        """Multi-CV metadynamics (orc_metad_multi), X and Vel in place.  gaussians = (centers [k][n],
+        widths [k][n], heights [k]) already present.  Returns V and the Gaussians after the run."""
+        arrs = self._cv_arrays(cvs)
+        n = len(cvs)
+        k0 = 0 if gaussians is None else len(gaussians[2])
+        c = np.zeros((k0 + n_deposits, n))
+        w = np.zeros((k0 + n_deposits, n))
+        h = np.zeros(k0 + n_deposits)
+        if k0:
+            c[:k0], w[:k0], h[:k0] = np.reshape(gaussians[0], (k0, n)), np.reshape(gaussians[1], (k0, n)), gaussians[2]
+        dw = np.ascontiguousarray(dep_widths, np.float64)
+        V = self.L.orc_metad_multi(self._sp, X.shape[0], _ptr(X), _ptr(Vel), float(dt), float(gamma),
+                                   float(temperature), int(seed), int(step0), int(n_deposits), int(stride), n,
+                                   *[_ptr(a) for a in arrs], float(height), _ptr(dw), k0, _ptr(c), _ptr(w), _ptr(h),
+                                   int(round_f32))
+        return V, (c, w, h)
 
     def step(self, X, V, G, dt, gamma, temperature, seed, step, round_f32=True):
         """One BAOAB / velocity-Verlet step in place; returns V_eff at the new positions."""

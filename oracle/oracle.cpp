@@ -667,6 +667,46 @@ double orc_bias_com(const orc_system* s, int N, const double* X, const int32_t* 
   return V;
 }
 
+// Multi-CV bias: n_cv CVs S_d (each the CV of orc_bias_com on its own groups, with its own
+// e2e and com flags; the groups of CV d are ga[ga_off[d] .. ga_off[d + 1]) and likewise gb) and
+// V_b = sum_k h_k exp(-sum_d (S_d - c_kd)^2 / (2 w_kd^2)), centres and widths [n_gauss][n_cv].
+// Adds dV_b/dX to G (if non-NULL); cv[n_cv] (if non-NULL) receives the S_d.  Returns V_b.
+double orc_bias_multi(const orc_system* s, int N, const double* X, int n_cv, const int32_t* ga,
+                      const int32_t* ga_off, const int32_t* gb, const int32_t* gb_off, const int32_t* e2e,
+                      const int32_t* com, int n_gauss, const double* centers, const double* widths,
+                      const double* heights, double* G, double* cv) {
+  const size_t n3 = 3 * (size_t)s->Q;
+  std::vector<std::vector<double>> dS(n_cv, std::vector<double>((size_t)N * n3, 0.0));
+  std::vector<double> S(n_cv), dV(n_cv, 0.0);
+  for (int d = 0; d < n_cv; ++d) {
+    const int32_t* a = ga + ga_off[d];
+    const int32_t* b = gb + gb_off[d];
+    const int na = ga_off[d + 1] - ga_off[d], nb = gb_off[d + 1] - gb_off[d];
+    S[d] = orc_cv_com(s, X + (size_t)(N - 1) * n3, a, na, b, nb, com[d], dS[d].data() + (size_t)(N - 1) * n3, 1.0);
+    if (e2e[d]) S[d] -= orc_cv_com(s, X, a, na, b, nb, com[d], dS[d].data(), -1.0);
+  }
+  double V = 0.0;
+  for (int k = 0; k < n_gauss; ++k) {
+    double q = 0.0;
+    for (int d = 0; d < n_cv; ++d) {
+      const double z = (S[d] - centers[(size_t)k * n_cv + d]) / widths[(size_t)k * n_cv + d];
+      q += z * z;
+    }
+    const double e = heights[k] * std::exp(-0.5 * q);
+    V += e;
+    for (int d = 0; d < n_cv; ++d) {
+      const double w = widths[(size_t)k * n_cv + d];
+      dV[d] += -e * (S[d] - centers[(size_t)k * n_cv + d]) / (w * w);
+    }
+  }
+  if (G)
+    for (int d = 0; d < n_cv; ++d)
+      for (size_t k = 0; k < dS[d].size(); ++k) G[k] += dV[d] * dS[d][k];
+  if (cv)
+    for (int d = 0; d < n_cv; ++d) cv[d] = S[d];
+  return V;
+}
+
 }  // extern "C"
 
 namespace {
@@ -761,6 +801,48 @@ double orc_metad(const orc_system* s, int N, double* X, double* Vel, double dt, 
     centers[ng] = S;
     heights[ng] = height;
     widths[ng] = width;
+    ++ng;
+    V = total(Xe.data(), G.data());
+  }
+  return V;
+}
+
+// Metadynamics of paths on n_cv CVs (orc_metad with the bias of orc_bias_multi): each deposit
+// is centred at the current S_d, with height `height` and widths dep_widths[d].  centers and
+// widths are [n_gauss0 + n_deposits][n_cv], heights [n_gauss0 + n_deposits].
+double orc_metad_multi(const orc_system* s, int N, double* X, double* Vel, double dt, double gamma,
+                       double temperature, uint64_t seed, uint64_t step0, int n_deposits, int stride, int n_cv,
+                       const int32_t* ga, const int32_t* ga_off, const int32_t* gb, const int32_t* gb_off,
+                       const int32_t* e2e, const int32_t* com, double height, const double* dep_widths,
+                       int n_gauss0, double* centers, double* widths, double* heights, int round_f32) {
+  const size_t tot = (size_t)N * 3 * (size_t)s->Q;
+  int ng = n_gauss0;
+  auto total = [&](const double* Xe, double* Gout) {
+    double V;
+    orc_veff(s, N, Xe, 0, 0.0, &V, Gout, nullptr, nullptr, nullptr, nullptr);
+    return V + orc_bias_multi(s, N, Xe, n_cv, ga, ga_off, gb, gb_off, e2e, com, ng, centers, widths, heights,
+                              Gout, nullptr);
+  };
+  auto rounded = [&](const double* x) {
+    std::vector<double> Xe(x, x + tot);
+    if (round_f32)
+      for (auto& v : Xe) v = (double)(float)v;
+    return Xe;
+  };
+  std::vector<double> G(tot), Snow(n_cv);
+  double V = total(rounded(X).data(), G.data());
+  uint64_t step = step0;
+  for (int dep = 0; dep < n_deposits; ++dep) {
+    for (int k = 0; k < stride; ++k)
+      V = baoab_step(s, N, X, Vel, G.data(), dt, gamma, temperature, seed, step++, round_f32, total);
+    const std::vector<double> Xe = rounded(X);
+    orc_bias_multi(s, N, Xe.data(), n_cv, ga, ga_off, gb, gb_off, e2e, com, 0, nullptr, nullptr, nullptr, nullptr,
+                   Snow.data());
+    for (int d = 0; d < n_cv; ++d) {
+      centers[(size_t)ng * n_cv + d] = Snow[d];
+      widths[(size_t)ng * n_cv + d] = dep_widths[d];
+    }
+    heights[ng] = height;
     ++ng;
     V = total(Xe.data(), G.data());
   }

@@ -533,3 +533,43 @@ def test_metad_energy_with_a_static_bias_is_conserved_to_second_order():
                         round_f32=False)
         drift.append(abs(Vt + 0.5 * np.sum(m * V ** 2) - E0))
     assert drift[1] > 0 and 3.0 < drift[0] / drift[1] < 5.0
+
+
+def test_multi_cv_bias_reduces_factorises_and_is_a_gradient():
+    w = workload(4, n_beads=3)
+    o = oracle.Oracle(w.system)
+    X = w.paths[0].astype(float)
+    ga, gb = w.cv_groups
+    gc_, gd = np.arange(10, 14), np.arange(300, 306)
+    # one CV: the single-CV bias
+    V1, G1, S1 = o.bias_multi(X, [(ga, gb, True, True)], [[0.3], [0.5]], [[0.05], [0.1]], [2.0, 1.5])
+    V0, G0, s0 = o.bias_com(X, ga, gb, [0.3, 0.5], [2.0, 1.5], [0.05, 0.1], e2e=True, com=True)
+    assert V1 == pytest.approx(V0, rel=1e-14) and S1[0] == pytest.approx(s0, rel=1e-14)
+    np.testing.assert_allclose(G1, G0, rtol=1e-12, atol=1e-15)
+    # two CVs, one Gaussian of unit height: the product of the one-dimensional factors
+    cvs = [(ga, gb, False, False), (gc_, gd, False, True)]
+    _, _, S = o.bias_multi(X, cvs, [[0.0, 0.0]], [[1.0, 1.0]], [0.0])
+    c, wd = np.array([S[0] - 0.04, S[1] + 0.1]), np.array([0.05, 0.2])
+    V2, G2, _ = o.bias_multi(X, cvs, [c], [wd], [1.0])
+    assert V2 == pytest.approx(np.exp(-0.5 * (0.04 / 0.05) ** 2) * np.exp(-0.5 * (0.1 / 0.2) ** 2), rel=1e-12)
+    # the gradient by central differences of V at a few coordinates of the last bead
+    h = 1e-6
+    for a in (ga[0], gb[1], gc_[2], gd[3]):
+        for k in range(3):
+            xp, xm = X.copy(), X.copy()
+            xp[-1, a, k] += h
+            xm[-1, a, k] -= h
+            fd = (o.bias_multi(xp, cvs, [c], [wd], [1.0])[0] - o.bias_multi(xm, cvs, [c], [wd], [1.0])[0]) / (2 * h)
+            assert fd == pytest.approx(G2[-1, a, k], rel=1e-5, abs=1e-9)
+
+
+def test_multi_cv_metad_with_one_cv_is_the_single_cv_loop():
+    sys, X0, ga, gb = _metad_setup()
+    o = oracle.Oracle(sys)
+    X1, V1 = X0.copy(), np.zeros_like(X0)
+    _, (c1, h1, w1) = o.metad(X1, V1, 2e-4, 5.0, 300.0, 7, 0, 2, 3, ga, gb, 30.0, 0.05, com=True)
+    X2, V2 = X0.copy(), np.zeros_like(X0)
+    _, (c2, w2, h2) = o.metad_multi(X2, V2, 2e-4, 5.0, 300.0, 7, 0, 2, 3, [(ga, gb, False, True)], 30.0, [0.05])
+    assert np.array_equal(X1, X2) and np.array_equal(V1, V2)
+    np.testing.assert_array_equal(c1, c2[:, 0])
+    assert np.array_equal(h1, h2) and np.array_equal(w1, w2[:, 0])
