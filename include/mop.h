@@ -161,24 +161,42 @@ mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const in
 mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed,
                     void* cuda_stream);
 
+/* Adds collective variable number *index (0, 1, ...; at most 4 per path) to the bias of path
+ * `path_id`: the distance of the centres of groups A and B, with the MOP_E2E and MOP_COM flags of
+ * mop_add_bias.  With several CVs the bias is a sum of multivariate Gaussians
+ *     h_k exp(-sum_q (S_q - c_kq)^2 / (2 w_kq^2)).
+ * deposit_width (nm, >= 0) is the width mop_metadynamics gives its Gaussians along this CV (0:
+ * the width passed to mop_metadynamics).  CVs can only be added while the path holds no
+ * Gaussians.  Errors: MOP_ERR_ARG, MOP_ERR_STATE (Gaussians present), MOP_ERR_CUDA. */
+mop_status mop_add_cv(mop_handle* h, int32_t path_id, const int32_t* grpA, int32_t nA, const int32_t* grpB,
+                      int32_t nB, int32_t flags, double deposit_width, int32_t* index);
+
+/* Appends one Gaussian on all CVs of path `path_id`: height and, per CV, centres[n_cv] and
+ * widths[n_cv] (host arrays).  Errors: MOP_ERR_ARG (widths <= 0, more than 4096 Gaussians),
+ * MOP_ERR_NONFINITE, MOP_ERR_STATE (no CV), MOP_ERR_CUDA. */
+mop_status mop_add_gaussian(mop_handle* h, int32_t path_id, double height, const double* centers,
+                            const double* widths);
+
 /* Metadynamics of paths (Sec. 1.2, with the deposition rule of Sec. 3: a new Gaussian every
  * `stride` MD steps, 500 in the paper).  Runs n_deposits rounds; each round is mop_step(stride,
  * dt_md, gamma, seed) on V_eff plus the bias deposited so far, then appends to every path with
- * CV groups (mop_add_bias) one Gaussian height * exp(-(S - S_now)^2 / (2 width^2)) centred at
- * the CV's value S_now at the current positions, computed on the device.  The gradient is then
+ * CVs (mop_add_bias, mop_add_cv) one Gaussian of the given height centred at the CVs' values at
+ * the current positions (computed on the device), with the width of each CV's deposit_width, or
+ * `width` where that is 0 (always for the CV of mop_add_bias).  The gradient is then
  * evaluated again before the next round, so its first half kick sees the new Gaussian.  Works
  * in graph mode (the rounds replay the captured step).  Synchronous.  Errors: MOP_ERR_ARG
  * (n_deposits < 0, stride < 1, non-finite height, width <= 0, more than 4096 Gaussians),
- * MOP_ERR_STATE (no path has CV groups), and those of mop_step. */
+ * MOP_ERR_STATE (no path has a CV), and those of mop_step. */
 mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, double dt_md, double gamma,
                             uint64_t seed, double height, double width, void* cuda_stream);
 
-/* Copies the Gaussians of path `path_id` (those of mop_add_bias and mop_metadynamics, in the
- * order they were added) into centers/heights/widths (host arrays of `cap` doubles each; any may
- * be NULL) and their number into *n (may exceed cap; then only cap are copied).  Synchronous.
- * Errors: MOP_ERR_ARG, MOP_ERR_CUDA. */
+/* Copies the Gaussians of path `path_id` (those of mop_add_bias, mop_add_gaussian and
+ * mop_metadynamics, in the order they were added): centers and widths as [k][n_cv] and heights
+ * as [k] (host arrays with room for `cap` Gaussians; any may be NULL), their number into *n (may
+ * exceed cap; then only cap are copied) and the number of CVs into *n_cv (may be NULL).
+ * Synchronous.  Errors: MOP_ERR_ARG, MOP_ERR_CUDA. */
 mop_status mop_get_gaussians(mop_handle* h, int32_t path_id, double* centers, double* heights, double* widths,
-                             int32_t cap, int32_t* n);
+                             int32_t cap, int32_t* n, int32_t* n_cv);
 
 /* Graph mode of mop_step (off by default).  When on, mop_step captures one MD step of all set
  * paths (integrator kernels plus a full V_eff + gradient evaluation, with no host

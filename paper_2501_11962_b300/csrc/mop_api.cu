@@ -220,16 +220,22 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.e_pair = P.e_pair.p;
     D.grad = dev_grad ? dev_grad + goff : P.grad_int.p;
     goff += 3 * (size_t)N * sc.Q;
-    D.nA = (int)P.hA.size();
-    D.nB = (int)P.hB.size();
+    D.n_cv = P.n_cv;
     D.n_gauss = P.n_gauss;
-    D.com = P.com;
-    D.e2e = P.e2e;
+    for (int q = 0; q <= kMaxCV; ++q) {
+      D.cv_a[q] = P.cv_a[q];
+      D.cv_b[q] = P.cv_b[q];
+    }
+    for (int q = 0; q < kMaxCV; ++q) {
+      D.cv_e2e[q] = P.cv_e2e[q];
+      D.cv_com[q] = P.cv_com[q];
+      D.cv_width[q] = P.cv_width[q];
+    }
     D.gA = P.gA.p;
     D.gB = P.gB.p;
     D.gc = P.gc.p;
-    D.gh = P.gh.p;
     D.gw = P.gw.p;
+    D.gh = P.gh.p;
     D.diag = P.diag.p;
     D.veff_out = dev_veff ? dev_veff + k : P.veff_int.p;
   }
@@ -654,6 +660,65 @@ mop_status mop_get_energies(mop_handle* h, int32_t path_id, double out[4]) {
   return MOP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// validates a group pair against the system
+mop_status check_groups(mop_handle* h, const int32_t* grpA, int32_t nA, const int32_t* grpB, int32_t nB) {
+  if (!grpA || !grpB || nA < 1 || nB < 1 || nA > kMaxGroup || nB > kMaxGroup)
+    return fail(h, MOP_ERR_ARG, "groups need 1..%d atoms each", kMaxGroup);
+  for (int k = 0; k < nA; ++k)
+    if (grpA[k] < 0 || grpA[k] >= h->sc.Q) return fail(h, MOP_ERR_ARG, "group A index out of range");
+  for (int k = 0; k < nB; ++k)
+    if (grpB[k] < 0 || grpB[k] >= h->sc.Q) return fail(h, MOP_ERR_ARG, "group B index out of range");
+  return MOP_OK;
+}
+
+// appends CV number P.n_cv (host copy, then the concatenated groups to the device)
+mop_status push_cv(mop_handle* h, PathHost& P, const int32_t* grpA, int32_t nA, const int32_t* grpB, int32_t nB,
+                   int32_t flags, double width) {
+  const int q = P.n_cv;
+  P.hA.insert(P.hA.end(), grpA, grpA + nA);
+  P.hB.insert(P.hB.end(), grpB, grpB + nB);
+  P.cv_a[q + 1] = (int)P.hA.size();
+  P.cv_b[q + 1] = (int)P.hB.size();
+  P.cv_e2e[q] = (flags & MOP_E2E) ? 1 : 0;
+  P.cv_com[q] = (flags & MOP_COM) ? 1 : 0;
+  P.cv_width[q] = width;
+  P.n_cv = q + 1;
+  mop_status s;
+  if ((s = upload(h, P.gA, P.hA.data(), P.hA.size())) || (s = upload(h, P.gB, P.hB.data(), P.hB.size()))) return s;
+  P.have_grad = false;
+  return MOP_OK;
+}
+
+mop_status ensure_gaussians(mop_handle* h, PathHost& P) {
+  CK(h, P.gc.ensure((size_t)kMaxGauss * kMaxCV));
+  CK(h, P.gw.ensure((size_t)kMaxGauss * kMaxCV));
+  CK(h, P.gh.ensure(kMaxGauss));
+  return MOP_OK;
+}
+
+// appends one Gaussian with n_cv centres and widths (host arrays)
+mop_status push_gaussian(mop_handle* h, PathHost& P, double height, const double* centers, const double* widths) {
+  if (P.n_gauss >= kMaxGauss) return fail(h, MOP_ERR_ARG, "more than %d Gaussians", kMaxGauss);
+  mop_status s = ensure_gaussians(h, P);
+  if (s) return s;
+  const size_t row = (size_t)P.n_gauss * kMaxCV;
+  CK(h, cudaDeviceSynchronize());
+  CK(h, cudaMemcpy(P.gc.p + row, centers, sizeof(double) * P.n_cv, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(P.gw.p + row, widths, sizeof(double) * P.n_cv, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(P.gh.p + P.n_gauss, &height, sizeof(double), cudaMemcpyHostToDevice));
+  ++P.n_gauss;
+  P.have_grad = false;
+  return MOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const int32_t* grpB, int32_t nB,
                         double s_center, double height, double width, int32_t path_id, int32_t flags) {
   if (!h) return MOP_ERR_ARG;
@@ -664,35 +729,56 @@ mop_status mop_add_bias(mop_handle* h, const int32_t* grpA, int32_t nA, const in
   if (!(width > 0)) return fail(h, MOP_ERR_ARG, "width must be > 0");
   CK(h, cudaSetDevice(h->device));
   PathHost& P = h->paths[path_id];
+  mop_status s;
   if (grpA || grpB) {
-    if (!grpA || !grpB || nA < 1 || nB < 1 || nA > kMaxGroup || nB > kMaxGroup)
-      return fail(h, MOP_ERR_ARG, "groups need 1..%d atoms each", kMaxGroup);
-    for (int k = 0; k < nA; ++k)
-      if (grpA[k] < 0 || grpA[k] >= h->sc.Q) return fail(h, MOP_ERR_ARG, "group A index out of range");
-    for (int k = 0; k < nB; ++k)
-      if (grpB[k] < 0 || grpB[k] >= h->sc.Q) return fail(h, MOP_ERR_ARG, "group B index out of range");
-    P.hA.assign(grpA, grpA + nA);
-    P.hB.assign(grpB, grpB + nB);
-    P.e2e = (flags & MOP_E2E) ? 1 : 0;
-    P.com = (flags & MOP_COM) ? 1 : 0;
-    mop_status s;
-    if ((s = upload(h, P.gA, P.hA.data(), P.hA.size())) || (s = upload(h, P.gB, P.hB.data(), P.hB.size())))
-      return s;
-  } else if (P.hA.empty()) {
+    if ((s = check_groups(h, grpA, nA, grpB, nB))) return s;
+    if (P.n_gauss > 0 && P.n_cv != 1)
+      return fail(h, MOP_ERR_STATE, "path %d holds Gaussians on %d CVs", path_id, P.n_cv);
+    // the single CV of this call replaces the path's CVs (its Gaussians are kept)
+    P.hA.clear();
+    P.hB.clear();
+    P.n_cv = 0;
+    if ((s = push_cv(h, P, grpA, nA, grpB, nB, flags, 0.0))) return s;
+  } else if (P.n_cv == 0) {
     return fail(h, MOP_ERR_STATE, "no CV groups defined for path %d", path_id);
+  } else if (P.n_cv != 1) {
+    return fail(h, MOP_ERR_STATE, "path %d has %d CVs: use mop_add_gaussian", path_id, P.n_cv);
   }
-  if (P.n_gauss >= kMaxGauss) return fail(h, MOP_ERR_ARG, "more than %d Gaussians", kMaxGauss);
-  // the Gaussians live on the device only (mop_metadynamics deposits there): append in place
-  CK(h, P.gc.ensure(kMaxGauss));
-  CK(h, P.gh.ensure(kMaxGauss));
-  CK(h, P.gw.ensure(kMaxGauss));
-  CK(h, cudaDeviceSynchronize());
-  CK(h, cudaMemcpy(P.gc.p + P.n_gauss, &s_center, sizeof(double), cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(P.gh.p + P.n_gauss, &height, sizeof(double), cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(P.gw.p + P.n_gauss, &width, sizeof(double), cudaMemcpyHostToDevice));
-  ++P.n_gauss;
-  P.have_grad = false;
+  return push_gaussian(h, P, height, &s_center, &width);
+}
+
+mop_status mop_add_cv(mop_handle* h, int32_t path_id, const int32_t* grpA, int32_t nA, const int32_t* grpB,
+                      int32_t nB, int32_t flags, double deposit_width, int32_t* index) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (path_id < 0 || path_id >= kMaxPaths) return fail(h, MOP_ERR_ARG, "path_id out of range");
+  if (!std::isfinite(deposit_width) || deposit_width < 0) return fail(h, MOP_ERR_ARG, "invalid deposit width");
+  PathHost& P = h->paths[path_id];
+  if (P.n_cv >= kMaxCV) return fail(h, MOP_ERR_ARG, "at most %d CVs per path", kMaxCV);
+  if (P.n_gauss > 0) return fail(h, MOP_ERR_STATE, "path %d already holds Gaussians", path_id);
+  mop_status s = check_groups(h, grpA, nA, grpB, nB);
+  if (s) return s;
+  CK(h, cudaSetDevice(h->device));
+  if ((s = push_cv(h, P, grpA, nA, grpB, nB, flags, deposit_width))) return s;
+  if (index) *index = P.n_cv - 1;
   return MOP_OK;
+}
+
+mop_status mop_add_gaussian(mop_handle* h, int32_t path_id, double height, const double* centers,
+                            const double* widths) {
+  if (!h) return MOP_ERR_ARG;
+  h->err.clear();
+  if (path_id < 0 || path_id >= kMaxPaths || !centers || !widths) return fail(h, MOP_ERR_ARG, "invalid argument");
+  PathHost& P = h->paths[path_id];
+  if (P.n_cv == 0) return fail(h, MOP_ERR_STATE, "no CVs defined for path %d", path_id);
+  if (!std::isfinite(height)) return fail(h, MOP_ERR_NONFINITE, "non-finite Gaussian parameter");
+  for (int q = 0; q < P.n_cv; ++q) {
+    if (!std::isfinite(centers[q]) || !std::isfinite(widths[q]))
+      return fail(h, MOP_ERR_NONFINITE, "non-finite Gaussian parameter");
+    if (!(widths[q] > 0)) return fail(h, MOP_ERR_ARG, "widths must be > 0");
+  }
+  CK(h, cudaSetDevice(h->device));
+  return push_gaussian(h, P, height, centers, widths);
 }
 
 }  // extern "C"
@@ -873,7 +959,7 @@ mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, d
   bool any = false;
   for (int id : ids) {
     const PathHost& P = h->paths[id];
-    if (P.hA.empty()) continue;
+    if (P.n_cv == 0) continue;
     any = true;
     if (P.n_gauss + n_deposits > kMaxGauss)
       return fail(h, MOP_ERR_ARG, "path %d would hold more than %d Gaussians", id, kMaxGauss);
@@ -882,10 +968,8 @@ mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, d
   CK(h, cudaSetDevice(h->device));
   for (int id : ids) {
     PathHost& P = h->paths[id];
-    if (P.hA.empty()) continue;
-    CK(h, P.gc.ensure(kMaxGauss));
-    CK(h, P.gh.ensure(kMaxGauss));
-    CK(h, P.gw.ensure(kMaxGauss));
+    if (P.n_cv == 0) continue;
+    if ((s = ensure_gaussians(h, P))) return s;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   for (int d = 0; d < n_deposits; ++d) {
@@ -896,7 +980,7 @@ mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, d
     CK(h, launch_deposit(h->sc, h->d_paths.p, (int)ids.size(), height, width, L));
     for (int id : ids) {
       PathHost& P = h->paths[id];
-      if (P.hA.empty()) continue;
+      if (P.n_cv == 0) continue;
       ++P.n_gauss;
       P.have_grad = false;   // the next round starts from a gradient with the new Gaussian
     }
@@ -906,19 +990,21 @@ mop_status mop_metadynamics(mop_handle* h, int32_t n_deposits, int32_t stride, d
 }
 
 mop_status mop_get_gaussians(mop_handle* h, int32_t path_id, double* centers, double* heights, double* widths,
-                             int32_t cap, int32_t* n) {
+                             int32_t cap, int32_t* n, int32_t* n_cv) {
   if (!h) return MOP_ERR_ARG;
   h->err.clear();
   if (path_id < 0 || path_id >= kMaxPaths || cap < 0 || !n) return fail(h, MOP_ERR_ARG, "invalid argument");
   const PathHost& P = h->paths[path_id];
   *n = P.n_gauss;
+  if (n_cv) *n_cv = P.n_cv;
   const int k = std::min(cap, P.n_gauss);
   if (k == 0) return MOP_OK;
   CK(h, cudaSetDevice(h->device));
   CK(h, cudaDeviceSynchronize());
-  if (centers) CK(h, cudaMemcpy(centers, P.gc.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
+  const size_t row = sizeof(double) * kMaxCV, w = sizeof(double) * P.n_cv;
+  if (centers) CK(h, cudaMemcpy2D(centers, w, P.gc.p, row, w, k, cudaMemcpyDeviceToHost));
+  if (widths) CK(h, cudaMemcpy2D(widths, w, P.gw.p, row, w, k, cudaMemcpyDeviceToHost));
   if (heights) CK(h, cudaMemcpy(heights, P.gh.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
-  if (widths) CK(h, cudaMemcpy(widths, P.gw.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
   return MOP_OK;
 }
 

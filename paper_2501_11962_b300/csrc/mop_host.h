@@ -81,9 +81,12 @@ struct PathHost {
   DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
   // bias
-  std::vector<int> hA, hB;
-  int n_gauss = 0;          // Gaussians in gc/gh/gw (capacity kMaxGauss)
-  int e2e = 0, com = 0;
+  std::vector<int> hA, hB;   // the groups of all CVs, concatenated
+  int n_cv = 0;
+  int cv_a[kMaxCV + 1] = {}, cv_b[kMaxCV + 1] = {};
+  int cv_e2e[kMaxCV] = {}, cv_com[kMaxCV] = {};
+  double cv_width[kMaxCV] = {};
+  int n_gauss = 0;          // Gaussians in gc/gw [kMaxGauss][kMaxCV] and gh [kMaxGauss]
   DevBuf<int> gA, gB;
   DevBuf<double> gc, gh, gw;
 };

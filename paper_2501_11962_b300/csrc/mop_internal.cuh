@@ -17,6 +17,7 @@ constexpr int kMaxTypes = 16;
 constexpr int kMaxPaths = 64;
 constexpr int kMaxGroup = 1024;   // atoms per CV group
 constexpr int kMaxGauss = 4096;   // Gaussians per path
+constexpr int kMaxCV = 4;         // collective variables per path (multivariate Gaussians)
 constexpr int kRedBlock = 256;    // threads of the elementwise kernels
 constexpr double kCoulombF = 138.935458;   // kJ mol^-1 nm e^-2
 constexpr double kBoltz = 0.0083144626;    // kJ mol^-1 K^-1
@@ -95,13 +96,18 @@ struct PathDev {
   unsigned long long* jacc;
   double* e_pair;          // [n_clu]
   double* grad;            // [N][Q][3] caller order
-  // bias
-  int nA, nB, n_gauss, e2e, com;   // com: mass-weighted group centres
+  // bias on n_cv CVs: CV d is the distance of the centres of groups gA[cv_a[d] .. cv_a[d + 1])
+  // and gB[cv_b[d] .. cv_b[d + 1]) (end-to-end form of Eq. 8 with cv_e2e, mass-weighted with
+  // cv_com); Gaussians k < n_gauss have centres gc[k][kMaxCV], widths gw[k][kMaxCV], height gh[k]
+  int n_cv, n_gauss;
+  int cv_a[kMaxCV + 1], cv_b[kMaxCV + 1];
+  int cv_e2e[kMaxCV], cv_com[kMaxCV];
+  double cv_width[kMaxCV];  // width of the Gaussians mop_metadynamics deposits (0: the call's)
   const int* gA;
   const int* gB;
-  double* gc;              // centres, heights, widths [kMaxGauss], n_gauss in use
-  double* gh;
+  double* gc;
   double* gw;
+  double* gh;
   double* diag;            // [8]: U1, E_spring, E_bias, CV, V_eff, U_pair, U_bonded
   double* veff_out;        // one double
 };

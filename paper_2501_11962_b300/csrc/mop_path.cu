@@ -456,19 +456,18 @@ __global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const Path
   }
 }
 
-// weight of atom a in a group centre: its mass with MOP_COM (centre of mass), else 1
-__device__ __forceinline__ double group_weight(const SysConsts& sc, const PathDev& P, int a) {
-  return P.com ? sc.mass[a] : 1.0;
-}
+// weight of atom a in a group centre: its mass for a mass-weighted CV (centre of mass), else 1
+__device__ __forceinline__ double group_weight(const SysConsts& sc, int com, int a) { return com ? sc.mass[a] : 1.0; }
 
 // weighted centre of a group at bead n, each atom unwrapped relative to the group's first atom;
 // *W gets the total weight
-__device__ void centroid(const SysConsts& sc, const PathDev& P, int n, const int* g, int ng, double* c, double* W) {
+__device__ void centroid(const SysConsts& sc, const PathDev& P, int n, const int* g, int ng, int com, double* c,
+                         double* W) {
   const size_t base = (size_t)n * 3 * P.Q;
   double x0[3], acc[3] = {0.0, 0.0, 0.0}, wt = 0.0;
   for (int d = 0; d < 3; ++d) x0[d] = P.x64 ? P.x64[base + 3 * (size_t)g[0] + d] : (double)P.x32[base + 3 * (size_t)g[0] + d];
   for (int k = 0; k < ng; ++k) {
-    const double m = group_weight(sc, P, g[k]);
+    const double m = group_weight(sc, com, g[k]);
     for (int d = 0; d < 3; ++d) {
       const double v = P.x64 ? P.x64[base + 3 * (size_t)g[k] + d] : (double)P.x32[base + 3 * (size_t)g[k] + d];
       double w = v - x0[d];
@@ -481,11 +480,12 @@ __device__ void centroid(const SysConsts& sc, const PathDev& P, int n, const int
   *W = wt;
 }
 
-// distance CV s = |c_A - c_B| (minimum image) at bead n; u = (c_A - c_B) / s
-__device__ double cv_at(const SysConsts& sc, const PathDev& P, int n, double* u, double* Wa, double* Wb) {
+// CV q: distance s = |c_A - c_B| (minimum image) of its groups at bead n; u = (c_A - c_B) / s,
+// Wa / Wb = the groups' total weights
+__device__ double cv_at(const SysConsts& sc, const PathDev& P, int n, int q, double* u, double* Wa, double* Wb) {
   double ca[3], cb[3];
-  centroid(sc, P, n, P.gA, P.nA, ca, Wa);
-  centroid(sc, P, n, P.gB, P.nB, cb, Wb);
+  centroid(sc, P, n, P.gA + P.cv_a[q], P.cv_a[q + 1] - P.cv_a[q], P.cv_com[q], ca, Wa);
+  centroid(sc, P, n, P.gB + P.cv_b[q], P.cv_b[q + 1] - P.cv_b[q], P.cv_com[q], cb, Wb);
   double s2 = 0.0;
   for (int d = 0; d < 3; ++d) {
     double w = ca[d] - cb[d];
@@ -498,67 +498,81 @@ __device__ double cv_at(const SysConsts& sc, const PathDev& P, int n, double* u,
   return s;
 }
 
-// metadynamics bias (one block per path)
+// value of CV q of a path: s at bead N, minus s at bead 1 for the end-to-end form (Eq. 8)
+__device__ double cv_value(const SysConsts& sc, const PathDev& P, int q, double* uN, double* u1, double* Wa,
+                           double* Wb) {
+  double S = cv_at(sc, P, P.N - 1, q, uN, Wa, Wb);
+  if (P.cv_e2e[q]) S -= cv_at(sc, P, 0, q, u1, Wa, Wb);
+  return S;
+}
+
+// metadynamics bias (one block per path): V_b = sum_k h_k exp(-sum_q (S_q - c_kq)^2 / (2 w_kq^2))
 __global__ void k_bias(SysConsts sc, const PathDev* __restrict__ paths, int n_paths) {
   __shared__ double sh[32];
-  __shared__ double sS;
+  __shared__ double sS[kMaxCV], sU[kMaxCV][2][3], sW[kMaxCV][2];
   const PathDev& P = paths[blockIdx.x];
-  const bool on = P.n_gauss > 0 && P.nA > 0 && P.nB > 0;
-  double uN[3], u1[3], Wa = 1.0, Wb = 1.0;
-  if (threadIdx.x == 0) {
-    double S = 0.0;
-    if (on) {
-      S = cv_at(sc, P, P.N - 1, uN, &Wa, &Wb);
-      if (P.e2e) S -= cv_at(sc, P, 0, u1, &Wa, &Wb);
-    }
-    sS = S;
-  }
+  const int nc = P.n_cv;
+  const bool on = P.n_gauss > 0 && nc > 0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < nc; ++q) sS[q] = cv_value(sc, P, q, sU[q][0], sU[q][1], &sW[q][0], &sW[q][1]);
   __syncthreads();
-  const double S = sS;
-  double V = 0.0, dV = 0.0;
+  double V = 0.0, dV[kMaxCV] = {0.0, 0.0, 0.0, 0.0};
   if (on)
     for (int k = threadIdx.x; k < P.n_gauss; k += blockDim.x) {
-      const double z = (S - P.gc[k]) / P.gw[k];
-      const double e = P.gh[k] * exp(-0.5 * z * z);
+      double z2 = 0.0;
+      for (int q = 0; q < nc; ++q) {
+        const double z = (sS[q] - P.gc[(size_t)k * kMaxCV + q]) / P.gw[(size_t)k * kMaxCV + q];
+        z2 += z * z;
+      }
+      const double e = P.gh[k] * exp(-0.5 * z2);
       V += e;
-      dV -= e * z / P.gw[k];
+      for (int q = 0; q < nc; ++q) {
+        const double w = P.gw[(size_t)k * kMaxCV + q];
+        dV[q] -= e * (sS[q] - P.gc[(size_t)k * kMaxCV + q]) / (w * w);
+      }
     }
   V = block_sum<kRedBlock>(V, sh);
-  dV = block_sum<kRedBlock>(dV, sh);
+#pragma unroll
+  for (int q = 0; q < kMaxCV; ++q) dV[q] = block_sum<kRedBlock>(dV[q], sh);
   if (threadIdx.x == 0) {
     if (on && P.grad) {
       const int nl = P.N - 1;
-      // ds/dx_k = +-(w_k / W) u for the atoms of group A / B (the total weights are the same
-      // at both beads)
-      for (int k = 0; k < P.nA; ++k) {
-        const double f = dV * group_weight(sc, P, P.gA[k]) / Wa;
-        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gA[k]) + d] += f * uN[d];
-        if (P.e2e)
-          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gA[k]) + d] -= f * u1[d];
-      }
-      for (int k = 0; k < P.nB; ++k) {
-        const double f = dV * group_weight(sc, P, P.gB[k]) / Wb;
-        for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + P.gB[k]) + d] -= f * uN[d];
-        if (P.e2e)
-          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)P.gB[k]) + d] += f * u1[d];
+      for (int q = 0; q < nc; ++q) {
+        // ds/dx_k = +-(w_k / W) u for the atoms of group A / B (the same weights at both beads)
+        const double *uN = sU[q][0], *u1 = sU[q][1];
+        for (int k = P.cv_a[q]; k < P.cv_a[q + 1]; ++k) {
+          const int a = P.gA[k];
+          const double f = dV[q] * group_weight(sc, P.cv_com[q], a) / sW[q][0];
+          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + a) + d] += f * uN[d];
+          if (P.cv_e2e[q])
+            for (int d = 0; d < 3; ++d) P.grad[3 * (size_t)a + d] -= f * u1[d];
+        }
+        for (int k = P.cv_b[q]; k < P.cv_b[q + 1]; ++k) {
+          const int b = P.gB[k];
+          const double f = dV[q] * group_weight(sc, P.cv_com[q], b) / sW[q][1];
+          for (int d = 0; d < 3; ++d) P.grad[3 * ((size_t)nl * P.Q + b) + d] -= f * uN[d];
+          if (P.cv_e2e[q])
+            for (int d = 0; d < 3; ++d) P.grad[3 * (size_t)b + d] += f * u1[d];
+        }
       }
     }
     P.diag[2] = on ? V : 0.0;
-    P.diag[3] = S;
+    P.diag[3] = nc > 0 ? sS[0] : 0.0;
   }
 }
 
-// metadynamics deposition (one block per path): a Gaussian centred at the current CV value
-// goes to slot n_gauss of every path with CV groups (the host counts the deposits)
+// metadynamics deposition (one block per path): a Gaussian centred at the current CV values goes
+// to row n_gauss of every path with CVs (the host counts the deposits); its width along CV q is
+// the CV's own deposit width, or `width` where that is 0
 __global__ void k_deposit(SysConsts sc, const PathDev* __restrict__ paths, double height, double width) {
   const PathDev& P = paths[blockIdx.x];
-  if (threadIdx.x != 0 || P.nA < 1 || P.nB < 1 || P.n_gauss >= kMaxGauss) return;
-  double u[3], Wa, Wb;
-  double S = cv_at(sc, P, P.N - 1, u, &Wa, &Wb);
-  if (P.e2e) S -= cv_at(sc, P, 0, u, &Wa, &Wb);
-  P.gc[P.n_gauss] = S;
+  if (threadIdx.x != 0 || P.n_cv < 1 || P.n_gauss >= kMaxGauss) return;
+  for (int q = 0; q < P.n_cv; ++q) {
+    double uN[3], u1[3], Wa, Wb;
+    P.gc[(size_t)P.n_gauss * kMaxCV + q] = cv_value(sc, P, q, uN, u1, &Wa, &Wb);
+    P.gw[(size_t)P.n_gauss * kMaxCV + q] = P.cv_width[q] > 0.0 ? P.cv_width[q] : width;
+  }
   P.gh[P.n_gauss] = height;
-  P.gw[P.n_gauss] = width;
 }
 
 // fixed-order sums of the partial energies -> V_eff (one block per path)

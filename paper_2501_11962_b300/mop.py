@@ -25,7 +25,7 @@ EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_vef
            "mop_get_energies", "mop_add_bias", "mop_step", "mop_kinetic_energy", "mop_last_launch_count",
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
            "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_measure_fp32_peak",
-           "mop_metadynamics", "mop_get_gaussians",
+           "mop_metadynamics", "mop_get_gaussians", "mop_add_cv", "mop_add_gaussian",
            "mop_last_error")
 
 
@@ -83,7 +83,9 @@ def load(build_if_needed: bool = True):
     L.mop_add_bias.argtypes = [p, p, i32, p, i32, d, d, d, i32, i32]
     L.mop_step.argtypes = [p, i32, d, d, C.c_uint64, p]
     L.mop_metadynamics.argtypes = [p, i32, i32, d, d, C.c_uint64, d, d, p]
-    L.mop_get_gaussians.argtypes = [p, i32, p, p, p, i32, p]
+    L.mop_get_gaussians.argtypes = [p, i32, p, p, p, i32, p, p]
+    L.mop_add_cv.argtypes = [p, i32, p, i32, p, i32, i32, d, p]
+    L.mop_add_gaussian.argtypes = [p, i32, d, p, p]
     L.mop_kinetic_energy.argtypes = [p, i32, p]
     L.mop_last_launch_count.argtypes = [p]
     L.mop_last_launch_count.restype = i32
@@ -257,13 +259,33 @@ class Engine:
         self._check(self.L.mop_step(self.h, n_steps, dt, gamma, seed, None), "mop_step")
 
     def gaussians(self, path_id: int):
-        """(centers, heights, widths) of the Gaussians of a path, in the order they were added."""
-        n = np.zeros(1, np.int32)
-        self._check(self.L.mop_get_gaussians(self.h, path_id, None, None, None, 0, _np_ptr(n)), "mop_get_gaussians")
-        c, hh, w = np.zeros(int(n[0])), np.zeros(int(n[0])), np.zeros(int(n[0]))
-        self._check(self.L.mop_get_gaussians(self.h, path_id, _np_ptr(c), _np_ptr(hh), _np_ptr(w), int(n[0]),
-                                             _np_ptr(n)), "mop_get_gaussians")
+        """(centers [k][n_cv], heights [k], widths [k][n_cv]) of a path's Gaussians, in the order
+        they were added."""
+        n, ncv = np.zeros(1, np.int32), np.zeros(1, np.int32)
+        self._check(self.L.mop_get_gaussians(self.h, path_id, None, None, None, 0, _np_ptr(n), _np_ptr(ncv)),
+                    "mop_get_gaussians")
+        k, q = int(n[0]), int(ncv[0])
+        c, hh, w = np.zeros((k, q)), np.zeros(k), np.zeros((k, q))
+        self._check(self.L.mop_get_gaussians(self.h, path_id, _np_ptr(c), _np_ptr(hh), _np_ptr(w), k, _np_ptr(n),
+                                             None), "mop_get_gaussians")
         return c, hh, w
+
+    def add_cv(self, path_id: int, groups, e2e=False, com=False, deposit_width: float = 0.0) -> int:
+        """Adds a CV (mop_add_cv); returns its index."""
+        ga = np.ascontiguousarray(groups[0], np.int32)
+        gb = np.ascontiguousarray(groups[1], np.int32)
+        idx = np.zeros(1, np.int32)
+        flags = (MOP_E2E if e2e else 0) | (MOP_COM if com else 0)
+        self._check(self.L.mop_add_cv(self.h, path_id, _np_ptr(ga), len(ga), _np_ptr(gb), len(gb), flags,
+                                      float(deposit_width), _np_ptr(idx)), "mop_add_cv")
+        return int(idx[0])
+
+    def add_gaussian(self, path_id: int, height: float, centers, widths):
+        """Appends one Gaussian on all CVs of the path (mop_add_gaussian)."""
+        c = np.ascontiguousarray(centers, np.float64)
+        w = np.ascontiguousarray(widths, np.float64)
+        self._check(self.L.mop_add_gaussian(self.h, path_id, float(height), _np_ptr(c), _np_ptr(w)),
+                    "mop_add_gaussian")
 
     def metadynamics(self, n_deposits: int, stride: int, dt: float, gamma: float, seed: int, height: float,
                      width: float):

@@ -198,6 +198,39 @@ def test_cfg4_uneven_batch_with_bias():
         assert e["cv"] == pytest.approx(S, rel=1e-9)
 
 
+@pytest.mark.parametrize("prec", [mop.MOP_PREC_MIXED, mop.MOP_PREC_FP64])
+def test_multi_cv_bias_matches_oracle(prec):
+    # two CVs and three multivariate Gaussians on the water box
+    w = workload(2, n_beads=5)
+    X = w.paths[0]
+    pos = X[-1].astype(np.float64)
+    cvs = [(np.arange(0, 6), np.arange(300, 309), True, True), (np.arange(900, 903), np.arange(1500, 1506), False, False)]
+    o = oracle.Oracle(w.system)
+    _, _, S = o.bias_multi(X.astype(np.float64), cvs, [[0.0, 0.0]], [[1.0, 1.0]], [0.0])
+    cen = [[S[0] + 0.02, S[1]], [S[0], S[1] - 0.03], [S[0] - 0.05, S[1] + 0.04]]
+    wid = [[0.05, 0.06], [0.04, 0.05], [0.06, 0.07]]
+    hei = [30.0, 20.0, 25.0]
+    eng = mop.Engine(w.system, precision=prec)
+    eng.set_path(0, X)
+    for ga, gb, e2e, com in cvs:
+        eng.add_cv(0, (ga, gb), e2e=e2e, com=com)
+    for c_, w_, h_ in zip(cen, wid, hei):
+        eng.add_gaussian(0, h_, c_, w_)
+    v, G = eng.veff_and_grad(0)
+    r = o.veff(X.astype(np.float64))
+    Vb, Gb, Sb = o.bias_multi(X.astype(np.float64), cvs, cen, wid, hei)
+    assert Vb > 1.0
+    tv, tf = (TOL_V, TOL_F) if prec == mop.MOP_PREC_MIXED else (TOL_F64, TOL_F64)
+    assert abs(v[0] - (r["veff"] + Vb)) / abs(r["veff"]) < tv
+    assert rel(G, r["G"] + Gb) < tf
+    e = eng.energies(0)
+    assert e["Ebias"] == pytest.approx(Vb, rel=1e-6) and e["cv"] == pytest.approx(Sb[0], rel=1e-9)
+    if prec == mop.MOP_PREC_FP64:
+        # the rest of the gradient agrees to rounding, so the bias gradient shows on its own
+        idx = np.concatenate([c[0] for c in cvs] + [c[1] for c in cvs])
+        np.testing.assert_allclose((G - r["G"])[[0, -1]][:, idx], Gb[[0, -1]][:, idx], rtol=1e-7, atol=1e-8)
+
+
 @pytest.mark.slow
 def test_cfg5_sampled_beads_match_oracle():
     w = workload(5)

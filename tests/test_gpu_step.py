@@ -87,6 +87,34 @@ def test_metadynamics_matches_oracle(com, graph):
                               gaussians=([s0 + 0.02], [20.0], [0.05]), round_f32=False)
     assert len(c) == 4 and np.abs(X - X0).max() > 1e-6
     assert np.abs(Xg - X).max() < 1e-6                  # float32 readback of FP64 positions
+    np.testing.assert_allclose(c[:, 0], co, rtol=1e-10)
+    assert np.array_equal(h, ho) and np.array_equal(wd[:, 0], wo)
+
+
+def test_multi_cv_metadynamics_matches_oracle():
+    # two CVs (a centre-of-mass end-to-end distance with its own deposit width, and a plain
+    # centroid distance) with multivariate Gaussians, deposited in graph mode
+    w = workload(1, n_beads=4)
+    X0 = w.paths[0]
+    cvs = [(np.arange(0, 4), np.arange(100, 104), True, True), (np.arange(20, 26), np.arange(200, 203), False, False)]
+    o = oracle.Oracle(w.system)
+    _, _, S0 = o.bias_multi(X0.astype(np.float64), cvs, [[0.0, 0.0]], [[1.0, 1.0]], [0.0])
+    g0 = ([[S0[0] + 0.01, S0[1] - 0.02]], [[0.05, 0.08]], [15.0])
+    eng = mop.Engine(w.system, precision=mop.MOP_PREC_FP64)
+    eng.set_path(0, X0)
+    assert eng.add_cv(0, cvs[0][:2], e2e=True, com=True, deposit_width=0.03) == 0
+    assert eng.add_cv(0, cvs[1][:2]) == 1
+    eng.add_gaussian(0, 15.0, g0[0][0], g0[1][0])
+    eng.set_graph_mode(True)
+    eng.metadynamics(2, 3, 2e-4, 5.0, 17, 8.0, 0.06)
+    Xg = eng.get_path(0).astype(np.float64)
+    c, h, wd = eng.gaussians(0)
+    X = X0.astype(np.float64).copy()
+    V = np.zeros_like(X)
+    _, (co, wo, ho) = o.metad_multi(X, V, 2e-4, 5.0, w.system.temperature, 17, 0, 2, 3, cvs, 8.0, [0.03, 0.06],
+                                    gaussians=g0, round_f32=False)
+    assert c.shape == (3, 2) and np.abs(X - X0).max() > 1e-6
+    assert np.abs(Xg - X).max() < 1e-6
     np.testing.assert_allclose(c, co, rtol=1e-10)
     assert np.array_equal(h, ho) and np.array_equal(wd, wo)
 
