@@ -64,6 +64,7 @@ struct PathHost {
   DevBuf<unsigned> emax;  // [3] float bits
   DevBuf<int> cbin, bincnt, binstart, bincur, binlist;
   DevBuf<double> cwrap;   // [max_clu][3]
+  DevBuf<float2> cwdf;    // [max_clu][3] the same as double-floats (mixed precision)
   DevBuf<float4> cbox;    // [max_clu][2]: FP32 wrapped centre, half extents
   DevBuf<int> lcnt;
   DevBuf<float4> abox;    // [max_slots] union sphere of each atom over the beads

@@ -326,7 +326,7 @@ __global__ void k_local_coords(SysConsts sc, const float* x32, const double* x64
 
 __global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const double* center, const float* hext,
                                int nb0, int nb1, int nb2, double bw0, double bw1, double bw2, double* cwrap,
-                               float4* cbox, int* cbin, int* bincnt) {
+                               float2* cwdf, float4* cbox, int* cbin, int* bincnt) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= max_clu || c >= meta[0]) return;
   int bidx[3];
@@ -337,6 +337,8 @@ __global__ void k_bin_clusters(SysConsts sc, const int* meta, int max_clu, const
     if (w >= sc.L[d]) w -= sc.L[d];
     if (w < 0.0) w = 0.0;
     cwrap[3 * c + d] = w;
+    const df wd = df_from_double(w);
+    cwdf[3 * c + d] = make_float2(wd.hi, wd.lo);
     bidx[d] = (int)fmin(fmax(w / bw[d], 0.0), (double)(nb[d] - 1));
   }
   const int bin = (bidx[0] * nb1 + bidx[1]) * nb2 + bidx[2];
@@ -443,7 +445,8 @@ __global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype)
 // largest count (a count above cap means the list must be rebuilt with a larger cap).
 template <bool F64>
 __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta_in, int max_clu,
-                                                   const double* cwrap, const float* hext, const unsigned* emax,
+                                                   const double* cwrap, const float2* cwdf, const float* hext,
+                                                   const unsigned* emax,
                                                    const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
                                                    double bw2, const int* binstart, const int* binlist,
                                                    const int* perm, const int* molr, const float4* abox,
@@ -461,6 +464,7 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
   const int nb[3] = {nb0, nb1, nb2};
   const double bw[3] = {bw0, bw1, bw2};
   double wi[3], ei[3];
+  float2 widf[3];   // own centre as double-floats (mixed precision)
   int bi[3], R[3];
   const int binc = cbin[ci];
   bi[2] = binc % nb2;
@@ -468,6 +472,7 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
   bi[0] = binc / (nb1 * nb2);
   for (int d = 0; d < 3; ++d) {
     wi[d] = cwrap[3 * ci + d];
+    if (!F64) widf[d] = cwdf[3 * ci + d];
     ei[d] = hext[3 * ci + d];
     const double em = __uint_as_float(emax[d]);
     const double reach = fmin(fmax((sc.rc + ei[d] + em) / bw[d] + 1e-6, 0.0), 3.0 * nb[d] + 1.0);
@@ -520,8 +525,23 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
             const float gz = fmaxf(0.f, fabsf(wif[2] - (cw.z + kk[2] * Lf[2])) - eif[2] - ce.z);
             box = gx * gx + gy * gy + gz * gz < rcs2;
           }
+          float Df[3] = {0.f, 0.f, 0.f};   // FP32 Delta for the warp's exact test and the entry
           if (box) {
-            for (int d = 0; d < 3; ++d) D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
+            for (int d = 0; d < 3; ++d) {
+              if (F64) {
+                D[d] = wi[d] - (cwrap[3 * cj + d] + kk[d] * sc.L[d]);
+                Df[d] = (float)D[d];
+              } else {
+                // the same difference exactly as a double-float on the FP32 pipes, rounded once:
+                // w_i - w_j by TwoSum plus the low parts, minus k L with k Lf exact by an FMA
+                const float2 wj = cwdf[3 * cj + d];
+                const float kf = (float)kk[d];
+                const float p = kf * sc.Lf[d];
+                df t = two_sum(widf[d].x, -wj.x);
+                t = df_add(t, df{-p, (widf[d].y - wj.y) - fmaf(kf, sc.Lf[d], -p)});
+                Df[d] = t.hi + (t.lo - kf * sc.Llo[d]);
+              }
+            }
             // the atom spheres of this lane's candidate, read by the whole warp below
 #pragma unroll
             for (int j = 0; j < kCL; ++j) jbox[warp][lane][j] = abox[cj * kCL + j];
@@ -534,9 +554,9 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
             const int src = __ffs(pend) - 1;
             pend &= pend - 1;
             const int cs = __shfl_sync(0xffffffffu, cj, src);
-            const float Dx = __shfl_sync(0xffffffffu, (float)D[0], src);
-            const float Dy = __shfl_sync(0xffffffffu, (float)D[1], src);
-            const float Dz = __shfl_sync(0xffffffffu, (float)D[2], src);
+            const float Dx = __shfl_sync(0xffffffffu, Df[0], src);
+            const float Dy = __shfl_sync(0xffffffffu, Df[1], src);
+            const float Dz = __shfl_sync(0xffffffffu, Df[2], src);
             const float4 bj0 = jbox[warp][src][jq], bj1 = jbox[warp][src][jq + 4];
             bool in0 = false, in1 = false;
             if (bi4.w >= 0.f) {
@@ -571,8 +591,8 @@ __global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta
               if (lane == src) {
                 const bool slf = self;
                 const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0) | (slf ? kSelfFlag : 0);
-                ent[base + count] = make_int4(cj | flags, __float_as_int((float)D[0]), __float_as_int((float)D[1]),
-                                              __float_as_int((float)D[2]));
+                ent[base + count] = make_int4(cj | flags, __float_as_int(Df[0]), __float_as_int(Df[1]),
+                                              __float_as_int(Df[2]));
                 if (F64) ent64[base + count] = make_double4_32a(D[0], D[1], D[2], 0.0);
                 emask[base + count] = m;
               }
@@ -635,6 +655,7 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_CK(P.emax.ensure(3));
   MOP_CK(P.cbin.ensure(max_clu));
   MOP_CK(P.cwrap.ensure(3 * (size_t)max_clu));
+  MOP_CK(P.cwdf.ensure(3 * (size_t)max_clu));
   MOP_CK(P.cbox.ensure(2 * (size_t)max_clu));
   MOP_CK(P.bincnt.ensure(nbins));
   MOP_CK(P.binstart.ensure(nbins + 1));
@@ -686,7 +707,7 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
     MOP_KL();
   }
   k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, P.hext.p, g.nb[0], g.nb[1],
-                                                   g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cbox.p,
+                                                   g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cwdf.p, P.cbox.p,
                                                    P.cbin.p, P.bincnt.p);
   MOP_KL();
   k_scan<<<1, 1024, 0, st>>>(P.bincnt.p, nbins, P.binstart.p, P.bincur.p, nullptr);
@@ -711,12 +732,12 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
     if (sync) MOP_CK(cudaMemsetAsync(P.meta.p + 2, 0, 2 * sizeof(int), st));
     const int blocks = nblk(max_clu, 4);
     if (f64)
-      k_pair_list<true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
+      k_pair_list<true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
                                                 g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
                                                 P.ent.p, P.ent64.p, P.emask.p, P.meta.p);
     else
-      k_pair_list<false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.hext.p, P.emax.p, P.cbin.p,
+      k_pair_list<false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
                                                  g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
                                                  P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
                                                  P.ent.p, nullptr, P.emask.p, P.meta.p);
