@@ -40,6 +40,7 @@ class OrcSystem(C.Structure):
         ("n_angles", C.c_int32), ("angle_ijk", C.c_void_p), ("angle_th0", C.c_void_p), ("angle_k", C.c_void_p),
         ("rc", C.c_double), ("eps_rf", C.c_double), ("cutoff_mode", C.c_int32),
         ("dt_path", C.c_double), ("nu_path", C.c_double),
+        ("elec", C.c_int32), ("ew_beta", C.c_double),
     ]
 
 
@@ -123,6 +124,8 @@ class Oracle:
         st.cutoff_mode = int(s.cutoff_mode)
         st.dt_path = float(s.dt_path)
         st.nu_path = float(s.nu_path)
+        st.elec = int(getattr(s, "elec", 0))
+        st.ew_beta = float(getattr(s, "ew_beta", 0.0))
         self._st = st
         self._sp = C.cast(C.pointer(st), C.c_void_p)
         self.L = lib()
@@ -168,6 +171,49 @@ class Oracle:
         res = {k: a for k, a in out.items() if a is not None}
         res.update(veff=float(v[0]), U1=float(parts[0]), Espring=float(parts[1]))
         return res
+
+    # --- Ewald electrostatics (ELEC_PME): real space, exclusions and self term in the C++ code,
+    # reciprocal space by SPME in numpy (oracle/pme.py)
+    def recip(self, x, v=None):
+        """Reciprocal-space energy and forces (and H v with a direction v) of one configuration."""
+        from . import pme
+        s = self.system
+        return pme.spme(np.asarray(x, np.float64), np.asarray(s.charge, np.float64), s.box, s.pme_grid,
+                        s.pme_order, s.ew_beta, v=v)
+
+    def veff_pme(self, X):
+        """V_eff (Eq. 3) and its exact gradient (Eqs. 5-7, FD term replaced by -H eta / 2) with
+        Ewald electrostatics: per bead F = F_real+bonded + F_recip, H eta likewise."""
+        s = self.system
+        X = np.ascontiguousarray(X, np.float64)
+        N = X.shape[0]
+        m = np.asarray(s.mass, np.float64)[:, None]
+        K = m * s.nu_path / (2.0 * s.dt_path)
+        c = s.dt_path / (m * s.nu_path)
+        n_force = 1 if N == 1 else N - 1
+        F = np.zeros_like(X)
+        U1 = 0.0
+        for n in range(n_force):
+            Fr, Ur = self.forces(X[n])
+            Er, Fk = self.recip(X[n])
+            F[n] = Fr + Fk
+            if n == 0:
+                U1 = Ur + Er
+        eta = np.zeros_like(X)
+        Heta = np.zeros_like(X)
+        for n in range(N - 1):
+            eta[n] = X[n + 1] - X[n] - c * F[n]
+            Heta[n] = self.hvp(X[n], eta[n]) + self.recip(X[n], v=eta[n])[2]
+        Es = float(np.sum(0.5 * K * eta[:N - 1] ** 2))
+        G = np.zeros_like(X)
+        if N == 1:
+            G[0] = -F[0]
+        else:
+            G[0] = -F[0] - K * eta[0] + 0.5 * Heta[0]
+            for n in range(1, N - 1):
+                G[n] = K * eta[n - 1] - K * eta[n] + 0.5 * Heta[n]
+            G[N - 1] = K * eta[N - 2]
+        return dict(veff=U1 + Es, U1=U1, Espring=Es, G=G, F=F, eta=eta, Heta=Heta)
 
     def veff_complex_dir(self, X, D, h: float = 1e-20) -> float:
         X = np.ascontiguousarray(X, np.float64)

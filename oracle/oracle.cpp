@@ -69,8 +69,24 @@ template <class T> T make(double a) { return T(a); }
 using cplx = std::complex<double>;
 inline cplx acos(const cplx& a) { return std::acos(a); }
 inline cplx sqrt(const cplx& a) { return std::sqrt(a); }
+inline Dual exp(Dual a) { const double e = std::exp(a.v); return {e, e * a.d}; }
 using std::acos;
 using std::sqrt;
+using std::exp;
+
+constexpr double kTwoOverSqrtPi = 1.1283791670955126;   // 2 / sqrt(pi)
+
+// erfc(b r) for the scalar types.  Dual carries the derivative -2b/sqrt(pi) exp(-b^2 r^2) r';
+// complex carries it on the imaginary part, which is exact to first order (the complex step
+// uses imaginary parts of 1e-20).
+inline double erfc_b(double r, double b) { return std::erfc(b * r); }
+inline Dual erfc_b(const Dual& r, double b) {
+  return {std::erfc(b * r.v), -kTwoOverSqrtPi * b * std::exp(-b * b * r.v * r.v) * r.d};
+}
+inline cplx erfc_b(const cplx& r, double b) {
+  const double x = r.real();
+  return {std::erfc(b * x), -kTwoOverSqrtPi * b * std::exp(-b * b * x * x) * r.imag()};
+}
 
 }  // namespace
 
@@ -101,6 +117,9 @@ struct orc_system {
   int32_t cutoff_mode;  // 0 = shifted force, 1 = potential shift
   double dt_path;
   double nu_path;
+  int32_t elec;         // 0 = reaction field, 1 = Ewald real space (erfc, with the exclusion and
+                        //     self terms; the reciprocal part is computed elsewhere)
+  double ew_beta;       // Ewald splitting parameter, 1/nm
 };
 
 }  // extern "C"
@@ -114,10 +133,12 @@ struct PairParams {
 
 struct Model {
   const orc_system& s;
+  bool ewald;
+  double beta;
   double krf, crf;
   double rc6, rc7, rc12, rc13;     // powers of rc for the cutoff constants
   std::vector<double> c6t, c12t;   // per type pair, Lorentz-Berthelot
-  explicit Model(const orc_system& sys) : s(sys) {
+  explicit Model(const orc_system& sys) : s(sys), ewald(sys.elec == 1), beta(sys.ew_beta) {
     const double rc = s.rc;
     krf = (s.eps_rf - 1.0) / ((2.0 * s.eps_rf + 1.0) * rc * rc * rc);
     crf = 1.0 / rc + krf * rc * rc;
@@ -147,10 +168,38 @@ struct Model {
     p.c12 = c12t[t];
     p.qq = kCoulomb * s.charge[i] * s.charge[j];
     const double rc = s.rc;
-    p.phi_rc = p.c12 / rc12 - p.c6 / rc6 + p.qq * (1.0 / rc + krf * rc * rc - crf);
-    p.dphi_rc = -12.0 * p.c12 / rc13 + 6.0 * p.c6 / rc7 +
-                p.qq * (-1.0 / (rc * rc) + 2.0 * krf * rc);
+    p.phi_rc = p.c12 / rc12 - p.c6 / rc6;
+    p.dphi_rc = -12.0 * p.c12 / rc13 + 6.0 * p.c6 / rc7;
+    if (ewald) {
+      const double e = std::erfc(beta * rc), g = kTwoOverSqrtPi * beta * std::exp(-beta * beta * rc * rc);
+      p.phi_rc += p.qq * e / rc;
+      p.dphi_rc -= p.qq * (e / (rc * rc) + g / rc);
+    } else {
+      p.phi_rc += p.qq * (1.0 / rc + krf * rc * rc - crf);
+      p.dphi_rc += p.qq * (-1.0 / (rc * rc) + 2.0 * krf * rc);
+    }
     return p;
+  }
+  // Ewald exclusion correction of an excluded pair: -f q_i q_j erf(beta r) / r (its reciprocal-
+  // space interaction is removed; no cutoff), value and r-derivative
+  template <class T>
+  void phi_excl(double qq, const T& r, T* val, T* der) const {
+    T ir = make<T>(1.0) / r;
+    T erf_ = make<T>(1.0) - erfc_b(r, beta);
+    *val = -qq * erf_ * ir;
+    *der = qq * (erf_ * ir * ir - kTwoOverSqrtPi * beta * exp(make<T>(-beta * beta) * r * r) * ir);
+  }
+  double phi_excl2(double qq, double r) const {
+    const double ir = 1.0 / r, erf_ = std::erf(beta * r), g = kTwoOverSqrtPi * beta * std::exp(-beta * beta * r * r);
+    // d2/dr2 of erf(b r)/r = 2 erf/r^3 - g (2/r^2 + 2 b^2)
+    return -qq * (2.0 * erf_ * ir * ir * ir - g * (2.0 * ir * ir + 2.0 * beta * beta));
+  }
+  // self term of the Ewald sum, -f beta / sqrt(pi) sum_i q_i^2 (a constant)
+  double self_energy() const {
+    if (!ewald) return 0.0;
+    double q2 = 0.0;
+    for (int i = 0; i < s.Q; ++i) q2 += s.charge[i] * s.charge[i];
+    return -kCoulomb * beta / std::sqrt(M_PI) * q2;
   }
   // phi(r) and phi'(r) with the cutoff modifier, for r < rc
   template <class T>
@@ -158,8 +207,16 @@ struct Model {
     T ir = make<T>(1.0) / r;
     T ir2 = ir * ir;
     T ir6 = ir2 * ir2 * ir2;
-    T v = p.c12 * ir6 * ir6 - p.c6 * ir6 + p.qq * (ir + krf * r * r - crf);
-    T d = (-12.0 * p.c12 * ir6 * ir6 + 6.0 * p.c6 * ir6) * ir + p.qq * (-ir2 + 2.0 * krf * r);
+    T v = p.c12 * ir6 * ir6 - p.c6 * ir6;
+    T d = (-12.0 * p.c12 * ir6 * ir6 + 6.0 * p.c6 * ir6) * ir;
+    if (ewald) {
+      const T e = erfc_b(r, beta);
+      v = v + p.qq * e * ir;
+      d = d - p.qq * (e * ir2 + kTwoOverSqrtPi * beta * exp(make<T>(-beta * beta) * r * r) * ir);
+    } else {
+      v = v + p.qq * (ir + krf * r * r - crf);
+      d = d + p.qq * (-ir2 + 2.0 * krf * r);
+    }
     if (s.cutoff_mode == 0) {
       v = v - p.phi_rc - (r - s.rc) * p.dphi_rc;
       d = d - p.dphi_rc;
@@ -172,7 +229,13 @@ struct Model {
   // second derivative phi''(r) (the modifiers are at most linear in r)
   double phi2(const PairParams& p, double r) const {
     double ir = 1.0 / r, ir2 = ir * ir, ir6 = ir2 * ir2 * ir2;
-    return (156.0 * p.c12 * ir6 * ir6 - 42.0 * p.c6 * ir6) * ir2 + p.qq * (2.0 * ir2 * ir + 2.0 * krf);
+    const double lj = (156.0 * p.c12 * ir6 * ir6 - 42.0 * p.c6 * ir6) * ir2;
+    if (ewald) {
+      // d2/dr2 of erfc(b r)/r = 2 erfc/r^3 + g (2/r^2 + 2 b^2), g = 2b/sqrt(pi) exp(-b^2 r^2)
+      const double g = kTwoOverSqrtPi * beta * std::exp(-beta * beta * r * r);
+      return lj + p.qq * (2.0 * std::erfc(beta * r) * ir2 * ir + g * (2.0 * ir2 + 2.0 * beta * beta));
+    }
+    return lj + p.qq * (2.0 * ir2 * ir + 2.0 * krf);
   }
 };
 
@@ -234,13 +297,16 @@ void nonbonded_T(const orc_system& s, const T* x, T* F, T* u, int method) {
   const Model m(s);
   std::vector<double> xr(3 * (size_t)s.Q);
   for (size_t k = 0; k < xr.size(); ++k) xr[k] = re(x[k]);
+  *u += m.self_energy();
   for_each_pair(s, xr.data(), method, [&](int i, int j) {
-    if (m.excluded(i, j)) return;
+    const bool ex = m.excluded(i, j);
+    if (ex && !m.ewald) return;
     T d[3];
     min_image(s, x + 3 * i, x + 3 * j, d);
     T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     T v, dv;
-    m.phi(m.params(i, j), r, &v, &dv);
+    if (ex) m.phi_excl(kCoulomb * s.charge[i] * s.charge[j], r, &v, &dv);
+    else m.phi(m.params(i, j), r, &v, &dv);
     *u += v;
     for (int k = 0; k < 3; ++k) {
       T f = -dv * d[k] / r;
@@ -327,14 +393,21 @@ void hvp_analytic(const orc_system& s, const double* x, const double* v, double*
     }
   };
   for_each_pair(s, x, method, [&](int i, int j) {
-    if (m.excluded(i, j)) return;
+    const bool ex = m.excluded(i, j);
+    if (ex && !m.ewald) return;
     double d[3];
     min_image(s, x + 3 * i, x + 3 * j, d);
     double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    PairParams p = m.params(i, j);
     double val, dv;
-    m.phi(p, r, &val, &dv);
-    apply_block(i, j, d, r, dv, m.phi2(p, r));
+    if (ex) {
+      const double qq = kCoulomb * s.charge[i] * s.charge[j];
+      m.phi_excl(qq, r, &val, &dv);
+      apply_block(i, j, d, r, dv, m.phi_excl2(qq, r));
+    } else {
+      PairParams p = m.params(i, j);
+      m.phi(p, r, &val, &dv);
+      apply_block(i, j, d, r, dv, m.phi2(p, r));
+    }
   });
   for (int b = 0; b < s.n_bonds; ++b) {
     int i = s.bond_ij[2 * b], j = s.bond_ij[2 * b + 1];

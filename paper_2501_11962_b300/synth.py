@@ -56,6 +56,10 @@ class System:
     dt_path: float = 0.002               # ps, time step of the discretised path
     nu_path: float = 5.0                 # 1/ps, friction of the path action
     temperature: float = 300.0           # K
+    elec: int = 0                        # ELEC_RF, or ELEC_PME (Ewald: real space + SPME)
+    ew_beta: float = 0.0                 # 1/nm, Ewald splitting parameter (ELEC_PME)
+    pme_grid: tuple = (0, 0, 0)          # SPME grid points per box edge (ELEC_PME)
+    pme_order: int = 4                   # B-spline order of the SPME (ELEC_PME)
     name: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -66,6 +70,38 @@ class System:
     @property
     def n_types(self) -> int:
         return int(self.lj_sigma.shape[0])
+
+
+ELEC_RF, ELEC_PME = 0, 1
+
+
+def _nice_fft_size(n: int) -> int:
+    """Smallest m >= n whose prime factors are 2, 3 and 5."""
+    m = max(int(n), 1)
+    while True:
+        k = m
+        for f in (2, 3, 5):
+            while k % f == 0:
+                k //= f
+        if k == 1:
+            return m
+        m += 1
+
+
+def with_pme(system: System, spacing: float = 0.12, rtol: float = 1e-5, order: int = 4) -> System:
+    """A copy of `system` with Ewald electrostatics: beta from erfc(beta rc) = rtol (bisection)
+    and an SPME grid of at most `spacing` nm (FFT-friendly sizes), B-splines of `order`."""
+    from math import erfc
+    lo, hi = 0.0, 100.0 / system.rc
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if erfc(mid * system.rc) > rtol:
+            lo = mid
+        else:
+            hi = mid
+    grid = tuple(_nice_fft_size(int(np.ceil(system.box[d] / spacing))) for d in range(3))
+    import dataclasses
+    return dataclasses.replace(system, elec=ELEC_PME, ew_beta=hi, pme_grid=grid, pme_order=order)
 
 
 @dataclass
