@@ -67,6 +67,9 @@ enum { MOP_PREC_MIXED = 0, /* FP32 pair arithmetic, FP64 accumulation and path t
 #define MOP_E2E 4          /* mop_add_bias: CV = s(R^N) - s(R^1) (Eq. 8) instead of s(R^N) */
 #define MOP_COM 8          /* mop_add_bias: mass-weighted group centres (centres of mass) */
 
+#define MOP_ELEC_RF 0      /* reaction-field electrostatics */
+#define MOP_ELEC_PME 1     /* Ewald electrostatics (real space + smooth particle-mesh Ewald) */
+
 /* fields for mop_get_field, each [N][Q][3] FP64 in the caller's atom order */
 enum { MOP_FIELD_FORCE = 0, /* F^n = -grad U(R^n) on the beads that need it */
        MOP_FIELD_ETA = 1,   /* eta^n = R^{n+1} - R^n - L^n, n < N */
@@ -102,6 +105,15 @@ typedef struct {
   int32_t hvp_mode;          /* MOP_HVP_ADJOINT | MOP_HVP_FD */
   double fd_h;               /* nm, largest atomic displacement of the FD mode */
   int32_t precision;         /* MOP_PREC_MIXED | MOP_PREC_FP64 */
+  /* electrostatics: MOP_ELEC_RF (reaction field, eps_rf) or MOP_ELEC_PME (Ewald: erfc(beta r)/r
+   * in real space with the cutoff modifier, the erf correction of excluded pairs and the self
+   * term, plus smooth particle-mesh Ewald in reciprocal space on a pme_grid grid with B-splines
+   * of pme_order; a grid of 0 x 0 x 0 leaves the reciprocal part out).  MOP_ELEC_PME needs
+   * MOP_PREC_MIXED. */
+  int32_t elec;
+  double ew_beta;            /* 1/nm, Ewald splitting parameter (> 0 with MOP_ELEC_PME) */
+  int32_t pme_grid[3];       /* grid points per box edge (each 0, or >= pme_order) */
+  int32_t pme_order;         /* 4..8 */
 } mop_system_desc;
 
 /* Validates `desc` and uploads it to `device`.  Errors: MOP_ERR_ARG (bad sizes, indices or

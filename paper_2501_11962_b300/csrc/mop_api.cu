@@ -3,6 +3,7 @@
 //   per path: spatial sort + cluster-pair list (mop_prep.cu)
 //   all paths, one launch each: pair force -> bonded + eta -> pair HVP (adjoint or FD) ->
 //   bonded HVP + gradient -> bias -> V_eff reduction
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -39,6 +40,7 @@ struct mop_handle {
   PathHost paths[kMaxPaths];
   DevBuf<PathDev> d_paths, d_one;
   DevBuf<double> e_bond, e_spring, scratch;
+  DevBuf<int2> excl;                      // Ewald exclusion pairs
   DevBuf<unsigned long long> counts;
   mop_tuning tuning{1.0, 0.5};
   double box[3] = {0.0, 0.0, 0.0};
@@ -175,6 +177,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.etamax.ensure(N));
     if (h->precision == MOP_PREC_MIXED) CK(h, P.jacc.ensure(nq3));
     CK(h, P.e_pair.ensure(h->grid.max_clu));
+    if (sc.elec == 1) CK(h, P.e_excl.ensure(std::max(1, (sc.n_excl + kRedBlock - 1) / kRedBlock)));
     CK(h, P.diag.ensure(8));
     CK(h, P.veff_int.ensure(1));
     CK(h, P.grad_int.ensure(3 * (size_t)N * sc.Q));
@@ -218,6 +221,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.etamax = P.etamax.p;
     D.jacc = h->precision == MOP_PREC_MIXED ? P.jacc.p : nullptr;
     D.e_pair = P.e_pair.p;
+    D.e_excl = sc.elec == 1 ? P.e_excl.p : nullptr;
     D.grad = dev_grad ? dev_grad + goff : P.grad_int.p;
     goff += 3 * (size_t)N * sc.Q;
     D.n_cv = P.n_cv;
@@ -261,12 +265,14 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, mark(1));
   CK(h, clear_jacc(false));
   CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
+  CK(h, launch_excl(sc, h->d_paths.p, np, max_nf, 0, L));
   CK(h, mark(2));
   CK(h, launch_e1(sc, h->d_paths.p, np, max_qpad, max_nf, L, h->e_bond.p, nbx));
   CK(h, mark(3));
   if (units_h > 0) {
     CK(h, clear_jacc(true));
     CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+    CK(h, launch_excl(sc, h->d_paths.p, np, max_n, fd ? 2 : 1, L));
   }
   CK(h, mark(4));
   CK(h, launch_e2(sc, h->d_paths.p, np, max_qpad, max_n, L, h->e_spring.p, nbx));
@@ -344,6 +350,14 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   if (d->rc >= 0.5 * std::min(d->box[0], std::min(d->box[1], d->box[2]))) return MOP_ERR_BOX;
   if (d->eps_rf < 1.0 || d->dt_path <= 0 || d->nu_path <= 0 || d->temperature < 0) return MOP_ERR_ARG;
   if (d->hvp_mode == MOP_HVP_FD && !(d->fd_h > 0)) return MOP_ERR_ARG;
+  if (d->elec != MOP_ELEC_RF && d->elec != MOP_ELEC_PME) return MOP_ERR_ARG;
+  if (d->elec == MOP_ELEC_PME) {
+    if (d->precision != MOP_PREC_MIXED || !std::isfinite(d->ew_beta) || !(d->ew_beta > 0)) return MOP_ERR_ARG;
+    if (d->pme_order < 4 || d->pme_order > 8) return MOP_ERR_ARG;
+    const bool none = d->pme_grid[0] == 0 && d->pme_grid[1] == 0 && d->pme_grid[2] == 0;
+    for (int k = 0; k < 3 && !none; ++k)
+      if (d->pme_grid[k] < d->pme_order || d->pme_grid[k] > 1024) return MOP_ERR_ARG;
+  }
   for (int i = 0; i < Q; ++i)
     if (d->type[i] < 0 || d->type[i] >= nt || !(d->mass[i] > 0)) return MOP_ERR_ARG;
   for (int t = 0; t < nt; ++t)
@@ -400,6 +414,22 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.k2rff = (float)sc.k2rf;
   sc.drff = (float)sc.drf;
   sc.fd_h = d->fd_h;
+  sc.elec = d->elec;
+  if (d->elec == MOP_ELEC_PME) {
+    // real-space Ewald: phi = f qq erfc(beta r)/r with the cutoff modifier; drf = phi'(rc)/(f qq)
+    const double b = d->ew_beta, ec = std::erfc(b * rc), gc = 2.0 / std::sqrt(M_PI) * b * std::exp(-b * b * rc * rc);
+    sc.krf = sc.crf = sc.k2rf = 0.0;
+    sc.krff = sc.crff = sc.k2rff = 0.f;
+    sc.drf = shifted ? -(ec / (rc * rc) + gc / rc) : 0.0;
+    sc.drff = (float)sc.drf;
+    sc.ewb = (float)b;
+    sc.ewb2 = (float)(b * b);
+    sc.ewc2 = (float)(2.0 / std::sqrt(M_PI) * b);
+    sc.ewec = (float)(ec / rc);
+    double q2 = 0.0;
+    for (int i = 0; i < Q; ++i) q2 += d->charge[i] * d->charge[i];
+    sc.e_self = -kCoulombF * b / std::sqrt(M_PI) * q2;
+  }
 
   std::vector<double> Kspr(Q), cL(Q), qs(Q);
   std::vector<float2> c_df(Q);
@@ -455,6 +485,26 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     }
   }
   for (size_t k = 0; k < incp.size(); ++k) incpf[k] = make_float2((float)incp[k].x, (float)incp[k].y);
+  // Ewald: the excluded pairs (same molecule, |local_i - local_j| <= 2), i < j
+  std::vector<int2> excl;
+  if (d->elec == MOP_ELEC_PME) {
+    std::vector<int> order(Q);
+    for (int i = 0; i < Q; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d->mol_id[a] < d->mol_id[b]; });
+    for (int a0 = 0; a0 < Q;) {
+      int a1 = a0;
+      while (a1 < Q && d->mol_id[order[a1]] == d->mol_id[order[a0]]) ++a1;
+      for (int u = a0; u < a1; ++u)
+        for (int v = u + 1; v < a1; ++v) {
+          const int i = std::min(order[u], order[v]), j = std::max(order[u], order[v]);
+          if (std::abs(d->mol_local[i] - d->mol_local[j]) <= 2) excl.push_back(make_int2(i, j));
+        }
+      a0 = a1;
+    }
+    std::sort(excl.begin(), excl.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+  }
+  sc.n_excl = (int)excl.size();
+  if (excl.empty()) excl.push_back(make_int2(0, 0));
   mop_status s;
   if ((s = upload(h, h->mass, d->mass, Q)) || (s = upload(h, h->Kspr, Kspr.data(), Q)) ||
       (s = upload(h, h->cL, cL.data(), Q)) || (s = upload(h, h->qs, qs.data(), Q)) ||
@@ -463,7 +513,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
       (s = upload(h, h->loc, d->mol_local, Q)) || (s = upload(h, h->inc_off, off.data(), Q + 1)) ||
       (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
       (s = upload(h, h->incpf, incpf.data(), incpf.size())) ||
-      (s = upload(h, h->tab, tab.data(), tab.size())) || (s = upload(h, h->tab64, tab64.data(), tab64.size()))) {
+      (s = upload(h, h->tab, tab.data(), tab.size())) || (s = upload(h, h->tab64, tab64.data(), tab64.size())) ||
+      (s = upload(h, h->excl, excl.data(), excl.size()))) {
     mop_destroy(h);
     return s;
   }
@@ -482,6 +533,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.incpf = h->incpf.p;
   sc.tab = h->tab.p;
   sc.tab64 = h->tab64.p;
+  sc.excl = h->excl.p;
 
   for (int k = 0; k < 3; ++k) h->box[k] = d->box[k];
   make_grid(h);
@@ -501,7 +553,7 @@ mop_status mop_destroy(mop_handle* h) {
   if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
   h->step_dev.release();
   h->d_one.release(); h->counts.release();
-  h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release();
+  h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release(); h->excl.release();
   for (auto& P : h->paths) {
     P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.reff.release(); P.colid.release();
     P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();
@@ -510,7 +562,7 @@ mop_status mop_destroy(mop_handle* h) {
     P.cwrap.release(); P.cwdf.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
-    P.eta32.release(); P.etamax.release(); P.jacc.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
+    P.eta32.release(); P.etamax.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
     P.gA.release(); P.gB.release(); P.gc.release(); P.gh.release(); P.gw.release();
   }
   delete h;

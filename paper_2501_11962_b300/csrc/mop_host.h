@@ -81,6 +81,7 @@ struct PathHost {
   DevBuf<unsigned> etamax;
   DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
+  DevBuf<double> e_excl;   // Ewald: bead-1 energy partials of the exclusion corrections
   // bias
   std::vector<int> hA, hB;   // the groups of all CVs, concatenated
   int n_cv = 0;
@@ -120,6 +121,7 @@ cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
                       double* e_bond, int nbx);
 cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
                       double* e_spring, int nbx);
+cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L);
 cudaError_t launch_deposit(const SysConsts& sc, const PathDev* d_paths, int n_paths, double height, double width,
                            Launch L);
 cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L);

@@ -40,6 +40,13 @@ struct SysConsts {
   double rc, rc2, krf, crf, k2rf, drf;   // RF constants; drf = phi'_RF(rc) / (f qi qj) if shifted
   float rcf, rc2f, krff, crff, k2rff, drff;
   double fd_h;
+  // Ewald electrostatics (elec = 1): erfc(beta r)/r in the pair kernels, the erf correction of
+  // excluded pairs, the self term, and the SPME reciprocal part
+  int elec;
+  float ewb, ewb2, ewc2, ewec;   // beta, beta^2, 2 beta / sqrt(pi), erfc(beta rc) / rc
+  double e_self;                 // -f beta / sqrt(pi) sum_i q_i^2
+  int n_excl;                    // excluded pairs (i < j, caller indices)
+  const int2* excl;
   // per-atom arrays in caller order
   const double* mass;
   const double* Kspr;   // m nu / (2 dt)
@@ -108,6 +115,7 @@ struct PathDev {
   double* gc;
   double* gw;
   double* gh;
+  double* e_excl;          // Ewald: bead-1 energy partials of the exclusion corrections
   double* diag;            // [8]: U1, E_spring, E_bias, CV, V_eff, U_pair, U_bonded
   double* veff_out;        // one double
 };

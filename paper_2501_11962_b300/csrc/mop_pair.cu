@@ -96,12 +96,15 @@ template <> struct Acc1<double> {
 
 template <class R> struct Cst {
   R rc, rc2, krf, crf, k2rf, drf;
+  R ewb, ewb2, ewc2, ewec;   // Ewald: beta, beta^2, 2 beta / sqrt(pi), erfc(beta rc) / rc
   __device__ __forceinline__ explicit Cst(const SysConsts& sc);
 };
 template <> __device__ __forceinline__ Cst<float>::Cst(const SysConsts& sc)
-    : rc(sc.rcf), rc2(sc.rc2f), krf(sc.krff), crf(sc.crff), k2rf(sc.k2rff), drf(sc.drff) {}
+    : rc(sc.rcf), rc2(sc.rc2f), krf(sc.krff), crf(sc.crff), k2rf(sc.k2rff), drf(sc.drff), ewb(sc.ewb),
+      ewb2(sc.ewb2), ewc2(sc.ewc2), ewec(sc.ewec) {}
 template <> __device__ __forceinline__ Cst<double>::Cst(const SysConsts& sc)
-    : rc(sc.rc), rc2(sc.rc2), krf(sc.krf), crf(sc.crf), k2rf(sc.k2rf), drf(sc.drf) {}
+    : rc(sc.rc), rc2(sc.rc2), krf(sc.krf), crf(sc.crf), k2rf(sc.k2rf), drf(sc.drf), ewb(0), ewb2(0), ewc2(0),
+      ewec(0) {}
 
 // g = -phi'_sf(r)/r from r^-1 powers; p = (12 c12, 6 c6, phi'_LJ(rc), phi_LJ(rc)), sh = phi'(rc)
 template <class R, class V4>
@@ -147,8 +150,24 @@ __device__ __forceinline__ R pair_g2(const PairK<R>& c, R rinv, R rinv2, R rinv6
 // One pair for one bead (i-atom of this lane at xs, j-atom xj); cutoff test against rc2e
 // (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-)
 // (MODE 2) into a[3] and the pair energy into e (ENERGY).
+// Ewald real space (EW): the electrostatic factor of g, qq (erfc(beta r)/r + 2 beta/sqrt(pi)
+// exp(-beta^2 r^2)), from erfc(beta r) (CUDA's erfcf) and c2E = 2 beta/sqrt(pi) exp(-beta^2 r^2)
+template <class R>
+__device__ __forceinline__ void ewald_terms(const Cst<R>& k, R r2, R rinv, R* ec, R* c2e) {
+  *ec = erfcf(k.ewb * (r2 * rinv));
+  *c2e = k.ewc2 * __expf(-k.ewb2 * r2);
+}
+
+// g = -phi'_sf(r) / r with Ewald real space: r^-2 [r^-6 (A r^-6 - B) + qq (ec r^-1 + c2E)] + sh r^-1
+template <class R>
+__device__ __forceinline__ R pair_g2_ew(const PairK<R>& c, R rinv, R rinv2, R rinv6, R ec, R c2e) {
+  const R t = fma(c.qq, fma(ec, rinv, c2e), rinv6 * fma(c.A, rinv6, -c.B));
+  return fma(rinv2, t, c.sh * rinv);
+}
+
 // HALF: the pair's contribution to atom i is also returned in f (atom j receives -f).
-template <class R, int MODE, bool ENERGY, bool HALF, class V4>
+// EW: Ewald real-space electrostatics instead of the reaction field.
+template <class R, int MODE, bool ENERGY, bool HALF, bool EW, class V4>
 __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R xs, R ys, R zs, const V4& xj, R rc2e,
                                          const R* ei, const R* ej, R eps, R ew, R* a, R& e, R* f) {
   const R dx = xs - xj.x, dy = ys - xj.y, dz = zs - xj.z;
@@ -158,7 +177,9 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
     const R rinv = Tr<R>::rsq(r2);
     const R rinv2 = rinv * rinv;
     const R rinv6 = rinv2 * rinv2 * rinv2;
-    R g = pair_g2<R>(c, rinv, rinv2, rinv6);
+    R ec = R(0), c2e = R(0);
+    if (EW) ewald_terms<R>(k, r2, rinv, &ec, &c2e);
+    R g = EW ? pair_g2_ew<R>(c, rinv, rinv2, rinv6, ec, c2e) : pair_g2<R>(c, rinv, rinv2, rinv6);
     g = in ? g : R(0);
     if (HALF) {
       f[0] = g * dx;
@@ -176,7 +197,7 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
       // phi(r) - phi(rc) - (r - rc) phi'(rc); phi_RF(rc) = 0 by the choice of c_rf
       const R r = r2 * rinv;
       const R elj = rinv6 * fma(c.A * R(1.0 / 12.0), rinv6, -c.B * R(1.0 / 6.0));
-      const R erf = c.qq * (rinv + fma(k.krf, r2, -k.crf));
+      const R erf = EW ? c.qq * fma(ec, rinv, -k.ewec) : c.qq * (rinv + fma(k.krf, r2, -k.crf));
       const R E = elj + erf - c.Ew - (r - k.rc) * c.sh;
       e = in ? fma(ew, E, e) : e;
     }
@@ -188,9 +209,19 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
     const R rinv2 = rinv * rinv;
     const R rinv3 = rinv * rinv2;
     const R rinv6 = rinv2 * rinv2 * rinv2;
-    const R g = pair_g2<R>(c, rinv, rinv2, rinv6);
-    // b = (phi'' + g) / r^2 = r^-4 r^-6 (14 A r^-6 - 8 B) + r^-3 (3 qq r^-2 + sh)
-    const R b = fma(rinv2 * rinv2, rinv6 * fma(c.A14, rinv6, -c.B8), rinv3 * fma(c.q3, rinv2, c.sh));
+    R g, b;
+    if (EW) {
+      // b = r^-4 r^-6 (14 A r^-6 - 8 B) + r^-3 [qq (3 ec r^-2 + c2E (3 r^-1 + 2 beta^2 r)) + sh]
+      R ec, c2e;
+      ewald_terms<R>(k, r2, rinv, &ec, &c2e);
+      g = pair_g2_ew<R>(c, rinv, rinv2, rinv6, ec, c2e);
+      const R el = fma(R(3) * ec, rinv2, c2e * fma(R(2) * k.ewb2, r2 * rinv, R(3) * rinv));
+      b = fma(rinv2 * rinv2, rinv6 * fma(c.A14, rinv6, -c.B8), rinv3 * fma(c.qq, el, c.sh));
+    } else {
+      g = pair_g2<R>(c, rinv, rinv2, rinv6);
+      // b = (phi'' + g) / r^2 = r^-4 r^-6 (14 A r^-6 - 8 B) + r^-3 (3 qq r^-2 + sh)
+      b = fma(rinv2 * rinv2, rinv6 * fma(c.A14, rinv6, -c.B8), rinv3 * fma(c.q3, rinv2, c.sh));
+    }
     const R s = fma(dx, ux, fma(dy, uy, dz * uz));
     const R t = in ? b * s : R(0);
     const R ng = in ? -g : R(0);
@@ -216,7 +247,14 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
       const R rinv = Tr<R>::rsq(r2);
       const R rinv2 = rinv * rinv;
       const R rinv6 = rinv2 * rinv2 * rinv2;
-      R g = pair_g2<R>(c, rinv, rinv2, rinv6);
+      R g;
+      if (EW) {
+        R ec, c2e;
+        ewald_terms<R>(k, r2, rinv, &ec, &c2e);
+        g = pair_g2_ew<R>(c, rinv, rinv2, rinv6, ec, c2e);
+      } else {
+        g = pair_g2<R>(c, rinv, rinv2, rinv6);
+      }
       g = in ? (sgn ? -g : g) : R(0);
       if (HALF) {
         f[0] = sgn ? fma(g, px, f[0]) : g * px;
@@ -352,7 +390,7 @@ __device__ __forceinline__ void j_flush(const JFlush& J, Stage<float, B>& S, int
 // One work unit: the i-cluster ci against its whole list, for the B beads n0 .. n0 + B - 1
 // (bead n0 + 1 of a unit past the last bead repeats bead n0 and is not written).  FP32 mode runs
 // on the half list (each cluster pair once, j-side sums to P.jacc), FP64 mode on the full list.
-template <class R, int MODE, bool ENERGY, int B>
+template <class R, int MODE, bool ENERGY, int B, bool EW>
 __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr<R>::V4* __restrict__ tab, int tstr,
                                           Stage<R, B>& S, const PathDev& P, int n0, int n_pass, int ci, int lane) {
   using V4 = typename Tr<R>::V4;
@@ -512,10 +550,10 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
             R* acc = (sizeof(R) == 4) ? a[b] : accd.a;
             R f[3];
             if (ENERGY && b == 0)   // energy of bead n0 (= bead 1) only
-              pair_one<R, MODE, true, HALF, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej,
+              pair_one<R, MODE, true, HALF, EW, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej,
                                                 eps[b], ew, acc, eacc.a, f);
             else
-              pair_one<R, MODE, false, HALF, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej,
+              pair_one<R, MODE, false, HALF, EW, V4>(k, pc, xs[b][0], xs[b][1], xs[b][2], S.x[b][sj], rce, ei[b], ej,
                                                  eps[b], ew, acc, eacc.a, f);
             if (HALF) {
 #pragma unroll
@@ -598,7 +636,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
 
 template <class R> struct BeadsPerUnit { static constexpr int value = sizeof(R) == 4 ? 2 : 1; };
 
-template <class R, int MODE>
+template <class R, int MODE, bool EW>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths,
                                                                       int n_paths, long long n_units) {
   using V4 = typename Tr<R>::V4;
@@ -631,24 +669,24 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pai
     const int n0 = (int)(v / P.n_clu) * B;
     const int ci = (int)(v % P.n_clu);
     if (ci >= __ldg(&P.meta[0])) continue;   // past the clusters of the current sort
-    if (MODE == 0 && n0 == 0) pair_unit<R, 0, true, B>(sc, tab, tstr, S, P, n0, n_pass, ci, lane);
-    else pair_unit<R, MODE, false, B>(sc, tab, tstr, S, P, n0, n_pass, ci, lane);
+    if (MODE == 0 && n0 == 0) pair_unit<R, 0, true, B, EW>(sc, tab, tstr, S, P, n0, n_pass, ci, lane);
+    else pair_unit<R, MODE, false, B, EW>(sc, tab, tstr, S, P, n0, n_pass, ci, lane);
   }
 }
 
-template <class R, int MODE>
+template <class R, int MODE, bool EW>
 cudaError_t launch_one(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int num_sms,
                        Launch L) {
   static int per_sm = 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R, MODE>, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R, MODE, EW>, 128, 0);
     if (e != cudaSuccess || per_sm <= 0) per_sm = 4;
   }
   const long long want_blocks = (n_units + 3) / 4;
   long long blocks = (long long)num_sms * per_sm;
   if (blocks > want_blocks) blocks = want_blocks;
   if (blocks < 1) blocks = 1;
-  k_pair<R, MODE><<<(int)blocks, 128, 0, L.st>>>(sc, d_paths, n_paths, n_units);
+  k_pair<R, MODE, EW><<<(int)blocks, 128, 0, L.st>>>(sc, d_paths, n_paths, n_units);
   ++*L.counter;
   return cudaGetLastError();
 }
@@ -732,14 +770,17 @@ int pair_beads_per_unit(int precision) { return precision == 1 ? 1 : 2; }
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
                         int num_sms, Launch L) {
   if (n_units <= 0) return cudaSuccess;
-  const bool f64 = sc.precision == 1;
+  const bool f64 = sc.precision == 1, ew = sc.elec == 1;   // Ewald runs in mixed precision only
   switch (mode) {
-    case 0: return f64 ? launch_one<double, 0>(sc, d_paths, n_paths, n_units, num_sms, L)
-                       : launch_one<float, 0>(sc, d_paths, n_paths, n_units, num_sms, L);
-    case 1: return f64 ? launch_one<double, 1>(sc, d_paths, n_paths, n_units, num_sms, L)
-                       : launch_one<float, 1>(sc, d_paths, n_paths, n_units, num_sms, L);
-    default: return f64 ? launch_one<double, 2>(sc, d_paths, n_paths, n_units, num_sms, L)
-                        : launch_one<float, 2>(sc, d_paths, n_paths, n_units, num_sms, L);
+    case 0: return f64 ? launch_one<double, 0, false>(sc, d_paths, n_paths, n_units, num_sms, L)
+                 : ew ? launch_one<float, 0, true>(sc, d_paths, n_paths, n_units, num_sms, L)
+                      : launch_one<float, 0, false>(sc, d_paths, n_paths, n_units, num_sms, L);
+    case 1: return f64 ? launch_one<double, 1, false>(sc, d_paths, n_paths, n_units, num_sms, L)
+                 : ew ? launch_one<float, 1, true>(sc, d_paths, n_paths, n_units, num_sms, L)
+                      : launch_one<float, 1, false>(sc, d_paths, n_paths, n_units, num_sms, L);
+    default: return f64 ? launch_one<double, 2, false>(sc, d_paths, n_paths, n_units, num_sms, L)
+                  : ew ? launch_one<float, 2, true>(sc, d_paths, n_paths, n_units, num_sms, L)
+                       : launch_one<float, 2, false>(sc, d_paths, n_paths, n_units, num_sms, L);
   }
 }
 

@@ -575,21 +575,94 @@ __global__ void k_deposit(SysConsts sc, const PathDev* __restrict__ paths, doubl
   P.gh[P.n_gauss] = height;
 }
 
+// Ewald exclusion corrections: the reciprocal sum includes every excluded pair, so each gets
+// phi_x(r) = -f q_i q_j erf(beta r) / r (no cutoff).  One thread per (excluded pair, bead):
+// MODE 0 the force (and bead-1 energy partials), MODE 1 H eta, MODE 2 the FD difference of the
+// force at R +- eps eta; +-f is added, fixed point, to the j-side sums of both atoms.
+__device__ __forceinline__ void excl_terms(const SysConsts& sc, float r2, float qq, float* g, float* b, float* e) {
+  const float rinv = rsqrtf(r2), r = r2 * rinv;
+  const float er = erff(sc.ewb * r), c2e = sc.ewc2 * __expf(-sc.ewb2 * r2);
+  // phi_x' = qq (erf / r^2 - c2E / r); g = -phi_x' / r; b = (phi_x'' + g) / r^2
+  *g = -qq * rinv * rinv * (er * rinv - c2e);
+  *b = -qq * rinv * rinv * rinv * (3.f * er * rinv * rinv - c2e * (3.f * rinv + 2.f * sc.ewb2 * r));
+  *e = -qq * er * rinv;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev* __restrict__ paths) {
+  __shared__ double sh[32];
+  const int p = blockIdx.z, n = blockIdx.y;
+  const PathDev& P = paths[p];
+  const int n_pass = MODE == 0 ? P.n_force : P.n_hvp;
+  if (n >= n_pass) return;   // whole block
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float en = 0.f;
+  if (t < sc.n_excl) {
+    const int2 ij = sc.excl[t];
+    float d[3];
+    mi_diff<float>(sc, P, n, ij.x, ij.y, d);
+    const float qq = (float)(sc.qs[ij.x] * sc.qs[ij.y]);
+    float f[3];
+    if (MODE == 0) {
+      float g, b, e;
+      excl_terms(sc, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], qq, &g, &b, &e);
+      for (int c = 0; c < 3; ++c) f[c] = g * d[c];
+      en = e;
+    } else {
+      float ei[3], ej[3], u[3];
+      eta_of<float>(P, n, ij.x, ei);
+      eta_of<float>(P, n, ij.y, ej);
+      for (int c = 0; c < 3; ++c) u[c] = ei[c] - ej[c];
+      if (MODE == 1) {
+        float g, b, e;
+        excl_terms(sc, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], qq, &g, &b, &e);
+        const float s = b * (d[0] * u[0] + d[1] * u[1] + d[2] * u[2]);
+        for (int c = 0; c < 3; ++c) f[c] = s * d[c] - g * u[c];   // A u
+      } else {
+        const float mx = __uint_as_float(P.etamax[n]);
+        const float eps = (float)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
+        float fp[3], fm[3];
+        for (int sg = 0; sg < 2; ++sg) {
+          float a[3];
+          for (int c = 0; c < 3; ++c) a[c] = d[c] + (sg ? -eps : eps) * u[c];
+          float g, b, e;
+          excl_terms(sc, a[0] * a[0] + a[1] * a[1] + a[2] * a[2], qq, &g, &b, &e);
+          for (int c = 0; c < 3; ++c) (sg ? fm : fp)[c] = g * a[c];
+        }
+        for (int c = 0; c < 3; ++c) f[c] = -(fp[c] - fm[c]) / (2.f * eps);   // H eta = -dF/de
+      }
+    }
+    unsigned long long* ji = P.jacc + 3 * ((size_t)n * P.Qpad + P.slot[ij.x]);
+    unsigned long long* jj = P.jacc + 3 * ((size_t)n * P.Qpad + P.slot[ij.y]);
+    for (int c = 0; c < 3; ++c) {
+      atomicAdd(ji + c, (unsigned long long)__float2ll_rn(f[c] * kFixScale));
+      atomicAdd(jj + c, (unsigned long long)__float2ll_rn(-f[c] * kFixScale));
+    }
+  }
+  if (MODE == 0 && n == 0) {
+    const double tot = block_sum<kRedBlock>((double)en, sh);
+    if (threadIdx.x == 0) P.e_excl[blockIdx.x] = tot;
+  }
+}
+
 // fixed-order sums of the partial energies -> V_eff (one block per path)
 __global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const double* e_bond, int sb, int nb1,
-                         const double* e_spring, int ss, int nb2) {
+                         const double* e_spring, int ss, int nb2, int n_excl_blk, double e_self) {
   // e_bond: nb1 partials per path (stride sb); e_spring: nb2 partials per path (stride ss)
   __shared__ double sh[32];
   const int p = blockIdx.x;
   const PathDev& P = paths[p];
   double up = 0.0, ub = 0.0, es = 0.0;
   for (int k = threadIdx.x; k < P.meta[0]; k += blockDim.x) up += P.e_pair[k];
+  if (P.e_excl)   // Ewald: exclusion corrections (self term added below)
+    for (int k = threadIdx.x; k < n_excl_blk; k += blockDim.x) up += P.e_excl[k];
   for (int k = threadIdx.x; k < nb1; k += blockDim.x) ub += e_bond[(size_t)p * sb + k];
   for (int k = threadIdx.x; k < nb2; k += blockDim.x) es += e_spring[(size_t)p * ss + k];
   up = block_sum<kRedBlock>(up, sh);
   ub = block_sum<kRedBlock>(ub, sh);
   es = block_sum<kRedBlock>(es, sh);
   if (threadIdx.x == 0) {
+    if (P.e_excl) up += e_self;
     const double U1 = up + ub;
     const double V = U1 + es + P.diag[2];
     P.diag[0] = U1;
@@ -697,6 +770,16 @@ cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L) {
+  if (sc.elec != 1 || sc.n_excl == 0) return cudaSuccess;
+  const dim3 grid((sc.n_excl + kRedBlock - 1) / kRedBlock, max_beads, n_paths);
+  if (mode == 0) k_excl<0><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  else if (mode == 1) k_excl<1><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  else k_excl<2><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_deposit(const SysConsts& sc, const PathDev* d_paths, int n_paths, double height, double width,
                            Launch L) {
   k_deposit<<<n_paths, 32, 0, L.st>>>(sc, d_paths, height, width);
@@ -713,7 +796,8 @@ cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L, const double* e_bond,
                           int sb, int nb1, const double* e_spring, int ss, int nb2) {
   (void)sc;
-  k_reduce<<<n_paths, kRedBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2);
+  k_reduce<<<n_paths, kRedBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2,
+                                             (sc.n_excl + kRedBlock - 1) / kRedBlock, sc.e_self);
   ++*L.counter;
   return cudaGetLastError();
 }

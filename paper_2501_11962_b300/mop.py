@@ -19,6 +19,7 @@ MOP_SHIFTED_FORCE, MOP_POT_SHIFT = 0, 1
 MOP_HVP_ADJOINT, MOP_HVP_FD = 0, 1
 MOP_PREC_MIXED, MOP_PREC_FP64 = 0, 1
 MOP_DEVPTR, MOP_INPUT_F64, MOP_E2E, MOP_COM = 1, 2, 4, 8
+MOP_ELEC_RF, MOP_ELEC_PME = 0, 1
 MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 
 EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_veff_and_grad", "mop_get_field",
@@ -50,6 +51,7 @@ class mop_system_desc(C.Structure):
         ("rc", C.c_double), ("eps_rf", C.c_double), ("cutoff_mode", C.c_int32),
         ("dt_path", C.c_double), ("nu_path", C.c_double), ("temperature", C.c_double),
         ("hvp_mode", C.c_int32), ("fd_h", C.c_double), ("precision", C.c_int32),
+        ("elec", C.c_int32), ("ew_beta", C.c_double), ("pme_grid", C.c_int32 * 3), ("pme_order", C.c_int32),
     ]
 
 
@@ -151,6 +153,10 @@ class Engine:
         d.rc, d.eps_rf, d.cutoff_mode = float(s.rc), float(s.eps_rf), int(s.cutoff_mode)
         d.dt_path, d.nu_path, d.temperature = float(s.dt_path), float(s.nu_path), float(s.temperature)
         d.hvp_mode, d.fd_h, d.precision = int(hvp_mode), float(fd_h), int(precision)
+        d.elec, d.ew_beta = int(getattr(s, "elec", MOP_ELEC_RF)), float(getattr(s, "ew_beta", 0.0))
+        for k, g in enumerate(getattr(s, "pme_grid", (0, 0, 0))):
+            d.pme_grid[k] = int(g)
+        d.pme_order = int(getattr(s, "pme_order", 4))
         h = C.c_void_p()
         st = self.L.mop_create(C.byref(d), device, C.byref(h))
         if st != MOP_OK:
