@@ -9,11 +9,12 @@ from pathlib import Path
 HERE = Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 LIB = HERE / "libmop.so"
-SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_path.cu", "mop_noalloc.cu", "mop_diag.cu"]
+SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_path.cu", "mop_pme.cu", "mop_noalloc.cu",
+           "mop_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 # FP32 subnormals never matter for forces, so the hot kernels flush them (shorter rsqrt path)
-PER_FILE = {"mop_pair.cu": ["-ftz=true"], "mop_path.cu": ["-ftz=true"]}
+PER_FILE = {"mop_pair.cu": ["-ftz=true"], "mop_path.cu": ["-ftz=true"], "mop_pme.cu": ["-ftz=true"]}
 
 
 def _stale() -> bool:
@@ -45,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed on {s}:\n{out.decode(errors='replace')}")
     tmp = LIB.with_suffix(".so.tmp")
-    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *objs, "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *objs, "-lcudart", "-lcufft"]
     subprocess.run(cmd, check=True)
     tmp.replace(LIB)
     return LIB

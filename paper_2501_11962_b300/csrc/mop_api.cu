@@ -41,6 +41,8 @@ struct mop_handle {
   DevBuf<PathDev> d_paths, d_one;
   DevBuf<double> e_bond, e_spring, scratch;
   DevBuf<int2> excl;                      // Ewald exclusion pairs
+  DevBuf<float> pme_theta;                // SPME kernel [K1][K2][K3 / 2 + 1]
+  PmePlans* pme = nullptr;                // cuFFT plans per bead count
   DevBuf<unsigned long long> counts;
   mop_tuning tuning{1.0, 0.5};
   double box[3] = {0.0, 0.0, 0.0};
@@ -178,6 +180,22 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     if (h->precision == MOP_PREC_MIXED) CK(h, P.jacc.ensure(nq3));
     CK(h, P.e_pair.ensure(h->grid.max_clu));
     if (sc.elec == 1) CK(h, P.e_excl.ensure(std::max(1, (sc.n_excl + kRedBlock - 1) / kRedBlock)));
+    const bool pme = sc.pme_nk > 0;
+    if (pme) {
+      const size_t nb = (size_t)std::max(n_force, n_hvp);
+      CK(h, P.pme_q.ensure(nb * sc.pme_nk));
+      CK(h, P.pme_r.ensure(nb * sc.pme_nk));
+      CK(h, P.pme_c.ensure(nb * sc.pme_nkc));
+      CK(h, P.pme_phi.ensure((size_t)n_force * sc.pme_nk));
+      CK(h, P.pme_phd.ensure(std::max<size_t>(1, (size_t)n_hvp * sc.pme_nk)));
+      CK(h, P.pme_e.ensure(pme_energy_blocks(sc)));
+      if (sync) {
+        std::string perr;
+        cudaError_t e = pme_plans_ensure(sc, h->pme, n_force, &perr);
+        if (e == cudaSuccess) e = pme_plans_ensure(sc, h->pme, n_hvp, &perr);
+        if (e != cudaSuccess) return fail(h, MOP_ERR_OOM, "%s", perr.c_str());
+      }
+    }
     CK(h, P.diag.ensure(8));
     CK(h, P.veff_int.ensure(1));
     CK(h, P.grad_int.ensure(3 * (size_t)N * sc.Q));
@@ -222,6 +240,15 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.jacc = h->precision == MOP_PREC_MIXED ? P.jacc.p : nullptr;
     D.e_pair = P.e_pair.p;
     D.e_excl = sc.elec == 1 ? P.e_excl.p : nullptr;
+    D.cwdf = P.cwdf.p;
+    if (pme) {
+      D.pme_q = P.pme_q.p;
+      D.pme_r = P.pme_r.p;
+      D.pme_c = P.pme_c.p;
+      D.pme_phi = P.pme_phi.p;
+      D.pme_phd = P.pme_phd.p;
+      D.pme_e = P.pme_e.p;
+    }
     D.grad = dev_grad ? dev_grad + goff : P.grad_int.p;
     goff += 3 * (size_t)N * sc.Q;
     D.n_cv = P.n_cv;
@@ -266,6 +293,11 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, clear_jacc(false));
   CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
   CK(h, launch_excl(sc, h->d_paths.p, np, max_nf, 0, L));
+  std::string perr;
+  if (sc.pme_nk > 0) {
+    cudaError_t e = launch_pme(sc, h->d_paths.p, pd.data(), np, max_nf, 0, h->pme, L, &perr);
+    if (e != cudaSuccess) return fail(h, MOP_ERR_CUDA, "SPME (forces): %s %s", cudaGetErrorString(e), perr.c_str());
+  }
   CK(h, mark(2));
   CK(h, launch_e1(sc, h->d_paths.p, np, max_qpad, max_nf, L, h->e_bond.p, nbx));
   CK(h, mark(3));
@@ -273,6 +305,10 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, clear_jacc(true));
     CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
     CK(h, launch_excl(sc, h->d_paths.p, np, max_n, fd ? 2 : 1, L));
+    if (sc.pme_nk > 0) {
+      cudaError_t e = launch_pme(sc, h->d_paths.p, pd.data(), np, max_n, 1, h->pme, L, &perr);
+      if (e != cudaSuccess) return fail(h, MOP_ERR_CUDA, "SPME (H eta): %s %s", cudaGetErrorString(e), perr.c_str());
+    }
   }
   CK(h, mark(4));
   CK(h, launch_e2(sc, h->d_paths.p, np, max_qpad, max_n, L, h->e_spring.p, nbx));
@@ -287,6 +323,69 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
 }
 
 void drop_graph(mop_handle* h);
+
+// M_p(t) at the integers t = 0..p-1, by the B-spline recursion
+// M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) / (n - 1) from M_2(0) = 0, M_2(1) = 1
+std::vector<double> bspline_integers(int p) {
+  std::vector<double> M = {0.0, 1.0};
+  for (int n = 3; n <= p; ++n) {
+    std::vector<double> B(n, 0.0);
+    for (int t = 0; t < n; ++t) {
+      const double a = t < n - 1 ? M[t] : 0.0, b = t >= 1 ? M[t - 1] : 0.0;
+      B[t] = (t * a + (n - t) * b) / (n - 1);
+    }
+    M = B;
+  }
+  return M;
+}
+
+// SPME grid constants of sc and the reciprocal kernel on the half spectrum [K1][K2][K3 / 2 + 1]:
+// theta(m) = exp(-pi^2 |m~|^2 / beta^2) / (pi V |m~|^2) |b1(m1) b2(m2) b3(m3)|^2, m~_d = m_d / L_d
+// (m folded to |m| <= K / 2), theta(0) = 0, |b(m)|^2 = 1 / |sum_k M_p(k + 1) exp(2 pi i m k / K)|^2.
+// Charges are sqrt(f) q, so f is not part of theta.
+std::vector<float> pme_kernel(const mop_system_desc* d, SysConsts* sc) {
+  const int p = d->pme_order;
+  const std::vector<double> Mi = bspline_integers(p);
+  double mod[3][1024];
+  for (int a = 0; a < 3; ++a) {
+    const int K = d->pme_grid[a];
+    sc->pme_K[a] = K;
+    const double kl = K / d->box[a];
+    const float hi = (float)kl;
+    sc->pme_kl[a] = make_float2(hi, (float)(kl - (double)hi));
+    for (int m = 0; m < K; ++m) {
+      double re = 0.0, im = 0.0;
+      for (int k = 0; k + 1 < p; ++k) {
+        const double ph = 2.0 * M_PI * (double)m * k / K;
+        re += Mi[k + 1] * std::cos(ph);
+        im += Mi[k + 1] * std::sin(ph);
+      }
+      mod[a][m] = 1.0 / (re * re + im * im);
+    }
+  }
+  sc->pme_order = p;
+  sc->pme_kc3 = sc->pme_K[2] / 2 + 1;
+  sc->pme_nk = (long long)sc->pme_K[0] * sc->pme_K[1] * sc->pme_K[2];
+  sc->pme_nkc = (long long)sc->pme_K[0] * sc->pme_K[1] * sc->pme_kc3;
+  const double V = d->box[0] * d->box[1] * d->box[2], b2 = d->ew_beta * d->ew_beta;
+  std::vector<float> th((size_t)sc->pme_nkc);
+  size_t o = 0;
+  for (int m1 = 0; m1 < sc->pme_K[0]; ++m1)
+    for (int m2 = 0; m2 < sc->pme_K[1]; ++m2)
+      for (int m3 = 0; m3 < sc->pme_kc3; ++m3, ++o) {
+        const int f[3] = {m1, m2, m3};
+        double k2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const int m = f[a] <= sc->pme_K[a] / 2 ? f[a] : f[a] - sc->pme_K[a];
+          const double k = m / d->box[a];
+          k2 += k * k;
+        }
+        th[o] = o == 0 ? 0.f
+                       : (float)(std::exp(-M_PI * M_PI * k2 / b2) / (M_PI * V * k2) * mod[0][m1] * mod[1][m2] *
+                                 mod[2][m3]);
+      }
+  return th;
+}
 
 // column grid of the cluster sort and bins of the pair search for the current tuning
 void make_grid(mop_handle* h) {
@@ -355,8 +454,13 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     if (d->precision != MOP_PREC_MIXED || !std::isfinite(d->ew_beta) || !(d->ew_beta > 0)) return MOP_ERR_ARG;
     if (d->pme_order < 4 || d->pme_order > 8) return MOP_ERR_ARG;
     const bool none = d->pme_grid[0] == 0 && d->pme_grid[1] == 0 && d->pme_grid[2] == 0;
-    for (int k = 0; k < 3 && !none; ++k)
+    for (int k = 0; k < 3 && !none; ++k) {
       if (d->pme_grid[k] < d->pme_order || d->pme_grid[k] > 1024) return MOP_ERR_ARG;
+      // odd orders: the spline moduli vanish at the Nyquist frequency of an even grid
+      if ((d->pme_order & 1) && !(d->pme_grid[k] & 1)) return MOP_ERR_ARG;
+    }
+    // the FD Hessian-vector product has no reciprocal-space counterpart
+    if (!none && d->hvp_mode == MOP_HVP_FD) return MOP_ERR_ARG;
   }
   for (int i = 0; i < Q; ++i)
     if (d->type[i] < 0 || d->type[i] >= nt || !(d->mass[i] > 0)) return MOP_ERR_ARG;
@@ -430,6 +534,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     for (int i = 0; i < Q; ++i) q2 += d->charge[i] * d->charge[i];
     sc.e_self = -kCoulombF * b / std::sqrt(M_PI) * q2;
   }
+  std::vector<float> theta;
+  if (d->elec == MOP_ELEC_PME && d->pme_grid[0] > 0) theta = pme_kernel(d, &sc);
 
   std::vector<double> Kspr(Q), cL(Q), qs(Q);
   std::vector<float2> c_df(Q);
@@ -514,7 +620,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
       (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
       (s = upload(h, h->incpf, incpf.data(), incpf.size())) ||
       (s = upload(h, h->tab, tab.data(), tab.size())) || (s = upload(h, h->tab64, tab64.data(), tab64.size())) ||
-      (s = upload(h, h->excl, excl.data(), excl.size()))) {
+      (s = upload(h, h->excl, excl.data(), excl.size())) ||
+      (s = upload(h, h->pme_theta, theta.data(), theta.size()))) {
     mop_destroy(h);
     return s;
   }
@@ -534,6 +641,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.tab = h->tab.p;
   sc.tab64 = h->tab64.p;
   sc.excl = h->excl.p;
+  sc.pme_theta = h->pme_theta.p;
+  h->pme = pme_plans_create();
 
   for (int k = 0; k < 3; ++k) h->box[k] = d->box[k];
   make_grid(h);
@@ -554,6 +663,8 @@ mop_status mop_destroy(mop_handle* h) {
   h->step_dev.release();
   h->d_one.release(); h->counts.release();
   h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release(); h->excl.release();
+  h->pme_theta.release();
+  if (h->pme) pme_plans_destroy(h->pme);
   for (auto& P : h->paths) {
     P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.reff.release(); P.colid.release();
     P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();

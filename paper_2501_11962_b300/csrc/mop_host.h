@@ -82,6 +82,12 @@ struct PathHost {
   DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
   DevBuf<double> e_excl;   // Ewald: bead-1 energy partials of the exclusion corrections
+  // SPME reciprocal space: fixed-point charge grids, FFT input, spectra, potential grids of the
+  // force and HVP passes [beads][grid points], bead-1 energy partials
+  DevBuf<unsigned long long> pme_q;
+  DevBuf<float> pme_r, pme_phi, pme_phd;
+  DevBuf<float2> pme_c;
+  DevBuf<double> pme_e;
   // bias
   std::vector<int> hA, hB;   // the groups of all CVs, concatenated
   int n_cv = 0;
@@ -128,6 +134,19 @@ cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L,
                           const double* e_bond, int e_bond_stride, int n_e1_blocks,
                           const double* e_spring, int e_spring_stride, int n_e2_blocks);
+// --- mop_pme.cu: SPME reciprocal space (forces into the j-side sums; mode 1: H eta) ----------
+struct PmePlans;
+PmePlans* pme_plans_create();
+void pme_plans_destroy(PmePlans* p);
+// plans for batches of `beads` grids; call outside stream capture
+cudaError_t pme_plans_ensure(const SysConsts& sc, PmePlans* plans, int beads, std::string* err);
+// mode 0: forces of beads [0, n_force) plus the bead-1 energy partials (pme_e); mode 1: H eta of
+// beads [0, n_hvp) (needs the potential grids of mode 0 and eta32)
+cudaError_t launch_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths,
+                       int max_beads, int mode, PmePlans* plans, Launch L, std::string* err);
+// blocks of bead-1 energy partials written by launch_pme
+inline int pme_energy_blocks(const SysConsts& sc) { return (int)((sc.pme_nkc + kRedBlock - 1) / kRedBlock); }
+
 cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, int N, double half_dt, Launch L);
 // the Philox step counter is read from device memory (*step), so a captured step can be replayed
 cudaError_t launch_drift(const SysConsts& sc, double* x64, double* vel, float* x32, int N, double dt,

@@ -47,6 +47,13 @@ struct SysConsts {
   double e_self;                 // -f beta / sqrt(pi) sum_i q_i^2
   int n_excl;                    // excluded pairs (i < j, caller indices)
   const int2* excl;
+  // smooth particle-mesh Ewald (pme_nk == 0: no reciprocal part)
+  int pme_order;
+  int pme_K[3];
+  int pme_kc3;                   // K3 / 2 + 1 (complex points along the last axis)
+  long long pme_nk, pme_nkc;     // real and complex points of one grid
+  float2 pme_kl[3];              // K / L as double-floats
+  const float* pme_theta;        // [K1][K2][K3 / 2 + 1] Ewald kernel times the B-spline moduli
   // per-atom arrays in caller order
   const double* mass;
   const double* Kspr;   // m nu / (2 dt)
@@ -116,6 +123,13 @@ struct PathDev {
   double* gw;
   double* gh;
   double* e_excl;          // Ewald: bead-1 energy partials of the exclusion corrections
+  const float2* cwdf;      // wrapped cluster centres as double-floats [n_clu][3]
+  unsigned long long* pme_q;   // SPME: fixed-point charge grids [beads][nk]
+  float* pme_r;                // float grids (FFT input) [beads][nk]
+  float2* pme_c;               // spectra [beads][nkc] (cufftComplex)
+  float* pme_phi;              // potential grids of the force pass [beads][nk]
+  float* pme_phd;              // potential grids of the derivative grids (HVP pass) [beads][nk]
+  double* pme_e;               // bead-1 energy partials
   double* diag;            // [8]: U1, E_spring, E_bias, CV, V_eff, U_pair, U_bonded
   double* veff_out;        // one double
 };

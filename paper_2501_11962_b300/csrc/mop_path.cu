@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev*
 
 // fixed-order sums of the partial energies -> V_eff (one block per path)
 __global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const double* e_bond, int sb, int nb1,
-                         const double* e_spring, int ss, int nb2, int n_excl_blk, double e_self) {
+                         const double* e_spring, int ss, int nb2, int n_excl_blk, double e_self, int n_pme_blk) {
   // e_bond: nb1 partials per path (stride sb); e_spring: nb2 partials per path (stride ss)
   __shared__ double sh[32];
   const int p = blockIdx.x;
@@ -656,6 +656,8 @@ __global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const d
   for (int k = threadIdx.x; k < P.meta[0]; k += blockDim.x) up += P.e_pair[k];
   if (P.e_excl)   // Ewald: exclusion corrections (self term added below)
     for (int k = threadIdx.x; k < n_excl_blk; k += blockDim.x) up += P.e_excl[k];
+  if (P.pme_e)    // SPME reciprocal-space energy of bead 1
+    for (int k = threadIdx.x; k < n_pme_blk; k += blockDim.x) up += P.pme_e[k];
   for (int k = threadIdx.x; k < nb1; k += blockDim.x) ub += e_bond[(size_t)p * sb + k];
   for (int k = threadIdx.x; k < nb2; k += blockDim.x) es += e_spring[(size_t)p * ss + k];
   up = block_sum<kRedBlock>(up, sh);
@@ -795,9 +797,9 @@ cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths
 
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L, const double* e_bond,
                           int sb, int nb1, const double* e_spring, int ss, int nb2) {
-  (void)sc;
   k_reduce<<<n_paths, kRedBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2,
-                                             (sc.n_excl + kRedBlock - 1) / kRedBlock, sc.e_self);
+                                             (sc.n_excl + kRedBlock - 1) / kRedBlock, sc.e_self,
+                                             pme_energy_blocks(sc));
   ++*L.counter;
   return cudaGetLastError();
 }

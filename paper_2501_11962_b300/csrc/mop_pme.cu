@@ -1,0 +1,341 @@
+// Smooth particle-mesh Ewald (reciprocal space) for every bead of a path (MOP_ELEC_PME).
+//
+// Essmann et al., J. Chem. Phys. 103, 8577 (1995): charges are spread with cardinal B-splines of
+// order P onto a K1 x K2 x K3 grid of the orthorhombic box, the grid is convolved with the Ewald
+// reciprocal kernel theta(m) = exp(-pi^2 |m~|^2 / beta^2) / (pi V |m~|^2) |b(m)|^2 by a real
+// FFT, and forces are gathered from the potential grid with the splines' derivatives.  The
+// adjoint Hessian-vector product needs one more spread (of the charge grid's derivative along
+// eta), one more FFT pair, and a gather with second derivatives of the splines:
+//     (H eta)_i = q_i sum_k [(eta_i . grad) grad M_i](k) phi(k) + q_i sum_k grad M_i(k) phi'(k),
+// with phi the potential grid of the force pass and phi' that of the derivative grid.
+// Grids of charges are summed as int64 fixed point, so results do not depend on the order of
+// the atomics; forces go into the path's fixed-point j-side sums.  The FFTs are cuFFT calls.
+#include <cufft.h>
+
+#include <map>
+#include <utility>
+
+#include "mop_host.h"
+
+namespace mop {
+
+// cuFFT plans per batch size (beads of one pass), created outside any stream capture
+struct PmePlans {
+  std::map<int, std::pair<cufftHandle, cufftHandle>> by_batch;   // R2C, C2R
+  ~PmePlans() {
+    for (auto& kv : by_batch) {
+      cufftDestroy(kv.second.first);
+      cufftDestroy(kv.second.second);
+    }
+  }
+};
+
+namespace {
+
+constexpr float kGridFixF = 1099511627776.0f;       // 2^40: fixed-point unit of the grids
+constexpr float kGridInv = 1.0f / 1099511627776.0f;
+
+// B-spline values M_P(w + t), t = 0..P-1 (w in [0, 1)), and the first and second derivatives
+// M_P' = M_{P-1}(x) - M_{P-1}(x - 1), M_P'' = M_{P-2}(x) - 2 M_{P-2}(x - 1) + M_{P-2}(x - 2), by
+// the recursion M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) / (n - 1).
+template <int P>
+__device__ __forceinline__ void spline(float w, float* M, float* dM, float* d2M) {
+  float A[P + 1], Am1[P + 1], Am2[P + 1];
+#pragma unroll
+  for (int t = 0; t <= P; ++t) A[t] = Am1[t] = Am2[t] = 0.f;
+  A[0] = w;
+  A[1] = 1.f - w;
+#pragma unroll
+  for (int n = 2; n < P; ++n) {
+#pragma unroll
+    for (int t = 0; t <= P; ++t) {
+      Am2[t] = Am1[t];
+      Am1[t] = A[t];
+    }
+    float B[P + 1];
+#pragma unroll
+    for (int t = 0; t <= P; ++t) {
+      const float x = w + (float)t;
+      const float a = t < n ? Am1[t] : 0.f;
+      const float b = t >= 1 ? Am1[t - 1] : 0.f;
+      B[t] = t <= n ? (x * a + ((float)(n + 1) - x) * b) / (float)n : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t <= P; ++t) A[t] = B[t];
+  }
+  // A = M_P, Am1 = M_{P-1}, Am2 = M_{P-2} (for P = 4: M_2 from the start)
+#pragma unroll
+  for (int t = 0; t < P; ++t) {
+    M[t] = A[t];
+    dM[t] = (t < P - 1 ? Am1[t] : 0.f) - (t >= 1 ? Am1[t - 1] : 0.f);
+    const float c0 = t < P - 2 ? Am2[t] : 0.f, c1 = (t >= 1 && t - 1 < P - 2) ? Am2[t - 1] : 0.f;
+    const float c2 = (t >= 2 && t - 2 < P - 2) ? Am2[t - 2] : 0.f;
+    d2M[t] = c0 - 2.f * c1 + c2;
+  }
+}
+
+// fractional grid coordinate of a point C + x (C a wrapped cluster centre as a double-float, x
+// the cluster-local coordinate) along d: u = K (C + x) / L, split into base = floor(u) and
+// w = u - base, both exact to the FP32 rounding of w
+__device__ __forceinline__ void grid_coord(const SysConsts& sc, float2 C, float x, int d, int* base, float* w) {
+  df s = two_sum(C.x, x);
+  s = fast_two_sum(s.hi, s.lo + C.y);
+  const float p = s.hi * sc.pme_kl[d].x;
+  const float e = fmaf(s.hi, sc.pme_kl[d].x, -p) + fmaf(s.hi, sc.pme_kl[d].y, s.lo * sc.pme_kl[d].x);
+  float b = floorf(p);
+  float ww = (p - b) + e;
+  if (ww < 0.f) {
+    b -= 1.f;
+    ww += 1.f;
+  } else if (ww >= 1.f) {
+    b += 1.f;
+    ww -= 1.f;
+  }
+  *base = (int)b;
+  *w = fminf(fmaxf(ww, 0.f), 0.99999994f);
+}
+
+__device__ __forceinline__ int wrap(int i, int K) {
+  i %= K;
+  return i < 0 ? i + K : i;
+}
+
+// splines of one slot at bead n: grid indices ix[d][t] and M, dM (scaled by K/L), d2M (by (K/L)^2)
+template <int P>
+__device__ __forceinline__ void slot_splines(const SysConsts& sc, const PathDev& P_, int n, int s, int (*ix)[P],
+                                             float (*M)[P], float (*dM)[P], float (*d2M)[P]) {
+  const float4 xl = P_.xq[(size_t)n * P_.Qpad + s];
+  const int c = s / kCL;
+  const float xv[3] = {xl.x, xl.y, xl.z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int b;
+    float w;
+    grid_coord(sc, P_.cwdf[3 * c + d], xv[d], d, &b, &w);
+    spline<P>(w, M[d], dM[d], d2M[d]);
+    const float kl = sc.pme_kl[d].x;
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+      ix[d][t] = wrap(b - t, sc.pme_K[d]);
+      dM[d][t] *= kl;
+      d2M[d][t] *= kl * kl;
+    }
+  }
+}
+
+// spreads the charges (DERIV = 0) or the charge grid's derivative along eta (DERIV = 1) of every
+// slot of bead n onto grid[n] (fixed point); grid: (slots, beads, paths)
+template <int P, int DERIV>
+__global__ void __launch_bounds__(kRedBlock) k_pme_spread(SysConsts sc, const PathDev* __restrict__ paths) {
+  const PathDev& Pd = paths[blockIdx.z];
+  const int n = blockIdx.y, s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_pass = DERIV ? Pd.n_hvp : Pd.n_force;
+  if (n >= n_pass || s >= __ldg(&Pd.meta[0]) * kCL) return;
+  const int a = Pd.perm[s];
+  if (a < 0) return;
+  const float q = (float)sc.qs[a];
+  if (q == 0.f) return;
+  int ix[3][P];
+  float M[3][P], dM[3][P], d2M[3][P];
+  slot_splines<P>(sc, Pd, n, s, ix, M, dM, d2M);
+  float eta[3] = {0.f, 0.f, 0.f};
+  if (DERIV) {
+    const float4 e = Pd.eta32[(size_t)n * Pd.Qpad + s];
+    eta[0] = e.x;
+    eta[1] = e.y;
+    eta[2] = e.z;
+  }
+  const int K1 = sc.pme_K[1], K2 = sc.pme_K[2];
+  unsigned long long* g = Pd.pme_q + (size_t)n * sc.pme_nk;
+#pragma unroll
+  for (int t0 = 0; t0 < P; ++t0)
+#pragma unroll
+    for (int t1 = 0; t1 < P; ++t1) {
+      const size_t row = ((size_t)ix[0][t0] * K1 + ix[1][t1]) * K2;
+#pragma unroll
+      for (int t2 = 0; t2 < P; ++t2) {
+        float v;
+        if (DERIV)
+          v = q * (dM[0][t0] * M[1][t1] * M[2][t2] * eta[0] + M[0][t0] * dM[1][t1] * M[2][t2] * eta[1] +
+                   M[0][t0] * M[1][t1] * dM[2][t2] * eta[2]);
+        else
+          v = q * M[0][t0] * M[1][t1] * M[2][t2];
+        atomicAdd(g + row + ix[2][t2], (unsigned long long)__float2ll_rn(v * kGridFixF));
+      }
+    }
+}
+
+// int64 fixed-point grids -> float grids (the FFT input), for beads [0, n_pass) of a path
+__global__ void k_pme_tofloat(const unsigned long long* __restrict__ q, float* r, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) r[t] = (float)(long long)q[t] * kGridInv;
+}
+
+// multiplies the spectra by theta (shared by all beads); with `energy`, bead 0's block partials
+// of E = 1/2 sum_m theta |F(m)|^2 over the half spectrum (weight 2 for 0 < m3 < K3/2)
+__global__ void __launch_bounds__(kRedBlock) k_pme_scale(SysConsts sc, cufftComplex* c, long long nkc, int beads,
+                                                         double* energy) {
+  __shared__ double sh[32];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  double e = 0.0;
+  if (n < beads && t < nkc) {
+    const float th = sc.pme_theta[t];
+    cufftComplex& v = c[(size_t)n * nkc + t];
+    if (energy && n == 0) {
+      const int m3 = (int)(t % sc.pme_kc3);
+      const double wgt = (m3 == 0 || 2 * m3 == sc.pme_K[2]) ? 1.0 : 2.0;
+      e = 0.5 * wgt * (double)th * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+    v.x *= th;
+    v.y *= th;
+  }
+  if (energy && n == 0) {
+    e = block_sum<kRedBlock>(e, sh);
+    if (threadIdx.x == 0) energy[blockIdx.x] = e;
+  }
+}
+
+// forces (MODE 0: F_i = -q_i sum_k grad M_i(k) phi(k)) or H eta (MODE 1) of every slot, added
+// to the fixed-point j-side sums; grid: (slots, beads, paths)
+template <int P, int MODE>
+__global__ void __launch_bounds__(kRedBlock) k_pme_gather(SysConsts sc, const PathDev* __restrict__ paths) {
+  const PathDev& Pd = paths[blockIdx.z];
+  const int n = blockIdx.y, s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_pass = MODE ? Pd.n_hvp : Pd.n_force;
+  if (n >= n_pass || s >= __ldg(&Pd.meta[0]) * kCL) return;
+  const int a = Pd.perm[s];
+  if (a < 0) return;
+  const float q = (float)sc.qs[a];
+  if (q == 0.f) return;
+  int ix[3][P];
+  float M[3][P], dM[3][P], d2M[3][P];
+  slot_splines<P>(sc, Pd, n, s, ix, M, dM, d2M);
+  float eta[3] = {0.f, 0.f, 0.f};
+  if (MODE) {
+    const float4 e = Pd.eta32[(size_t)n * Pd.Qpad + s];
+    eta[0] = e.x;
+    eta[1] = e.y;
+    eta[2] = e.z;
+  }
+  const int K1 = sc.pme_K[1], K2 = sc.pme_K[2];
+  const float* phi = Pd.pme_phi + (size_t)n * sc.pme_nk;
+  const float* phd = MODE ? Pd.pme_phd + (size_t)n * sc.pme_nk : nullptr;
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int t0 = 0; t0 < P; ++t0)
+#pragma unroll
+    for (int t1 = 0; t1 < P; ++t1) {
+      const size_t row = ((size_t)ix[0][t0] * K1 + ix[1][t1]) * K2;
+#pragma unroll
+      for (int t2 = 0; t2 < P; ++t2) {
+        const float p = phi[row + ix[2][t2]];
+        const float g0 = dM[0][t0] * M[1][t1] * M[2][t2], g1 = M[0][t0] * dM[1][t1] * M[2][t2],
+                    g2 = M[0][t0] * M[1][t1] * dM[2][t2];
+        if (MODE == 0) {
+          acc[0] = fmaf(g0, p, acc[0]);
+          acc[1] = fmaf(g1, p, acc[1]);
+          acc[2] = fmaf(g2, p, acc[2]);
+        } else {
+          const float pd = phd[row + ix[2][t2]];
+          // (eta . grad) grad of M0 M1 M2 at this point
+          const float h00 = d2M[0][t0] * M[1][t1] * M[2][t2], h11 = M[0][t0] * d2M[1][t1] * M[2][t2],
+                      h22 = M[0][t0] * M[1][t1] * d2M[2][t2];
+          const float h01 = dM[0][t0] * dM[1][t1] * M[2][t2], h02 = dM[0][t0] * M[1][t1] * dM[2][t2],
+                      h12 = M[0][t0] * dM[1][t1] * dM[2][t2];
+          acc[0] += (h00 * eta[0] + h01 * eta[1] + h02 * eta[2]) * p + g0 * pd;
+          acc[1] += (h01 * eta[0] + h11 * eta[1] + h12 * eta[2]) * p + g1 * pd;
+          acc[2] += (h02 * eta[0] + h12 * eta[1] + h22 * eta[2]) * p + g2 * pd;
+        }
+      }
+    }
+  // forces: -q grad E; H eta: +q (...)
+  const float sgn = MODE ? q : -q;
+  unsigned long long* dst = Pd.jacc + 3 * ((size_t)n * Pd.Qpad + s);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) atomicAdd(dst + d, (unsigned long long)__float2ll_rn(sgn * acc[d] * kFixScale));
+}
+
+template <int P>
+cudaError_t run_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths, int max_beads,
+                    int mode, PmePlans& plans, Launch L, std::string* err) {
+  int max_qpad = 0;
+  for (int p = 0; p < n_paths; ++p) max_qpad = std::max(max_qpad, h_paths[p].Qpad);
+  const dim3 sgrid((max_qpad + kRedBlock - 1) / kRedBlock, max_beads, n_paths);
+  for (int p = 0; p < n_paths; ++p) {
+    const PathDev& D = h_paths[p];
+    const int beads = mode ? D.n_hvp : D.n_force;
+    if (beads <= 0) continue;
+    cudaError_t e = cudaMemsetAsync(D.pme_q, 0, sizeof(unsigned long long) * sc.pme_nk * beads, L.st);
+    if (e != cudaSuccess) return e;
+  }
+  if (mode == 0) k_pme_spread<P, 0><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  else k_pme_spread<P, 1><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  ++*L.counter;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int p = 0; p < n_paths; ++p) {
+    const PathDev& D = h_paths[p];
+    const int beads = mode ? D.n_hvp : D.n_force;
+    if (beads <= 0) continue;
+    const long long nr = (long long)sc.pme_nk * beads;
+    k_pme_tofloat<<<(int)((nr + 255) / 256), 256, 0, L.st>>>(D.pme_q, D.pme_r, nr);
+    ++*L.counter;
+    auto it = plans.by_batch.find(beads);
+    if (it == plans.by_batch.end()) {
+      if (err) *err = "no FFT plan for this bead count (evaluate once without stream capture first)";
+      return cudaErrorNotReady;
+    }
+    cufftSetStream(it->second.first, L.st);
+    cufftSetStream(it->second.second, L.st);
+    if (cufftExecR2C(it->second.first, D.pme_r, D.pme_c) != CUFFT_SUCCESS) {
+      if (err) *err = "cufftExecR2C failed";
+      return cudaErrorUnknown;
+    }
+    const dim3 cgrid((unsigned)((sc.pme_nkc + kRedBlock - 1) / kRedBlock), beads);
+    k_pme_scale<<<cgrid, kRedBlock, 0, L.st>>>(sc, D.pme_c, sc.pme_nkc, beads, mode == 0 ? D.pme_e : nullptr);
+    ++*L.counter;
+    float* out = mode ? D.pme_phd : D.pme_phi;
+    if (cufftExecC2R(it->second.second, D.pme_c, out) != CUFFT_SUCCESS) {
+      if (err) *err = "cufftExecC2R failed";
+      return cudaErrorUnknown;
+    }
+  }
+  if (mode == 0) k_pme_gather<P, 0><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  else k_pme_gather<P, 1><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+PmePlans* pme_plans_create() { return new PmePlans(); }
+void pme_plans_destroy(PmePlans* p) { delete p; }
+
+// makes sure plans exist for a batch of `beads` transforms (never inside a stream capture)
+cudaError_t pme_plans_ensure(const SysConsts& sc, PmePlans* plans, int beads, std::string* err) {
+  if (beads <= 0 || plans->by_batch.count(beads)) return cudaSuccess;
+  int n[3] = {sc.pme_K[0], sc.pme_K[1], sc.pme_K[2]};
+  cufftHandle f = 0, b = 0;
+  if (cufftPlanMany(&f, 3, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, beads) != CUFFT_SUCCESS ||
+      cufftPlanMany(&b, 3, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, beads) != CUFFT_SUCCESS) {
+    if (f) cufftDestroy(f);
+    if (err) *err = "cufftPlanMany failed";
+    return cudaErrorMemoryAllocation;
+  }
+  plans->by_batch[beads] = {f, b};
+  return cudaSuccess;
+}
+
+cudaError_t launch_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths,
+                       int max_beads, int mode, PmePlans* plans, Launch L, std::string* err) {
+  switch (sc.pme_order) {
+    case 4: return run_pme<4>(sc, d_paths, h_paths, n_paths, max_beads, mode, *plans, L, err);
+    case 5: return run_pme<5>(sc, d_paths, h_paths, n_paths, max_beads, mode, *plans, L, err);
+    case 6: return run_pme<6>(sc, d_paths, h_paths, n_paths, max_beads, mode, *plans, L, err);
+    case 7: return run_pme<7>(sc, d_paths, h_paths, n_paths, max_beads, mode, *plans, L, err);
+    default: return run_pme<8>(sc, d_paths, h_paths, n_paths, max_beads, mode, *plans, L, err);
+  }
+}
+
+}  // namespace mop

@@ -94,3 +94,23 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.mop_destroy(None) == mop.MOP_OK
     assert lib.mop_veff_and_grad(None, 0, None, None, 0, None) == mop.MOP_ERR_ARG
     assert lib.mop_last_launch_count(None) == 0
+
+
+def _pme(d, grid=(24, 24, 24), order=4, beta=3.0, hvp=0):
+    d.elec, d.ew_beta, d.pme_order, d.hvp_mode = mop.MOP_ELEC_PME, beta, order, hvp
+    for k in range(3):
+        d.pme_grid[k] = grid[k]
+    return d
+
+
+def test_create_validates_the_ewald_parameters(fcc):
+    d, keep = _desc(fcc, rc=1.0)
+    # the finite-difference HVP has no reciprocal-space counterpart; a grid-free Ewald is fine to check
+    assert _create(_pme(d, hvp=1)) == mop.MOP_ERR_ARG
+    # odd B-spline orders need odd grids (the moduli vanish at an even grid's Nyquist frequency)
+    assert _create(_pme(d, order=5)) == mop.MOP_ERR_ARG
+    assert _create(_pme(d, order=3)) == mop.MOP_ERR_ARG
+    assert _create(_pme(d, order=9, grid=(25, 25, 25))) == mop.MOP_ERR_ARG
+    assert _create(_pme(d, grid=(24, 3, 24))) == mop.MOP_ERR_ARG
+    assert _create(_pme(d, beta=-1.0)) == mop.MOP_ERR_ARG
+    assert _create(_pme(d, beta=float("nan"))) == mop.MOP_ERR_ARG

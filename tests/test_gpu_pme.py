@@ -41,3 +41,90 @@ def test_ewald_real_space_matches_oracle(hvp):
         # an FP32 central difference at h = 1e-4 nm carries ~1e-4 of its own error (as with the
         # reaction field): the FD path is compared with the oracle's FD of Eq. 5 at that level
         assert errs["Heta"] < 1e-3 and errs["G"] < 1e-3
+
+
+def pme_errors(eng, path_id, X, v, G, r):
+    N = X.shape[0]
+    F = eng.get_field(path_id, mop.MOP_FIELD_FORCE)[:N - 1]
+    eta = eng.get_field(path_id, mop.MOP_FIELD_ETA)[:N - 1]
+    He = eng.get_field(path_id, mop.MOP_FIELD_HETA)[:N - 1]
+    return dict(F=rel(F, r["F"][:N - 1]), eta=rel(eta, r["eta"][:N - 1]), Heta=rel(He, r["Heta"][:N - 1]),
+                G=rel(G, r["G"]), V=abs(v - r["veff"]) / abs(r["veff"]))
+
+
+def assert_within_bars(errs):
+    assert errs["F"] < TOL_F and errs["eta"] < TOL_F and errs["G"] < TOL_F, errs
+    assert errs["Heta"] < TOL_H and errs["V"] < TOL_V, errs
+
+
+def test_spme_matches_oracle():
+    # real space, exclusions, self term and the SPME reciprocal part (forces, bead-1 energy and
+    # the adjoint H eta through the derivative grid)
+    w = workload(2, n_beads=6)
+    sys = synth.with_pme(w.system)
+    X = w.paths[0]
+    eng = mop.Engine(sys)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff_pme(X.astype(np.float64))
+    errs = pme_errors(eng, 0, X, v[0], G, r)
+    print("spme", sys.pme_grid, errs)
+    assert_within_bars(errs)
+    # the reciprocal part is not negligible here: without it the oracle's forces differ by far more
+    no_recip = oracle.Oracle(dataclasses.replace(sys, pme_grid=(0, 0, 0))).veff(
+        X.astype(np.float64), want=("F",), hvp_mode=oracle.HVP_ANALYTIC)
+    assert rel(no_recip["F"][:X.shape[0] - 1], r["F"][:X.shape[0] - 1]) > 100 * TOL_F
+
+
+@pytest.mark.parametrize("order", [6, 7])
+def test_spme_higher_orders_match_oracle(order):
+    w = workload(2, n_beads=3)
+    base = synth.with_pme(w.system, order=order)
+    grid = tuple(k + 1 if order % 2 and k % 2 == 0 else k for k in base.pme_grid)   # odd orders: odd grids
+    sys = dataclasses.replace(base, pme_grid=grid)
+    X = w.paths[0]
+    eng = mop.Engine(sys)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff_pme(X.astype(np.float64))
+    errs = pme_errors(eng, 0, X, v[0], G, r)
+    print("spme order", order, grid, errs)
+    assert_within_bars(errs)
+
+
+def test_spme_uneven_paths_in_one_launch():
+    # two paths of different lengths evaluated together (one FFT batch per path)
+    w = workload(2, n_beads=6)
+    sys = synth.with_pme(w.system)
+    paths = [w.paths[0], np.ascontiguousarray(w.paths[0][::-1][:4])]
+    eng = mop.Engine(sys)
+    for p, X in enumerate(paths):
+        eng.set_path(p, X)
+    v, G = eng.veff_and_grad(-1)
+    o = oracle.Oracle(sys)
+    off = 0
+    for p, X in enumerate(paths):
+        r = o.veff_pme(X.astype(np.float64))
+        errs = pme_errors(eng, p, X, v[p], G[off:off + X.shape[0]], r)
+        off += X.shape[0]
+        print("spme batch", p, errs)
+        assert_within_bars(errs)
+
+
+def test_spme_graph_step_matches_eager_steps():
+    # the captured step replays the FFTs and the fixed-point grids bit for bit
+    w = workload(2, n_beads=8)
+    sys = synth.with_pme(w.system)
+    engs = []
+    for graph in (False, True):
+        eng = mop.Engine(sys)
+        eng.set_path(0, w.paths[0])
+        eng.set_graph_mode(graph)
+        engs.append(eng)
+    engs[0].step(4, 1e-5, 2.0, seed=3)
+    engs[1].step(4, 1e-5, 2.0, seed=3)
+    assert np.array_equal(engs[0].get_path(0), engs[1].get_path(0))
+    va, ga = engs[0].veff_and_grad(0)
+    vb, gb = engs[1].veff_and_grad(0)
+    assert np.array_equal(va, vb) and np.array_equal(ga, gb)
+    assert np.isfinite(va).all()
