@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default neighbour-search geometry")
     ap.add_argument("--no-metad", action="store_true", help="skip the metadynamics production-loop timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the multi-path batching timing")
+    ap.add_argument("--no-pme", action="store_true", help="skip the Ewald / SPME electrostatics timing")
     return ap.parse_args()
 
 
@@ -384,6 +385,43 @@ def run_ours(args, world, rank, local):
                  "note": "host wall clock of the synchronous C-ABI call (V_eff only read back)"}
         eb.close()
 
+    # Ewald electrostatics on the same path: real-space erfc with exclusion corrections alone, then
+    # with the SPME reciprocal part (order-4 B-splines, grid spacing <= 0.12 nm, erfc(beta rc) =
+    # 1e-5); the difference is the cost of the reciprocal part (spread, FFTs, gather, both passes)
+    pme = None
+    if not args.no_pme and rank == 0 and prec == mop.MOP_PREC_MIXED:
+        import dataclasses
+        sys_pme = synth.with_pme(w.system)
+        pme = {"grid": list(sys_pme.pme_grid), "order": sys_pme.pme_order, "ew_beta_per_nm": sys_pme.ew_beta}
+        for label, sysx in (("real_space_only", dataclasses.replace(sys_pme, pme_grid=(0, 0, 0))),
+                            ("spme", sys_pme)):
+            ep = mop.Engine(sysx, precision=prec, device=local)
+            ep.set_tuning(tuned["col_factor"], tuned["bin_factor"])
+            ep.set_profiling(True)
+
+            def pstep():
+                ep.set_path(0, Xd, stream=stream.cuda_stream)
+                ep.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+
+            for _ in range(3):
+                pstep()
+            torch.cuda.synchronize()
+            k = max(3, args.steps // 2)
+            pp = []
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                pstep()
+                pp.append(ep.pass_ms())
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / k
+            pme[label] = {"ms_per_step": t, "value": N * Q / (t * 1e-3), "unit": UNIT,
+                          "pass_ms": {kk: float(np.mean([q[kk] for q in pp])) for kk in pp[0]}}
+            ep.close()
+        pme["reciprocal_ms_per_step"] = pme["spme"]["ms_per_step"] - pme["real_space_only"]["ms_per_step"]
+        pme["reaction_field_ms_per_step"] = ms
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         ns = cpu_sample_beads(w)
@@ -402,6 +440,7 @@ def run_ours(args, world, rank, local):
                        "hvp": "adjoint", "l2": "inputs larger than L2 (115 MB coordinates per step, >1 GB fields)",
                        "parallelism": f"{world} independent replica(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fd_hvp": fd, "metad": metad, "batch": batch,
+            "pme": pme,
             "pass_ms": mean_pass, "tuning": tuned, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
         }

@@ -151,11 +151,27 @@ __device__ __forceinline__ R pair_g2(const PairK<R>& c, R rinv, R rinv2, R rinv6
 // (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-)
 // (MODE 2) into a[3] and the pair energy into e (ENERGY).
 // Ewald real space (EW): the electrostatic factor of g, qq (erfc(beta r)/r + 2 beta/sqrt(pi)
-// exp(-beta^2 r^2)), from erfc(beta r) (CUDA's erfcf) and c2E = 2 beta/sqrt(pi) exp(-beta^2 r^2)
+// exp(-beta^2 r^2)).  One Gaussian G = exp(-beta^2 r^2) serves both terms: erfc(x) = G erfcx(x)
+// with the scaled complementary error function erfcx(x) ~ P(x) / Q(x), a rational least-squares
+// fit on [0, 6] written by fit_erfcx.py of this package (relative error 2.3e-8 for these FP32
+// coefficients in exact arithmetic, about 4e-7 as evaluated here), and c2E = 2 beta/sqrt(pi) G.
+__constant__ float kErfcxP[5] = {1.000000001e+00f, 1.182015100e+00f, 6.738669810e-01f, 2.021642005e-01f, 2.727379694e-02f};
+__constant__ float kErfcxQ[6] = {1.000000000e+00f, 2.310394391e+00f, 2.280865520e+00f, 1.217721130e+00f, 3.583920058e-01f, 4.833927675e-02f};
+
+__device__ __forceinline__ float erfcx_rational(float x) {
+  float p = kErfcxP[4], q = kErfcxQ[5];
+#pragma unroll
+  for (int i = 3; i >= 0; --i) p = fmaf(p, x, kErfcxP[i]);
+#pragma unroll
+  for (int i = 4; i >= 0; --i) q = fmaf(q, x, kErfcxQ[i]);
+  return p * __frcp_rn(q);
+}
+
 template <class R>
 __device__ __forceinline__ void ewald_terms(const Cst<R>& k, R r2, R rinv, R* ec, R* c2e) {
-  *ec = erfcf(k.ewb * (r2 * rinv));
-  *c2e = k.ewc2 * __expf(-k.ewb2 * r2);
+  const R G = __expf(-k.ewb2 * r2);
+  *ec = G * erfcx_rational(k.ewb * (r2 * rinv));
+  *c2e = k.ewc2 * G;
 }
 
 // g = -phi'_sf(r) / r with Ewald real space: r^-2 [r^-6 (A r^-6 - B) + qq (ec r^-1 + c2E)] + sh r^-1
@@ -480,7 +496,8 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
     __syncwarp();
     V4 fx[B], fe[B];
     int ft = 0;
-    auto fetch = [&](int blk) {
+    // forced inline: as a call, fx and fe would live in local memory
+    auto fetch = [&](int blk) __attribute__((always_inline)) {
       const int e = 4 * blk + sk;
       if (e < nc) {
         const int sj = (S.ent[e].x & kCluMask) * kCL + sa;

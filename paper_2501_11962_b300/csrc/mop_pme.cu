@@ -12,6 +12,7 @@
 // the atomics; forces go into the path's fixed-point j-side sums.  The FFTs are cuFFT calls.
 #include <cufft.h>
 
+#include <algorithm>
 #include <map>
 #include <utility>
 
@@ -256,6 +257,115 @@ __global__ void __launch_bounds__(kRedBlock) k_pme_gather(SysConsts sc, const Pa
   for (int d = 0; d < 3; ++d) atomicAdd(dst + d, (unsigned long long)__float2ll_rn(sgn * acc[d] * kFixScale));
 }
 
+// ---- order-4 spreading: one warp per (cluster, bead) ------------------------------------------
+// Lane l < 24 evaluates the splines of atom l / 3 of the cluster along dimension l % 3 once; the
+// stencil is then walked two atoms at a time with lane = 16 h + 4 t1 + t2 (atom 2 p + h), each lane
+// taking the four points t0 = 0..3 of its (t1, t2) column.  The four lanes of a (t0, t1) row add
+// to consecutive grid words, so their atomics share memory sectors (about half the time of one
+// thread per atom walking its 64 points).  Gathering stays one thread per atom: there the
+// overlapping stencils of a warp hit in L1 and cross-lane traffic only costs.
+struct Spl4 {
+  int b;                 // base grid index along this lane's dimension
+  float M[4], dM[4];     // values and d/dx (scaled by K/L)
+  float q, e;            // sqrt(f) q of the atom (0: padding), eta along this dimension
+};
+
+template <bool ETA>
+__device__ __forceinline__ void lane_spline4(const SysConsts& sc, const PathDev& Pd, int n, int c, int lane,
+                                             Spl4& S) {
+  S.b = 0;
+  S.q = S.e = 0.f;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) S.M[t] = S.dM[t] = 0.f;
+  if (lane >= 24) return;
+  const int a = lane / 3, d = lane - 3 * a;
+  const size_t k = (size_t)n * Pd.Qpad + c * kCL + a;
+  const float4 xl = Pd.xq[k];
+  const float x = d == 0 ? xl.x : (d == 1 ? xl.y : xl.z);
+  float w, d2[4];
+  grid_coord(sc, Pd.cwdf[3 * c + d], x, d, &S.b, &w);
+  spline<4>(w, S.M, S.dM, d2);
+  const float kl = sc.pme_kl[d].x;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) S.dM[t] *= kl;
+  S.q = xl.w;   // padding slots carry 0
+  if (ETA) {
+    const float4 e = Pd.eta32[k];
+    S.e = d == 0 ? e.x : (d == 1 ? e.y : e.z);
+  }
+}
+
+__device__ __forceinline__ float sel4(const float (&v)[4], int t) {
+  return t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
+}
+
+// atom A's splines as this lane uses them: the whole t0 row of dimension 0, the (t1, t2) entries
+struct Walk4 {
+  int b0, r12;       // base along 0; grid offset of this lane's (t1, t2) column
+  float q, e0, e1, e2;
+  float M0[4], dM0[4];
+  float m1, dm1, m2, dm2;
+};
+
+template <bool ETA>
+__device__ __forceinline__ void walk4(const SysConsts& sc, const Spl4& S, int A, int t1, int t2, Walk4& W) {
+  const unsigned full = 0xffffffffu;
+  const int s0 = 3 * A, s1 = s0 + 1, s2 = s0 + 2;
+  float M1[4], M2[4], dM1[4], dM2[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    W.M0[t] = __shfl_sync(full, S.M[t], s0);
+    W.dM0[t] = __shfl_sync(full, S.dM[t], s0);
+    M1[t] = __shfl_sync(full, S.M[t], s1);
+    dM1[t] = __shfl_sync(full, S.dM[t], s1);
+    M2[t] = __shfl_sync(full, S.M[t], s2);
+    dM2[t] = __shfl_sync(full, S.dM[t], s2);
+  }
+  W.m1 = sel4(M1, t1);
+  W.dm1 = sel4(dM1, t1);
+  W.m2 = sel4(M2, t2);
+  W.dm2 = sel4(dM2, t2);
+  W.q = __shfl_sync(full, S.q, s0);
+  if (ETA) {
+    W.e0 = __shfl_sync(full, S.e, s0);
+    W.e1 = __shfl_sync(full, S.e, s1);
+    W.e2 = __shfl_sync(full, S.e, s2);
+  }
+  W.b0 = __shfl_sync(full, S.b, s0);
+  const int b1 = __shfl_sync(full, S.b, s1), b2 = __shfl_sync(full, S.b, s2);
+  W.r12 = wrap(b1 - t1, sc.pme_K[1]) * sc.pme_K[2] + wrap(b2 - t2, sc.pme_K[2]);
+}
+
+template <int DERIV>
+__global__ void __launch_bounds__(128) k_pme_spread4(SysConsts sc, const PathDev* __restrict__ paths) {
+  const PathDev& Pd = paths[blockIdx.z];
+  const int n = blockIdx.y, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int n_pass = DERIV ? Pd.n_hvp : Pd.n_force;
+  if (n >= n_pass || c >= __ldg(&Pd.meta[0])) return;   // whole warps
+  Spl4 S;
+  lane_spline4<DERIV == 1>(sc, Pd, n, c, lane, S);
+  const int h = lane >> 4, t1 = (lane >> 2) & 3, t2 = lane & 3;
+  const size_t plane = (size_t)sc.pme_K[1] * sc.pme_K[2];
+  unsigned long long* g = Pd.pme_q + (size_t)n * sc.pme_nk;
+#pragma unroll 1
+  for (int p = 0; p < 4; ++p) {
+    Walk4 W;
+    walk4<DERIV == 1>(sc, S, 2 * p + h, t1, t2, W);
+    if (W.q == 0.f) continue;
+#pragma unroll
+    for (int t0 = 0; t0 < 4; ++t0) {
+      float v;
+      if (DERIV)
+        v = W.q * (W.dM0[t0] * W.m1 * W.m2 * W.e0 + W.M0[t0] * (W.dm1 * W.m2 * W.e1 + W.m1 * W.dm2 * W.e2));
+      else
+        v = W.q * W.M0[t0] * W.m1 * W.m2;
+      atomicAdd(g + wrap(W.b0 - t0, sc.pme_K[0]) * plane + W.r12,
+                (unsigned long long)__float2ll_rn(v * kGridFixF));
+    }
+  }
+}
+
 template <int P>
 cudaError_t run_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths, int max_beads,
                     int mode, PmePlans& plans, Launch L, std::string* err) {
@@ -269,8 +379,16 @@ cudaError_t run_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* 
     cudaError_t e = cudaMemsetAsync(D.pme_q, 0, sizeof(unsigned long long) * sc.pme_nk * beads, L.st);
     if (e != cudaSuccess) return e;
   }
-  if (mode == 0) k_pme_spread<P, 0><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
-  else k_pme_spread<P, 1><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  int max_clu = 0;
+  for (int p = 0; p < n_paths; ++p) max_clu = std::max(max_clu, h_paths[p].n_clu);
+  const dim3 wgrid((max_clu + 3) / 4, max_beads, n_paths);
+  if (P == 4) {
+    if (mode == 0) k_pme_spread4<0><<<wgrid, 128, 0, L.st>>>(sc, d_paths);
+    else k_pme_spread4<1><<<wgrid, 128, 0, L.st>>>(sc, d_paths);
+  } else {
+    if (mode == 0) k_pme_spread<P, 0><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+    else k_pme_spread<P, 1><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  }
   ++*L.counter;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
