@@ -290,6 +290,125 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
   }
 }
 
+// ---- two beads per instruction (FP32 mode) ------------------------------------------------
+// A lane evaluates the same (i, j) pair for the two beads of its unit with the same pair
+// constants, so the FP32 arithmetic of both runs in packed f32x2 instructions (fma/add/mul.f32x2,
+// sm_100 family): half the issue slots for the same FMA-pipe work.  Only rsqrt, exp2, the
+// reciprocal and the cutoff selects stay per bead.  x = bead n0, y = bead n0 + 1.
+#ifndef MOP_PACK2
+#define MOP_PACK2 1
+#endif
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// pair constants of one (entry, half) duplicated into both lanes of the f32x2 operands
+struct PairK2 {
+  float2 A, nB, qq, sh, nqk;   // 12 c12, -6 c6, f qi qj, phi'(rc), -qq 2 k_rf
+  float2 A14, nB8, q3;         // HVP: 14 * 12 c12, -8 * 6 c6, 3 qq
+};
+
+template <int MODE>
+__device__ __forceinline__ PairK2 pair_consts2(const PairK<float>& c) {
+  PairK2 d;
+  d.A = dup2(c.A);
+  d.nB = dup2(-c.B);
+  d.qq = dup2(c.qq);
+  d.sh = dup2(c.sh);
+  d.nqk = dup2(-c.qk);
+  if (MODE == 1) {
+    d.A14 = dup2(c.A14);
+    d.nB8 = dup2(-c.B8);
+    d.q3 = dup2(c.q3);
+  }
+  return d;
+}
+
+// Ewald: erfc(beta r) = G erfcx(beta r) and the force term 2 beta/sqrt(pi) G for both beads
+__device__ __forceinline__ void ewald_terms2(const Cst<float>& k, float2 r2, float2 rinv, float2* ec, float2* c2e) {
+  const float2 y = mul2(r2, dup2(-k.ewb2 * 1.4426950408889634f));   // -beta^2 r^2 log2(e)
+  const float2 G = make_float2(ex2_approx(y.x), ex2_approx(y.y));
+  const float2 x = mul2(dup2(k.ewb), mul2(r2, rinv));
+  float2 p = dup2(kErfcxP[4]), q = dup2(kErfcxQ[5]);
+#pragma unroll
+  for (int i = 3; i >= 0; --i) p = fma2(p, x, dup2(kErfcxP[i]));
+#pragma unroll
+  for (int i = 4; i >= 0; --i) q = fma2(q, x, dup2(kErfcxQ[i]));
+  *ec = mul2(G, mul2(p, make_float2(__frcp_rn(q.x), __frcp_rn(q.y))));
+  *c2e = mul2(dup2(k.ewc2), G);
+}
+
+// One pair for both beads of the unit (HALF list): MODE 0 force, MODE 1 adjoint H eta.  xs and
+// xj: the i- and j-atom per dimension (bead x, bead y), one of them shifted by the entry's Delta;
+// ei/ej eta (MODE 1).  Adds the i-side term to a and returns it in f.  ENERGY: also adds ew times
+// the pair energy of bead x (the first bead of the unit) to e.
+template <int MODE, bool EW, bool ENERGY = false>
+__device__ __forceinline__ void pair_two(const Cst<float>& k, const PairK2& c, const float2 (&xs)[3], const float2 (&xj)[3],
+                                         float rc2e, const float2 (&ei)[3], const float2 (&ej)[3], float2 (&a)[3],
+                                         float2 (&f)[3], const PairK<float>* ce = nullptr, float ew = 0.f,
+                                         float* e = nullptr) {
+  const float2 d[3] = {sub2(xs[0], xj[0]), sub2(xs[1], xj[1]), sub2(xs[2], xj[2])};
+  const float2 r2 = fma2(d[0], d[0], fma2(d[1], d[1], mul2(d[2], d[2])));
+  const bool in0 = r2.x < rc2e, in1 = r2.y < rc2e;
+  const float2 rinv = rsq2(r2);
+  const float2 rinv2 = mul2(rinv, rinv);
+  const float2 rinv6 = mul2(mul2(rinv2, rinv2), rinv2);
+  const float2 lj = mul2(rinv6, fma2(c.A, rinv6, c.nB));   // r^-6 (A r^-6 - B)
+  float2 g, ec, c2e;
+  if (EW) {
+    ewald_terms2(k, r2, rinv, &ec, &c2e);
+    g = fma2(rinv2, fma2(c.qq, fma2(ec, rinv, c2e), lj), mul2(c.sh, rinv));
+  } else {
+    g = fma2(rinv2, fma2(c.qq, rinv, lj), fma2(c.sh, rinv, c.nqk));
+  }
+  if (MODE == 0) {
+    g = make_float2(in0 ? g.x : 0.f, in1 ? g.y : 0.f);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      f[q] = mul2(g, d[q]);
+      a[q] = add2(a[q], f[q]);
+    }
+    if (ENERGY) {
+      // phi(r) - phi(rc) - (r - rc) phi'(rc) of bead x
+      const float r = r2.x * rinv.x;
+      const float elj = rinv6.x * fmaf(ce->A * (1.f / 12.f), rinv6.x, -ce->B * (1.f / 6.f));
+      const float el = EW ? ce->qq * fmaf(ec.x, rinv.x, -k.ewec) : ce->qq * (rinv.x + fmaf(k.krf, r2.x, -k.crf));
+      const float E = elj + el - ce->Ew - (r - k.rc) * ce->sh;
+      *e = in0 ? fmaf(ew, E, *e) : *e;
+    }
+  } else {
+    const float2 u[3] = {sub2(ei[0], ej[0]), sub2(ei[1], ej[1]), sub2(ei[2], ej[2])};
+    const float2 rinv3 = mul2(rinv, rinv2);
+    const float2 ljb = mul2(mul2(rinv2, rinv2), mul2(rinv6, fma2(c.A14, rinv6, c.nB8)));
+    float2 b;
+    if (EW) {
+      // r^-3 [qq (3 ec r^-2 + c2E (3 r^-1 + 2 beta^2 r)) + sh]
+      const float2 el = fma2(mul2(dup2(3.f), ec), rinv2,
+                             mul2(c2e, fma2(dup2(2.f * k.ewb2), mul2(r2, rinv), mul2(dup2(3.f), rinv))));
+      b = fma2(rinv3, fma2(c.qq, el, c.sh), ljb);
+    } else {
+      b = fma2(rinv3, fma2(c.q3, rinv2, c.sh), ljb);
+    }
+    const float2 sdot = fma2(d[0], u[0], fma2(d[1], u[1], mul2(d[2], u[2])));
+    float2 t = mul2(b, sdot);
+    t = make_float2(in0 ? t.x : 0.f, in1 ? t.y : 0.f);
+    const float2 ng = make_float2(in0 ? -g.x : 0.f, in1 ? -g.y : 0.f);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      f[q] = fma2(ng, u[q], mul2(t, d[q]));
+      a[q] = add2(a[q], f[q]);
+    }
+  }
+}
+
 // j-partial staging of one entry: value (h, c, b) of i-lane ii and j-atom jq at
 // ii * kJpRow + jq * 6 + h * 24 + 2c + b.  Both the 64-bit stores (16 lanes per phase: 8 ii x
 // 2 jq) and the 64-bit loads of the 24 summing lanes then hit every bank once per phase.
@@ -457,7 +576,25 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   }
   const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * tstr;
   const R qi = xi[0].w;
+  // both beads in f32x2 instructions (forces, with the bead-1 energy in the first units, and the
+  // adjoint HVP; the FD mode keeps the scalar path)
+  constexpr bool PACK = MOP_PACK2 && sizeof(R) == 4 && B == 2 && MODE != 2;
+  float2 a2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  float2 ei2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ei2[c] = make_float2((float)ei[0][c], (float)ei[B - 1][c]);
   R a[B][3];
+  // packed partial sums -> a[b][c] (zero between folds) before each fold
+  auto unpack = [&]() __attribute__((always_inline)) {
+    if constexpr (PACK) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a[0][c] = a2[c].x;
+        a[B - 1][c] = a2[c].y;
+        a2[c] = make_float2(0.f, 0.f);
+      }
+    }
+  };
   Acc3<R> accd;   // FP64 mode accumulates directly (B == 1)
 #pragma unroll
   for (int b = 0; b < B; ++b) a[b][0] = a[b][1] = a[b][2] = R(0);
@@ -555,6 +692,22 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           const int sj = so + 4 * h;
           const PairK<R> pc = pair_consts<R, MODE, V4>(k, tabrow[S.t[sj]], qi * S.x[0][sj].w);
           const R rce = h ? rcB : rcA;
+          if constexpr (PACK) {
+            const float2 xs2[3] = {make_float2(xs[0][0], xs[B - 1][0]), make_float2(xs[0][1], xs[B - 1][1]),
+                                   make_float2(xs[0][2], xs[B - 1][2])};
+            const V4 ej0 = MODE == 1 ? S.e[0][sj] : V4{}, ej1 = MODE == 1 ? S.e[B - 1][sj] : V4{};
+            const V4 xj0 = S.x[0][sj], xj1 = S.x[B - 1][sj];
+            const float2 xj2[3] = {make_float2(xj0.x, xj1.x), make_float2(xj0.y, xj1.y), make_float2(xj0.z, xj1.z)};
+            const float2 ej2[3] = {make_float2(ej0.x, ej1.x), make_float2(ej0.y, ej1.y), make_float2(ej0.z, ej1.z)};
+            float2 f2[3];
+            pair_two<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), xs2, xj2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              jf[h][c][0] = f2[c].x;
+              jf[h][c][B - 1] = f2[c].y;
+            }
+            continue;
+          }
 #pragma unroll
           for (int b = 0; b < B; ++b) {
             R ej[3] = {R(0), R(0), R(0)};
@@ -584,11 +737,13 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         }
       }
       if ((blk & 3) == 3) {
+        unpack();
         fold_into<R, B>(S, a, lane);
         if (ENERGY) eacc.fold();
       }
     }
   }
+  unpack();
   fold_into<R, B>(S, a, lane);
   if (ENERGY) eacc.fold();
   const bool valid = __ldg(&P.perm[si]) >= 0;
