@@ -114,3 +114,6 @@ def test_create_validates_the_ewald_parameters(fcc):
     assert _create(_pme(d, grid=(24, 3, 24))) == mop.MOP_ERR_ARG
     assert _create(_pme(d, beta=-1.0)) == mop.MOP_ERR_ARG
     assert _create(_pme(d, beta=float("nan"))) == mop.MOP_ERR_ARG
+    # Ewald runs in mixed precision only
+    d.precision = mop.MOP_PREC_FP64
+    assert _create(_pme(d)) == mop.MOP_ERR_ARG

@@ -128,3 +128,22 @@ def test_spme_graph_step_matches_eager_steps():
     vb, gb = engs[1].veff_and_grad(0)
     assert np.array_equal(va, vb) and np.array_equal(ga, gb)
     assert np.isfinite(va).all()
+
+
+@pytest.mark.parametrize("n_beads", [1, 2])
+def test_spme_short_paths_match_oracle(n_beads):
+    # N = 1: V_eff = U(R1) with the reciprocal energy, G = -F (no eta, no HVP pass);
+    # N = 2: one force bead, one HVP bead
+    w = workload(2, n_beads=3)
+    sys = synth.with_pme(w.system)
+    X = np.ascontiguousarray(w.paths[0][:n_beads])
+    eng = mop.Engine(sys)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff_pme(X.astype(np.float64))
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V
+    assert rel(G, r["G"]) < TOL_F
+    F = eng.get_field(0, mop.MOP_FIELD_FORCE)[:max(1, n_beads - 1)]
+    assert rel(F, r["F"][:max(1, n_beads - 1)]) < TOL_F
+    if n_beads == 1:
+        assert rel(G[0], -r["F"][0]) < TOL_F
