@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-metad", action="store_true", help="skip the metadynamics production-loop timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the multi-path batching timing")
     ap.add_argument("--no-pme", action="store_true", help="skip the Ewald / SPME electrostatics timing")
+    ap.add_argument("--no-skin", action="store_true", help="skip the Verlet-skin (kept pair list) timing")
     return ap.parse_args()
 
 
@@ -422,6 +423,39 @@ def run_ours(args, world, rank, local):
         pme["reciprocal_ms_per_step"] = pme["spme"]["ms_per_step"] - pme["real_space_only"]["ms_per_step"]
         pme["reaction_field_ms_per_step"] = ms
 
+    # Verlet skin: evaluations of the same path that keep the list built for rc + skin (the sort
+    # and the list build are skipped; the pair kernels walk the longer list)
+    skin = None
+    if not args.no_skin and rank == 0 and prec == mop.MOP_PREC_MIXED:
+        skin = {"rebuilt_every_evaluation_ms": ms}
+        for sk in (0.02, 0.05):
+            es = mop.Engine(w.system, precision=prec, device=local)
+            es.set_tuning(tuned["col_factor"], tuned["bin_factor"])
+            es.set_list_skin(sk)
+            es.set_profiling(True)
+            es.set_path(0, Xd, stream=stream.cuda_stream)
+            es.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)   # builds the list
+            torch.cuda.synchronize()
+            for _ in range(2):
+                es.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            k = max(3, args.steps // 2)
+            pp = []
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                es.veff_and_grad_device(veff, grad, 0, stream=stream.cuda_stream)
+                pp.append(es.pass_ms())
+            b.record(stream)
+            torch.cuda.synchronize()
+            _, listed_sk = es.count_pairs(0)
+            builds, reuses = es.list_stats(0)
+            skin[f"{sk:g}_nm"] = {"kept_list_ms": a.elapsed_time(b) / k, "listed_pairs_per_launch": listed_sk,
+                                  "builds": builds, "reuses": reuses,
+                                  "pass_ms": {kk: float(np.mean([q[kk] for q in pp])) for kk in pp[0]}}
+            es.close()
+        skin["listed_pairs_per_launch_without_skin"] = listed
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         ns = cpu_sample_beads(w)
@@ -440,7 +474,7 @@ def run_ours(args, world, rank, local):
                        "hvp": "adjoint", "l2": "inputs larger than L2 (115 MB coordinates per step, >1 GB fields)",
                        "parallelism": f"{world} independent replica(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fd_hvp": fd, "metad": metad, "batch": batch,
-            "pme": pme,
+            "pme": pme, "skin": skin,
             "pass_ms": mean_pass, "tuning": tuned, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
         }

@@ -237,6 +237,21 @@ mop_status mop_get_tuning(const mop_handle* h, mop_tuning* t);
  * Synchronous.  Errors: MOP_ERR_STATE (path not set), MOP_ERR_CUDA. */
 mop_status mop_autotune(mop_handle* h, int32_t path_id, mop_tuning* best, double* best_ms);
 
+/* Verlet skin of the cluster-pair lists (NEXT row "shared list with a skin across steps").
+ * skin_nm > 0: each path's list is built for the cutoff rc + skin_nm (every atom's union sphere
+ * over the beads grows by skin_nm / 2) together with a device copy of the coordinates, and later
+ * evaluations keep the sort, the clusters and the list as long as no atom of any bead has moved
+ * more than skin_nm / 2 from that copy (a device reduction and one 4-byte read per evaluation);
+ * only the cluster-local coordinates are then recomputed.  Results differ from a rebuilt list
+ * only by rounding (the pair kernels still test r < rc).  0 (default): rebuild at every
+ * evaluation.  Applies to mixed-precision evaluations outside CUDA-graph capture (a captured step
+ * always rebuilds).  Errors: MOP_ERR_ARG (negative or non-finite skin, or skin >= L/2 - rc). */
+mop_status mop_set_list_skin(mop_handle* h, double skin_nm);
+
+/* Lists built and lists reused by the evaluations of `path_id` since it was set (instrumentation
+ * of mop_set_list_skin; either output may be NULL). */
+mop_status mop_get_list_stats(const mop_handle* h, int32_t path_id, int64_t* builds, int64_t* reuses);
+
 /* Kinetic energy sum_i m_i |v_i|^2 / 2 over all beads of `path_id` (synchronous). */
 mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke);
 

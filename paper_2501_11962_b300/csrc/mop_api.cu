@@ -43,6 +43,7 @@ struct mop_handle {
   DevBuf<int2> excl;                      // Ewald exclusion pairs
   DevBuf<float> pme_theta;                // SPME kernel [K1][K2][K3 / 2 + 1]
   PmePlans* pme = nullptr;                // cuFFT plans per bead count
+  double skin = 0.0;                      // Verlet skin of the pair lists (0: rebuild every time)
   DevBuf<unsigned long long> counts;
   mop_tuning tuning{1.0, 0.5};
   double box[3] = {0.0, 0.0, 0.0};
@@ -165,7 +166,36 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   for (size_t k = 0; k < ids.size(); ++k) {
     PathHost& P = h->paths[ids[k]];
     std::string err;
-    cudaError_t e = prep_path(sc, h->grid, P, margin, L, &err, sync);
+    // Verlet skin: keep the sort and the list while no atom has moved more than skin / 2
+    const bool skin = h->skin > 0.0 && sync && h->precision == MOP_PREC_MIXED;
+    bool reuse = false;
+    if (skin && P.list_ok && P.list_N == P.N) {
+      CK(h, launch_max_disp(P.x32.p, P.xref.p, (long long)P.N * sc.Q, P.dmax.p, L));
+      unsigned d2bits = 0;
+      CK(h, cudaMemcpyAsync(&d2bits, P.dmax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(h, cudaStreamSynchronize(st));
+      float d2;
+      memcpy(&d2, &d2bits, sizeof(d2));
+      reuse = (double)d2 < 0.25 * h->skin * h->skin;
+    }
+    cudaError_t e;
+    if (reuse) {
+      e = prep_coords(sc, h->grid, P, margin + 0.5 * h->skin, L);
+      ++P.reuses;
+    } else {
+      e = prep_path(sc, h->grid, P, skin ? margin + 0.5 * h->skin : margin, L, &err, sync);
+      if (e == cudaSuccess) {
+        ++P.builds;
+        P.list_ok = false;
+        if (skin) {
+          CK(h, P.xref.ensure(3 * (size_t)P.N * sc.Q));
+          CK(h, P.dmax.ensure(1));
+          CK(h, cudaMemcpyAsync(P.xref.p, P.x32.p, sizeof(float) * 3 * (size_t)P.N * sc.Q, cudaMemcpyDeviceToDevice, st));
+          P.list_ok = true;
+          P.list_N = P.N;
+        }
+      }
+    }
     if (e != cudaSuccess) return fail(h, e == cudaErrorMemoryAllocation ? MOP_ERR_OOM : MOP_ERR_CUDA, "%s", err.c_str());
     const int N = P.N, Qpad = h->grid.max_clu * kCL;   // fixed slot stride (capture safe)
     const int n_force = N == 1 ? 1 : N - 1, n_hvp = N - 1;
@@ -1058,7 +1088,27 @@ mop_status mop_set_tuning(mop_handle* h, const mop_tuning* t) {
   for (auto& P : h->paths) {
     P.sized = false;     // strides and list shapes change: rebuild synchronously
     P.have_grad = false;
+    P.list_ok = false;
   }
+  return MOP_OK;
+}
+
+mop_status mop_set_list_skin(mop_handle* h, double skin_nm) {
+  if (!h) return MOP_ERR_ARG;
+  if (!std::isfinite(skin_nm) || skin_nm < 0.0) return fail(h, MOP_ERR_ARG, "skin must be finite and >= 0");
+  const double half_box = 0.5 * std::min(h->box[0], std::min(h->box[1], h->box[2]));
+  if (skin_nm > 0.0 && h->sc.rc + skin_nm >= half_box) return fail(h, MOP_ERR_ARG, "rc + skin must stay below L/2");
+  h->skin = skin_nm;
+  for (auto& P : h->paths) P.list_ok = false;
+  return MOP_OK;
+}
+
+mop_status mop_get_list_stats(const mop_handle* h, int32_t path_id, int64_t* builds, int64_t* reuses) {
+  if (!h || path_id < 0 || path_id >= kMaxPaths) return MOP_ERR_ARG;
+  const PathHost& P = h->paths[path_id];
+  if (!P.set) return MOP_ERR_STATE;
+  if (builds) *builds = P.builds;
+  if (reuses) *reuses = P.reuses;
   return MOP_OK;
 }
 

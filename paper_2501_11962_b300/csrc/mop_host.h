@@ -82,6 +82,12 @@ struct PathHost {
   DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
   DevBuf<double> e_excl;   // Ewald: bead-1 energy partials of the exclusion corrections
+  // Verlet skin: coordinates at the last list build and the largest squared displacement since
+  DevBuf<float> xref;
+  DevBuf<unsigned> dmax;
+  bool list_ok = false;     // the list was built with the skin for the current bead count
+  int list_N = 0;
+  long long builds = 0, reuses = 0;
   // SPME reciprocal space: fixed-point charge grids, FFT input, spectra, potential grids of the
   // force and HVP passes [beads][grid points], bead-1 energy partials
   DevBuf<unsigned long long> pme_q;
@@ -109,6 +115,11 @@ struct Launch {
 // synchronous build and records an overflow in meta[3].
 cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L,
                       std::string* err, bool sync);
+
+// Verlet skin (mixed precision): *dmax2 = max over atoms and beads of |x - xref|^2 (float bits;
+// +inf for non-finite input), and the cluster-local coordinates of a kept sort and list.
+cudaError_t launch_max_disp(const float* x, const float* xref, long long n_atoms_beads, unsigned* dmax2, Launch L);
+cudaError_t prep_coords(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L);
 
 // --- mop_pair.cu: pair kernels over every unit of every path -------------------------------
 // mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP.  A unit is one i-cluster for

@@ -8,6 +8,7 @@
 // listed (with its periodic image) when the union boxes are closer than rc, so the list is
 // exact for every bead without a Verlet buffer.  Coordinates are stored relative to the
 // cluster centre so that FP32 pair differences stay accurate in large boxes.
+#include <algorithm>
 #include <cstdio>
 
 #include "mop_host.h"
@@ -628,6 +629,43 @@ inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
     ++*L.counter;                                         \
     MOP_CK(cudaGetLastError());                           \
   } while (0)
+
+namespace {
+__global__ void k_max_disp(const float* __restrict__ x, const float* __restrict__ xref, long long n, unsigned* dmax2) {
+  __shared__ float sh[8];
+  float m = 0.f;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const float dx = x[3 * t] - xref[3 * t], dy = x[3 * t + 1] - xref[3 * t + 1], dz = x[3 * t + 2] - xref[3 * t + 2];
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    m = (d2 <= 3.0e38f) ? fmaxf(m, d2) : INFINITY;   // NaN or overflow: force a rebuild
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+    atomicMax(dmax2, __float_as_uint(m));   // non-negative floats order like their bits
+  }
+}
+}  // namespace
+
+cudaError_t launch_max_disp(const float* x, const float* xref, long long n, unsigned* dmax2, Launch L) {
+  cudaError_t e = cudaMemsetAsync(dmax2, 0, sizeof(unsigned), L.st);
+  if (e != cudaSuccess) return e;
+  const long long blocks = std::min<long long>((n + 255) / 256, 148LL * 8);
+  k_max_disp<<<(int)std::max<long long>(blocks, 1), 256, 0, L.st>>>(x, xref, n, dmax2);
+  ++*L.counter;
+  return cudaGetLastError();
+}
+
+cudaError_t prep_coords(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L) {
+  const int max_slots = g.max_clu * kCL;
+  k_local_box32<<<nblk(max_slots, 256), 256, 0, L.st>>>(sc, P.x32.p, P.N, P.reff.p, P.perm.p, P.meta.p, max_slots,
+                                                        P.center.p, margin, P.xq.p, P.ts.p, P.eta32.p, P.abox.p);
+  ++*L.counter;
+  return cudaGetLastError();
+}
 
 cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L, std::string* err,
                       bool sync) {

@@ -27,7 +27,7 @@ EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_vef
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
            "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_measure_fp32_peak",
            "mop_metadynamics", "mop_get_gaussians", "mop_add_cv", "mop_add_gaussian",
-           "mop_last_error")
+           "mop_set_list_skin", "mop_get_list_stats", "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -99,6 +99,8 @@ def load(build_if_needed: bool = True):
     L.mop_set_tuning.argtypes = [p, p]
     L.mop_get_tuning.argtypes = [p, p]
     L.mop_autotune.argtypes = [p, i32, p, p]
+    L.mop_set_list_skin.argtypes = [p, d]
+    L.mop_get_list_stats.argtypes = [p, i32, p, p]
     L.mop_last_error.argtypes = [p]
     L.mop_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -257,6 +259,16 @@ class Engine:
         t, ms = mop_tuning(), C.c_double()
         self._check(self.L.mop_autotune(self.h, path_id, C.byref(t), C.byref(ms)), "mop_autotune")
         return dict(col_factor=t.col_factor, bin_factor=t.bin_factor), ms.value
+
+    def set_list_skin(self, skin_nm: float):
+        """Verlet skin of the pair lists (0: rebuild at every evaluation)."""
+        self._check(self.L.mop_set_list_skin(self.h, float(skin_nm)), "mop_set_list_skin")
+
+    def list_stats(self, path_id: int) -> tuple:
+        """(lists built, lists reused) by the evaluations of path_id."""
+        b, r = C.c_int64(), C.c_int64()
+        self._check(self.L.mop_get_list_stats(self.h, path_id, C.byref(b), C.byref(r)), "mop_get_list_stats")
+        return b.value, r.value
 
     def set_graph_mode(self, on: bool = True):
         self._check(self.L.mop_set_graph_mode(self.h, int(on)), "mop_set_graph_mode")
