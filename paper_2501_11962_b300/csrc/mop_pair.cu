@@ -153,18 +153,25 @@ __device__ __forceinline__ R pair_g2(const PairK<R>& c, R rinv, R rinv2, R rinv6
 // Ewald real space (EW): the electrostatic factor of g, qq (erfc(beta r)/r + 2 beta/sqrt(pi)
 // exp(-beta^2 r^2)).  One Gaussian G = exp(-beta^2 r^2) serves both terms: erfc(x) = G erfcx(x)
 // with the scaled complementary error function erfcx(x) ~ P(x) / Q(x), a rational least-squares
-// fit on [0, 6] written by fit_erfcx.py of this package (relative error 2.3e-8 for these FP32
-// coefficients in exact arithmetic, about 4e-7 as evaluated here), and c2E = 2 beta/sqrt(pi) G.
-__constant__ float kErfcxP[5] = {1.000000001e+00f, 1.182015100e+00f, 6.738669810e-01f, 2.021642005e-01f, 2.727379694e-02f};
-__constant__ float kErfcxQ[6] = {1.000000000e+00f, 2.310394391e+00f, 2.280865520e+00f, 1.217721130e+00f, 3.583920058e-01f, 4.833927675e-02f};
+// fit of degrees 3 / 4 on [0, 6] written by fit_erfcx.py of this package (relative error 2.5e-7
+// for these FP32 coefficients in exact arithmetic, about 5e-7 as evaluated here), and
+// c2E = 2 beta/sqrt(pi) G.  Q(x) >= 1, so the approximate reciprocal (rel. error ~1 ulp) serves.
+__constant__ float kErfcxP[4] = {9.999999234e-01f, 9.697673345e-01f, 4.351839909e-01f, 8.235789757e-02f};
+__constant__ float kErfcxQ[5] = {1.000000000e+00f, 2.098139719e+00f, 1.802774676e+00f, 7.701872587e-01f, 1.460288291e-01f};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __device__ __forceinline__ float erfcx_rational(float x) {
-  float p = kErfcxP[4], q = kErfcxQ[5];
+  float p = kErfcxP[3], q = kErfcxQ[4];
 #pragma unroll
-  for (int i = 3; i >= 0; --i) p = fmaf(p, x, kErfcxP[i]);
+  for (int i = 2; i >= 0; --i) p = fmaf(p, x, kErfcxP[i]);
 #pragma unroll
-  for (int i = 4; i >= 0; --i) q = fmaf(q, x, kErfcxQ[i]);
-  return p * __frcp_rn(q);
+  for (int i = 3; i >= 0; --i) q = fmaf(q, x, kErfcxQ[i]);
+  return p * rcp_approx(q);
 }
 
 template <class R>
@@ -337,12 +344,12 @@ __device__ __forceinline__ void ewald_terms2(const Cst<float>& k, float2 r2, flo
   const float2 y = mul2(r2, dup2(-k.ewb2 * 1.4426950408889634f));   // -beta^2 r^2 log2(e)
   const float2 G = make_float2(ex2_approx(y.x), ex2_approx(y.y));
   const float2 x = mul2(dup2(k.ewb), mul2(r2, rinv));
-  float2 p = dup2(kErfcxP[4]), q = dup2(kErfcxQ[5]);
+  float2 p = dup2(kErfcxP[3]), q = dup2(kErfcxQ[4]);
 #pragma unroll
-  for (int i = 3; i >= 0; --i) p = fma2(p, x, dup2(kErfcxP[i]));
+  for (int i = 2; i >= 0; --i) p = fma2(p, x, dup2(kErfcxP[i]));
 #pragma unroll
-  for (int i = 4; i >= 0; --i) q = fma2(q, x, dup2(kErfcxQ[i]));
-  *ec = mul2(G, mul2(p, make_float2(__frcp_rn(q.x), __frcp_rn(q.y))));
+  for (int i = 3; i >= 0; --i) q = fma2(q, x, dup2(kErfcxQ[i]));
+  *ec = mul2(G, mul2(p, make_float2(rcp_approx(q.x), rcp_approx(q.y))));
   *c2e = mul2(dup2(k.ewc2), G);
 }
 

@@ -1,6 +1,6 @@
 """Generates the rational approximation of the scaled complementary error function used by the
 Ewald real-space pair kernels: erfcx(x) = exp(x^2) erfc(x) ~ P(x) / Q(x) on [0, XMAX], P of degree
-4 and Q of degree 5 (Q(0) = 1), all coefficients positive, so that an FP32 Horner evaluation has no
+3 and Q of degree 4 (Q(0) = 1), all coefficients positive, so that an FP32 Horner evaluation has no
 cancellation.  The kernels then form erfc(beta r) = exp(-beta^2 r^2) P/Q and reuse the Gaussian for
 the force term 2 beta / sqrt(pi) exp(-beta^2 r^2).
 
@@ -13,7 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 XMAX = 6.0          # beta rc up to 6: erfc(6) = 2e-17, beyond any useful real-space tolerance
-DEG_P, DEG_Q = 4, 5
+DEG_P, DEG_Q = 3, 4
 
 
 def fit(xmax: float = XMAX, m: int = DEG_P, n: int = DEG_Q, nodes: int = 6000, iters: int = 40):

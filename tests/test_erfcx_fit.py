@@ -1,5 +1,5 @@
 """The rational erfcx table of the Ewald pair kernels (csrc/mop_pair.cu) against math.erfc: the
-coefficients as compiled (FP32) reproduce erfc(x) exp(x^2) to 5e-8 in FP64 arithmetic and to 6e-7
+coefficients as compiled (FP32) reproduce erfc(x) exp(x^2) to 3e-7 in FP64 arithmetic and to 6e-7
 in an FP32 Horner evaluation with fused multiply-adds, over the range of beta r the kernels use."""
 import math
 import re
@@ -21,13 +21,13 @@ def erfc_ref(x):
 
 def test_erfcx_table_matches_erfc():
     P, Q = table("kErfcxP"), table("kErfcxQ")
-    assert len(P) == 5 and len(Q) == 6 and (P > 0).all() and (Q > 0).all()
+    assert len(P) == 4 and len(Q) == 5 and (P > 0).all() and (Q > 0).all()
     x = np.linspace(0.0, 6.0, 60001)
     ref = erfc_ref(x)
     p64 = np.polyval(P[::-1].astype(np.float64), x)
     q64 = np.polyval(Q[::-1].astype(np.float64), x)
     rel64 = np.abs(np.exp(-x * x) * p64 / q64 - ref) / ref
-    assert rel64.max() < 5e-8, rel64.max()
+    assert rel64.max() < 3e-7, rel64.max()
     # FP32 with fused multiply-adds: products of two floats are exact in FP64, one rounding per step
     x32 = x.astype(np.float32)
 
