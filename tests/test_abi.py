@@ -117,3 +117,9 @@ def test_create_validates_the_ewald_parameters(fcc):
     # Ewald runs in mixed precision only
     d.precision = mop.MOP_PREC_FP64
     assert _create(_pme(d)) == mop.MOP_ERR_ARG
+
+
+def test_create_rejects_an_empty_system(fcc):
+    d, keep = _desc(fcc)
+    d.n_atoms = 0
+    assert _create(d) == mop.MOP_ERR_ARG
