@@ -444,8 +444,11 @@ __global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype)
 // (two atom pairs per lane), and so does the exclusion mask (bit j * 8 + i).  Entries of cluster ci
 // go to ent[ci * cap ...] in bin order (deterministic); lcnt[ci] = their number; meta[2] =
 // largest count (a count above cap means the list must be rebuilt with a larger cap).
+#ifndef MOP_LIST_MINB
+#define MOP_LIST_MINB 6   // 80 registers: 6 blocks (24 warps) per SM hide the latency of the bin walk
+#endif
 template <bool F64>
-__global__ void __launch_bounds__(128) k_pair_list(SysConsts sc, const int* meta_in, int max_clu,
+__global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, const int* meta_in, int max_clu,
                                                    const double* cwrap, const float2* cwdf, const float* hext,
                                                    const unsigned* emax,
                                                    const int* cbin, int nb0, int nb1, int nb2, double bw0, double bw1,
