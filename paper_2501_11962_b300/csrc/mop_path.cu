@@ -334,7 +334,23 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
 // more than FP32.  F^n = F_nonbonded (double-float from the pair kernel) + F_bonded;
 // eta^n = (R^{n+1} - R^n) - c F^n in double-float (the difference of nearly equal terms when
 // the path is close to a solution of Eq. 1), stored rounded to FP32; bonded energy of bead 1.
-__global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+#ifndef MOP_E1_MINB
+#define MOP_E1_MINB 6   // 40 registers
+#endif
+#ifndef MOP_E2_MINB
+#define MOP_E2_MINB 4   // 64 registers: 4 blocks of 256 per SM instead of 3 (E2 0.68 -> 0.59 ms at config 5)
+#endif
+#if MOP_E1_MINB > 0
+#define MOP_E1_BOUNDS __launch_bounds__(kRedBlock, MOP_E1_MINB)
+#else
+#define MOP_E1_BOUNDS __launch_bounds__(kRedBlock)
+#endif
+#if MOP_E2_MINB > 0
+#define MOP_E2_BOUNDS __launch_bounds__(kRedBlock, MOP_E2_MINB)
+#else
+#define MOP_E2_BOUNDS __launch_bounds__(kRedBlock)
+#endif
+__global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
                                                         double* e_bond, int nbx) {
   __shared__ double shw[kRedBlock / 32];
   const int p = blockIdx.z, n = blockIdx.y;
@@ -394,7 +410,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e1_mixed(SysConsts sc, const Path
 // H eta (pair part from the HVP kernel + bonded part), the gradient of Eqs. 5-7 in FP32 from the
 // FP32-rounded eta, spring energy summed as double-floats per warp and in FP64 per block.
 template <bool FD>
-__global__ void __launch_bounds__(kRedBlock) k_e2_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
+__global__ void MOP_E2_BOUNDS k_e2_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
                                                         double* e_spring, int nbx, int maxN) {
   __shared__ double shw[kRedBlock / 32];
   const int p = blockIdx.z, n = blockIdx.y;
