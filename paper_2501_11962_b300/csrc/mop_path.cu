@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* _
 #define MOP_E1_MINB 6   // 40 registers
 #endif
 #ifndef MOP_E2_MINB
-#define MOP_E2_MINB 4   // 64 registers: 4 blocks of 256 per SM instead of 3 (E2 0.68 -> 0.59 ms at config 5)
+#define MOP_E2_MINB 4   // 64 registers: 4 blocks of 256 per SM instead of 3 (E2 0.68 -> 0.59 ms at 150k atoms x 64 beads)
 #endif
 #if MOP_E1_MINB > 0
 #define MOP_E1_BOUNDS __launch_bounds__(kRedBlock, MOP_E1_MINB)
