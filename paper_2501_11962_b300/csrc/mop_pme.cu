@@ -199,8 +199,11 @@ __global__ void __launch_bounds__(kRedBlock) k_pme_scale(SysConsts sc, cufftComp
 
 // forces (MODE 0: F_i = -q_i sum_k grad M_i(k) phi(k)) or H eta (MODE 1) of every slot, added
 // to the fixed-point j-side sums; grid: (slots, beads, paths)
+#ifndef MOP_GATHER_MINB
+#define MOP_GATHER_MINB 3   // H eta gather: 3 blocks of 256 per SM (80 registers); the force gather runs 4
+#endif
 template <int P, int MODE>
-__global__ void __launch_bounds__(kRedBlock) k_pme_gather(SysConsts sc, const PathDev* __restrict__ paths) {
+__global__ void __launch_bounds__(kRedBlock, MODE ? MOP_GATHER_MINB : 4) k_pme_gather(SysConsts sc, const PathDev* __restrict__ paths) {
   const PathDev& Pd = paths[blockIdx.z];
   const int n = blockIdx.y, s = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_pass = MODE ? Pd.n_hvp : Pd.n_force;
