@@ -40,7 +40,7 @@ struct mop_handle {
   PathHost paths[kMaxPaths];
   DevBuf<PathDev> d_paths, d_one;
   DevBuf<double> e_bond, e_spring, scratch;
-  DevBuf<int2> excl;                      // Ewald exclusion pairs
+  DevBuf<int> excl_off, excl_nb;          // Ewald exclusion partners of every atom (CSR)
   DevBuf<float> pme_theta;                // SPME kernel [K1][K2][K3 / 2 + 1]
   PmePlans* pme = nullptr;                // cuFFT plans per bead count
   double skin = 0.0;                      // Verlet skin of the pair lists (0: rebuild every time)
@@ -209,7 +209,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.etamax.ensure(N));
     if (h->precision == MOP_PREC_MIXED) CK(h, P.jacc.ensure(nq3));
     CK(h, P.e_pair.ensure(h->grid.max_clu));
-    if (sc.elec == 1) CK(h, P.e_excl.ensure(std::max(1, (sc.n_excl + kRedBlock - 1) / kRedBlock)));
+    if (sc.elec == 1) CK(h, P.e_excl.ensure(std::max(1, excl_energy_blocks(sc))));
     const bool pme = sc.pme_nk > 0;
     if (pme) {
       const size_t nb = (size_t)std::max(n_force, n_hvp);
@@ -640,7 +640,24 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     std::sort(excl.begin(), excl.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
   }
   sc.n_excl = (int)excl.size();
-  if (excl.empty()) excl.push_back(make_int2(0, 0));
+  // both directions, each atom's partners in ascending order
+  std::vector<int> exoff(Q + 1, 0), exnb(std::max<size_t>(1, 2 * excl.size()));
+  for (const int2& e : excl) {
+    exoff[e.x + 1]++;
+    exoff[e.y + 1]++;
+  }
+  for (int i = 0; i < Q; ++i) exoff[i + 1] += exoff[i];
+  {
+    std::vector<std::vector<int>> nb(Q);
+    for (const int2& e : excl) {
+      nb[e.x].push_back(e.y);
+      nb[e.y].push_back(e.x);
+    }
+    for (int i = 0; i < Q; ++i) {
+      std::sort(nb[i].begin(), nb[i].end());
+      std::copy(nb[i].begin(), nb[i].end(), exnb.begin() + exoff[i]);
+    }
+  }
   mop_status s;
   if ((s = upload(h, h->mass, d->mass, Q)) || (s = upload(h, h->Kspr, Kspr.data(), Q)) ||
       (s = upload(h, h->cL, cL.data(), Q)) || (s = upload(h, h->qs, qs.data(), Q)) ||
@@ -650,7 +667,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
       (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
       (s = upload(h, h->incpf, incpf.data(), incpf.size())) ||
       (s = upload(h, h->tab, tab.data(), tab.size())) || (s = upload(h, h->tab64, tab64.data(), tab64.size())) ||
-      (s = upload(h, h->excl, excl.data(), excl.size())) ||
+      (s = upload(h, h->excl_off, exoff.data(), exoff.size())) || (s = upload(h, h->excl_nb, exnb.data(), exnb.size())) ||
       (s = upload(h, h->pme_theta, theta.data(), theta.size()))) {
     mop_destroy(h);
     return s;
@@ -670,7 +687,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.incpf = h->incpf.p;
   sc.tab = h->tab.p;
   sc.tab64 = h->tab64.p;
-  sc.excl = h->excl.p;
+  sc.excl_off = h->excl_off.p;
+  sc.excl_nb = h->excl_nb.p;
   sc.pme_theta = h->pme_theta.p;
   h->pme = pme_plans_create();
 
@@ -692,7 +710,7 @@ mop_status mop_destroy(mop_handle* h) {
   if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
   h->step_dev.release();
   h->d_one.release(); h->counts.release();
-  h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release(); h->excl.release();
+  h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release(); h->excl_off.release(); h->excl_nb.release();
   h->pme_theta.release();
   if (h->pme) pme_plans_destroy(h->pme);
   for (auto& P : h->paths) {

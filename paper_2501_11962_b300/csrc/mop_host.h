@@ -139,6 +139,8 @@ cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
 cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
                       double* e_spring, int nbx);
 cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L);
+// blocks of bead-1 energy partials launch_excl writes (e_excl)
+inline int excl_energy_blocks(const SysConsts& sc) { return sc.n_excl ? (sc.Q + kRedBlock - 1) / kRedBlock : 0; }
 cudaError_t launch_deposit(const SysConsts& sc, const PathDev* d_paths, int n_paths, double height, double width,
                            Launch L);
 cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L);

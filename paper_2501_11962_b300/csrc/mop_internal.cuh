@@ -46,7 +46,8 @@ struct SysConsts {
   float ewb, ewb2, ewc2, ewec;   // beta, beta^2, 2 beta / sqrt(pi), erfc(beta rc) / rc
   double e_self;                 // -f beta / sqrt(pi) sum_i q_i^2
   int n_excl;                    // excluded pairs (i < j, caller indices)
-  const int2* excl;
+  const int* excl_off;           // atom a's excluded partners: excl_nb[excl_off[a] .. excl_off[a + 1])
+  const int* excl_nb;
   // smooth particle-mesh Ewald (pme_nk == 0: no reciprocal part)
   int pme_order;
   int pme_K[3];

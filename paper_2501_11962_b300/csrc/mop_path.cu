@@ -604,6 +604,10 @@ __device__ __forceinline__ void excl_terms(const SysConsts& sc, float r2, float 
   *e = -qq * er * rinv;
 }
 
+// One thread per atom (caller order) and bead: the corrections of all its excluded pairs, summed
+// in registers and added to the atom's own fixed-point j-side sums with a plain read-modify-write
+// (the pair kernel has finished, and no other thread owns the row), so no atomics.  Each pair is
+// evaluated from both ends; its energy is counted by the lower index.
 template <int MODE>
 __global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev* __restrict__ paths) {
   __shared__ double sh[32];
@@ -611,49 +615,55 @@ __global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev*
   const PathDev& P = paths[p];
   const int n_pass = MODE == 0 ? P.n_force : P.n_hvp;
   if (n >= n_pass) return;   // whole block
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
   float en = 0.f;
-  if (t < sc.n_excl) {
-    const int2 ij = sc.excl[t];
-    float d[3];
-    mi_diff<float>(sc, P, n, ij.x, ij.y, d);
-    const float qq = (float)(sc.qs[ij.x] * sc.qs[ij.y]);
-    float f[3];
-    if (MODE == 0) {
-      float g, b, e;
-      excl_terms(sc, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], qq, &g, &b, &e);
-      for (int c = 0; c < 3; ++c) f[c] = g * d[c];
-      en = e;
-    } else {
-      float ei[3], ej[3], u[3];
-      eta_of<float>(P, n, ij.x, ei);
-      eta_of<float>(P, n, ij.y, ej);
-      for (int c = 0; c < 3; ++c) u[c] = ei[c] - ej[c];
-      if (MODE == 1) {
-        float g, b, e;
-        excl_terms(sc, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], qq, &g, &b, &e);
-        const float s = b * (d[0] * u[0] + d[1] * u[1] + d[2] * u[2]);
-        for (int c = 0; c < 3; ++c) f[c] = s * d[c] - g * u[c];   // A u
+  const int t0 = a < sc.Q ? sc.excl_off[a] : 0, t1 = a < sc.Q ? sc.excl_off[a + 1] : 0;
+  if (t1 > t0) {
+    const double qa = sc.qs[a];
+    float ea[3] = {0.f, 0.f, 0.f};
+    if (MODE >= 1) eta_of<float>(P, n, a, ea);
+    float eps = 0.f;
+    if (MODE == 2) {
+      const float mx = __uint_as_float(P.etamax[n]);
+      eps = (float)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
+    }
+    float fa[3] = {0.f, 0.f, 0.f};
+    for (int t = t0; t < t1; ++t) {
+      const int b = sc.excl_nb[t];
+      float d[3];
+      mi_diff<float>(sc, P, n, a, b, d);   // x_a - x_b
+      const float qq = (float)(qa * sc.qs[b]);
+      float f[3];
+      if (MODE == 0) {
+        float g, bb, e;
+        excl_terms(sc, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], qq, &g, &bb, &e);
+        for (int c = 0; c < 3; ++c) f[c] = g * d[c];
+        if (a < b) en += e;
       } else {
-        const float mx = __uint_as_float(P.etamax[n]);
-        const float eps = (float)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
-        float fp[3], fm[3];
-        for (int sg = 0; sg < 2; ++sg) {
-          float a[3];
-          for (int c = 0; c < 3; ++c) a[c] = d[c] + (sg ? -eps : eps) * u[c];
-          float g, b, e;
-          excl_terms(sc, a[0] * a[0] + a[1] * a[1] + a[2] * a[2], qq, &g, &b, &e);
-          for (int c = 0; c < 3; ++c) (sg ? fm : fp)[c] = g * a[c];
+        float eb[3], u[3];
+        eta_of<float>(P, n, b, eb);
+        for (int c = 0; c < 3; ++c) u[c] = ea[c] - eb[c];
+        if (MODE == 1) {
+          float g, bb, e;
+          excl_terms(sc, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], qq, &g, &bb, &e);
+          const float s = bb * (d[0] * u[0] + d[1] * u[1] + d[2] * u[2]);
+          for (int c = 0; c < 3; ++c) f[c] = s * d[c] - g * u[c];   // A u
+        } else {
+          float fp[3], fm[3];
+          for (int sg = 0; sg < 2; ++sg) {
+            float w[3];
+            for (int c = 0; c < 3; ++c) w[c] = d[c] + (sg ? -eps : eps) * u[c];
+            float g, bb, e;
+            excl_terms(sc, w[0] * w[0] + w[1] * w[1] + w[2] * w[2], qq, &g, &bb, &e);
+            for (int c = 0; c < 3; ++c) (sg ? fm : fp)[c] = g * w[c];
+          }
+          for (int c = 0; c < 3; ++c) f[c] = -(fp[c] - fm[c]) / (2.f * eps);   // H eta = -dF/de
         }
-        for (int c = 0; c < 3; ++c) f[c] = -(fp[c] - fm[c]) / (2.f * eps);   // H eta = -dF/de
       }
+      for (int c = 0; c < 3; ++c) fa[c] += f[c];
     }
-    unsigned long long* ji = P.jacc + 3 * ((size_t)n * P.Qpad + P.slot[ij.x]);
-    unsigned long long* jj = P.jacc + 3 * ((size_t)n * P.Qpad + P.slot[ij.y]);
-    for (int c = 0; c < 3; ++c) {
-      atomicAdd(ji + c, (unsigned long long)__float2ll_rn(f[c] * kFixScale));
-      atomicAdd(jj + c, (unsigned long long)__float2ll_rn(-f[c] * kFixScale));
-    }
+    unsigned long long* J = P.jacc + 3 * ((size_t)n * P.Qpad + P.slot[a]);
+    for (int c = 0; c < 3; ++c) J[c] += (unsigned long long)__float2ll_rn(fa[c] * kFixScale);
   }
   if (MODE == 0 && n == 0) {
     const double tot = block_sum<kRedBlock>((double)en, sh);
@@ -790,7 +800,7 @@ cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
 
 cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L) {
   if (sc.elec != 1 || sc.n_excl == 0) return cudaSuccess;
-  const dim3 grid((sc.n_excl + kRedBlock - 1) / kRedBlock, max_beads, n_paths);
+  const dim3 grid((sc.Q + kRedBlock - 1) / kRedBlock, max_beads, n_paths);
   if (mode == 0) k_excl<0><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
   else if (mode == 1) k_excl<1><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
   else k_excl<2><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
@@ -814,7 +824,7 @@ cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L, const double* e_bond,
                           int sb, int nb1, const double* e_spring, int ss, int nb2) {
   k_reduce<<<n_paths, kRedBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2,
-                                             (sc.n_excl + kRedBlock - 1) / kRedBlock, sc.e_self,
+                                             excl_energy_blocks(sc), sc.e_self,
                                              pme_energy_blocks(sc));
   ++*L.counter;
   return cudaGetLastError();
