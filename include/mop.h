@@ -139,6 +139,10 @@ mop_status mop_get_path(mop_handle* h, int32_t path_id, float* xyz, int32_t flag
  * for every set path when path_id = -1, in one pass of the kernels.  veff: [1] or [P] doubles
  * (P = number of set paths, in path-id order); grad: [N][Q][3] doubles (concatenated over
  * paths in path-id order when path_id = -1), dV_eff/dR (not the force); grad may be NULL.
+ * Host buffers: the call returns when they are filled.  A pinned (page-locked) host grad of one
+ * mixed-precision path without an SPME grid is filled while the kernels run: the HVP pass runs
+ * in bead chunks and each chunk's rows are copied on a second stream as soon as they are final
+ * (the rows the bias changes, last); the result is bitwise that of the other paths.
  * Errors: MOP_ERR_STATE (path not set), MOP_ERR_NONFINITE (non-finite V_eff, host calls
  * only), MOP_ERR_CUDA, MOP_ERR_OOM. */
 mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, double* grad,

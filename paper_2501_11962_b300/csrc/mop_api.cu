@@ -16,6 +16,10 @@
 
 using namespace mop;
 
+namespace mop {
+constexpr int kCopyChunks = 8;   // bead chunks of the HVP pass whose gradients are copied while later chunks run
+}
+
 struct mop_handle {
   int device = 0;
   int num_sms = 148;
@@ -52,6 +56,9 @@ struct mop_handle {
   // instrumentation
   bool profiling = false;
   cudaEvent_t ev[7] = {};
+  // gradient copies to pinned host memory overlapped with the HVP pass (mop_veff_and_grad)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t cev[kCopyChunks] = {};
   // CUDA-graph mode of mop_step
   bool graph_mode = false;
   cudaGraphExec_t graph_exec = nullptr;
@@ -152,8 +159,11 @@ mop_status upload(mop_handle* h, DevBuf<T>& b, const T* src, size_t n) {
 // sync = false makes the call stream-capture safe: no host synchronisation, no allocation (the
 // buffers must already have their size from an earlier synchronous call) and no host-to-device
 // copy of the path table (it must already be on the device).
+// host_grad (pinned host memory, one path, mixed precision, no SPME grid): the HVP pass runs in
+// kCopyChunks bead chunks, each followed by its E2, and the finished gradient rows are copied to
+// host_grad on a second stream while later chunks compute; *copied is set when that happened.
 mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff, double* dev_grad,
-                    cudaStream_t st, bool sync = true) {
+                    cudaStream_t st, bool sync = true, double* host_grad = nullptr, bool* copied = nullptr) {
   SysConsts& sc = h->sc;
   Launch L{st, &h->launches};
   const bool fd = h->hvp_mode == MOP_HVP_FD;
@@ -331,6 +341,53 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, mark(2));
   CK(h, launch_e1(sc, h->d_paths.p, np, max_qpad, max_nf, L, h->e_bond.p, nbx));
   CK(h, mark(3));
+  if (copied) *copied = false;
+  const bool overlap = host_grad && np == 1 && sync && h->precision == MOP_PREC_MIXED && sc.pme_nk == 0 &&
+                       pd[0].n_hvp >= 2 * kCopyChunks && units_h > 0;
+  if (overlap) {
+    const PathDev& D = pd[0];
+    const int N = D.N, nh = D.n_hvp, pairs = (nh + 1) / 2;   // HVP units come in bead pairs
+    if (!h->copy_stream) CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (auto& e : h->cev)
+      if (!e) CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    bool e2e_cv = false;   // an end-to-end CV puts bias gradient on bead 1 too
+    for (int q = 0; q < D.n_cv; ++q) e2e_cv = e2e_cv || D.cv_e2e[q];
+    const double* gdev = D.grad;
+    const size_t row = 3 * (size_t)sc.Q;
+    std::vector<std::pair<int, int>> after_bias;
+    CK(h, clear_jacc(true));
+    for (int c = 0; c < kCopyChunks; ++c) {
+      const int p0 = pairs * c / kCopyChunks, p1 = pairs * (c + 1) / kCopyChunks;
+      const int b0 = 2 * p0, hb1 = std::min(2 * p1, nh);          // HVP beads of the chunk
+      const int b1 = c == kCopyChunks - 1 ? N : 2 * p1;            // E2 beads (the last takes bead N)
+      CK(h, launch_pair(sc, h->d_paths.p, 1, (long long)p1 * D.n_clu, fd ? 2 : 1, h->num_sms, L,
+                        (long long)p0 * D.n_clu));
+      CK(h, launch_excl(sc, h->d_paths.p, 1, max_n, fd ? 2 : 1, L, b0, hb1 - b0));
+      CK(h, launch_e2(sc, h->d_paths.p, 1, max_qpad, max_n, L, h->e_spring.p, nbx, b0, b1 - b0));
+      // the bias adds to bead N (last chunk) and, for an end-to-end CV, to bead 1: copy those after it
+      if (c == kCopyChunks - 1 || (c == 0 && e2e_cv)) {
+        after_bias.push_back({b0, b1});
+        continue;
+      }
+      CK(h, cudaEventRecord(h->cev[c], st));
+      CK(h, cudaStreamWaitEvent(h->copy_stream, h->cev[c], 0));
+      CK(h, cudaMemcpyAsync(host_grad + b0 * row, gdev + b0 * row, sizeof(double) * row * (b1 - b0),
+                            cudaMemcpyDeviceToHost, h->copy_stream));
+    }
+    CK(h, mark(4));
+    CK(h, mark(5));
+    CK(h, launch_bias(sc, h->d_paths.p, np, L));
+    CK(h, launch_reduce(sc, h->d_paths.p, np, L, h->e_bond.p, sb, sb, h->e_spring.p, ss, ss));
+    CK(h, mark(6));
+    for (const auto& r : after_bias)
+      CK(h, cudaMemcpyAsync(host_grad + r.first * row, gdev + r.first * row, sizeof(double) * row * (r.second - r.first),
+                            cudaMemcpyDeviceToHost, st));
+    if (copied) *copied = true;
+    for (int id : ids) h->paths[id].have_grad = true;
+    h->last_ids = ids;
+    h->last_pd = pd;
+    return MOP_OK;
+  }
   if (units_h > 0) {
     CK(h, clear_jacc(true));
     CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
@@ -708,6 +765,9 @@ mop_status mop_destroy(mop_handle* h) {
     if (e) cudaEventDestroy(e);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  for (auto& e : h->cev)
+    if (e) cudaEventDestroy(e);
   h->step_dev.release();
   h->d_one.release(); h->counts.release();
   h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release(); h->excl_off.release(); h->excl_nb.release();
@@ -804,7 +864,15 @@ mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, doubl
   CK(h, cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const bool dev = flags & MOP_DEVPTR;
-  s = evaluate(h, ids, dev ? veff : nullptr, dev ? grad : nullptr, st);
+  // a pinned host gradient buffer lets the gradient copy overlap the HVP pass (one path)
+  double* host_grad = nullptr;
+  if (!dev && grad && ids.size() == 1) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, grad) == cudaSuccess && at.type == cudaMemoryTypeHost) host_grad = grad;
+    cudaGetLastError();
+  }
+  bool copied = false;
+  s = evaluate(h, ids, dev ? veff : nullptr, dev ? grad : nullptr, st, true, host_grad, &copied);
   if (s) return s;
   if (!dev) {
     size_t goff = 0;
@@ -813,10 +881,12 @@ mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, doubl
       PathHost& P = h->paths[ids[k]];
       CK(h, cudaMemcpyAsync(&v[k], P.veff_int.p, sizeof(double), cudaMemcpyDeviceToHost, st));
       const size_t n = 3 * (size_t)P.N * h->sc.Q;
-      if (grad) CK(h, cudaMemcpyAsync(grad + goff, P.grad_int.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (grad && !copied)
+        CK(h, cudaMemcpyAsync(grad + goff, P.grad_int.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
       goff += n;
     }
     CK(h, cudaStreamSynchronize(st));
+    if (copied) CK(h, cudaStreamSynchronize(h->copy_stream));
     for (size_t k = 0; k < ids.size(); ++k) {
       if (veff) veff[k] = v[k];
       if (!std::isfinite(v[k])) return fail(h, MOP_ERR_NONFINITE, "V_eff of path %d is not finite", ids[k]);

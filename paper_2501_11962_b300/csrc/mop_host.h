@@ -125,8 +125,9 @@ cudaError_t prep_coords(const SysConsts& sc, const Grid& g, PathHost& P, double 
 // mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP.  A unit is one i-cluster for
 // pair_beads_per_unit(precision) consecutive beads.
 int pair_beads_per_unit(int precision);
+// units [u_begin, n_units) only (a bead range of a single path: units are bead-major)
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
-                        int mode, int num_sms, Launch L);
+                        int mode, int num_sms, Launch L, long long u_begin = 0);
 
 cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
                                unsigned long long* counts, int num_sms, Launch L);
@@ -136,9 +137,11 @@ cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int 
 // max_beads * nbx partials per path
 cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
                       double* e_bond, int nbx);
+// beads [n_begin, n_begin + n_count) (default: all max_beads)
 cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
-                      double* e_spring, int nbx);
-cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L);
+                      double* e_spring, int nbx, int n_begin = 0, int n_count = -1);
+cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L,
+                        int n_begin = 0, int n_count = -1);
 // blocks of bead-1 energy partials launch_excl writes (e_excl)
 inline int excl_energy_blocks(const SysConsts& sc) { return sc.n_excl ? (sc.Q + kRedBlock - 1) / kRedBlock : 0; }
 cudaError_t launch_deposit(const SysConsts& sc, const PathDev* d_paths, int n_paths, double height, double width,

@@ -817,7 +817,7 @@ template <class R> struct BeadsPerUnit { static constexpr int value = sizeof(R) 
 
 template <class R, int MODE, bool EW>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pair(SysConsts sc, const PathDev* __restrict__ paths,
-                                                                      int n_paths, long long n_units) {
+                                                                      int n_paths, long long u_begin, long long n_units) {
   using V4 = typename Tr<R>::V4;
   constexpr int B = BeadsPerUnit<R>::value;
   // type-pair table with an odd row stride: the 8 i-lanes of a quarter-warp (one j type, up to
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pai
   const int lane = threadIdx.x & 31;
   Stage<R, B>& S = stage[threadIdx.x >> 5];
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nw) {
+  for (long long u = u_begin + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); u < n_units; u += nw) {
     int p = 0;
     if (MODE == 0) {
       while (p + 1 < n_paths && paths[p + 1].unit_off <= u) ++p;
@@ -854,18 +854,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MOP_PAIR_MINB : 2) k_pai
 }
 
 template <class R, int MODE, bool EW>
-cudaError_t launch_one(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int num_sms,
-                       Launch L) {
+cudaError_t launch_one(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long u_begin, long long n_units,
+                       int num_sms, Launch L) {
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R, MODE, EW>, 128, 0);
     if (e != cudaSuccess || per_sm <= 0) per_sm = 4;
   }
-  const long long want_blocks = (n_units + 3) / 4;
+  const long long want_blocks = (n_units - u_begin + 3) / 4;
   long long blocks = (long long)num_sms * per_sm;
   if (blocks > want_blocks) blocks = want_blocks;
   if (blocks < 1) blocks = 1;
-  k_pair<R, MODE, EW><<<(int)blocks, 128, 0, L.st>>>(sc, d_paths, n_paths, n_units);
+  k_pair<R, MODE, EW><<<(int)blocks, 128, 0, L.st>>>(sc, d_paths, n_paths, u_begin, n_units);
   ++*L.counter;
   return cudaGetLastError();
 }
@@ -947,19 +947,19 @@ cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int 
 int pair_beads_per_unit(int precision) { return precision == 1 ? 1 : 2; }
 
 cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
-                        int num_sms, Launch L) {
-  if (n_units <= 0) return cudaSuccess;
+                        int num_sms, Launch L, long long u_begin) {
+  if (n_units <= u_begin) return cudaSuccess;
   const bool f64 = sc.precision == 1, ew = sc.elec == 1;   // Ewald runs in mixed precision only
   switch (mode) {
-    case 0: return f64 ? launch_one<double, 0, false>(sc, d_paths, n_paths, n_units, num_sms, L)
-                 : ew ? launch_one<float, 0, true>(sc, d_paths, n_paths, n_units, num_sms, L)
-                      : launch_one<float, 0, false>(sc, d_paths, n_paths, n_units, num_sms, L);
-    case 1: return f64 ? launch_one<double, 1, false>(sc, d_paths, n_paths, n_units, num_sms, L)
-                 : ew ? launch_one<float, 1, true>(sc, d_paths, n_paths, n_units, num_sms, L)
-                      : launch_one<float, 1, false>(sc, d_paths, n_paths, n_units, num_sms, L);
-    default: return f64 ? launch_one<double, 2, false>(sc, d_paths, n_paths, n_units, num_sms, L)
-                  : ew ? launch_one<float, 2, true>(sc, d_paths, n_paths, n_units, num_sms, L)
-                       : launch_one<float, 2, false>(sc, d_paths, n_paths, n_units, num_sms, L);
+    case 0: return f64 ? launch_one<double, 0, false>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L)
+                 : ew ? launch_one<float, 0, true>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L)
+                      : launch_one<float, 0, false>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L);
+    case 1: return f64 ? launch_one<double, 1, false>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L)
+                 : ew ? launch_one<float, 1, true>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L)
+                      : launch_one<float, 1, false>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L);
+    default: return f64 ? launch_one<double, 2, false>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L)
+                  : ew ? launch_one<float, 2, true>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L)
+                       : launch_one<float, 2, false>(sc, d_paths, n_paths, u_begin, n_units, num_sms, L);
   }
 }
 

@@ -278,9 +278,9 @@ __global__ void __launch_bounds__(kRedBlock) k_e1(SysConsts sc, const PathDev* _
 // E2: bonded H eta, H eta total, path gradient (caller order), spring energy
 template <class R, bool FD>
 __global__ void __launch_bounds__(kRedBlock) k_e2(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                                  double* e_spring, int nbx, int maxN) {
+                                                  double* e_spring, int nbx, int maxN, int n_begin) {
   __shared__ double sh[32];
-  const int p = blockIdx.z, n = blockIdx.y;
+  const int p = blockIdx.z, n = n_begin + blockIdx.y;
   const PathDev& P = paths[p];
   double* part = e_spring + ((size_t)p * maxN + n) * nbx + blockIdx.x;
   if (n >= P.N) {
@@ -411,9 +411,9 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
 // FP32-rounded eta, spring energy summed as double-floats per warp and in FP64 per block.
 template <bool FD>
 __global__ void MOP_E2_BOUNDS k_e2_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
-                                                        double* e_spring, int nbx, int maxN) {
+                                                        double* e_spring, int nbx, int maxN, int n_begin) {
   __shared__ double shw[kRedBlock / 32];
-  const int p = blockIdx.z, n = blockIdx.y;
+  const int p = blockIdx.z, n = n_begin + blockIdx.y;
   const PathDev& P = paths[p];
   double* part = e_spring + ((size_t)p * maxN + n) * nbx + blockIdx.x;
   if (n >= P.N) {
@@ -609,9 +609,9 @@ __device__ __forceinline__ void excl_terms(const SysConsts& sc, float r2, float 
 // (the pair kernel has finished, and no other thread owns the row), so no atomics.  Each pair is
 // evaluated from both ends; its energy is counted by the lower index.
 template <int MODE>
-__global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev* __restrict__ paths) {
+__global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev* __restrict__ paths, int n_begin) {
   __shared__ double sh[32];
-  const int p = blockIdx.z, n = blockIdx.y;
+  const int p = blockIdx.z, n = n_begin + blockIdx.y;
   const PathDev& P = paths[p];
   const int n_pass = MODE == 0 ? P.n_force : P.n_hvp;
   if (n >= n_pass) return;   // whole block
@@ -783,27 +783,32 @@ cudaError_t launch_e1(const SysConsts& sc, const PathDev* d_paths, int n_paths, 
 }
 
 cudaError_t launch_e2(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_qpad, int max_beads, Launch L,
-                      double* e_spring, int nbx) {
-  dim3 grid(nbx, max_beads, n_paths);
+                      double* e_spring, int nbx, int n_begin, int n_count) {
+  if (n_count < 0) n_count = max_beads;
+  if (n_count == 0) return cudaSuccess;
+  dim3 grid(nbx, n_count, n_paths);
   const bool fd = sc.hvp_mode == 1;
   (void)max_qpad;
   if (sc.precision == 1) {
-    if (fd) k_e2<double, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
-    else k_e2<double, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
+    if (fd) k_e2<double, true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads, n_begin);
+    else k_e2<double, false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads, n_begin);
   } else {
-    if (fd) k_e2_mixed<true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
-    else k_e2_mixed<false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads);
+    if (fd) k_e2_mixed<true><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads, n_begin);
+    else k_e2_mixed<false><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_paths, e_spring, nbx, max_beads, n_begin);
   }
   ++*L.counter;
   return cudaGetLastError();
 }
 
-cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L) {
+cudaError_t launch_excl(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_beads, int mode, Launch L,
+                        int n_begin, int n_count) {
   if (sc.elec != 1 || sc.n_excl == 0) return cudaSuccess;
-  const dim3 grid((sc.Q + kRedBlock - 1) / kRedBlock, max_beads, n_paths);
-  if (mode == 0) k_excl<0><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
-  else if (mode == 1) k_excl<1><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
-  else k_excl<2><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths);
+  if (n_count < 0) n_count = max_beads;
+  if (n_count == 0) return cudaSuccess;
+  const dim3 grid((sc.Q + kRedBlock - 1) / kRedBlock, n_count, n_paths);
+  if (mode == 0) k_excl<0><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_begin);
+  else if (mode == 1) k_excl<1><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_begin);
+  else k_excl<2><<<grid, kRedBlock, 0, L.st>>>(sc, d_paths, n_begin);
   ++*L.counter;
   return cudaGetLastError();
 }
