@@ -361,8 +361,37 @@ template <int MODE, bool EW, bool ENERGY = false>
 __device__ __forceinline__ void pair_two(const Cst<float>& k, const PairK2& c, const float2 (&xs)[3], const float2 (&xj)[3],
                                          float rc2e, const float2 (&ei)[3], const float2 (&ej)[3], float2 (&a)[3],
                                          float2 (&f)[3], const PairK<float>* ce = nullptr, float ew = 0.f,
-                                         float* e = nullptr) {
+                                         float* e = nullptr, float2 eps2 = float2{0.f, 0.f}) {
   const float2 d[3] = {sub2(xs[0], xj[0]), sub2(xs[1], xj[1]), sub2(xs[2], xj[2])};
+  if constexpr (MODE == 2) {
+    // F(+) - F(-) at the pair separated by d +- eps (e_i - e_j), both beads at once
+    const float2 u[3] = {mul2(eps2, sub2(ei[0], ej[0])), mul2(eps2, sub2(ei[1], ej[1])), mul2(eps2, sub2(ei[2], ej[2]))};
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const float2 q[3] = {sgn ? sub2(d[0], u[0]) : add2(d[0], u[0]), sgn ? sub2(d[1], u[1]) : add2(d[1], u[1]),
+                           sgn ? sub2(d[2], u[2]) : add2(d[2], u[2])};
+      const float2 r2 = fma2(q[0], q[0], fma2(q[1], q[1], mul2(q[2], q[2])));
+      const bool in0 = r2.x < rc2e, in1 = r2.y < rc2e;
+      const float2 rinv = rsq2(r2);
+      const float2 rinv2 = mul2(rinv, rinv);
+      const float2 rinv6 = mul2(mul2(rinv2, rinv2), rinv2);
+      const float2 lj = mul2(rinv6, fma2(c.A, rinv6, c.nB));
+      float2 g;
+      if (EW) {
+        float2 ec, c2e;
+        ewald_terms2(k, r2, rinv, &ec, &c2e);
+        g = fma2(rinv2, fma2(c.qq, fma2(ec, rinv, c2e), lj), mul2(c.sh, rinv));
+      } else {
+        g = fma2(rinv2, fma2(c.qq, rinv, lj), fma2(c.sh, rinv, c.nqk));
+      }
+      g = make_float2(in0 ? (sgn ? -g.x : g.x) : 0.f, in1 ? (sgn ? -g.y : g.y) : 0.f);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) f[t] = sgn ? fma2(g, q[t], f[t]) : mul2(g, q[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) a[t] = add2(a[t], f[t]);
+    return;
+  }
   const float2 r2 = fma2(d[0], d[0], fma2(d[1], d[1], mul2(d[2], d[2])));
   const bool in0 = r2.x < rc2e, in1 = r2.y < rc2e;
   const float2 rinv = rsq2(r2);
@@ -583,9 +612,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   }
   const V4* __restrict__ tabrow = tab + __ldg(&P.ts[si]) * tstr;
   const R qi = xi[0].w;
-  // both beads in f32x2 instructions (forces, with the bead-1 energy in the first units, and the
-  // adjoint HVP; the FD mode keeps the scalar path)
-  constexpr bool PACK = MOP_PACK2 && sizeof(R) == 4 && B == 2 && MODE != 2;
+  // both beads in f32x2 instructions (forces with the bead-1 energy in the first units, the
+  // adjoint HVP and the FD difference)
+  constexpr bool PACK = MOP_PACK2 && sizeof(R) == 4 && B == 2;
   float2 a2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   float2 ei2[3];
 #pragma unroll
@@ -702,12 +731,13 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           if constexpr (PACK) {
             const float2 xs2[3] = {make_float2(xs[0][0], xs[B - 1][0]), make_float2(xs[0][1], xs[B - 1][1]),
                                    make_float2(xs[0][2], xs[B - 1][2])};
-            const V4 ej0 = MODE == 1 ? S.e[0][sj] : V4{}, ej1 = MODE == 1 ? S.e[B - 1][sj] : V4{};
+            const V4 ej0 = MODE >= 1 ? S.e[0][sj] : V4{}, ej1 = MODE >= 1 ? S.e[B - 1][sj] : V4{};
             const V4 xj0 = S.x[0][sj], xj1 = S.x[B - 1][sj];
             const float2 xj2[3] = {make_float2(xj0.x, xj1.x), make_float2(xj0.y, xj1.y), make_float2(xj0.z, xj1.z)};
             const float2 ej2[3] = {make_float2(ej0.x, ej1.x), make_float2(ej0.y, ej1.y), make_float2(ej0.z, ej1.z)};
             float2 f2[3];
-            pair_two<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), xs2, xj2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a);
+            pair_two<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), xs2, xj2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a,
+                                       make_float2((float)eps[0], (float)eps[B - 1]));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               jf[h][c][0] = f2[c].x;
