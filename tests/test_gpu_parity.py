@@ -1,6 +1,6 @@
 """CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances (relative 2-norms over all beads and atoms, the spec bar):
+Tolerances (relative 2-norms over all beads and atoms, the required accuracy):
   forces F^n <= 1e-5, H eta <= 1e-4, V_eff <= 1e-6 (mixed precision);
   FP64 mode: 1e-9.
 The gradient G, eta and the energy parts are reported and held to the same bars as the
