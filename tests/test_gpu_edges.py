@@ -14,11 +14,11 @@ from tests.test_gpu_parity import TOL_F, TOL_H, TOL_V, rel
 pytestmark = pytest.mark.gpu
 
 
-def tiny_system(seed=5):
-    """13 atoms in a 2.4 nm box: two bent 3-atom molecules and 7 single atoms, 2 LJ types,
+def tiny_system(seed=5, box=(2.4, 2.4, 2.4)):
+    """13 atoms in a small box: two bent 3-atom molecules and 7 single atoms, 2 LJ types,
     charges summing to zero, no two atoms closer than 0.25 nm (nearest image)."""
     rng = np.random.default_rng(seed)
-    box = np.array([2.4, 2.4, 2.4])
+    box = np.array(box, dtype=np.float64)
     pos = []
     for m in range(2):                              # molecules: bond 0.15 nm, angle ~109.5 deg
         while True:
@@ -114,3 +114,33 @@ def test_sixty_four_paths_in_one_call():
     with pytest.raises(mop.MopError) as ei:
         eng.set_path(64, X)
     assert ei.value.status == mop.MOP_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [mop.MOP_PREC_MIXED, mop.MOP_PREC_FP64])
+def test_non_cubic_box_matches_oracle(prec):
+    # three different box edges (minimum image, cluster columns and bins per dimension)
+    sys, pos = tiny_system(seed=8, box=(2.3, 2.6, 2.9))
+    X = tiny_path(pos, seed=4)
+    eng = mop.Engine(sys, precision=prec)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff(X.astype(np.float64), want=("G", "F"), hvp_mode=oracle.HVP_ANALYTIC)
+    tol = 1e-8 if prec == mop.MOP_PREC_FP64 else 1.0
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V * tol
+    assert rel(G, r["G"]) < TOL_F * tol
+
+
+def test_non_cubic_spme_grid_matches_oracle():
+    # K1 != K2 != K3: the grid index order of spreading, the FFT layout, the kernel and gathering
+    sys, pos = tiny_system(seed=8, box=(2.3, 2.6, 2.9))
+    sys = dataclasses.replace(synth.with_pme(sys), pme_grid=(20, 24, 27))
+    X = tiny_path(pos, seed=4)
+    eng = mop.Engine(sys)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff_pme(X.astype(np.float64))
+    N = X.shape[0]
+    H = eng.get_field(0, mop.MOP_FIELD_HETA)[:N - 1]
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V
+    assert rel(G, r["G"]) < TOL_F
+    assert rel(H, r["Heta"][:N - 1]) < TOL_H
