@@ -265,3 +265,28 @@ def test_cfg5_sampled_beads_match_oracle():
     assert errs["F"] < TOL_F and errs["eta"] < TOL_F and errs["G"] < TOL_F
     assert errs["Heta"] < TOL_H
     assert errs["V"] < TOL_V and errs["U1"] < TOL_V
+
+
+def test_autograd_gradient_matches_central_differences():
+    """The torch.autograd.Function's gradient against a central difference of V_eff itself along
+    random directions (FP64 mode and FP64 coordinates, so the difference is not drowned in
+    rounding)."""
+    import torch
+    w = workload(1, n_beads=6)
+    X = torch.tensor(w.paths[0], dtype=torch.float64, device="cuda")
+    eng = mop.Engine(w.system, precision=mop.MOP_PREC_FP64)
+    c = X.clone().requires_grad_(True)
+    V = mop.veff(c, eng, 0)
+    V.backward()
+    G = c.grad.detach()
+    rng = np.random.default_rng(17)
+    h = 1e-5
+    for _ in range(3):
+        D = torch.tensor(rng.normal(size=tuple(X.shape)), dtype=torch.float64, device="cuda")
+        D /= torch.linalg.norm(D)
+        with torch.no_grad():
+            vp = mop.veff(X + h * D, eng, 0).item()
+            vm = mop.veff(X - h * D, eng, 0).item()
+        fd = (vp - vm) / (2.0 * h)
+        an = float((G * D).sum())
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1.0), (fd, an)
