@@ -147,3 +147,27 @@ def test_spme_short_paths_match_oracle(n_beads):
     assert rel(F, r["F"][:max(1, n_beads - 1)]) < TOL_F
     if n_beads == 1:
         assert rel(G[0], -r["F"][0]) < TOL_F
+
+
+def test_spme_metadynamics_graph_equals_eager():
+    # the production loop on an Ewald system: rounds of MD steps with a Gaussian deposited on a
+    # centre-of-mass end-to-end CV after each round, captured (graph) and eager, bit for bit
+    w = workload(2, n_beads=6)
+    sys = synth.with_pme(w.system)
+    X = w.paths[0]
+    pos = X[-1].astype(np.float64)
+    ga = synth.nearest_group(pos, np.asarray(sys.box), pos[0], 8)
+    gb = synth.nearest_group(pos, np.asarray(sys.box), pos[1500], 8)
+    runs = []
+    for graph in (False, True):
+        eng = mop.Engine(sys)
+        eng.set_path(0, X)
+        eng.add_bias(0, 0.0, 0.0, 0.1, groups=(ga, gb), e2e=True, com=True)
+        eng.set_graph_mode(graph)
+        eng.metadynamics(3, 2, 1e-6, 5.0, 7, 1.0, 0.1)
+        runs.append((eng.get_path(0), eng.gaussians(0), eng.veff_and_grad(0)))
+    (x0, g0, (v0, G0)), (x1, g1, (v1, G1)) = runs
+    assert len(g0[0]) == 4 and np.isfinite(v0).all()   # the zero-height one plus three deposits
+    assert np.array_equal(x0, x1)
+    assert np.array_equal(g0[0], g1[0]) and np.array_equal(g0[1], g1[1])
+    assert np.array_equal(v0, v1) and np.array_equal(G0, G1)
