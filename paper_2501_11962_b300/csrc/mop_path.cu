@@ -671,8 +671,10 @@ __global__ void __launch_bounds__(kRedBlock) k_excl(SysConsts sc, const PathDev*
   }
 }
 
-// fixed-order sums of the partial energies -> V_eff (one block per path)
-__global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const double* e_bond, int sb, int nb1,
+// fixed-order sums of the partial energies (10^4 - 10^5 per path) -> V_eff, one block per path
+constexpr int kReduceBlock = 1024;
+__global__ void __launch_bounds__(kReduceBlock)
+    k_reduce(const PathDev* __restrict__ paths, int n_paths, const double* e_bond, int sb, int nb1,
                          const double* e_spring, int ss, int nb2, int n_excl_blk, double e_self, int n_pme_blk) {
   // e_bond: nb1 partials per path (stride sb); e_spring: nb2 partials per path (stride ss)
   __shared__ double sh[32];
@@ -686,9 +688,9 @@ __global__ void k_reduce(const PathDev* __restrict__ paths, int n_paths, const d
     for (int k = threadIdx.x; k < n_pme_blk; k += blockDim.x) up += P.pme_e[k];
   for (int k = threadIdx.x; k < nb1; k += blockDim.x) ub += e_bond[(size_t)p * sb + k];
   for (int k = threadIdx.x; k < nb2; k += blockDim.x) es += e_spring[(size_t)p * ss + k];
-  up = block_sum<kRedBlock>(up, sh);
-  ub = block_sum<kRedBlock>(ub, sh);
-  es = block_sum<kRedBlock>(es, sh);
+  up = block_sum<kReduceBlock>(up, sh);
+  ub = block_sum<kReduceBlock>(ub, sh);
+  es = block_sum<kReduceBlock>(es, sh);
   if (threadIdx.x == 0) {
     if (P.e_excl) up += e_self;
     const double U1 = up + ub;
@@ -828,7 +830,7 @@ cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths
 
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L, const double* e_bond,
                           int sb, int nb1, const double* e_spring, int ss, int nb2) {
-  k_reduce<<<n_paths, kRedBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2,
+  k_reduce<<<n_paths, kReduceBlock, 0, L.st>>>(d_paths, n_paths, e_bond, sb, nb1, e_spring, ss, nb2,
                                              excl_energy_blocks(sc), sc.e_self,
                                              pme_energy_blocks(sc));
   ++*L.counter;

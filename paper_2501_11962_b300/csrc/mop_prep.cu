@@ -100,23 +100,43 @@ __global__ void k_fill_columns(int Q, const int* colid, int* colinfo, int* colat
   colatoms[pos] = i;
 }
 
-// rank inside the column by (z, atom index): deterministic slot of every atom
-__global__ void k_rank(int Q, const double* ref, const int* colid, const int* colcnt, const int* colinfo,
-                       const int* colatoms, int* perm, int* slot) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Q) return;
-  const int col = colid[i];
-  const int st = colinfo[3 * col], cnt = colcnt[col];
-  const double zi = ref[3 * i + 2];
-  int rank = 0;
-  for (int k = 0; k < cnt; ++k) {
-    const int j = colatoms[st + k];
-    const double zj = ref[3 * j + 2];
-    rank += (zj < zi) || (zj == zi && j < i);
+// rank inside the column by (z, atom index): deterministic slot of every atom.  One block per
+// column; the column's (z, index) pairs pass through shared memory in tiles, and each thread
+// counts the atoms that precede its own.  The wrapped z is >= 0 (or NaN, rejected later), so
+// its bit pattern, with -0 taken as +0, orders like the value: integer compares instead of the
+// FP64 pipe.
+constexpr int kRankTile = 1024;
+__device__ __forceinline__ unsigned long long z_key(double z) {
+  return z == 0.0 ? 0ull : (unsigned long long)__double_as_longlong(z);
+}
+__global__ void k_rank(const double* ref, const int* colcnt, const int* colinfo, const int* colatoms, int* perm,
+                       int* slot) {
+  __shared__ unsigned long long zs[kRankTile];
+  __shared__ int js[kRankTile];
+  const int col = blockIdx.x;
+  const int st = colinfo[3 * col], cnt = colcnt[col], s0 = colinfo[3 * col + 1];
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int i = k < cnt ? colatoms[st + k] : -1;
+    const unsigned long long zi = i >= 0 ? z_key(ref[3 * i + 2]) : 0ull;
+    int rank = 0;
+    for (int t0 = 0; t0 < cnt; t0 += kRankTile) {
+      const int nt = min(kRankTile, cnt - t0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const int j = colatoms[st + t0 + t];
+        js[t] = j;
+        zs[t] = z_key(ref[3 * j + 2]);
+      }
+      __syncthreads();
+      if (i >= 0)
+        for (int t = 0; t < nt; ++t) rank += (zs[t] < zi) || (zs[t] == zi && js[t] < i);
+    }
+    if (i >= 0) {
+      perm[s0 + rank] = i;
+      slot[i] = s0 + rank;
+    }
   }
-  const int s = colinfo[3 * col + 1] + rank;
-  perm[s] = i;
-  slot[i] = s;
 }
 
 // Mixed precision: the caller's FP32 coordinate x taken at the periodic image nearest its
@@ -726,8 +746,7 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
   MOP_KL();
   k_fill_columns<<<nblk(Q, bs), bs, 0, st>>>(Q, P.colid.p, P.colinfo.p, P.colatoms.p);
   MOP_KL();
-  k_rank<<<nblk(Q, bs), bs, 0, st>>>(Q, P.ref.p, P.colid.p, P.colcnt.p, P.colinfo.p, P.colatoms.p, P.perm.p,
-                                     P.slot.p);
+  k_rank<<<ncol, bs, 0, st>>>(P.ref.p, P.colcnt.p, P.colinfo.p, P.colatoms.p, P.perm.p, P.slot.p);
   MOP_KL();
   if (f64) {
     k_cluster_bbox<<<nblk((long long)max_clu * 32, bs), bs, 0, st>>>(sc, x32, x64, N, P.ref.p, P.perm.p, P.meta.p,
