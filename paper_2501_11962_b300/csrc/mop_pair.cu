@@ -310,6 +310,9 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
 #ifndef MOP_ILV
 #define MOP_ILV 1
 #endif
+#ifndef MOP_ILV_ALL
+#define MOP_ILV_ALL 0   // 1: also for the reaction-field HVP and FD kernels
+#endif
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -592,13 +595,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       eps[b] = (R)(mx > 0.f ? sc.fd_h / (double)mx : sc.fd_h);
     }
   }
-  const V4* __restrict__ xqs[B];
-  size_t eos[B];
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    eos[b] = (size_t)nb[b] * P.Qpad;
-    xqs[b] = Tr<R>::xq(P) + eos[b];
-  }
+  // slot offset of the unit's first bead, and of its last bead from the first
+  const size_t eos0 = (size_t)nb[0] * P.Qpad;
+  const int edb = (nb[B - 1] - nb[0]) * P.Qpad;
   // half list: j-side flush constants; atom j gets -f, or +f / (2 eps) in FD mode
   float jscale[B];
 #pragma unroll
@@ -622,7 +621,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   constexpr bool PACK = MOP_PACK2 && sizeof(R) == 4 && B == 2;
   // interleaved j staging: measured faster for the force kernels and the Ewald HVP (-0.15 to
   // -0.21 ms per pass on the 150k-atom path), slower for the reaction-field HVP (+0.12 ms)
-  constexpr bool ILV = PACK && MOP_ILV && (MODE == 0 || EW);
+  constexpr bool ILV = PACK && MOP_ILV && (MODE == 0 || EW || MOP_ILV_ALL);
   float2 a2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   float2 ei2[3];
 #pragma unroll
@@ -685,8 +684,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         ft = __ldg(&P.ts[sj]);
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-          fx[b] = xqs[b][sj];
-          if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, eos[b] + sj);
+          const size_t o = eos0 + (b ? edb : 0) + sj;
+          fx[b] = Tr<R>::xq(P)[o];
+          if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, o);
         }
       }
     };

@@ -76,6 +76,26 @@ def test_tiny_ragged_system_matches_oracle(prec):
     assert rel(G, r["G"]) < TOL_F * tol
 
 
+def test_sort_with_equal_and_zero_z_matches_oracle():
+    """The spatial sort ranks atoms inside a column by (z of bead 1, atom index).  Four atoms at
+    z = 0 exactly and two with equal z (all 13 atoms share one column here) must still get
+    distinct slots: any slot collision loses an atom and breaks parity."""
+    sys, pos = tiny_system()
+    X = tiny_path(pos)
+    for a in (6, 7, 8, 9):
+        X[0, a, 2] = np.float32(0.0)
+    X[0, 11, 2] = X[0, 10, 2]
+    eng = mop.Engine(sys)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff(X.astype(np.float64), want=("G", "F", "Heta"), hvp_mode=oracle.HVP_ANALYTIC)
+    N = X.shape[0]
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V
+    assert rel(eng.get_field(0, mop.MOP_FIELD_FORCE)[:N - 1], r["F"][:N - 1]) < TOL_F
+    assert rel(eng.get_field(0, mop.MOP_FIELD_HETA)[:N - 1], r["Heta"][:N - 1]) < TOL_H
+    assert rel(G, r["G"]) < TOL_F
+
+
 def test_tiny_ragged_system_with_spme_matches_oracle():
     sys, pos = tiny_system()
     sys = synth.with_pme(sys)
