@@ -483,6 +483,11 @@ template <class R, int B> struct Stage {
   R hl[B][6][32];            // folded sums: hi x 3, lo x 3 (FP32 mode)
   // half list (FP32 mode): j-side partials of kJBatch entries
   float jp[kJBatch][kCL * kJpRow];
+  // FP32 HVP and FD units: the j fetch's base pointers (coordinates and eta of the unit's first
+  // bead, types), kept here instead of in registers
+  const float4* fxq;
+  const float4* feta;
+  const int* fts;
 };
 
 template <class R, class V4>
@@ -648,6 +653,17 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       for (int c = 0; c < 6; ++c) S.hl[b][c][lane] = 0.f;
   }
   Acc1<R> eacc;
+  // HVP and FD kernels (FP32): the j fetch's base pointers live in shared memory, freeing
+  // registers (spill 24 -> 8 B, H eta 16.68 -> 16.60 ms on the 150k-atom path); the force
+  // kernels measured slower that way (13.01 -> 13.33 ms) and keep them in registers
+  constexpr bool SPTR = sizeof(R) == 4 && MODE >= 1;
+  if constexpr (SPTR) {
+    if (lane == 0) {
+      S.fxq = P.xq + eos0;
+      S.feta = P.eta32 + eos0;
+      S.fts = P.ts;
+    }
+  }
   const int cnt = __ldg(&P.lcnt[ci]);
   const size_t eb = (size_t)ci * P.cap;
   const int mshift = jj * kCL + i;   // exclusion bit of pair (i, jj); pair (i, jj + 4) is 32 higher
@@ -681,12 +697,23 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       const int e = 4 * blk + sk;
       if (e < nc) {
         const int sj = (S.ent[e].x & kCluMask) * kCL + sa;
-        ft = __ldg(&P.ts[sj]);
+        if constexpr (SPTR) {
+          ft = __ldg(S.fts + sj);
+          const float4* xb = S.fxq;
+          const float4* eb4 = S.feta;
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-          const size_t o = eos0 + (b ? edb : 0) + sj;
-          fx[b] = Tr<R>::xq(P)[o];
-          if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, o);
+          for (int b = 0; b < B; ++b) {
+            fx[b] = __ldg(xb + (b ? edb : 0) + sj);
+            if (MODE >= 1) fe[b] = __ldg(eb4 + (b ? edb : 0) + sj);
+          }
+        } else {
+          ft = __ldg(&P.ts[sj]);
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const size_t o = eos0 + (b ? edb : 0) + sj;
+            fx[b] = Tr<R>::xq(P)[o];
+            if (MODE >= 1) fe[b] = load_eta4<R, V4>(P, o);
+          }
         }
       }
     };
