@@ -687,7 +687,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       }
       S.ent[lane] = en;
       S.m[lane] = m;
-      S.d[lane] = dv;
+      if constexpr (sizeof(R) == 8) S.d[lane] = dv;
     }
     __syncwarp();
     V4 fx[B], fe[B];
@@ -742,14 +742,23 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
 #pragma unroll kQUnroll
       for (int q = 0; q < 4; ++q) {
         const int e = 4 * blk + q;
-        const int fl = S.ent[e].x;
+        // FP32: one 128-bit read gives the entry's flags and its Delta (y, z, w)
+        const int4 E = S.ent[e];
+        const int fl = E.x;
         R rcA = k.rc2, rcB = k.rc2;
         if (fl < 0) {
           const unsigned long long m = S.m[e] >> mshift;
           rcA = (m & 1ull) ? R(-1) : k.rc2;
           rcB = ((m >> 32) & 1ull) ? R(-1) : k.rc2;
         }
-        const V4 D = S.d[e];
+        V4 D;
+        if constexpr (sizeof(R) == 4) {
+          D.x = __int_as_float(E.y);
+          D.y = __int_as_float(E.z);
+          D.z = __int_as_float(E.w);
+        } else {
+          D = S.d[e];
+        }
         const int so = q * kCL + jj;
         const R ew = (fl & kSelfFlag) ? R(0.5) : R(1);   // the self entry sees each pair twice
         R jf[2][3][B];
