@@ -762,12 +762,14 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         const int so = q * kCL + jj;
         const R ew = (fl & kSelfFlag) ? R(0.5) : R(1);   // the self entry sees each pair twice
         R jf[2][3][B];
+        if constexpr (!PACK) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int b = 0; b < B; ++b) jf[h][c][b] = R(0);
+              for (int b = 0; b < B; ++b) jf[h][c][b] = R(0);
+        }
         R xs[B][3];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -806,11 +808,10 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
             float2 f2[3];
             pair_two<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), xs2, xj2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a,
                                        make_float2((float)eps[0], (float)eps[B - 1]));
+            // straight to this lane's staging row; the row of a half without its bit is never read
+            float2* w = reinterpret_cast<float2*>(S.jp[q % kJBatch] + J.w) + h * 12;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              jf[h][c][0] = f2[c].x;
-              jf[h][c][B - 1] = f2[c].y;
-            }
+            for (int c = 0; c < 3; ++c) w[c] = f2[c];
             continue;
           }
 #pragma unroll
@@ -837,7 +838,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           }
         }
         if constexpr (HALF) {
-          j_stage<B>(S.jp[q % kJBatch], J, jf);
+          if constexpr (!PACK) j_stage<B>(S.jp[q % kJBatch], J, jf);
           if (q % kJBatch == kJBatch - 1) j_flush<B>(J, S, e - (kJBatch - 1), jacc, jscale);
         }
       }
