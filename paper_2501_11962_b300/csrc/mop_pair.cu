@@ -310,8 +310,8 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
 #ifndef MOP_ILV
 #define MOP_ILV 1
 #endif
-// packed units skip a listed half with no pair within rc in either bead (warp vote); on for the
-// Ewald kernels and the reaction-field HVP (the reaction-field force kernel measured slower)
+// packed units skip a listed half with no pair within rc in either bead (warp vote); FD units
+// with the radius rc + 2 h of their displaced pairs
 #ifndef MOP_SKIP
 #define MOP_SKIP 1
 #endif
@@ -632,10 +632,11 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   // interleaved j staging: measured faster for the force kernels and the Ewald HVP (-0.15 to
   // -0.21 ms per pass on the 150k-atom path), slower for the reaction-field HVP (+0.12 ms)
   constexpr bool ILV = PACK && MOP_ILV && (MODE == 0 || EW || MOP_ILV_ALL);
-  // half skipping by warp vote: measured faster for the Ewald force (-0.45 ms) and H eta
-  // (-0.87 ms) and the reaction-field H eta (-0.06 ms), slower for the reaction-field force
-  // (+0.22 ms); never for FD, whose pairs are evaluated at displaced positions
-  constexpr bool SKIP = PACK && MOP_SKIP && (MODE == 1 || (MODE == 0 && EW));
+  // half skipping by warp vote (measured faster for every packed kernel)
+  constexpr bool SKIP = PACK && MOP_SKIP;
+  // FD pairs sit at d +- u with |u| = eps |eta_i - eta_j| <= 2 h (eps = h / max |eta|): a half
+  // with no |d| < rc + 2 h in either bead holds no pair the FD difference can see
+  const float rskip2 = MODE == 2 ? (float)((sc.rc + 2.0 * sc.fd_h) * (sc.rc + 2.0 * sc.fd_h)) : 0.f;
   float2 a2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   float2 ei2[3];
 #pragma unroll
@@ -793,6 +794,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           const int sj = so + 4 * h;
           const R qj = ILV ? S.x[B - 1][sj].z : S.x[0][sj].w;
           const R rce = h ? rcB : rcA;
+          // the type-pair row is read before the skip vote: read after it, its latency showed
+          // (reaction-field force 12.27 -> 12.66 ms, H eta 15.42 -> 15.70 ms)
+          const V4 tp = tabrow[S.t[sj]];
           if constexpr (PACK) {
             const float2 xs2[3] = {make_float2(xs[0][0], xs[B - 1][0]), make_float2(xs[0][1], xs[B - 1][1]),
                                    make_float2(xs[0][2], xs[B - 1][2])};
@@ -820,12 +824,13 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
               // that the flush does not read the row either
               const float2 d0 = sub2(xs2[0], xj2[0]), d1 = sub2(xs2[1], xj2[1]), d2 = sub2(xs2[2], xj2[2]);
               const float2 r2 = fma2(d0, d0, fma2(d1, d1, mul2(d2, d2)));
-              if (!__any_sync(0xffffffffu, r2.x < rce || r2.y < rce)) {
+              const float rv = MODE == 2 ? (rce > 0.f ? rskip2 : -1.f) : rce;
+              if (!__any_sync(0xffffffffu, r2.x < rv || r2.y < rv)) {
                 if (lane == 0) S.ent[e].x &= ~(1 << (29 + h));
                 continue;
               }
             }
-            const PairK<R> pc = pair_consts<R, MODE, V4>(k, tabrow[S.t[sj]], qi * qj);
+            const PairK<R> pc = pair_consts<R, MODE, V4>(k, tp, qi * qj);
             float2 f2[3];
             pair_two<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), xs2, xj2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a,
                                        make_float2((float)eps[0], (float)eps[B - 1]));
@@ -835,7 +840,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
             for (int c = 0; c < 3; ++c) w[c] = f2[c];
             continue;
           }
-          const PairK<R> pc = pair_consts<R, MODE, V4>(k, tabrow[S.t[sj]], qi * qj);
+          const PairK<R> pc = pair_consts<R, MODE, V4>(k, tp, qi * qj);
 #pragma unroll
           for (int b = 0; b < B; ++b) {
             R ej[3] = {R(0), R(0), R(0)};
