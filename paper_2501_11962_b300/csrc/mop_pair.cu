@@ -370,12 +370,12 @@ __device__ __forceinline__ void ewald_terms2(const Cst<float>& k, float2 r2, flo
 // xj: the i- and j-atom per dimension (bead x, bead y), one of them shifted by the entry's Delta;
 // ei/ej eta (MODE 1).  Adds the i-side term to a and returns it in f.  ENERGY: also adds ew times
 // the pair energy of bead x (the first bead of the unit) to e.
+// pair_two_d takes the separation d = xs - xj and r2 = |d|^2 already formed (r2 unused by FD).
 template <int MODE, bool EW, bool ENERGY = false>
-__device__ __forceinline__ void pair_two(const Cst<float>& k, const PairK2& c, const float2 (&xs)[3], const float2 (&xj)[3],
-                                         float rc2e, const float2 (&ei)[3], const float2 (&ej)[3], float2 (&a)[3],
-                                         float2 (&f)[3], const PairK<float>* ce = nullptr, float ew = 0.f,
-                                         float* e = nullptr, float2 eps2 = float2{0.f, 0.f}) {
-  const float2 d[3] = {sub2(xs[0], xj[0]), sub2(xs[1], xj[1]), sub2(xs[2], xj[2])};
+__device__ __forceinline__ void pair_two_d(const Cst<float>& k, const PairK2& c, const float2 (&d)[3], float2 r2,
+                                           float rc2e, const float2 (&ei)[3], const float2 (&ej)[3], float2 (&a)[3],
+                                           float2 (&f)[3], const PairK<float>* ce = nullptr, float ew = 0.f,
+                                           float* e = nullptr, float2 eps2 = float2{0.f, 0.f}) {
   if constexpr (MODE == 2) {
     // F(+) - F(-) at the pair separated by d +- eps (e_i - e_j), both beads at once
     const float2 u[3] = {mul2(eps2, sub2(ei[0], ej[0])), mul2(eps2, sub2(ei[1], ej[1])), mul2(eps2, sub2(ei[2], ej[2]))};
@@ -405,7 +405,6 @@ __device__ __forceinline__ void pair_two(const Cst<float>& k, const PairK2& c, c
     for (int t = 0; t < 3; ++t) a[t] = add2(a[t], f[t]);
     return;
   }
-  const float2 r2 = fma2(d[0], d[0], fma2(d[1], d[1], mul2(d[2], d[2])));
   const bool in0 = r2.x < rc2e, in1 = r2.y < rc2e;
   const float2 rinv = rsq2(r2);
   const float2 rinv2 = mul2(rinv, rinv);
@@ -456,6 +455,16 @@ __device__ __forceinline__ void pair_two(const Cst<float>& k, const PairK2& c, c
       a[q] = add2(a[q], f[q]);
     }
   }
+}
+
+template <int MODE, bool EW, bool ENERGY = false>
+__device__ __forceinline__ void pair_two(const Cst<float>& k, const PairK2& c, const float2 (&xs)[3], const float2 (&xj)[3],
+                                         float rc2e, const float2 (&ei)[3], const float2 (&ej)[3], float2 (&a)[3],
+                                         float2 (&f)[3], const PairK<float>* ce = nullptr, float ew = 0.f,
+                                         float* e = nullptr, float2 eps2 = float2{0.f, 0.f}) {
+  const float2 d[3] = {sub2(xs[0], xj[0]), sub2(xs[1], xj[1]), sub2(xs[2], xj[2])};
+  const float2 r2 = MODE == 2 ? float2{0.f, 0.f} : fma2(d[0], d[0], fma2(d[1], d[1], mul2(d[2], d[2])));
+  pair_two_d<MODE, EW, ENERGY>(k, c, d, r2, rc2e, ei, ej, a, f, ce, ew, e, eps2);
 }
 
 // j-partial staging of one entry: value (h, c, b) of i-lane ii and j-atom jq at
@@ -818,12 +827,13 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
               ej2[1] = make_float2(ej0.y, ej1.y);
               ej2[2] = make_float2(ej0.z, ej1.z);
             }
+            // separation and squared distance of both beads, shared by the skip vote and the pair
+            const float2 dd[3] = {sub2(xs2[0], xj2[0]), sub2(xs2[1], xj2[1]), sub2(xs2[2], xj2[2])};
+            const float2 r2 = fma2(dd[0], dd[0], fma2(dd[1], dd[1], mul2(dd[2], dd[2])));
             if constexpr (SKIP) {
               // the list holds this half for some bead of the path; when no lane has a pair
               // within rc in either bead of the unit, the warp skips it and clears its bit, so
               // that the flush does not read the row either
-              const float2 d0 = sub2(xs2[0], xj2[0]), d1 = sub2(xs2[1], xj2[1]), d2 = sub2(xs2[2], xj2[2]);
-              const float2 r2 = fma2(d0, d0, fma2(d1, d1, mul2(d2, d2)));
               const float rv = MODE == 2 ? (rce > 0.f ? rskip2 : -1.f) : rce;
               if (!__any_sync(0xffffffffu, r2.x < rv || r2.y < rv)) {
                 if (lane == 0) S.ent[e].x &= ~(1 << (29 + h));
@@ -832,8 +842,8 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
             }
             const PairK<R> pc = pair_consts<R, MODE, V4>(k, tp, qi * qj);
             float2 f2[3];
-            pair_two<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), xs2, xj2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a,
-                                       make_float2((float)eps[0], (float)eps[B - 1]));
+            pair_two_d<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), dd, r2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a,
+                                         make_float2((float)eps[0], (float)eps[B - 1]));
             // straight to this lane's staging row; the row of a half without its bit is never read
             float2* w = reinterpret_cast<float2*>(S.jp[q % kJBatch] + J.w) + h * 12;
 #pragma unroll
