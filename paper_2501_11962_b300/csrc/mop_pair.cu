@@ -742,8 +742,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
     for (int blk = 0; blk < nblk; ++blk) {
       __syncwarp();
       if constexpr (ILV) {
+        // (z, z', q, type): the packed kernels read the j type from here, not from S.t
         S.x[0][lane] = V4{fx[0].x, fx[B - 1].x, fx[0].y, fx[B - 1].y};
-        S.x[B - 1][lane] = V4{fx[0].z, fx[B - 1].z, fx[0].w, fx[0].w};
+        S.x[B - 1][lane] = V4{fx[0].z, fx[B - 1].z, fx[0].w, __int_as_float(ft)};
         if (MODE >= 1) {
           S.e[0][lane] = V4{fe[0].x, fe[B - 1].x, fe[0].y, fe[B - 1].y};
           S.e[B - 1][lane] = V4{fe[0].z, fe[B - 1].z, R(0), R(0)};
@@ -755,7 +756,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           if (MODE >= 1) S.e[b][lane] = fe[b];
         }
       }
-      S.t[lane] = ft;
+      if constexpr (!ILV) S.t[lane] = ft;
       __syncwarp();
       if (blk + 1 < nblk) fetch(blk + 1);
       // entries past the end of the chunk were staged with no half bits
@@ -805,7 +806,9 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           const R rce = h ? rcB : rcA;
           // the type-pair row is read before the skip vote: read after it, its latency showed
           // (reaction-field force 12.27 -> 12.66 ms, H eta 15.42 -> 15.70 ms)
-          const V4 tp = tabrow[S.t[sj]];
+          // interleaved staging carries the j type in (z, z', q, type); measured for the other
+          // layout too (bead 1's w), where the H eta kernel lost 0.1 ms
+          const V4 tp = tabrow[ILV ? __float_as_int(S.x[B - 1][sj].w) : S.t[sj]];
           if constexpr (PACK) {
             const float2 xs2[3] = {make_float2(xs[0][0], xs[B - 1][0]), make_float2(xs[0][1], xs[B - 1][1]),
                                    make_float2(xs[0][2], xs[B - 1][2])};
