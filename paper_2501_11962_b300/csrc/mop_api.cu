@@ -364,15 +364,20 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
                         (long long)p0 * D.n_clu));
       CK(h, launch_excl(sc, h->d_paths.p, 1, max_n, fd ? 2 : 1, L, b0, hb1 - b0));
       CK(h, launch_e2(sc, h->d_paths.p, 1, max_qpad, max_n, L, h->e_spring.p, nbx, b0, b1 - b0));
-      // the bias adds to bead N (last chunk) and, for an end-to-end CV, to bead 1: copy those after it
-      if (c == kCopyChunks - 1 || (c == 0 && e2e_cv)) {
-        after_bias.push_back({b0, b1});
-        continue;
-      }
+      // the bias adds to the row of bead N and, for an end-to-end CV, of bead 1: those rows are
+      // copied after it, the rest of the chunk now
       CK(h, cudaEventRecord(h->cev[c], st));
       CK(h, cudaStreamWaitEvent(h->copy_stream, h->cev[c], 0));
-      CK(h, cudaMemcpyAsync(host_grad + b0 * row, gdev + b0 * row, sizeof(double) * row * (b1 - b0),
-                            cudaMemcpyDeviceToHost, h->copy_stream));
+      int r0 = b0;
+      for (int b = b0; b <= b1; ++b) {
+        const bool touched = b < b1 && (b == N - 1 || (b == 0 && e2e_cv));
+        if (b < b1 && !touched) continue;
+        if (b > r0)
+          CK(h, cudaMemcpyAsync(host_grad + r0 * row, gdev + r0 * row, sizeof(double) * row * (b - r0),
+                                cudaMemcpyDeviceToHost, h->copy_stream));
+        if (touched) after_bias.push_back({b, b + 1});
+        r0 = b + 1;
+      }
     }
     CK(h, mark(4));
     CK(h, mark(5));
