@@ -491,8 +491,8 @@ template <class R, int B> struct Stage {
   V4 x[B][32];               // j coordinates + charge
   V4 e[B][32];               // j eta (HVP / FD)
   V4 d[32];                  // Delta of each staged entry
-  int4 ent[32];              // entries of the chunk
-  unsigned long long m[32];  // exclusion masks of the chunk
+  int4 ent[2][32];              // entries of the chunk (FP32: two buffers, the next chunk in flight)
+  unsigned long long m[2][32];  // exclusion masks of the chunk
   int t[32];                 // j types
   R hl[B][6][32];            // folded sums: hi x 3, lo x 3 (FP32 mode)
   // half list (FP32 mode): j-side partials of kJBatch entries
@@ -536,6 +536,21 @@ __device__ __forceinline__ unsigned long long to_fix(float s) {
   return (unsigned long long)__float2ll_rn(s * kFixScale);
 }
 
+// cp.async (sm_80+): global -> shared copies that bypass registers; waited with wait_group 0
+#ifndef MOP_ASYNC_ENT
+#define MOP_ASYNC_ENT 1
+#endif
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Per-lane constants of the half-list j-side flush, fixed for a whole unit.
 struct JFlush {
   int w;         // float offset of this lane's 12 j-partials in a staging slot
@@ -564,12 +579,12 @@ __device__ __forceinline__ void j_stage(float* slot, const JFlush& J, const floa
 // The self entry and entries past the end of the chunk add nothing.  jscale[b] maps a sum to
 // the value added (sign and FD scale).
 template <int B>
-__device__ __forceinline__ void j_flush(const JFlush& J, Stage<float, B>& S, int e0, unsigned long long* jacc,
+__device__ __forceinline__ void j_flush(const JFlush& J, Stage<float, B>& S, int cb, int e0, unsigned long long* jacc,
                                         const float* jscale) {
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < kJBatch; ++q) {
-    const int fl = S.ent[e0 + q].x;
+    const int fl = S.ent[cb][e0 + q].x;
     if ((fl & J.hbit) && !(fl & kSelfFlag)) {
       const float* r = &S.jp[q][J.r];
       float2 t[kCL];
@@ -688,10 +703,32 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   const size_t eb = (size_t)ci * P.cap;
   const int mshift = jj * kCL + i;   // exclusion bit of pair (i, jj); pair (i, jj + 4) is 32 higher
   const int sa = lane & 7, sk = lane >> 3;   // staging role: atom sa of block entry sk
+  // force kernels: each 32-entry chunk of the list (entries and masks) is copied into shared
+  // memory by cp.async while the previous chunk is processed; entries past the list are zero (no
+  // bits).  Measured: reaction-field force 12.20 -> 12.05 ms; the H eta kernels lost (+0.08 ms,
+  // Ewald +0.94 ms) and load each chunk when they reach it.
+  constexpr bool ASYNC = sizeof(R) == 4 && MOP_ASYNC_ENT && MODE == 0;
+  auto issue = [&](int c0n, int buf) __attribute__((always_inline)) {
+    if (lane < cnt - c0n) {
+      cp_async16(&S.ent[buf][lane], &P.ent[eb + c0n + lane]);
+      cp_async8(&S.m[buf][lane], &P.emask[eb + c0n + lane]);
+    } else {
+      S.ent[buf][lane] = make_int4(0, 0, 0, 0);
+    }
+    cp_async_commit();
+  };
+  int cb = 0;
+  if constexpr (ASYNC) {
+    if (cnt > 0) issue(0, 0);
+  }
   for (int c0 = 0; c0 < cnt; c0 += 32) {
     const int nc = min(32, cnt - c0);
     __syncwarp();
-    {
+    if constexpr (ASYNC) {
+      cp_async_wait_all();
+      __syncwarp();
+      if (c0 + 32 < cnt) issue(c0 + 32, cb ^ 1);
+    } else {
       int4 en = make_int4(0, 0, 0, 0);
       unsigned long long m = 0ull;
       V4 dv;
@@ -705,18 +742,18 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         dv.z = D[2];
         dv.w = R(0);
       }
-      S.ent[lane] = en;
-      S.m[lane] = m;
+      S.ent[cb][lane] = en;
+      S.m[cb][lane] = m;
       if constexpr (sizeof(R) == 8) S.d[lane] = dv;
+      __syncwarp();
     }
-    __syncwarp();
     V4 fx[B], fe[B];
     int ft = 0;
     // forced inline: as a call, fx and fe would live in local memory
     auto fetch = [&](int blk) __attribute__((always_inline)) {
       const int e = 4 * blk + sk;
       if (e < nc) {
-        const int sj = (S.ent[e].x & kCluMask) * kCL + sa;
+        const int sj = (S.ent[cb][e].x & kCluMask) * kCL + sa;
         if constexpr (SPTR) {
           ft = __ldg(S.fts + sj);
           const float4* xb = S.fxq;
@@ -764,11 +801,11 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
       for (int q = 0; q < 4; ++q) {
         const int e = 4 * blk + q;
         // FP32: one 128-bit read gives the entry's flags and its Delta (y, z, w)
-        const int4 E = S.ent[e];
+        const int4 E = S.ent[cb][e];
         const int fl = E.x;
         R rcA = k.rc2, rcB = k.rc2;
         if (fl < 0) {
-          const unsigned long long m = S.m[e] >> mshift;
+          const unsigned long long m = S.m[cb][e] >> mshift;
           rcA = (m & 1ull) ? R(-1) : k.rc2;
           rcB = ((m >> 32) & 1ull) ? R(-1) : k.rc2;
         }
@@ -839,7 +876,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
               // that the flush does not read the row either
               const float rv = MODE == 2 ? (rce > 0.f ? rskip2 : -1.f) : rce;
               if (!__any_sync(0xffffffffu, r2.x < rv || r2.y < rv)) {
-                if (lane == 0) S.ent[e].x &= ~(1 << (29 + h));
+                if (lane == 0) S.ent[cb][e].x &= ~(1 << (29 + h));
                 continue;
               }
             }
@@ -879,7 +916,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         }
         if constexpr (HALF) {
           if constexpr (!PACK) j_stage<B>(S.jp[q % kJBatch], J, jf);
-          if (q % kJBatch == kJBatch - 1) j_flush<B>(J, S, e - (kJBatch - 1), jacc, jscale);
+          if (q % kJBatch == kJBatch - 1) j_flush<B>(J, S, cb, e - (kJBatch - 1), jacc, jscale);
         }
       }
       if ((blk & 3) == 3) {
@@ -888,6 +925,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
         if (ENERGY) eacc.fold();
       }
     }
+    if constexpr (ASYNC) cb ^= 1;
   }
   unpack();
   fold_into<R, B>(S, a, lane);
