@@ -315,6 +315,11 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
 #ifndef MOP_SKIP
 #define MOP_SKIP 1
 #endif
+// adjoint H eta kernels read the j eta after the skip vote (H eta -0.09 ms, Ewald H eta
+// -0.32 ms on the 150k-atom path; the FD kernels measured 1% slower that way and read it before)
+#ifndef MOP_EJ_LATE
+#define MOP_EJ_LATE 1
+#endif
 #ifndef MOP_ILV_ALL
 #define MOP_ILV_ALL 0   // 1: also for the reaction-field HVP and FD kernels
 #endif
@@ -849,24 +854,32 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           if constexpr (PACK) {
             const float2 xs2[3] = {make_float2(xs[0][0], xs[B - 1][0]), make_float2(xs[0][1], xs[B - 1][1]),
                                    make_float2(xs[0][2], xs[B - 1][2])};
-            const V4 ej0 = MODE >= 1 ? S.e[0][sj] : V4{}, ej1 = MODE >= 1 ? S.e[B - 1][sj] : V4{};
             const V4 xj0 = S.x[0][sj], xj1 = S.x[B - 1][sj];
             float2 xj2[3], ej2[3];
             if constexpr (ILV) {
               xj2[0] = make_float2(xj0.x, xj0.y);
               xj2[1] = make_float2(xj0.z, xj0.w);
               xj2[2] = make_float2(xj1.x, xj1.y);
-              ej2[0] = make_float2(ej0.x, ej0.y);
-              ej2[1] = make_float2(ej0.z, ej0.w);
-              ej2[2] = make_float2(ej1.x, ej1.y);
             } else {
               xj2[0] = make_float2(xj0.x, xj1.x);
               xj2[1] = make_float2(xj0.y, xj1.y);
               xj2[2] = make_float2(xj0.z, xj1.z);
-              ej2[0] = make_float2(ej0.x, ej1.x);
-              ej2[1] = make_float2(ej0.y, ej1.y);
-              ej2[2] = make_float2(ej0.z, ej1.z);
             }
+            // the j-atom's eta (HVP, FD), read after the skip vote
+            auto load_ej = [&]() __attribute__((always_inline)) {
+              const V4 ej0 = MODE >= 1 ? S.e[0][sj] : V4{}, ej1 = MODE >= 1 ? S.e[B - 1][sj] : V4{};
+              if constexpr (ILV) {
+                ej2[0] = make_float2(ej0.x, ej0.y);
+                ej2[1] = make_float2(ej0.z, ej0.w);
+                ej2[2] = make_float2(ej1.x, ej1.y);
+              } else {
+                ej2[0] = make_float2(ej0.x, ej1.x);
+                ej2[1] = make_float2(ej0.y, ej1.y);
+                ej2[2] = make_float2(ej0.z, ej1.z);
+              }
+            };
+            constexpr bool EJL = MOP_EJ_LATE && MODE == 1;
+            if constexpr (!EJL) load_ej();
             // separation and squared distance of both beads, shared by the skip vote and the pair
             const float2 dd[3] = {sub2(xs2[0], xj2[0]), sub2(xs2[1], xj2[1]), sub2(xs2[2], xj2[2])};
             const float2 r2 = fma2(dd[0], dd[0], fma2(dd[1], dd[1], mul2(dd[2], dd[2])));
@@ -880,6 +893,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
                 continue;
               }
             }
+            if constexpr (EJL) load_ej();
             const PairK<R> pc = pair_consts<R, MODE, V4>(k, tp, qi * qj);
             float2 f2[3];
             pair_two_d<MODE, EW, ENERGY>(k, pair_consts2<MODE>(pc), dd, r2, rce, ei2, ej2, a2, f2, &pc, ew, &eacc.a,
