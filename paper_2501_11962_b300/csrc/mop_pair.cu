@@ -493,12 +493,12 @@ constexpr int kQUnroll = MOP_Q_UNROLL;
 // sums (hi, lo) of every lane.
 template <class R, int B> struct Stage {
   using V4 = typename Tr<R>::V4;
-  V4 x[B][32];               // j coordinates + charge
-  V4 e[B][32];               // j eta (HVP / FD)
-  V4 d[32];                  // Delta of each staged entry
-  int4 ent[2][32];              // entries of the chunk (FP32: two buffers, the next chunk in flight)
+  V4 x[B][32];                  // j coordinates + charge (interleaved layout: x x' y y', z z' q type)
+  V4 e[B][32];                  // j eta (HVP / FD)
+  V4 d[32];                     // Delta of each staged entry (FP64; FP32 reads it from the entry)
+  int4 ent[2][32];              // entries of the chunk (force kernels: two buffers, the next in flight)
   unsigned long long m[2][32];  // exclusion masks of the chunk
-  int t[32];                 // j types
+  int t[32];                    // j types (layouts without the type in x)
   R hl[B][6][32];            // folded sums: hi x 3, lo x 3 (FP32 mode)
   // half list (FP32 mode): j-side partials of kJBatch entries
   float jp[kJBatch][kCL * kJpRow];
@@ -567,7 +567,8 @@ struct JFlush {
 };
 
 // Stores this lane's j-side contributions of one entry: jf[h][c][b] belongs to j-atom
-// (lane >> 3) + 4h, component c, bead b.
+// (lane >> 3) + 4h, component c, bead b (unpacked units; packed units store each active half
+// right after its pair evaluation).
 template <int B>
 __device__ __forceinline__ void j_stage(float* slot, const JFlush& J, const float (&jf)[2][3][B]) {
   static_assert(B == 2, "the j-partial layout holds two beads");
@@ -581,8 +582,8 @@ __device__ __forceinline__ void j_stage(float* slot, const JFlush& J, const floa
 // Half list: sums the staged j-side contributions of kJBatch entries (the first is entry e0 of
 // the chunk) over the 8 i-lanes in a fixed order and adds them, fixed point, to each
 // j-cluster's atoms of both beads.  Lane < 24 reads j-atom a = lane / 3, component lane % 3.
-// The self entry and entries past the end of the chunk add nothing.  jscale[b] maps a sum to
-// the value added (sign and FD scale).
+// The self entry, entries past the end of the chunk and halves whose bit is clear (not listed, or
+// skipped by the vote) add nothing.  jscale[b] maps a sum to the value added (sign and FD scale).
 template <int B>
 __device__ __forceinline__ void j_flush(const JFlush& J, Stage<float, B>& S, int cb, int e0, unsigned long long* jacc,
                                         const float* jscale) {
