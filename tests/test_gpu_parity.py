@@ -290,3 +290,30 @@ def test_autograd_gradient_matches_central_differences():
         fd = (vp - vm) / (2.0 * h)
         an = float((G * D).sum())
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1.0), (fd, an)
+
+
+def test_spread_out_beads_skip_empty_halves_and_match_oracle():
+    """Beads 4..6 of the path are those of beads 1..3 moved by 0.25 nm along x.  The list, built
+    from each atom's union over all beads, then holds many half-clusters that have no pair within
+    rc for a given bead pair; the pair kernels skip those by warp vote and clear their bits for
+    the j-side flush (the force, adjoint H eta and FD kernels).  Results match the oracle."""
+    w = workload(2, n_beads=3)
+    X3 = w.paths[0]
+    X = np.concatenate([X3, X3 + np.float32(0.25) * np.array([1.0, 0.0, 0.0], np.float32)]).astype(np.float32)
+    N = X.shape[0]
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "Heta"), hvp_mode=oracle.HVP_ANALYTIC)
+    eng = mop.Engine(w.system)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V
+    assert rel(eng.get_field(0, mop.MOP_FIELD_FORCE)[:N - 1], r["F"][:N - 1]) < TOL_F
+    assert rel(eng.get_field(0, mop.MOP_FIELD_HETA)[:N - 1], r["Heta"][:N - 1]) < TOL_H
+    assert rel(G, r["G"]) < TOL_F
+    # the FD path (skip radius rc + 2h) against the oracle's analytic H eta, on the beads whose
+    # eta does not span the 0.25 nm jump (there eps = h / max |eta| is 60 times smaller and FD's
+    # own rounding error grows accordingly)
+    ef = mop.Engine(w.system, hvp_mode=mop.MOP_HVP_FD, fd_h=1e-4)
+    ef.set_path(0, X)
+    ef.veff_and_grad(0)
+    keep = [0, 1, 3, 4]
+    assert rel(ef.get_field(0, mop.MOP_FIELD_HETA)[keep], r["Heta"][keep]) < 1e-3
