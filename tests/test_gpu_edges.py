@@ -76,6 +76,31 @@ def test_tiny_ragged_system_matches_oracle(prec):
     assert rel(G, r["G"]) < TOL_F * tol
 
 
+@pytest.mark.parametrize("prec", [mop.MOP_PREC_MIXED, mop.MOP_PREC_FP64])
+def test_potential_shift_cutoff_matches_oracle(prec):
+    """The potential-shift modifier (phi(r) - phi(rc), force cut at rc) instead of the shifted
+    force.  On this 13-atom system no pair lies within FP32 rounding of rc, so both precisions
+    take the same in/out decision per pair as the oracle."""
+    sys, pos = tiny_system()
+    sys = dataclasses.replace(sys, cutoff_mode=synth.CUTOFF_POT_SHIFT)
+    X = tiny_path(pos)
+    eng = mop.Engine(sys, precision=prec)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff(X.astype(np.float64), want=("G", "F", "Heta"), hvp_mode=oracle.HVP_ANALYTIC)
+    N = X.shape[0]
+    tol = 1e-8 if prec == mop.MOP_PREC_FP64 else 1.0
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V * tol
+    assert rel(eng.get_field(0, mop.MOP_FIELD_FORCE)[:N - 1], r["F"][:N - 1]) < TOL_F * tol
+    assert rel(eng.get_field(0, mop.MOP_FIELD_HETA)[:N - 1], r["Heta"][:N - 1]) < TOL_H * tol
+    assert rel(G, r["G"]) < TOL_F * tol
+    # the shift changes the energy, not the forces inside rc: V_eff differs from the shifted-force
+    # system's by the cutoff terms
+    ref = mop.Engine(dataclasses.replace(sys, cutoff_mode=synth.CUTOFF_SHIFTED_FORCE), precision=prec)
+    ref.set_path(0, X)
+    assert ref.veff_and_grad(0)[0][0] != v[0]
+
+
 def test_sort_with_equal_and_zero_z_matches_oracle():
     """The spatial sort ranks atoms inside a column by (z of bead 1, atom index).  Four atoms at
     z = 0 exactly and two with equal z (all 13 atoms share one column here) must still get
