@@ -320,8 +320,8 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
 #ifndef MOP_EJ_LATE
 #define MOP_EJ_LATE 1
 #endif
-#ifndef MOP_ILV_ALL
-#define MOP_ILV_ALL 0   // 1: also for the reaction-field HVP and FD kernels
+#ifndef MOP_SPTR
+#define MOP_SPTR 1   // HVP and FD kernels: the j fetch's base pointers in shared memory
 #endif
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -659,9 +659,10 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   // both beads in f32x2 instructions (forces with the bead-1 energy in the first units, the
   // adjoint HVP and the FD difference)
   constexpr bool PACK = MOP_PACK2 && sizeof(R) == 4 && B == 2;
-  // interleaved j staging: measured faster for the force kernels and the Ewald HVP (-0.15 to
-  // -0.21 ms per pass on the 150k-atom path), slower for the reaction-field HVP (+0.12 ms)
-  constexpr bool ILV = PACK && MOP_ILV && (MODE == 0 || EW || MOP_ILV_ALL);
+  // interleaved j staging (with the j type in it): measured faster for every packed kernel once
+  // their registers were trimmed (reaction-field H eta 15.44 -> 15.10 ms, force -0.15 ms, Ewald
+  // -0.2 ms per pass on the 150k-atom path)
+  constexpr bool ILV = PACK && MOP_ILV;
   // half skipping by warp vote (measured faster for every packed kernel)
   constexpr bool SKIP = PACK && MOP_SKIP;
   // FD pairs sit at d +- u with |u| = eps |eta_i - eta_j| <= 2 h (eps = h / max |eta|): a half
@@ -697,7 +698,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
   // HVP and FD kernels (FP32): the j fetch's base pointers live in shared memory, freeing
   // registers (spill 24 -> 8 B, H eta 16.68 -> 16.60 ms on the 150k-atom path); the force
   // kernels measured slower that way (13.01 -> 13.33 ms) and keep them in registers
-  constexpr bool SPTR = sizeof(R) == 4 && MODE >= 1;
+  constexpr bool SPTR = sizeof(R) == 4 && MODE >= 1 && MOP_SPTR;
   if constexpr (SPTR) {
     if (lane == 0) {
       S.fxq = P.xq + eos0;
@@ -849,8 +850,7 @@ __device__ __forceinline__ void pair_unit(const SysConsts& sc, const typename Tr
           const R rce = h ? rcB : rcA;
           // the type-pair row is read before the skip vote: read after it, its latency showed
           // (reaction-field force 12.27 -> 12.66 ms, H eta 15.42 -> 15.70 ms)
-          // interleaved staging carries the j type in (z, z', q, type); measured for the other
-          // layout too (bead 1's w), where the H eta kernel lost 0.1 ms
+          // interleaved staging carries the j type in (z, z', q, type)
           const V4 tp = tabrow[ILV ? __float_as_int(S.x[B - 1][sj].w) : S.t[sj]];
           if constexpr (PACK) {
             const float2 xs2[3] = {make_float2(xs[0][0], xs[B - 1][0]), make_float2(xs[0][1], xs[B - 1][1]),
