@@ -288,11 +288,15 @@ mop_status mop_measure_fp32_peak(int32_t device, double* tflops);
  * every allocation.  Returns, in *out (device pointer, one double), the spring energy
  *     sum_{n < n_springs} sum_i K_i/2 |eta^n_i|^2,   K_i = mass_i nu_path / (2 dt_path),
  * of eta [n_springs][n_atoms][3] (device, FP64, as mop_get_field returns it) and mass
- * [n_atoms] (device, FP64), with the same deterministic two-stage reduction as
- * mop_veff_and_grad.  No handle is needed and nothing is allocated: the block partial sums live
- * in a fixed array of 65,536 doubles (512 KiB) that every GPU loading the library keeps until
- * the process exits.  n_springs * ceil(n_atoms / 256) must not exceed 65,536 (MOP_ERR_ARG
- * otherwise).  Work is enqueued on cuda_stream on the current device; the first call on a
+ * [n_atoms] (device, FP64).  The reduction is deterministic and fixed-order (FP64 sums over
+ * tiles of 256 atoms, then over the tiles); it is not the engine's reduction, so the result
+ * agrees with the E_spring of mop_veff_and_grad to rounding (within 1e-6 relative), not bit for
+ * bit.  No handle is needed and nothing is allocated: the block partial sums live in a fixed
+ * array of 65,536 doubles (512 KiB) that every GPU loading the library keeps until the process
+ * exits.  n_springs * ceil(n_atoms / 256) must not exceed 65,536 (MOP_ERR_ARG otherwise; for
+ * example up to 65,536 springs of at most 256 atoms).  Errors are taken from this call's own
+ * runtime calls: an error the caller left pending is neither cleared nor reported as this
+ * call's.  Work is enqueued on cuda_stream on the current device; the first call on a
  * device looks up the array's device address, so make it before any stream capture.  All calls
  * share the array: calls that overlap on the GPU race.  Errors: MOP_ERR_ARG, MOP_ERR_CUDA. */
 mop_status mop_spring_energy_noalloc(const double* eta, const double* mass, int32_t n_springs, int32_t n_atoms,

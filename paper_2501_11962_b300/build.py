@@ -9,12 +9,13 @@ from pathlib import Path
 HERE = Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 LIB = HERE / "libmop.so"
-SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_path.cu", "mop_pme.cu", "mop_noalloc.cu",
-           "mop_diag.cu"]
+SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_pairb.cu", "mop_path.cu", "mop_pme.cu",
+           "mop_noalloc.cu", "mop_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 # FP32 subnormals never matter for forces, so the hot kernels flush them (shorter rsqrt path)
-PER_FILE = {"mop_pair.cu": ["-ftz=true"], "mop_path.cu": ["-ftz=true"], "mop_pme.cu": ["-ftz=true"]}
+PER_FILE = {"mop_pair.cu": ["-ftz=true"], "mop_pairb.cu": ["-ftz=true"], "mop_path.cu": ["-ftz=true"],
+            "mop_pme.cu": ["-ftz=true"]}
 
 
 def _stale() -> bool:

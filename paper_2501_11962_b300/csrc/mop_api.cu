@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -209,6 +210,14 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     if (e != cudaSuccess) return fail(h, e == cudaErrorMemoryAllocation ? MOP_ERR_OOM : MOP_ERR_CUDA, "%s", err.c_str());
     const int N = P.N, Qpad = h->grid.max_clu * kCL;   // fixed slot stride (capture safe)
     const int n_force = N == 1 ? 1 : N - 1, n_hvp = N - 1;
+    if (sc.bl) {
+      // bead-lane kernels read the coordinates transposed (beads innermost)
+      CK(h, P.xb.ensure((size_t)bl_groups(n_force) * Qpad * 3 * 32));
+      CK(h, launch_bl_transpose(P.xq.p, n_force, Qpad, h->grid.max_clu, P.meta.p, P.xb.p, L));
+      if (n_hvp > 0) CK(h, P.etab.ensure((size_t)bl_groups(n_hvp) * Qpad * 3 * 32));
+    }
+    // j-side sums: the half-list kernels, and the Ewald exclusion and SPME passes
+    const bool use_jacc = h->precision == MOP_PREC_MIXED && (!sc.bl || sc.elec == 1);
     const size_t nq3 = 3 * (size_t)N * Qpad;
     CK(h, P.Fnb.ensure(3 * (size_t)n_force * Qpad));
     CK(h, P.F.ensure(nq3));
@@ -217,7 +226,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.Hnb.ensure(nq3));
     CK(h, P.Heta.ensure(nq3));
     CK(h, P.etamax.ensure(N));
-    if (h->precision == MOP_PREC_MIXED) CK(h, P.jacc.ensure(nq3));
+    if (use_jacc) CK(h, P.jacc.ensure(nq3));
     CK(h, P.e_pair.ensure(h->grid.max_clu));
     if (sc.elec == 1) CK(h, P.e_excl.ensure(std::max(1, excl_energy_blocks(sc))));
     const bool pme = sc.pme_nk > 0;
@@ -251,9 +260,10 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.meta = P.meta.p;
     D.unit_off = units;
     D.unit_off_h = units_h;
-    const int bpu = pair_beads_per_unit(h->precision);
-    units += (long long)((n_force + bpu - 1) / bpu) * h->grid.max_clu;
-    units_h += (long long)((n_hvp + bpu - 1) / bpu) * h->grid.max_clu;
+    const int bpu = sc.bl ? kBLBeads : pair_beads_per_unit(h->precision);
+    const int upc = sc.bl ? pairb_units_per_cluster() : 1;   // units per cluster and bead group
+    units += (long long)((n_force + bpu - 1) / bpu) * h->grid.max_clu * upc;
+    units_h += (long long)((n_hvp + bpu - 1) / bpu) * h->grid.max_clu * upc;
     max_qpad = std::max(max_qpad, Qpad);
     max_nf = std::max(max_nf, n_force);
     max_n = std::max(max_n, N);
@@ -277,7 +287,9 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.Hnb = P.Hnb.p;
     D.Heta = P.Heta.p;
     D.etamax = P.etamax.p;
-    D.jacc = h->precision == MOP_PREC_MIXED ? P.jacc.p : nullptr;
+    D.jacc = use_jacc ? P.jacc.p : nullptr;
+    D.xb = sc.bl ? P.xb.p : nullptr;
+    D.etab = sc.bl && n_hvp > 0 ? P.etab.p : nullptr;
     D.e_pair = P.e_pair.p;
     D.e_excl = sc.elec == 1 ? P.e_excl.p : nullptr;
     D.cwdf = P.cwdf.p;
@@ -331,7 +343,12 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   };
   CK(h, mark(1));
   CK(h, clear_jacc(false));
-  CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
+  if (sc.bl) {
+    CK(h, launch_pairb(sc, h->d_paths.p, np, units, 0, L));
+    CK(h, launch_energy1(sc, h->d_paths.p, np, h->grid.max_clu, L));
+  } else {
+    CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
+  }
   CK(h, launch_excl(sc, h->d_paths.p, np, max_nf, 0, L));
   std::string perr;
   if (sc.pme_nk > 0) {
@@ -340,9 +357,13 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   }
   CK(h, mark(2));
   CK(h, launch_e1(sc, h->d_paths.p, np, max_qpad, max_nf, L, h->e_bond.p, nbx));
+  if (sc.bl) {
+    for (const PathDev& D : pd)
+      if (D.n_hvp > 0) CK(h, launch_bl_transpose(D.eta32, D.n_hvp, D.Qpad, D.n_clu, D.meta, const_cast<float2*>(D.etab), L));
+  }
   CK(h, mark(3));
   if (copied) *copied = false;
-  const bool overlap = host_grad && np == 1 && sync && h->precision == MOP_PREC_MIXED && sc.pme_nk == 0 &&
+  const bool overlap = host_grad && np == 1 && sync && h->precision == MOP_PREC_MIXED && !sc.bl && sc.pme_nk == 0 &&
                        pd[0].n_hvp >= 2 * kCopyChunks && units_h > 0;
   if (overlap) {
     const PathDev& D = pd[0];
@@ -395,7 +416,8 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   }
   if (units_h > 0) {
     CK(h, clear_jacc(true));
-    CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+    if (sc.bl) CK(h, launch_pairb(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, L));
+    else CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
     CK(h, launch_excl(sc, h->d_paths.p, np, max_n, fd ? 2 : 1, L));
     if (sc.pme_nk > 0) {
       cudaError_t e = launch_pme(sc, h->d_paths.p, pd.data(), np, max_n, 1, h->pme, L, &perr);
@@ -587,6 +609,12 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.cutoff_mode = d->cutoff_mode;
   sc.precision = d->precision;
   sc.hvp_mode = d->hvp_mode;
+  // mixed precision runs the bead-lane pair kernels; MOP_PAIR_KERNELS=half selects the
+  // half-list kernels instead (kept for comparison)
+  {
+    const char* pk = getenv("MOP_PAIR_KERNELS");
+    sc.bl = (d->precision == MOP_PREC_MIXED && !(pk && strcmp(pk, "half") == 0)) ? 1 : 0;
+  }
   for (int k = 0; k < 3; ++k) {
     sc.L[k] = d->box[k];
     sc.invL[k] = 1.0 / d->box[k];

@@ -72,6 +72,7 @@ struct PathHost {
   DevBuf<int> meta;       // [4]: clusters, (scan total), largest list, sticky overflow flag
   DevBuf<float4> xq;
   DevBuf<double4_32a> xq64;
+  DevBuf<float2> xb, etab;   // bead-lane kernels: transposed coordinates and eta
   DevBuf<int4> ent;
   DevBuf<double4_32a> ent64;
   DevBuf<unsigned long long> emask;
@@ -131,6 +132,22 @@ cudaError_t launch_pair(const SysConsts& sc, const PathDev* d_paths, int n_paths
 
 cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units,
                                unsigned long long* counts, int num_sms, Launch L);
+
+// --- mop_pairb.cu: bead-lane pair kernels (mixed precision, full list with pair masks) ------
+// A unit is one i-cluster, or a part of one, for a group of kBLBeads beads: a path has
+// ceil(beads / kBLBeads) x n_clu x pairb_units_per_cluster() units, group-major.  mode 0 =
+// force, 1 = adjoint HVP, 2 = FD HVP.
+int pairb_units_per_cluster();
+cudaError_t launch_pairb(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
+                         Launch L);
+// bead-1 pair energy of every path into e_pair (one warp per i-cluster); grid over max_clu
+cudaError_t launch_energy1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_clu, Launch L);
+// rows [0, n_valid) of src float4 [rows][Qpad] (x, y, z, *) into the transposed bead-lane
+// layout dst float2 [G][Qpad][3][32], G = ceil(n_valid / kBLBeads); beads past n_valid repeat
+// bead n_valid - 1
+cudaError_t launch_bl_transpose(const float4* src, int n_valid, int Qpad, int max_clu, const int* meta, float2* dst,
+                                Launch L);
+inline int bl_groups(int beads) { return (beads + kBLBeads - 1) / kBLBeads; }
 
 // --- mop_path.cu: bonded terms, eta, path gradient, bias, reductions, integrator ----------
 // grids: (slot blocks of 256, beads, paths); e_bond gets nbx partials per path, e_spring

@@ -29,6 +29,11 @@ constexpr int kSelfFlag = 1 << 28;
 // integer addition makes the atomics order-independent, so results stay bitwise reproducible
 constexpr float kFixScale = 8388608.0f;           // 2^23
 constexpr float kFixInv = 1.0f / 8388608.0f;
+// Bead-lane pair kernels (mixed precision): one warp evaluates one i-cluster for a group of 64
+// beads, lane l holding beads 64 g + l and 64 g + 32 + l as the two halves of f32x2 operands.
+// Their coordinates and eta are kept transposed, float2 [group][slot][3][32], so that a warp
+// reads one component of one atom for all 64 beads as 256 contiguous bytes.
+constexpr int kBLBeads = 64;
 
 // System-wide constants, passed by value to kernels.
 struct SysConsts {
@@ -73,6 +78,10 @@ struct SysConsts {
   // type-pair tables: (12 c12, 6 c6, phi'_LJ(rc) if shifted else 0, phi_LJ(rc))
   const float4* tab;
   const double4_32a* tab64;
+  // mixed precision: 1 = bead-lane pair kernels on a full list whose entries carry a 64-bit mask
+  // of the candidate atom pairs (emask bit j * 8 + i: the atoms' union spheres come within rc
+  // and the pair is not excluded); 0 = the half-list kernels
+  int bl;
 };
 
 // Device view of one path of a multi-path launch.
@@ -96,7 +105,12 @@ struct PathDev {
   const unsigned* ctype;    // packed LJ types of each cluster (4 bits per atom)
   const int4* ent;          // x = cj | self << 28 | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
   const double4_32a* ent64;
-  const unsigned long long* emask;   // excluded atom pairs of an entry: bit j * 8 + i
+  const unsigned long long* emask;   // excluded atom pairs of an entry (bit j * 8 + i), or with
+                                     // bead-lane kernels the candidate pairs of the entry
+  // bead-lane kernels: coordinates (cluster-local) and eta transposed, float2 [G][Qpad][3][32]
+  // with G = ceil(beads / 64); element (g, s, c, l) = (bead 64 g + l, bead 64 g + 32 + l)
+  const float2* xb;
+  const float2* etab;
   // FP64 mode: [N][Qpad][3] doubles.  Mixed mode views of the same buffers: Fnb and F as
   // double-float (hi, lo) x 3 (float2 [N][Qpad][3]), Hnb and Heta as float4 [N][Qpad].
   double* Fnb;

@@ -15,6 +15,7 @@
 //   g  = -phi'_sf(r)/r                     force on i: g d,  d = r_i - r_j
 //   b  = (phi''(r) + g) / r^2              H block A = b d d^T - g I,  A u with u = eta_i - eta_j
 #include "mop_host.h"
+#include "mop_pairmath.cuh"
 
 // resident 128-thread blocks per SM requested for the FP32 pair kernels (register budget)
 #ifndef MOP_PAIR_MINB
@@ -151,29 +152,7 @@ __device__ __forceinline__ R pair_g2(const PairK<R>& c, R rinv, R rinv2, R rinv6
 // (negative for an excluded pair).  Accumulates F (MODE 0), H eta (MODE 1) or F(+) - F(-)
 // (MODE 2) into a[3] and the pair energy into e (ENERGY).
 // Ewald real space (EW): the electrostatic factor of g, qq (erfc(beta r)/r + 2 beta/sqrt(pi)
-// exp(-beta^2 r^2)).  One Gaussian G = exp(-beta^2 r^2) serves both terms: erfc(x) = G erfcx(x)
-// with the scaled complementary error function erfcx(x) ~ P(x) / Q(x), a rational least-squares
-// fit of degrees 3 / 4 on [0, 6] written by fit_erfcx.py of this package (relative error 2.5e-7
-// for these FP32 coefficients in exact arithmetic, about 5e-7 as evaluated here), and
-// c2E = 2 beta/sqrt(pi) G.  Q(x) >= 1, so the approximate reciprocal (rel. error ~1 ulp) serves.
-__constant__ float kErfcxP[4] = {9.999999234e-01f, 9.697673345e-01f, 4.351839909e-01f, 8.235789757e-02f};
-__constant__ float kErfcxQ[5] = {1.000000000e+00f, 2.098139719e+00f, 1.802774676e+00f, 7.701872587e-01f, 1.460288291e-01f};
-
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float erfcx_rational(float x) {
-  float p = kErfcxP[3], q = kErfcxQ[4];
-#pragma unroll
-  for (int i = 2; i >= 0; --i) p = fmaf(p, x, kErfcxP[i]);
-#pragma unroll
-  for (int i = 3; i >= 0; --i) q = fmaf(q, x, kErfcxQ[i]);
-  return p * rcp_approx(q);
-}
-
+// exp(-beta^2 r^2)), from erfc(x) = exp(-x^2) erfcx(x) (erfcx_rational of mop_pairmath.cuh).
 template <class R>
 __device__ __forceinline__ void ewald_terms(const Cst<R>& k, R r2, R rinv, R* ec, R* c2e) {
   const R G = __expf(-k.ewb2 * r2);
@@ -323,18 +302,6 @@ __device__ __forceinline__ void pair_one(const Cst<R>& k, const PairK<R>& c, R x
 #ifndef MOP_SPTR
 #define MOP_SPTR 1   // HVP and FD kernels: the j fetch's base pointers in shared memory
 #endif
-__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // pair constants of one (entry, half) duplicated into both lanes of the f32x2 operands
 struct PairK2 {
   float2 A, nB, qq, sh, nqk;   // 12 c12, -6 c6, f qi qj, phi'(rc), -qq 2 k_rf
@@ -357,18 +324,9 @@ __device__ __forceinline__ PairK2 pair_consts2(const PairK<float>& c) {
   return d;
 }
 
-// Ewald: erfc(beta r) = G erfcx(beta r) and the force term 2 beta/sqrt(pi) G for both beads
+// Ewald: erfc(beta r) and the force term 2 beta/sqrt(pi) G for both beads
 __device__ __forceinline__ void ewald_terms2(const Cst<float>& k, float2 r2, float2 rinv, float2* ec, float2* c2e) {
-  const float2 y = mul2(r2, dup2(-k.ewb2 * 1.4426950408889634f));   // -beta^2 r^2 log2(e)
-  const float2 G = make_float2(ex2_approx(y.x), ex2_approx(y.y));
-  const float2 x = mul2(dup2(k.ewb), mul2(r2, rinv));
-  float2 p = dup2(kErfcxP[3]), q = dup2(kErfcxQ[4]);
-#pragma unroll
-  for (int i = 2; i >= 0; --i) p = fma2(p, x, dup2(kErfcxP[i]));
-#pragma unroll
-  for (int i = 3; i >= 0; --i) q = fma2(q, x, dup2(kErfcxQ[i]));
-  *ec = mul2(G, mul2(p, make_float2(rcp_approx(q.x), rcp_approx(q.y))));
-  *c2e = mul2(dup2(k.ewc2), G);
+  ewald_terms2(k.ewb, k.ewb2, k.ewc2, r2, rinv, ec, c2e);
 }
 
 // One pair for both beads of the unit (HALF list): MODE 0 force, MODE 1 adjoint H eta.  xs and
@@ -1082,7 +1040,7 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
     const size_t eb = (size_t)ci * P.cap;
     for (int e = 0; e < P.lcnt[ci]; ++e) {
       const int4 en = P.ent[eb + e];
-      const unsigned long long m = (en.x < 0) ? P.emask[eb + e] : 0ull;
+      const unsigned long long m = (en.x < 0 || sc.bl) ? P.emask[eb + e] : 0ull;
       const int cj = en.x & kCluMask;
       double D[3];
       if (P.ent64) {
@@ -1093,6 +1051,8 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
       for (int h = 0; h < 2; ++h) {
         if (!(en.x & (1 << (29 + h)))) continue;
         const int jl = jj + 4 * h, sj = cj * kCL + jl;
+        // bead-lane list: only the entry's candidate pairs are evaluated (none of them excluded)
+        if (sc.bl && !((m >> (jl * kCL + i)) & 1ull)) continue;
         double a[3], b[3];
         if (P.xq64) {
           const double4_32a x = P.xq64[bo + ci * kCL + i], y = P.xq64[bo + sj];
@@ -1111,7 +1071,8 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
         // each pair in both orders
         const int wgt = (P.jacc && !(en.x & kSelfFlag)) ? 2 : 1;
         listed += 1;
-        inside += (vi && vj && r2 < sc.rc2 && !((m >> (jl * kCL + i)) & 1ull)) ? wgt : 0;
+        const bool excluded = !sc.bl && ((m >> (jl * kCL + i)) & 1ull);
+        inside += (vi && vj && r2 < sc.rc2 && !excluded) ? wgt : 0;
       }
     }
   }

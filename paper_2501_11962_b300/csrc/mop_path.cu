@@ -371,7 +371,7 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
       bonded_force<float, float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
       for (int c = 0; c < 3; ++c) {
         F[c] = df_add_f(df{Fnb[c].x, Fnb[c].y}, Fb[c]);
-        F[c] = df_add(F[c], fix_to_df((long long)P.jacc[3 * k + c]));   // j-side sums of the half list
+        if (P.jacc) F[c] = df_add(F[c], fix_to_df((long long)P.jacc[3 * k + c]));   // j-side sums
       }
       if (P.N > 1) {
         const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
@@ -440,9 +440,11 @@ __global__ void MOP_E2_BOUNDS k_e2_mixed(SysConsts sc, const PathDev* __restrict
       }
       if (n < P.N - 1) {
         const float4 hn = reinterpret_cast<const float4*>(P.Hnb)[k];
-        const unsigned long long* J = P.jacc + 3 * k;   // j-side sums of the half list
-        float H[3] = {hn.x + __ll2float_rn((long long)J[0]) * kFixInv, hn.y + __ll2float_rn((long long)J[1]) * kFixInv,
-                      hn.z + __ll2float_rn((long long)J[2]) * kFixInv};
+        float H[3] = {hn.x, hn.y, hn.z};
+        if (P.jacc) {   // j-side sums
+          const unsigned long long* J = P.jacc + 3 * k;
+          for (int c = 0; c < 3; ++c) H[c] += __ll2float_rn((long long)J[c]) * kFixInv;
+        }
         double eps = 0.0;
         if (FD) {
           const float mx = __uint_as_float(P.etamax[n]);

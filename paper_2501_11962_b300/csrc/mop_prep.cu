@@ -464,10 +464,14 @@ __global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype)
 // (two atom pairs per lane), and so does the exclusion mask (bit j * 8 + i).  Entries of cluster ci
 // go to ent[ci * cap ...] in bin order (deterministic); lcnt[ci] = their number; meta[2] =
 // largest count (a count above cap means the list must be rebuilt with a larger cap).
+// HALF: every unordered cluster pair once (half-list kernels).  Otherwise every pair from both
+// sides; without F64 (bead-lane kernels) emask then holds the entry's candidate atom pairs (the
+// union spheres within reach, exclusions removed, bit j * 8 + i) and an entry whose candidates
+// are all excluded is dropped.
 #ifndef MOP_LIST_MINB
 #define MOP_LIST_MINB 6   // 80 registers: 6 blocks (24 warps) per SM hide the latency of the bin walk
 #endif
-template <bool F64>
+template <bool F64, bool HALF>
 __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, const int* meta_in, int max_clu,
                                                    const double* cwrap, const float2* cwdf, const float* hext,
                                                    const unsigned* emax,
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
           double D[3] = {0.0, 0.0, 0.0};
           if (t < nbin) {
             cj = binlist[s0 + t];
-            if (!F64) {
+            if (HALF) {
               // half list: every unordered cluster pair (with its image) once; the parity rule
               // gives each cluster about half of its neighbours
               self = cj == ci && kk[0] == 0 && kk[1] == 0 && kk[2] == 0;
@@ -595,8 +599,34 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
                 in1 = ux * ux + uy * uy + uz * uz < lim * lim;
               }
             }
-            const unsigned hm = (__ballot_sync(0xffffffffu, in0) ? 1u : 0u) | (__ballot_sync(0xffffffffu, in1) ? 2u : 0u);
+            const unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
+            const unsigned hm = (b0 ? 1u : 0u) | (b1 ? 2u : 0u);
             if (!hm) continue;   // warp-uniform
+            constexpr bool PM = !F64 && !HALF;   // candidate-pair masks
+            unsigned long long pm = 0ull;
+            if (PM) {
+              // exclusions only matter for clusters whose molecule ranges overlap
+              pm = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
+              const int mj0 = molr[2 * cs], mj1 = molr[2 * cs + 1];
+              if (mi0 <= mj1 && mj0 <= mi1) {
+                bool x0 = false, x1 = false;
+                if (ai >= 0) {
+                  const int a0 = perm[cs * kCL + jq], a1 = perm[cs * kCL + jq + 4];
+                  x0 = a0 >= 0 && sc.mol[a0] == mol_i && abs(sc.loc[a0] - loc_i) <= 2;
+                  x1 = a1 >= 0 && sc.mol[a1] == mol_i && abs(sc.loc[a1] - loc_i) <= 2;
+                }
+                pm &= ~((unsigned long long)__ballot_sync(0xffffffffu, x0) |
+                        ((unsigned long long)__ballot_sync(0xffffffffu, x1) << 32));
+              }
+              if (!pm) continue;   // warp-uniform: every candidate pair is excluded
+              if (count < cap && lane == src) {
+                ent[base + count] = make_int4(cj | (int)(hm << 29) | (self ? kSelfFlag : 0), __float_as_int(Df[0]),
+                                              __float_as_int(Df[1]), __float_as_int(Df[2]));
+                emask[base + count] = pm;
+              }
+              ++count;
+              continue;
+            }
             if (count < cap) {
               // exclusions, bit j * 8 + i (the lane index for j < 4, + 32 for j >= 4); only
               // clusters whose molecule ranges overlap can hold excluded pairs
@@ -792,15 +822,22 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
     if (sync) MOP_CK(cudaMemsetAsync(P.meta.p + 2, 0, 2 * sizeof(int), st));
     const int blocks = nblk(max_clu, 4);
     if (f64)
-      k_pair_list<true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
+      k_pair_list<true, false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
                                                 g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
                                                 P.ent.p, P.ent64.p, P.emask.p, P.meta.p);
+    else if (sc.bl)
+      k_pair_list<false, false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
+                                                        P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2],
+                                                        P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.abox.p,
+                                                        P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr, P.emask.p,
+                                                        P.meta.p);
     else
-      k_pair_list<false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
-                                                 g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
-                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
-                                                 P.ent.p, nullptr, P.emask.p, P.meta.p);
+      k_pair_list<false, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
+                                                       P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2],
+                                                       P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.abox.p,
+                                                       P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr, P.emask.p,
+                                                       P.meta.p);
     MOP_KL();
     if (!sync) return cudaSuccess;   // capture-safe: an overflow shows up in the sticky flag
     int meta[4];

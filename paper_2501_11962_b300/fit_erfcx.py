@@ -6,7 +6,7 @@ the force term 2 beta / sqrt(pi) exp(-beta^2 r^2).
 
 The fit is linearised least squares on the relative error (Sanathanan-Koerner iteration: each
 step solves min sum w (P - y Q)^2 / (Q_prev y)^2), with weights raised where the error peaks, at
-Chebyshev nodes of [0, XMAX].  Run it to print the C table that csrc/mop_pair.cu holds.
+Chebyshev nodes of [0, XMAX].  Run it to print the C table that csrc/mop_pairmath.cuh holds.
 """
 from __future__ import annotations
 

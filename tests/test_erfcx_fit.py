@@ -1,4 +1,4 @@
-"""The rational erfcx table of the Ewald pair kernels (csrc/mop_pair.cu) against math.erfc: the
+"""The rational erfcx table of the Ewald pair kernels (csrc/mop_pairmath.cuh) against math.erfc: the
 coefficients as compiled (FP32) reproduce erfc(x) exp(x^2) to 3e-7 in FP64 arithmetic and to 6e-7
 in an FP32 Horner evaluation with fused multiply-adds, over the range of beta r the kernels use."""
 import math
@@ -7,7 +7,7 @@ from pathlib import Path
 
 import numpy as np
 
-SRC = Path(__file__).resolve().parents[1] / "paper_2501_11962_b300" / "csrc" / "mop_pair.cu"
+SRC = Path(__file__).resolve().parents[1] / "paper_2501_11962_b300" / "csrc" / "mop_pairmath.cuh"
 
 
 def table(name):

@@ -48,3 +48,42 @@ def test_spring_energy_noalloc_rejects_oversized_input():
     # 65,537 tiles of 256 atoms exceed the 65,536 partial sums of the static array
     st = lib.mop_spring_energy_noalloc(p, p, 1, 65537 * 256, 0.002, 5.0, p, None)
     assert st == mop.MOP_ERR_ARG
+
+
+def test_spring_energy_noalloc_at_the_spring_limit():
+    """65,536 springs of 256 atoms: exactly the 65,536 block sums the static array holds, with
+    more springs than one grid dimension of 65,535 could carry."""
+    import torch
+    lib = mop.load()
+    S, Q = 65536, 256
+    g = torch.Generator(device="cpu").manual_seed(1234)
+    eta_h = torch.randn(S, Q, 3, generator=g, dtype=torch.float64) * 0.01
+    mass_h = torch.rand(Q, generator=g, dtype=torch.float64) * 30.0 + 1.0
+    dt, nu = 0.002, 5.0
+    K = mass_h.numpy() * nu / (2.0 * dt)
+    ref = float(np.sum(0.5 * K[None, :] * np.sum(eta_h.numpy() ** 2, axis=2)))
+    eta, mass = eta_h.cuda(), mass_h.cuda()
+    out = torch.empty(1, device="cuda", dtype=torch.float64)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        st = lib.mop_spring_energy_noalloc(C.c_void_p(eta.data_ptr()), C.c_void_p(mass.data_ptr()), S, Q, dt, nu,
+                                           C.c_void_p(out.data_ptr()), stream)
+        assert st == mop.MOP_OK
+        torch.cuda.synchronize()
+        assert abs(out.item() - ref) / abs(ref) < 1e-12, (out.item(), ref)
+    # one spring more does not fit
+    st = lib.mop_spring_energy_noalloc(C.c_void_p(eta.data_ptr()), C.c_void_p(mass.data_ptr()), S + 1, Q, dt, nu,
+                                       C.c_void_p(out.data_ptr()), stream)
+    assert st == mop.MOP_ERR_ARG
+
+
+def test_spring_energy_noalloc_rejects_the_largest_atom_count():
+    """n_atoms = 2^31 - 1 must be rejected by the size check (no 32-bit overflow of the tile
+    count), before any memory is touched."""
+    import torch
+    lib = mop.load()
+    t = torch.zeros(3, device="cuda", dtype=torch.float64)
+    p = C.c_void_p(t.data_ptr())
+    st = lib.mop_spring_energy_noalloc(p, p, 1, 2**31 - 1, 0.002, 5.0, p, None)
+    assert st == mop.MOP_ERR_ARG
