@@ -26,17 +26,29 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "path-gradient evals/s (bead·atoms/s) at Q=150k, N=64; adjoint vs FD-HVP at tol"
 UNIT = "bead*atoms/s"
-# canonical flop counts per unique in-cutoff pair (FADD/FMUL = 1, FFMA = 2, rsqrt not counted)
-FLOPS_FORCE = 36
-FLOPS_HVP = 59
+# Canonical flop counts per unique in-cutoff pair of the hot-path scope: about 30 FP32 flops for
+# the force and 40 for the adjoint HVP.  The itemised counts of the written formulas (FADD/FMUL =
+# 1, FFMA = 2, rsqrt not counted) are 36 and 59; both fractions are reported.
+FLOPS_FORCE = 30
+FLOPS_HVP = 40
+FLOPS_FORCE_ITEMISED = 36
+FLOPS_HVP_ITEMISED = 59
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 FD_SWEEP = (1e-5, 3e-5, 1e-4, 3e-4, 1e-3)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels on
 # this workload, from the ncu launch list in profiles/launches_cfg5_Q150k_N64.md.  Valid only
 # for the kernel sources they were measured on: any change to them makes `traffic` null.
-PAIR_TRAFFIC = {"sources_sha256_16": "5e9b5f2207f444ed", "k_pair<float,0>": 1047.3e6, "k_pair<float,1>": 1411.1e6}
-PAIR_SOURCES = ("mop_pair.cu", "mop_prep.cu", "mop_internal.cuh")
+PAIR_TRAFFIC = {"sources_sha256_16": "", "k_pairb<0,RF>": None, "k_pairb<1,RF>": None}
+PAIR_SOURCES = ("mop_pairb.cu", "mop_pairmath.cuh", "mop_prep.cu", "mop_internal.cuh")
+# arithmetic of the mixed-precision path, quantity by quantity
+PRECISION = {"pair_arithmetic": "f32 (two beads per f32x2 instruction)",
+             "forces_F": "double-float (f32 hi + lo): f32 pair sums folded by TwoSum, bonded f32 added exactly",
+             "eta": "double-float from the exact R^{n+1} - R^n and the double-float c F; f32 copy for the HVP",
+             "H_eta": "f32 (pair and bonded terms)",
+             "gradient_G": "double-float K (eta^{n-1} - eta^n) + H eta / 2 (- F^1), written as f64",
+             "energies": "double-float per warp, f64 per block and across blocks",
+             "ewald_j_side_and_grids": "int64 fixed point (2^-23 forces, 2^-40 SPME charge grids)"}
 
 
 def pair_sources_sha() -> str:
@@ -63,9 +75,22 @@ def parse():
     return ap.parse_args()
 
 
-def workload_name(cfg, N, Q):
+def workload_name(cfg, N, Q, relaxed=False):
     names = {5: "chains+water membrane-sized synthetic system", 4: "water+ion", 3: "water", 2: "water", 1: "LJ fcc"}
-    return f"cfg{cfg} {names.get(cfg, '')}: Q={Q}, N={N}"
+    return f"cfg{cfg} {names.get(cfg, '')}{' (relaxed)' if relaxed else ''}: Q={Q}, N={N}"
+
+
+# Relaxed base structures (200 steps of capped steepest descent on the oracle's forces, written by
+# tests/golden/relax_inputs.py); the beads are drawn around them
+RELAXED = ROOT / "tests" / "golden" / "relaxed"
+
+
+def workload(cfg, n_beads=None):
+    """The benchmark workload: the relaxed structure when it is stored, else the generated one."""
+    from paper_2501_11962_b300 import synth
+    f = RELAXED / f"cfg{cfg}.npy"
+    base = np.load(f) if f.exists() else None
+    return synth.config(cfg, n_beads=n_beads, base=base), base is not None
 
 
 class ClockSampler:
@@ -178,7 +203,7 @@ def run_reference(args, world, rank):
     from paper_2501_11962_b300 import synth
     if rank != 0:
         return
-    w = synth.config(args.config, n_beads=args.beads)
+    w, relaxed = workload(args.config, args.beads)
     N, Q = w.paths[0].shape[:2]
     ns = cpu_sample_beads(w)
     times = []
@@ -194,7 +219,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.config, N, Q), "Q": Q, "N": N, "paths": 1},
+        "config": {"workload": workload_name(args.config, N, Q, relaxed), "Q": Q, "N": N, "paths": 1},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -212,7 +237,7 @@ def run_ours(args, world, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = synth.config(args.config, n_beads=args.beads)
+    w, relaxed = workload(args.config, args.beads)
     X = w.paths[0]
     N, Q = X.shape[:2]
     prec = mop.MOP_PREC_FP64 if w.precision == "fp64" else mop.MOP_PREC_MIXED
@@ -252,27 +277,36 @@ def run_ours(args, world, rank, local):
     value = world * N * Q / (ms * 1e-3)
     mean_pass = {k: float(np.mean([p[k] for p in passes])) for k in passes[0]}
 
-    # roofline of the dominant pair kernel (FP32 ALU bound)
+    # roofline of the dominant pair kernel (FP32 ALU bound).  The pass times come from the
+    # library's CUDA events on the launching stream; the pair passes are one pair-kernel launch
+    # each, plus the small bead-1 energy kernel in the force pass.
     unique, listed = eng.count_pairs(0)
-    n_force = N - 1 if N > 1 else 1
     flops = {"pair_force": unique * FLOPS_FORCE, "pair_hvp": unique * FLOPS_HVP}
+    flops_it = {"pair_force": unique * FLOPS_FORCE_ITEMISED, "pair_hvp": unique * FLOPS_HVP_ITEMISED}
     dom = max(("pair_force", "pair_hvp"), key=lambda k: mean_pass[k])
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops[dom] / (mean_pass[dom] * 1e-3) / 1e12
+    achieved_it = flops_it[dom] / (mean_pass[dom] * 1e-3) / 1e12
     fma_peak = mop.measure_fp32_peak(local)      # dependent-FMA microkernel on this GPU, now
     ach_force = flops["pair_force"] / (mean_pass["pair_force"] * 1e-3) / 1e12
-    kname = "k_pair<float," + ("0>" if dom == "pair_force" else "1>")
-    traffic = PAIR_TRAFFIC.get(kname) if (args.config == 5 and N == 64 and
+    half = os.environ.get("MOP_PAIR_KERNELS") == "half" or prec == mop.MOP_PREC_FP64
+    mode = "0" if dom == "pair_force" else "1"
+    kname = (f"k_pair<float,{mode}>" if prec != mop.MOP_PREC_FP64 else f"k_pair<double,{mode}>") if half \
+        else f"k_pairb<{mode},RF>"
+    traffic = PAIR_TRAFFIC.get(kname) if (args.config == 5 and N == 64 and not half and
                                           pair_sources_sha() == PAIR_TRAFFIC["sources_sha256_16"]) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kname,
-                "unique_pairs_per_launch": unique, "listed_pairs_per_launch": listed,
+                "unique_pairs_per_launch": unique, "evaluated_pairs_per_launch": listed,
                 "flops_per_unique_pair": FLOPS_FORCE if dom == "pair_force" else FLOPS_HVP,
                 "peak_note": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {SM_MAX_MHZ:.0f} MHz",
                 "peak_measured_fma": fma_peak, "frac_of_measured_fma": achieved / fma_peak,
+                "itemised": {"flops_per_unique_pair": FLOPS_FORCE_ITEMISED if dom == "pair_force" else FLOPS_HVP_ITEMISED,
+                             "achieved": achieved_it, "frac": achieved_it / peak},
                 "pair_force": {"achieved": ach_force, "frac": ach_force / peak,
-                               "frac_of_measured_fma": ach_force / fma_peak}}
+                               "frac_of_measured_fma": ach_force / fma_peak,
+                               "itemised_frac": flops_it["pair_force"] / (mean_pass["pair_force"] * 1e-3) / 1e12 / peak}}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.tensor(X).pin_memory()
@@ -330,32 +364,65 @@ def run_ours(args, world, rank, local):
               "reaches_1e-4": bool(errs[best] <= 1e-4),
               "adjoint_over_fd_speed": value / world / vals[best] if vals.get(best) else None}
 
-    # the metadynamics production loop (mop_metadynamics, graph mode) on the same path: MD steps
-    # of all beads with one Gaussian deposited per round.  The synthetic structure is unrelaxed
-    # and its path gradients are large, so the timing run uses a tiny dt (the cost does not
-    # depend on it) to keep the pair lists within the capacity the captured graph was sized for.
-    metad = None
-    if not args.no_metad and rank == 0:
-        em = mop.Engine(w.system, precision=prec, device=local)
-        em.set_tuning(tuned["col_factor"], tuned["bin_factor"])
-        em.set_path(0, X)
-        pos = X[-1].astype(np.float64)
-        ga = synth.nearest_group(pos, np.asarray(w.system.box), pos[0], 8)
-        gb = synth.nearest_group(pos, np.asarray(w.system.box), pos[Q // 2], 8)
+    # The metadynamics production loop (mop_metadynamics, graph mode): BAOAB MD of all beads with
+    # one Gaussian deposited per round on a centre-of-mass end-to-end CV.  The time step is the
+    # stable one of this action: its c F term gives the path Hessian eigenvalues
+    # dt_path omega^4 / (2 nu) for a physical vibration omega, about (5,100 ps^-1)^2 for the
+    # flexible O-H bond at dt_path = 2 fs and nu = 5 ps^-1, so velocity Verlet needs dt < 0.39 fs;
+    # 0.2 fs is used.  The path starts stationary (every bead at the relaxed base structure) and
+    # the thermostat spreads it; the beads of the evaluation workload, independent displacements
+    # of 0.01 nm, are far from a solution of Eq. 1 and heat up violently under these dynamics.
+    # It runs on the relaxed water box (config 3, Q = 24,000) and on this workload.  Every captured step
+    # rebuilds the pair lists; a list that outgrows the capacity the graph was sized for makes
+    # mop_step restore its state and repeat the batch with a larger capacity.
+    def metad_run(wm, Nm, label):
+        Qm = wm.system.n_atoms
+        Xm = np.repeat(np.asarray(wm.system.extra["base"], np.float32)[None], Nm, axis=0)
+        em = mop.Engine(wm.system, precision=prec, device=local)
+        em.set_path(0, Xm)
+        em.veff_and_grad(0, want_grad=False)
+        _, pairs0 = em.count_pairs(0)
+        pos = Xm[-1].astype(np.float64)
+        ga = synth.nearest_group(pos, np.asarray(wm.system.box), pos[0], 8)
+        gb = synth.nearest_group(pos, np.asarray(wm.system.box), pos[Qm // 2], 8)
         em.add_bias(0, 0.0, 0.0, 0.1, groups=(ga, gb), e2e=True, com=True)
         em.set_graph_mode(True)
-        rounds, stride, dt_md = 2, 10, 1e-6
-        em.metadynamics(1, 2, dt_md, 5.0, 3, 1.0, 0.1)         # capture and warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        em.metadynamics(rounds, stride, dt_md, 5.0, 3, 1.0, 0.1)
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
-        metad = {"md_steps_per_s": rounds * stride / t, "ms_per_md_step": t / (rounds * stride) * 1e3,
-                 "bead_atom_steps_per_s": N * Q * rounds * stride / t, "rounds": rounds, "stride": stride,
-                 "dt_ps": dt_md, "gamma_per_ps": 5.0, "graph_mode": True,
-                 "note": "host wall clock over the rounds, including one synchronous re-evaluation per deposit"}
+        rounds, stride, dt_md = 4, 25, 2e-4
+        b0, _ = em.list_stats(0)
+        failed = None
+        try:
+            em.metadynamics(1, 2, dt_md, 5.0, 3, 1.0, 0.1)         # capture and warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            em.metadynamics(rounds, stride, dt_md, 5.0, 3, 1.0, 0.1)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            failed = False
+        except mop.MopError as e:
+            if e.status not in (mop.MOP_ERR_STATE, mop.MOP_ERR_OOM, mop.MOP_ERR_NONFINITE):
+                raise
+            failed, t = e.status, float("nan")
+        b1, _ = em.list_stats(0)
+        pairs1 = None
+        if not failed:
+            em.veff_and_grad(0, want_grad=False)
+            _, pairs1 = em.count_pairs(0)
+        out = {"workload": label, "start": "stationary path (all beads at the relaxed base structure)",
+               "evaluated_pairs_per_launch_at_start": pairs0, "evaluated_pairs_per_launch_at_end": pairs1,
+               "md_steps_per_s": rounds * stride / t,
+               "ms_per_md_step": t / (rounds * stride) * 1e3, "bead_atom_steps_per_s": Nm * Qm * rounds * stride / t,
+               "rounds": rounds, "stride": stride, "dt_ps": dt_md, "gamma_per_ps": 5.0, "graph_mode": True,
+               "failed_with_status": failed, "step_batches_rerun_after_list_overflow": em.list_overflows(0),
+               "synchronous_list_builds": b1 - b0,
+               "note": "host wall clock over the rounds, including one synchronous re-evaluation per deposit"}
         em.close()
+        return out
+
+    metad = None
+    if not args.no_metad and rank == 0:
+        w3, rel3 = workload(3, n_beads=N)
+        metad = {"water": metad_run(w3, N, workload_name(3, N, w3.system.n_atoms, rel3)),
+                 "this_workload": metad_run(w, N, workload_name(args.config, N, Q, relaxed))}
 
     # batching: the 8 paths of uneven length of the water + ion workload (config 4, 968 beads)
     # in one call, every pass one launch over all paths, against the same paths one call each
@@ -468,9 +535,10 @@ def run_ours(args, world, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 pair math, f64 accumulation" if prec == 0 else "f64",
+            "vs_baseline": None, "dtype": "f32" if prec == 0 else "f64",
+            "precision": PRECISION if prec == 0 else "f64 everywhere",
             "data": "synthetic",
-            "config": {"workload": workload_name(args.config, N, Q), "Q": Q, "N": N, "paths": 1,
+            "config": {"workload": workload_name(args.config, N, Q, relaxed), "Q": Q, "N": N, "paths": 1,
                        "hvp": "adjoint", "l2": "inputs larger than L2 (115 MB coordinates per step, >1 GB fields)",
                        "parallelism": f"{world} independent replica(s), one per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fd_hvp": fd, "metad": metad, "batch": batch,

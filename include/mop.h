@@ -58,8 +58,12 @@ enum { MOP_HVP_ADJOINT = 0, /* exact, forward-over-reverse pair/bond/angle kerne
        MOP_HVP_FD = 1 };    /* paper Eq. 5: [F(R + eps eta) - F(R - eps eta)] / (2 eps),
                                eps = fd_h / max_i |eta_i| per bead */
 /* arithmetic of the pair kernels */
-enum { MOP_PREC_MIXED = 0, /* FP32 pair arithmetic, FP64 accumulation and path terms */
-       MOP_PREC_FP64 = 1 };/* FP64 everywhere */
+/* MOP_PREC_MIXED: FP32 pair arithmetic; forces F, eta and the gradient G in double-float (an
+ * FP32 hi + lo pair, error-free transformations on the FP32 pipes; G written as FP64); H eta in
+ * FP32; energies summed as double-floats and in FP64; the Ewald exclusion and SPME terms add
+ * into int64 fixed point.  MOP_PREC_FP64: FP64 everywhere. */
+enum { MOP_PREC_MIXED = 0,
+       MOP_PREC_FP64 = 1 };
 
 /* call flags */
 #define MOP_DEVPTR 1       /* pointer arguments are device pointers; call is asynchronous */
@@ -218,10 +222,17 @@ mop_status mop_get_gaussians(mop_handle* h, int32_t path_id, double* centers, do
  * paths (integrator kernels plus a full V_eff + gradient evaluation, with no host
  * synchronisation inside) into a CUDA graph on a stream of the handle, and replays it n_steps
  * times.  The graph is captured again when the set of paths, dt, gamma or seed changes.  The
- * pair lists keep the capacity sized by the last synchronous evaluation (with 25% headroom); if a
- * list outgrows it during the replays, mop_step returns MOP_ERR_STATE and the steps since the
- * last synchronous call are invalid. */
+ * pair lists keep the capacity sized by the last synchronous evaluation (with 25% headroom).  If a
+ * list outgrows it during the replays, mop_step restores the positions, velocities, gradients and
+ * noise counter it held before them, grows the capacity to 1.25 times the largest list the replays
+ * met, captures the step again and replays the n_steps again (mop_get_list_overflows counts these
+ * repeats); after three attempts it returns MOP_ERR_STATE and the steps are invalid. */
 mop_status mop_set_graph_mode(mop_handle* h, int32_t on);
+
+/* *overflows = number of graph-mode step batches of path `path_id` that were run again because a
+ * pair list outgrew its capacity (mop_set_graph_mode).  No counterpart in the paper.  Errors:
+ * MOP_ERR_ARG, MOP_ERR_STATE (path not set). */
+mop_status mop_get_list_overflows(const mop_handle* h, int32_t path_id, int64_t* overflows);
 
 /* Geometry of the neighbour search, chosen by the autotuner.  col_factor scales the x-y width of
  * the columns that are cut into 8-atom clusters (1 = near-cubic clusters); bin_factor sets the

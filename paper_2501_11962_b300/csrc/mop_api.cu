@@ -4,6 +4,7 @@
 //   all paths, one launch each: pair force -> bonded + eta -> pair HVP (adjoint or FD) ->
 //   bonded HVP + gradient -> bias -> V_eff reduction
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -19,6 +20,64 @@ using namespace mop;
 
 namespace mop {
 constexpr int kCopyChunks = 8;   // bead chunks of the HVP pass whose gradients are copied while later chunks run
+
+namespace failhook {
+// MOP_FAIL_ALLOC, parsed once: each "<call>:<k>" fires once per process
+struct FailSpec {
+  std::string call;
+  int k;
+  std::atomic<bool> fired{false};
+};
+std::vector<FailSpec*>& fail_specs() {
+  static std::vector<FailSpec*> specs = [] {
+    std::vector<FailSpec*> v;
+    if (const char* env = getenv("MOP_FAIL_ALLOC")) {
+      std::string all(env);
+      size_t pos = 0;
+      while (pos <= all.size()) {
+        const size_t end = std::min(all.find(',', pos), all.size());
+        const std::string item = all.substr(pos, end - pos);
+        const size_t c = item.find(':');
+        if (c != std::string::npos) {
+          FailSpec* f = new FailSpec();
+          f->call = item.substr(0, c);
+          f->k = atoi(item.c_str() + c + 1);
+          v.push_back(f);
+        }
+        pos = end + 1;
+      }
+    }
+    return v;
+  }();
+  return specs;
+}
+thread_local const char* t_call = nullptr;
+thread_local int t_allocs = 0;
+}  // namespace failhook
+using failhook::FailSpec;
+using failhook::fail_specs;
+using failhook::t_call;
+using failhook::t_allocs;
+
+void alloc_hook_enter(const char* call) {
+  t_call = call;
+  t_allocs = 0;
+}
+
+// marks the body of an entry point for MOP_FAIL_ALLOC
+struct AllocScope {
+  explicit AllocScope(const char* call) { alloc_hook_enter(call); }
+  ~AllocScope() { alloc_hook_enter(nullptr); }
+};
+
+bool alloc_hook_fail() {
+  const std::vector<FailSpec*>& v = fail_specs();
+  if (v.empty() || !t_call) return false;
+  ++t_allocs;
+  for (FailSpec* f : v)
+    if (f->call == t_call && f->k == t_allocs && !f->fired.exchange(true)) return true;
+  return false;
+}
 }
 
 struct mop_handle {
@@ -34,7 +93,7 @@ struct mop_handle {
   // device copies of the system
   DevBuf<double> mass, Kspr, cL, qs;
   DevBuf<float2> c_df;
-  DevBuf<float> Kf;
+  DevBuf<float2> K_df;
   DevBuf<int> type, mol, loc, inc_off;
   DevBuf<int4> inc;
   DevBuf<double2> incp;
@@ -122,8 +181,10 @@ __global__ void k_d2f(const double* in, float* out, long long n, int* bad) {
 
 // slot-ordered field -> caller-ordered [N][Q][3], zero rows outside [0, n_rows).
 // fmt 0: FP64 x 3; 1: double-float (hi, lo) x 3; 2: float4
-__global__ void k_gather_field(const void* f, int fmt, const int* slot, int Q, int Qpad, int N, int n_rows,
-                               double* out) {
+// fmt 0: double [rows][Qpad][3]; 1: double-float float2 [rows][Qpad][3]; 2: float4 [rows][Qpad];
+// 3: double-float float4 hi [rows][Qpad] plus float4 lo (f2)
+__global__ void k_gather_field(const void* f, const float4* f2, int fmt, const int* slot, int Q, int Qpad, int N,
+                               int n_rows, double* out) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (atoms, beads)
   if (a >= Q) return;
   const int n = blockIdx.y;
@@ -139,6 +200,10 @@ __global__ void k_gather_field(const void* f, int fmt, const int* slot, int Q, i
       } else {
         const float4 w = ((const float4*)f)[k];
         v = c == 0 ? w.x : (c == 1 ? w.y : w.z);
+        if (fmt == 3) {
+          const float4 l = f2[k];
+          v += c == 0 ? l.x : (c == 1 ? l.y : l.z);
+        }
       }
     }
     out[3 * t + c] = v;
@@ -223,6 +288,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.F.ensure(nq3));
     if (h->precision == MOP_PREC_FP64) CK(h, P.eta.ensure(nq3));
     CK(h, P.eta32.ensure((size_t)N * Qpad));
+    if (h->precision == MOP_PREC_MIXED) CK(h, P.etalo.ensure((size_t)N * Qpad));
     CK(h, P.Hnb.ensure(nq3));
     CK(h, P.Heta.ensure(nq3));
     CK(h, P.etamax.ensure(N));
@@ -284,6 +350,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.F = P.F.p;
     D.eta = P.eta.p;
     D.eta32 = P.eta32.p;
+    D.etalo = h->precision == MOP_PREC_MIXED ? P.etalo.p : nullptr;
     D.Hnb = P.Hnb.p;
     D.Heta = P.Heta.p;
     D.etamax = P.etamax.p;
@@ -540,6 +607,7 @@ extern "C" {
 mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   if (!out) return MOP_ERR_ARG;
   *out = nullptr;
+  AllocScope scope("mop_create");
   if (!d) return MOP_ERR_ARG;
   const int Q = d->n_atoms, nt = d->n_types;
   if (Q < 1 || nt < 1 || nt > kMaxTypes) return MOP_ERR_ARG;
@@ -659,7 +727,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
 
   std::vector<double> Kspr(Q), cL(Q), qs(Q);
   std::vector<float2> c_df(Q);
-  std::vector<float> Kf(Q);
+  std::vector<float2> K_df(Q);
   const double sqf = std::sqrt(kCoulombF);
   for (int i = 0; i < Q; ++i) {
     Kspr[i] = d->mass[i] * d->nu_path / (2.0 * d->dt_path);
@@ -667,7 +735,8 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     qs[i] = d->charge[i] * sqf;
     const float ch = (float)cL[i];
     c_df[i] = make_float2(ch, (float)(cL[i] - (double)ch));
-    Kf[i] = (float)Kspr[i];
+    const float kh = (float)Kspr[i];
+    K_df[i] = make_float2(kh, (float)(Kspr[i] - (double)kh));
   }
   // type-pair table (Lorentz-Berthelot)
   std::vector<float4> tab(kMaxTypes * kMaxTypes);
@@ -751,7 +820,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   mop_status s;
   if ((s = upload(h, h->mass, d->mass, Q)) || (s = upload(h, h->Kspr, Kspr.data(), Q)) ||
       (s = upload(h, h->cL, cL.data(), Q)) || (s = upload(h, h->qs, qs.data(), Q)) ||
-      (s = upload(h, h->c_df, c_df.data(), Q)) || (s = upload(h, h->Kf, Kf.data(), Q)) ||
+      (s = upload(h, h->c_df, c_df.data(), Q)) || (s = upload(h, h->K_df, K_df.data(), Q)) ||
       (s = upload(h, h->type, d->type, Q)) || (s = upload(h, h->mol, d->mol_id, Q)) ||
       (s = upload(h, h->loc, d->mol_local, Q)) || (s = upload(h, h->inc_off, off.data(), Q + 1)) ||
       (s = upload(h, h->inc, inc.data(), inc.size())) || (s = upload(h, h->incp, incp.data(), incp.size())) ||
@@ -767,7 +836,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.cL = h->cL.p;
   sc.qs = h->qs.p;
   sc.c_df = h->c_df.p;
-  sc.Kf = h->Kf.p;
+  sc.K_df = h->K_df.p;
   sc.type = h->type.p;
   sc.mol = h->mol.p;
   sc.loc = h->loc.p;
@@ -791,7 +860,7 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
 mop_status mop_destroy(mop_handle* h) {
   if (!h) return MOP_OK;
   cudaSetDevice(h->device);
-  h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release(); h->c_df.release(); h->Kf.release();
+  h->mass.release(); h->Kspr.release(); h->cL.release(); h->qs.release(); h->c_df.release(); h->K_df.release();
   h->type.release(); h->mol.release(); h->loc.release(); h->inc_off.release();
   h->inc.release(); h->incp.release(); h->incpf.release(); h->tab.release(); h->tab64.release();
   for (auto& e : h->ev)
@@ -807,14 +876,14 @@ mop_status mop_destroy(mop_handle* h) {
   h->pme_theta.release();
   if (h->pme) pme_plans_destroy(h->pme);
   for (auto& P : h->paths) {
-    P.x32.release(); P.x64.release(); P.vel.release(); P.ref.release(); P.reff.release(); P.colid.release();
+    P.x32.release(); P.x64.release(); P.vel.release(); P.snap_x64.release(); P.snap_vel.release(); P.snap_grad.release(); P.snap_x32.release(); P.ref.release(); P.reff.release(); P.colid.release();
     P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();
     P.ts.release(); P.center.release(); P.hext.release(); P.molr.release(); P.emax.release();
     P.cbin.release(); P.bincnt.release(); P.binstart.release(); P.bincur.release(); P.binlist.release();
     P.cwrap.release(); P.cwdf.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
-    P.eta32.release(); P.etamax.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
+    P.eta32.release(); P.etalo.release(); P.etamax.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
     P.gA.release(); P.gB.release(); P.gc.release(); P.gh.release(); P.gw.release();
   }
   delete h;
@@ -829,8 +898,13 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
   if (n_beads < 1) return fail(h, MOP_ERR_ARG, "n_beads must be >= 1");
   if (!xyz) return fail(h, MOP_ERR_ARG, "xyz is NULL");
   CK(h, cudaSetDevice(h->device));
+  AllocScope scope("mop_set_path");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   PathHost& P = h->paths[path_id];
+  // until this call succeeds the path holds no valid coordinates (a failure leaves it unset, and
+  // every other path of the handle as it was)
+  if (P.set) drop_graph(h);
+  P.set = false;
   const size_t n = 3 * (size_t)n_beads * h->sc.Q;
   const bool dev = flags & MOP_DEVPTR, f64 = flags & MOP_INPUT_F64;
   CK(h, P.x32.ensure(n));
@@ -891,6 +965,7 @@ mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, doubl
   if (!h) return MOP_ERR_ARG;
   h->err.clear();
   h->launches = 0;
+  AllocScope scope("mop_veff_and_grad");
   std::vector<int> ids;
   mop_status s = select_paths(h, path_id, &ids);
   if (s) return s;
@@ -943,7 +1018,7 @@ mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* 
   const bool mixed = h->precision == MOP_PREC_MIXED;
   switch (field) {
     case MOP_FIELD_FORCE: f = P.F.p; rows = N == 1 ? 1 : N - 1; fmt = mixed ? 1 : 0; break;
-    case MOP_FIELD_ETA: f = mixed ? (const void*)P.eta32.p : P.eta.p; rows = N - 1; fmt = mixed ? 2 : 0; break;
+    case MOP_FIELD_ETA: f = mixed ? (const void*)P.eta32.p : P.eta.p; rows = N - 1; fmt = mixed ? 3 : 0; break;
     case MOP_FIELD_HETA: f = P.Heta.p; rows = N - 1; fmt = mixed ? 2 : 0; break;
     default: return fail(h, MOP_ERR_ARG, "unknown field %d", field);
   }
@@ -953,7 +1028,8 @@ mop_status mop_get_field(mop_handle* h, int32_t path_id, int32_t field, double* 
     CK(h, h->scratch.ensure(n));
     dst = h->scratch.p;
   }
-  k_gather_field<<<dim3(nblk(h->sc.Q, 256), N), 256, 0, st>>>(f, fmt, P.slot.p, h->sc.Q, Qpad, N, rows, dst);
+  k_gather_field<<<dim3(nblk(h->sc.Q, 256), N), 256, 0, st>>>(f, fmt == 3 ? P.etalo.p : nullptr, fmt, P.slot.p,
+                                                                h->sc.Q, Qpad, N, rows, dst);
   CK(h, cudaGetLastError());
   if (!(flags & MOP_DEVPTR)) {
     CK(h, cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1182,19 +1258,71 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
     h->graph_gamma = gamma;
     h->graph_seed = seed;
   }
-  for (int k = 0; k < n_steps; ++k) CK(h, cudaGraphLaunch(h->graph_exec, gs));
-  CK(h, cudaStreamSynchronize(gs));
-  // a list that outgrew its capacity during the replays invalidates those steps
+  // The replays rebuild every list on the device with the capacity of the last synchronous build
+  // (25% headroom).  A list that outgrows it sets a sticky flag and invalidates the replayed
+  // steps: the integrator state is then restored from a snapshot taken here, the capacity grows
+  // to 1.25 x the largest count the replays met, and the steps run again (at most 3 attempts).
   for (int id : ids) {
-    int flag = 0;
-    CK(h, cudaMemcpy(&flag, h->paths[id].meta.p + 3, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) {
-      drop_graph(h);
-      h->paths[id].sized = false;
-      return fail(h, MOP_ERR_STATE,
-                  "pair list of path %d outgrew its capacity during graph replay; steps since the last "
-                  "synchronous call are invalid (set the path again)", id);
+    PathHost& P = h->paths[id];
+    const size_t n = 3 * (size_t)P.N * h->sc.Q;
+    CK(h, P.snap_x64.ensure(n));
+    CK(h, P.snap_vel.ensure(n));
+    CK(h, P.snap_grad.ensure(n));
+    CK(h, P.snap_x32.ensure(n));
+    CK(h, cudaMemcpyAsync(P.snap_x64.p, P.x64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, gs));
+    CK(h, cudaMemcpyAsync(P.snap_vel.p, P.vel.p, n * sizeof(double), cudaMemcpyDeviceToDevice, gs));
+    CK(h, cudaMemcpyAsync(P.snap_grad.p, P.grad_int.p, n * sizeof(double), cudaMemcpyDeviceToDevice, gs));
+    CK(h, cudaMemcpyAsync(P.snap_x32.p, P.x32.p, n * sizeof(float), cudaMemcpyDeviceToDevice, gs));
+  }
+  unsigned long long step0 = 0;
+  CK(h, cudaMemcpyAsync(&step0, h->step_dev.p, sizeof(step0), cudaMemcpyDeviceToHost, gs));
+  CK(h, cudaStreamSynchronize(gs));
+  for (int attempt = 0;; ++attempt) {
+    for (int k = 0; k < n_steps; ++k) CK(h, cudaGraphLaunch(h->graph_exec, gs));
+    CK(h, cudaStreamSynchronize(gs));
+    bool over = false;
+    for (int id : ids) {
+      PathHost& P = h->paths[id];
+      int meta[4];
+      CK(h, cudaMemcpy(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost));
+      if (!meta[3]) continue;
+      over = true;
+      ++P.overflows;
+      P.cap = std::max(P.cap, (meta[2] + meta[2] / 4 + 31) / 32 * 32);
+      P.sized = false;
+      CK(h, cudaMemset(P.meta.p + 3, 0, sizeof(int)));
     }
+    if (!over) break;
+    drop_graph(h);
+    if (attempt == 2)
+      return fail(h, MOP_ERR_STATE,
+                  "pair lists kept outgrowing their capacity during graph replay; steps since the last "
+                  "synchronous call are invalid (set the paths again)");
+    for (int id : ids) {
+      PathHost& P = h->paths[id];
+      const size_t n = 3 * (size_t)P.N * h->sc.Q;
+      CK(h, cudaMemcpyAsync(P.x64.p, P.snap_x64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, gs));
+      CK(h, cudaMemcpyAsync(P.vel.p, P.snap_vel.p, n * sizeof(double), cudaMemcpyDeviceToDevice, gs));
+      CK(h, cudaMemcpyAsync(P.grad_int.p, P.snap_grad.p, n * sizeof(double), cudaMemcpyDeviceToDevice, gs));
+      CK(h, cudaMemcpyAsync(P.x32.p, P.snap_x32.p, n * sizeof(float), cudaMemcpyDeviceToDevice, gs));
+    }
+    CK(h, cudaMemcpyAsync(h->step_dev.p, &step0, sizeof(step0), cudaMemcpyHostToDevice, gs));
+    // a synchronous evaluation at the restored positions sizes the lists with the new capacity
+    // and uploads the path table; then the step is captured again
+    if ((s = evaluate(h, ids, nullptr, nullptr, gs))) return s;
+    CK(h, cudaStreamSynchronize(gs));
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    s = step_body(h, ids, dt_md, gamma, seed, gs, false);
+    cudaError_t ce = cudaStreamEndCapture(gs, &g);
+    if (s) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    CK(h, ce);
+    ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, ce);
   }
   return MOP_OK;
 }
@@ -1230,6 +1358,14 @@ mop_status mop_get_list_stats(const mop_handle* h, int32_t path_id, int64_t* bui
   if (!P.set) return MOP_ERR_STATE;
   if (builds) *builds = P.builds;
   if (reuses) *reuses = P.reuses;
+  return MOP_OK;
+}
+
+mop_status mop_get_list_overflows(const mop_handle* h, int32_t path_id, int64_t* overflows) {
+  if (!h || !overflows || path_id < 0 || path_id >= kMaxPaths) return MOP_ERR_ARG;
+  const PathHost& P = h->paths[path_id];
+  if (!P.set) return MOP_ERR_STATE;
+  *overflows = P.overflows;
   return MOP_OK;
 }
 

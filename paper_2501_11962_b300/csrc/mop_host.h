@@ -10,6 +10,13 @@
 
 namespace mop {
 
+// Allocation-failure injection for tests, on the host side (no device fault): with the
+// environment variable MOP_FAIL_ALLOC = "<call>:<k>[,<call>:<k>...]", the k-th device allocation
+// inside the next call of that entry point (mop_create, mop_set_path, mop_veff_and_grad) fails
+// once with cudaErrorMemoryAllocation instead of reaching cudaMalloc.  Unset, it does nothing.
+void alloc_hook_enter(const char* call);   // at the entry of those calls
+bool alloc_hook_fail();                    // true: fail this allocation
+
 // Grow-only device buffer.  ensure() reports allocation failure through its return value.
 template <class T>
 struct DevBuf {
@@ -21,7 +28,7 @@ struct DevBuf {
     p = nullptr;
     cap = 0;
     size_t want = n > 0 ? n : 1;
-    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    cudaError_t e = alloc_hook_fail() ? cudaErrorMemoryAllocation : cudaMalloc(&p, want * sizeof(T));
     if (e != cudaSuccess) { p = nullptr; return e; }
     cap = want;
     return cudaSuccess;
@@ -78,11 +85,16 @@ struct PathHost {
   DevBuf<unsigned long long> emask;
   // fields
   DevBuf<double> Fnb, F, eta, Hnb, Heta, grad_int;
-  DevBuf<float4> eta32;
+  DevBuf<float4> eta32, etalo;
   DevBuf<unsigned> etamax;
   DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
   DevBuf<double> e_excl;   // Ewald: bead-1 energy partials of the exclusion corrections
+  // graph-mode steps: the integrator state before the replays, restored when a list outgrew its
+  // capacity so that the replays can run again with a larger one
+  DevBuf<double> snap_x64, snap_vel, snap_grad;
+  DevBuf<float> snap_x32;
+  long long overflows = 0;  // graph-mode step batches of this path run again after a list overflow
   // Verlet skin: coordinates at the last list build and the largest squared displacement since
   DevBuf<float> xref;
   DevBuf<unsigned> dmax;

@@ -66,7 +66,7 @@ struct SysConsts {
   const double* cL;     // dt / (m nu)
   const double* qs;     // q sqrt(f)
   const float2* c_df;   // c_i as a double-float (hi, lo) pair
-  const float* Kf;      // K_i rounded to FP32
+  const float2* K_df;   // K_i as a double-float (hi, lo) pair
   const int* type;
   const int* mol;
   const int* loc;
@@ -117,6 +117,7 @@ struct PathDev {
   double* F;
   double* eta;
   float4* eta32;
+  float4* etalo;           // mixed mode: eta - eta32 (eta as the double-float eta32 + etalo)
   double* Hnb;
   double* Heta;
   unsigned* etamax;        // [N] float bits of max_i |eta_i|

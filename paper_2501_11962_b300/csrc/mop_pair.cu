@@ -1,16 +1,22 @@
-// Pair kernels of the hot path: nonbonded force F(R^n), adjoint Hessian-vector product
+// Cluster-pair kernels of the hot path: nonbonded force F(R^n), adjoint Hessian-vector product
 // H(R^n) eta^n, and the paper's finite-difference stand-in F(R + eps eta) - F(R - eps eta).
+// These run the FP64 mode (MOP_PREC_FP64, config 1) and, selected with MOP_PAIR_KERNELS=half, the
+// half-list form of the mixed mode; mixed precision otherwise runs the bead-lane kernels of
+// mop_pairb.cu.
 //
 // Paper: the three do_force calls per bead of Sec. 2.1 (Fig. 2) carry "the majority of the
-// computational effort"; the FD term is the last term of Eq. 5.  Here one persistent launch
-// covers every (path, bead, i-cluster) unit of every path.
+// computational effort"; the FD term is the last term of Eq. 5.  One launch covers every (path,
+// bead, i-cluster) unit of every path.
 //
-// Work unit = one warp x one i-cluster (8 atoms) x one bead, over the i-cluster's full list of
-// j-clusters (both directions are listed, so no j-force is written and no atomics are needed).
-// Lane l handles i-atom (l & 7) against j-atoms (l >> 3) and (l >> 3) + 4 of each j-cluster.
-// Pair arithmetic is FP32 (MOP_PREC_MIXED) or FP64; FP32 partial sums over 16 j-clusters are
-// folded into an FP32 (hi, lo) pair by TwoSum, and the four lanes of an i-atom are summed in
-// FP64.  Pair potential (r < rc, shifted-force modifier by default):
+// Work unit = one warp x one i-cluster (8 atoms) x B beads (FP64: 1; FP32: 2, in f32x2).  Lane l
+// handles i-atom (l & 7) against j-atoms (l >> 3) and (l >> 3) + 4 of each listed j-cluster.
+// FP64 mode walks the full list (every cluster pair from both sides), so each i-atom's sum is
+// complete in its own warp and nothing else is written.  The FP32 half-list form walks each
+// unordered cluster pair once: the j-atoms' share (-f) is summed over the warp and added to
+// jacc as 2^-23 fixed point with 64-bit integer atomics (order-independent, so the result is
+// bitwise reproducible).  FP32 partial sums over 16 j-clusters are folded into an FP32 (hi, lo)
+// pair by TwoSum, and the four lanes of an i-atom are summed as double-floats (FP64 mode sums in
+// FP64).  Pair potential (r < rc, shifted-force modifier by default):
 //   phi(r) = c12 r^-12 - c6 r^-6 + f q_i q_j (1/r + k_rf r^2 - c_rf)
 //   g  = -phi'_sf(r)/r                     force on i: g d,  d = r_i - r_j
 //   b  = (phi''(r) + g) / r^2              H block A = b d d^T - g I,  A u with u = eta_i - eta_j

@@ -52,6 +52,14 @@ constexpr int kBLIlp = MOP_BL_ILP;
 #ifndef MOP_BL_JPF_F
 #define MOP_BL_JPF_F 0
 #endif
+// L1 prefetch of the next j-atom's rows (prefetch.global.L1, no registers held)
+#ifndef MOP_BL_L1PF
+#define MOP_BL_L1PF 0
+#endif
+// HVP and FD kernels: the i-atoms' eta in shared memory instead of registers (more warps)
+#ifndef MOP_BL_EISH
+#define MOP_BL_EISH 0
+#endif
 #ifndef MOP_BL_JPF_H
 #define MOP_BL_JPF_H 0
 #endif
@@ -77,6 +85,7 @@ template <int MODE> struct BLWarp {
   unsigned long long m[32];
   float4 pt[kBLI * kMaxTypes * BLRow<MODE>::value];
   float2 hl[2 * kBLI * 3][32];   // lane's folded sums: hi at [a * 3 + c], lo at [3 kBLI + a * 3 + c]
+  float2 ei[MOP_BL_EISH && MODE >= 1 ? kBLI * 3 : 1][32];   // i-atoms' eta (MOP_BL_EISH)
 };
 
 // Constants of one pair (both halves equal) for the f32x2 arithmetic.
@@ -256,7 +265,12 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
     for (int c = 0; c < 3; ++c) {
       const size_t o = ((size_t)(ci * kCL + a0 + a) * 3 + c) * 32;
       xi[a][c] = __ldg(xg + o);
-      ei[a][c] = MODE >= 1 ? __ldg(eg + o) : make_float2(0.f, 0.f);
+      if constexpr (MOP_BL_EISH && MODE >= 1) {
+        S.ei[a * 3 + c][lane] = __ldg(eg + o);
+        ei[a][c] = make_float2(0.f, 0.f);
+      } else {
+        ei[a][c] = MODE >= 1 ? __ldg(eg + o) : make_float2(0.f, 0.f);
+      }
       acc[a][c] = make_float2(0.f, 0.f);
     }
   __syncwarp();
@@ -285,6 +299,15 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
     }
     J.qj = dup2(__ldg(&P.xq[sj]).w);
     J.tj = __ldg(&P.ts[sj]) * NR;
+  };
+  auto prefetch_j = [&](int cj, int jj) __attribute__((always_inline)) {
+    const int sj = cj * kCL + jj;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = ((size_t)sj * 3 + c) * 32;
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(xg + o));
+      if (MODE >= 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(eg + o));
+    }
   };
   for (int c0 = 0; c0 < cnt; c0 += 32) {
     const int nc = min(32, cnt - c0);
@@ -320,10 +343,12 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
           c.sh = fma2(c.qq, k.drf, make_float2(t1.z, t1.w));
           if constexpr (MODE == 0) {
             bl_force<EW>(k, c, sc.rc2f, xi[i], xj, acc[i]);
-          } else if constexpr (MODE == 1) {
-            bl_hvp<EW>(k, c, sc.rc2f, tp[2], xi[i], xj, ei[i], cur.e, acc[i]);
           } else {
-            bl_fd<EW>(k, c, sc.rc2f, eps2, xi[i], xj, ei[i], cur.e, acc[i]);
+            float2 eii[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) eii[cc] = MOP_BL_EISH ? S.ei[i * 3 + cc][lane] : ei[i][cc];
+            if constexpr (MODE == 1) bl_hvp<EW>(k, c, sc.rc2f, tp[2], xi[i], xj, eii, cur.e, acc[i]);
+            else bl_fd<EW>(k, c, sc.rc2f, eps2, xi[i], xj, eii, cur.e, acc[i]);
           }
         };
         // groups of kBLIlp i-atoms whose candidate bits are all set are evaluated together (their
@@ -361,6 +386,10 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
 #pragma unroll
       for (int jj = 0; jj < kCL; ++jj) {
         if (!((Mi >> (8 * jj)) & 0xffull)) continue;   // warp-uniform
+        if constexpr (MOP_BL_L1PF) {
+          // the next j-atom's rows move towards L1 while this one is evaluated (no registers)
+          if (jj + 1 < kCL && ((Mi >> (8 * (jj + 1))) & 0xffull)) prefetch_j(cj, jj + 1);
+        }
         BLJ cur;
         load_j(cj, jj, cur);
         eval_j(cur, jj);
@@ -493,9 +522,11 @@ cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, l
 // phi_sf(r) = phi(r) - phi(rc) - (r - rc) phi'(rc) (sh = phi'(rc) = 0 with the potential shift).
 template <bool EW>
 __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __restrict__ paths, int max_clu) {
+  __shared__ int4 sent[4][32];
+  __shared__ unsigned long long sm[4][32];
   const PathDev& P = paths[blockIdx.y];
-  const int lane = threadIdx.x & 31;
-  const int ci = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ci = blockIdx.x * 4 + w;
   if (ci >= max_clu || ci >= __ldg(&P.meta[0])) return;   // warp-uniform
   const int i = lane & 7, jq = lane >> 3;
   const int si = ci * kCL + i;
@@ -504,41 +535,50 @@ __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __
   const int cnt = __ldg(&P.lcnt[ci]);
   const size_t eb = (size_t)ci * P.cap;
   float acc = 0.f, hi = 0.f, lo = 0.f;
-  for (int e = 0; e < cnt; ++e) {
-    const int4 E = __ldg(&P.ent[eb + e]);
-    const unsigned long long M = __ldg(&P.emask[eb + e]);
-    const int cj = E.x & kCluMask;
-    const float Dx = __int_as_float(E.y), Dy = __int_as_float(E.z), Dz = __int_as_float(E.w);
+  for (int c0 = 0; c0 < cnt; c0 += 32) {
+    // the warp loads 32 entries at once; the j-atom loads of an entry then depend on a
+    // shared-memory read only
+    const int nc = min(32, cnt - c0);
+    __syncwarp();
+    if (lane < nc) {
+      sent[w][lane] = __ldg(&P.ent[eb + c0 + lane]);
+      sm[w][lane] = __ldg(&P.emask[eb + c0 + lane]);
+    }
+    __syncwarp();
+    for (int e = 0; e < nc; ++e) {
+      const int4 E = sent[w][e];
+      const unsigned long long M = sm[w][e];
+      const int cj = E.x & kCluMask;
+      const float Dx = __int_as_float(E.y), Dy = __int_as_float(E.z), Dz = __int_as_float(E.w);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = jq + 4 * h;
-      if (!((M >> (j * kCL + i)) & 1ull)) continue;
-      const int sj = cj * kCL + j;
-      const float4 xj = __ldg(&P.xq[sj]);
-      const float4 p = sc.tab[ti * sc.n_types + __ldg(&P.ts[sj])];
-      const float dx = xi.x + Dx - xj.x, dy = xi.y + Dy - xj.y, dz = xi.z + Dz - xj.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (!(r2 < sc.rc2f)) continue;
-      const float rinv = rsqrtf(r2);
-      const float r = r2 * rinv;
-      const float rinv6 = rinv * rinv * rinv * rinv * rinv * rinv;
-      const float qq = xi.w * xj.w;
-      const float sh = fmaf(qq, sc.drff, p.z);
-      const float elj = rinv6 * fmaf(p.x * (1.f / 12.f), rinv6, -p.y * (1.f / 6.f));
-      float el;
-      if constexpr (EW) {
-        const float x = sc.ewb * r;
-        const float ec = ex2_approx(-sc.ewb2 * r2 * 1.4426950408889634f) * erfcx_rational(x);
-        el = qq * fmaf(ec, rinv, -sc.ewec);
-      } else {
-        el = qq * (rinv + fmaf(sc.krff, r2, -sc.crff));
+      for (int h = 0; h < 2; ++h) {
+        const int j = jq + 4 * h;
+        if (!((M >> (j * kCL + i)) & 1ull)) continue;
+        const int sj = cj * kCL + j;
+        const float4 xj = __ldg(&P.xq[sj]);
+        const float4 p = __ldg(&sc.tab[ti * sc.n_types + __ldg(&P.ts[sj])]);
+        const float dx = xi.x + Dx - xj.x, dy = xi.y + Dy - xj.y, dz = xi.z + Dz - xj.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(r2 < sc.rc2f)) continue;
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float rinv6 = rinv * rinv * rinv * rinv * rinv * rinv;
+        const float qq = xi.w * xj.w;
+        const float sh = fmaf(qq, sc.drff, p.z);
+        const float elj = rinv6 * fmaf(p.x * (1.f / 12.f), rinv6, -p.y * (1.f / 6.f));
+        float el;
+        if constexpr (EW) {
+          const float x = sc.ewb * r;
+          const float ec = ex2_approx(-sc.ewb2 * r2 * 1.4426950408889634f) * erfcx_rational(x);
+          el = qq * fmaf(ec, rinv, -sc.ewec);
+        } else {
+          el = qq * (rinv + fmaf(sc.krff, r2, -sc.crff));
+        }
+        acc += elj + el - p.w - (r - sc.rcf) * sh;
       }
-      acc += elj + el - p.w - (r - sc.rcf) * sh;
     }
-    if ((e & 15) == 15) {
-      two_sum_add(hi, lo, acc);
-      acc = 0.f;
-    }
+    two_sum_add(hi, lo, acc);
+    acc = 0.f;
   }
   two_sum_add(hi, lo, acc);
   const df v = df_warp_sum(df{hi, lo});

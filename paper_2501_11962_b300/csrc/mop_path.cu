@@ -365,7 +365,7 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
     const float2* Fnb = reinterpret_cast<const float2*>(P.Fnb) + 3 * k;
     float2* Fo = reinterpret_cast<float2*>(P.F) + 3 * k;
     df F[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    float4 ef = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ef = make_float4(0.f, 0.f, 0.f, 0.f), efl = ef;
     {
       float Fb[3] = {0.f, 0.f, 0.f};
       bonded_force<float, float, float>(sc, P, a, n, Fb, n == 0 ? &eb : nullptr);
@@ -376,19 +376,24 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
       if (P.N > 1) {
         const size_t b0 = (size_t)n * 3 * P.Q + 3 * (size_t)a, b1 = b0 + 3 * (size_t)P.Q;
         const float2 cc = sc.c_df[a];
-        float e[3];
+        float e[3], el[3];
         for (int c = 0; c < 3; ++c) {
           const df d = two_sum(P.x32[b1 + c], -P.x32[b0 + c]);   // exact R^{n+1} - R^n
           const df cf = df_mul(df{cc.x, cc.y}, F[c]);
-          const df et = df_add(d, df_neg(cf));
-          e[c] = et.hi + et.lo;
+          const df et = df_add(d, df_neg(cf));   // normalised: hi = FP32 rounding of eta
+          e[c] = et.hi;
+          el[c] = et.lo;
         }
         ef = make_float4(e[0], e[1], e[2], 0.f);
+        efl = make_float4(el[0], el[1], el[2], 0.f);
         if (sc.hvp_mode == 1) nbits = __float_as_uint(sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) * 1.000001f);
       }
     }
     for (int c = 0; c < 3; ++c) Fo[c] = make_float2(F[c].hi, F[c].lo);
-    if (P.N > 1) P.eta32[k] = ef;
+    if (P.N > 1) {
+      P.eta32[k] = ef;
+      P.etalo[k] = efl;
+    }
   }
   if (sc.hvp_mode == 1) {
     // one atomic per warp (all lanes belong to bead n)
@@ -407,8 +412,10 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
   }
 }
 
-// H eta (pair part from the HVP kernel + bonded part), the gradient of Eqs. 5-7 in FP32 from the
-// FP32-rounded eta, spring energy summed as double-floats per warp and in FP64 per block.
+// H eta (pair part from the HVP kernel + bonded part, FP32), the gradient of Eqs. 5-7 in
+// double-float, G^n = K (eta^{n-1} - eta^n) + H eta^n / 2 (- F^1 at bead 1), from the double-float
+// eta and F of E1, written as FP64; spring energy summed as double-floats per warp and in FP64
+// per block.
 template <bool FD>
 __global__ void MOP_E2_BOUNDS k_e2_mixed(SysConsts sc, const PathDev* __restrict__ paths, int n_paths,
                                                         double* e_spring, int nbx, int maxN, int n_begin) {
@@ -426,21 +433,26 @@ __global__ void MOP_E2_BOUNDS k_e2_mixed(SysConsts sc, const PathDev* __restrict
     const int s = P.slot[a];
     const size_t k = (size_t)n * P.Qpad + s;
     {
-      const float K = sc.Kf[a];
-      float g[3] = {0.f, 0.f, 0.f};
-      if (n == 0) {
-        const float2* F1 = reinterpret_cast<const float2*>(P.F) + 3 * (size_t)s;
-        for (int c = 0; c < 3; ++c) g[c] = -(F1[c].x + F1[c].y);
-      }
+      const float2 Kv = sc.K_df[a];
+      const df K{Kv.x, Kv.y};
+      // eta^{n-1} - eta^n as double-floats (eta^{-1} = eta^{N-1} = 0)
+      df d[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
       if (n > 0) {
-        const float4 ep = P.eta32[k - P.Qpad];
-        g[0] += K * ep.x;
-        g[1] += K * ep.y;
-        g[2] += K * ep.z;
+        const float4 h = P.eta32[k - P.Qpad], l = P.etalo[k - P.Qpad];
+        d[0] = df{h.x, l.x};
+        d[1] = df{h.y, l.y};
+        d[2] = df{h.z, l.z};
       }
+      float H[3] = {0.f, 0.f, 0.f};
       if (n < P.N - 1) {
+        const float4 h = P.eta32[k], l = P.etalo[k];
+        d[0] = df_add(d[0], df{-h.x, -l.x});
+        d[1] = df_add(d[1], df{-h.y, -l.y});
+        d[2] = df_add(d[2], df{-h.z, -l.z});
         const float4 hn = reinterpret_cast<const float4*>(P.Hnb)[k];
-        float H[3] = {hn.x, hn.y, hn.z};
+        H[0] = hn.x;
+        H[1] = hn.y;
+        H[2] = hn.z;
         if (P.jacc) {   // j-side sums
           const unsigned long long* J = P.jacc + 3 * k;
           for (int c = 0; c < 3; ++c) H[c] += __ll2float_rn((long long)J[c]) * kFixInv;
@@ -452,16 +464,19 @@ __global__ void MOP_E2_BOUNDS k_e2_mixed(SysConsts sc, const PathDev* __restrict
         }
         bonded_hvp<float, FD, float>(sc, P, a, n, eps, H);
         reinterpret_cast<float4*>(P.Heta)[k] = make_float4(H[0], H[1], H[2], 0.f);
-        const float4 e = P.eta32[k];
-        g[0] += fmaf(-K, e.x, 0.5f * H[0]);
-        g[1] += fmaf(-K, e.y, 0.5f * H[1]);
-        g[2] += fmaf(-K, e.z, 0.5f * H[2]);
-        es = 0.5f * K * (e.x * e.x + e.y * e.y + e.z * e.z);
+        es = 0.5f * Kv.x * (h.x * h.x + h.y * h.y + h.z * h.z);
+      }
+      df g[3];
+      for (int c = 0; c < 3; ++c) g[c] = df_add_f(df_mul(K, d[c]), 0.5f * H[c]);
+      if (n == 0) {
+        const float2* F1 = reinterpret_cast<const float2*>(P.F) + 3 * (size_t)s;
+        for (int c = 0; c < 3; ++c) g[c] = df_add(g[c], df{-F1[c].x, -F1[c].y});
       }
       double* G = P.grad + 3 * ((size_t)n * P.Q + a);
-      G[0] = widen(g[0]);
-      G[1] = widen(g[1]);
-      G[2] = widen(g[2]);
+      // hi + lo is exact in FP64; the halves are widened on the integer pipes
+      G[0] = widen(g[0].hi) + widen(g[0].lo);
+      G[1] = widen(g[1].hi) + widen(g[1].lo);
+      G[2] = widen(g[2].hi) + widen(g[2].lo);
     }
   }
   const df w = df_warp_sum(df{es, 0.f});

@@ -27,7 +27,7 @@ EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_vef
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
            "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_measure_fp32_peak",
            "mop_metadynamics", "mop_get_gaussians", "mop_add_cv", "mop_add_gaussian",
-           "mop_set_list_skin", "mop_get_list_stats", "mop_last_error")
+           "mop_set_list_skin", "mop_get_list_stats", "mop_get_list_overflows", "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -101,6 +101,7 @@ def load(build_if_needed: bool = True):
     L.mop_autotune.argtypes = [p, i32, p, p]
     L.mop_set_list_skin.argtypes = [p, d]
     L.mop_get_list_stats.argtypes = [p, i32, p, p]
+    L.mop_get_list_overflows.argtypes = [p, i32, p]
     L.mop_last_error.argtypes = [p]
     L.mop_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -269,6 +270,12 @@ class Engine:
         b, r = C.c_int64(), C.c_int64()
         self._check(self.L.mop_get_list_stats(self.h, path_id, C.byref(b), C.byref(r)), "mop_get_list_stats")
         return b.value, r.value
+
+    def list_overflows(self, path_id: int) -> int:
+        """Graph-mode step batches of path_id run again after a pair list outgrew its capacity."""
+        n = C.c_int64()
+        self._check(self.L.mop_get_list_overflows(self.h, path_id, C.byref(n)), "mop_get_list_overflows")
+        return n.value
 
     def set_graph_mode(self, on: bool = True):
         self._check(self.L.mop_set_graph_mode(self.h, int(on)), "mop_set_graph_mode")

@@ -453,11 +453,21 @@ def nearest_group(pos: np.ndarray, box: np.ndarray, center: np.ndarray, k: int) 
 UNEVEN_BEADS = (24, 40, 64, 96, 128, 160, 200, 256)
 
 
-def config(k: int, n_beads: int | None = None, seed: int | None = None) -> Workload:
-    """Workload k (1..5).  `n_beads` overrides the bead count of every path."""
+def config(k: int, n_beads: int | None = None, seed: int | None = None, base=None) -> Workload:
+    """Workload k (1..5).  `n_beads` overrides the bead count of every path; `base` (Q x 3)
+    replaces the generated base structure (for example a relaxed copy of it) before the beads
+    are drawn around it.  The base structure in use is kept in system.extra["base"]."""
     s = 1000 + k if seed is None else seed
+    w = _config(k, n_beads, s, base)
+    return w
+
+
+def _config(k: int, n_beads, s: int, base) -> Workload:
+    def pick(pos):
+        return pos if base is None else np.asarray(base, np.float64).reshape(pos.shape)
     if k == 1:
         sys, pos = lj_fcc()
+        pos = pick(pos)
         sys.name = "cfg1_lj256"
         N = 16 if n_beads is None else n_beads
         w = Workload(sys, [make_path(pos, N, s)], precision="fp64", fd_h=1e-5, label="cfg1")
@@ -465,17 +475,23 @@ def config(k: int, n_beads: int | None = None, seed: int | None = None) -> Workl
         return w
     if k == 2:
         sys, pos = water_box(1000, rc=0.9, seed=s)
+        pos = pick(pos)
         sys.name = "cfg2_water1000"
+        sys.extra["base"] = pos
         N = 64 if n_beads is None else n_beads
         return Workload(sys, [make_path(pos, N, s + 100)], label="cfg2")
     if k == 3:
         sys, pos = water_box(8000, rc=1.0, seed=s)
+        pos = pick(pos)
         sys.name = "cfg3_water8000"
+        sys.extra["base"] = pos
         N = 128 if n_beads is None else n_beads
         return Workload(sys, [make_path(pos, N, s + 100)], label="cfg3")
     if k == 4:
         sys, pos = water_box(3333, rc=1.0, seed=s, n_ions=1)
+        pos = pick(pos)
         sys.name = "cfg4_water3333_ion"
+        sys.extra["base"] = pos
         beads = UNEVEN_BEADS if n_beads is None else (n_beads,) * len(UNEVEN_BEADS)
         paths = [make_path(pos, n, s + 100 + p) for p, n in enumerate(beads)]
         rng = np.random.default_rng(s + 7)
@@ -486,7 +502,9 @@ def config(k: int, n_beads: int | None = None, seed: int | None = None) -> Workl
                         bias=dict(height=1.0, width=0.05), label="cfg4")
     if k == 5:
         sys, pos = chains_and_water(seed=s)
+        pos = pick(pos)
         sys.name = "cfg5_chains_water150k"
+        sys.extra["base"] = pos
         N = 64 if n_beads is None else n_beads
         return Workload(sys, [make_path(pos, N, s + 100)], label="cfg5")
     raise ValueError(f"no workload {k}")

@@ -17,12 +17,17 @@ def pytest_configure(config):
 _CACHE = {}
 
 
-def workload(k, **kw):
-    """Seeded workload k (1..5), cached per test session."""
+RELAXED = ROOT / "tests" / "golden" / "relaxed"
+
+
+def workload(k, relaxed=False, **kw):
+    """Seeded workload k (1..5), cached per test session.  relaxed: around the stored relaxed
+    base structure (tests/golden/relax_inputs.py) instead of the generated one."""
     from paper_2501_11962_b300 import synth
-    key = (k, tuple(sorted(kw.items())))
+    key = (k, relaxed, tuple(sorted(kw.items())))
     if key not in _CACHE:
-        _CACHE[key] = synth.config(k, **kw)
+        base = np.load(RELAXED / f"cfg{k}.npy") if relaxed else None
+        _CACHE[key] = synth.config(k, base=base, **kw)
     return _CACHE[key]
 
 

@@ -1,7 +1,7 @@
 """mop_step in CUDA-graph mode: one captured MD step of several uneven paths (sort, list, pair
 kernels, bonded terms, gradient and integrator, no host synchronisation) replayed n times must
-reproduce the eager steps exactly, and replays split over several calls must continue the
-Philox step counter."""
+reproduce the eager steps exactly, replays split over several calls must continue the Philox
+step counter, and a list that outgrows its capacity during the replays must be recovered from."""
 import numpy as np
 import pytest
 
@@ -47,14 +47,30 @@ def test_graph_recaptures_on_new_parameters():
     assert np.isfinite(x2).all()
 
 
-def test_graph_replay_reports_list_overflow():
-    # from these unrelaxed structures a large step moves atoms far enough that the lists outgrow
-    # the capacity sized before the capture; mop_step must say so rather than return bad steps
-    eng = make_engine(True)
-    with pytest.raises(mop.MopError) as ei:
-        for _ in range(20):
-            eng.step(5, 5e-4, 2.0, seed=9)
-    assert ei.value.status == mop.MOP_ERR_STATE
+def test_graph_replay_recovers_from_list_overflow():
+    """Every bead starts at the same relaxed structure, so the lists are sized for beads with no
+    spread; 300 steps of 0.2 fs with a 3000 K thermostat then spread the beads and the lists
+    outgrow that capacity during the replays.  mop_step must notice, restore the state it held
+    before the replays, grow the capacity and run the steps again: the trajectory equals the
+    eager one bit for bit, stays finite, and the repeat is counted."""
+    import dataclasses
+    w = workload(4, relaxed=True)
+    base = np.asarray(w.system.extra["base"], np.float32)
+    hot = dataclasses.replace(w.system, temperature=3000.0)
+    engines = []
+    for graph in (False, True):
+        eng = mop.Engine(hot)
+        for p, n in enumerate((24, 40)):
+            eng.set_path(p, np.repeat(base[None], n, axis=0))
+        eng.set_graph_mode(graph)
+        eng.step(300, 2e-4, 50.0, seed=5)
+        engines.append(eng)
+    eager, graph = engines
+    assert sum(graph.list_overflows(p) for p in (0, 1)) > 0
+    for p in (0, 1):
+        a, b = eager.get_path(p), graph.get_path(p)
+        assert np.isfinite(b).all()
+        assert np.array_equal(a, b), p
 
 
 def test_autotune_keeps_results():
