@@ -9,7 +9,7 @@ from pathlib import Path
 HERE = Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 LIB = HERE / "libmop.so"
-SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_pairb.cu", "mop_path.cu", "mop_pme.cu",
+SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_pairb.cu", "mop_path.cu", "mop_pme.cu", "mop_fft.cu",
            "mop_noalloc.cu", "mop_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed on {s}:\n{out.decode(errors='replace')}")
     tmp = LIB.with_suffix(".so.tmp")
-    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *objs, "-lcudart", "-lcufft"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *objs, "-lcudart"]
     subprocess.run(cmd, check=True)
     tmp.replace(LIB)
     return LIB

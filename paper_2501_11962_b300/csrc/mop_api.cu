@@ -299,7 +299,6 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     if (pme) {
       const size_t nb = (size_t)std::max(n_force, n_hvp);
       CK(h, P.pme_q.ensure(nb * sc.pme_nk));
-      CK(h, P.pme_r.ensure(nb * sc.pme_nk));
       CK(h, P.pme_c.ensure(nb * sc.pme_nkc));
       CK(h, P.pme_phi.ensure((size_t)n_force * sc.pme_nk));
       CK(h, P.pme_phd.ensure(std::max<size_t>(1, (size_t)n_hvp * sc.pme_nk)));
@@ -362,7 +361,6 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.cwdf = P.cwdf.p;
     if (pme) {
       D.pme_q = P.pme_q.p;
-      D.pme_r = P.pme_r.p;
       D.pme_c = P.pme_c.p;
       D.pme_phi = P.pme_phi.p;
       D.pme_phd = P.pme_phd.p;
@@ -638,6 +636,9 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
     const bool none = d->pme_grid[0] == 0 && d->pme_grid[1] == 0 && d->pme_grid[2] == 0;
     for (int k = 0; k < 3 && !none; ++k) {
       if (d->pme_grid[k] < d->pme_order || d->pme_grid[k] > 1024) return MOP_ERR_ARG;
+      // the grid's FFT runs radices 2, 3, 4, 5 and 7
+      int rad[kFftMaxStages], nr = 0;
+      if (!fft_factor(d->pme_grid[k], rad, &nr)) return MOP_ERR_ARG;
       // odd orders: the spline moduli vanish at the Nyquist frequency of an even grid
       if ((d->pme_order & 1) && !(d->pme_grid[k] & 1)) return MOP_ERR_ARG;
     }

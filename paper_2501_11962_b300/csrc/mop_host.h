@@ -104,7 +104,7 @@ struct PathHost {
   // SPME reciprocal space: fixed-point charge grids, FFT input, spectra, potential grids of the
   // force and HVP passes [beads][grid points], bead-1 energy partials
   DevBuf<unsigned long long> pme_q;
-  DevBuf<float> pme_r, pme_phi, pme_phd;
+  DevBuf<float> pme_phi, pme_phd;
   DevBuf<float2> pme_c;
   DevBuf<double> pme_e;
   // bias
@@ -179,6 +179,32 @@ cudaError_t launch_bias(const SysConsts& sc, const PathDev* d_paths, int n_paths
 cudaError_t launch_reduce(const SysConsts& sc, const PathDev* d_paths, int n_paths, Launch L,
                           const double* e_bond, int e_bond_stride, int n_e1_blocks,
                           const double* e_spring, int e_spring_stride, int n_e2_blocks);
+// --- mop_fft.cu: batched 3-D FFT convolution of the SPME grids --------------------------------
+constexpr int kFftMaxStages = 16;
+constexpr int kFftMaxLen = 2048;   // grid points per axis (factors 2, 3, 5, 7 only)
+// one axis of the transform: its length, radices (8, 4, 2, 3, 5, 7), twiddles exp(-2 pi i k / n)
+struct FftAxis {
+  int n, nr;
+  int radix[kFftMaxStages];
+  unsigned magic;   // ceil(2^32 / n): idx / n as a multiply-high
+  const float2* tw;
+};
+// lines of length n a block transforms at once (one per lane): 32, or fewer for long lines
+// (about 3,200 complex values per shared-memory buffer), and at most `columns`
+inline int fft_lines_per_block(int n, int columns) {
+  int l = n > 0 ? 3200 / n - 1 : 1;
+  if (l > 32) l = 32;
+  if (l > columns) l = columns;
+  return l < 1 ? 1 : l;
+}
+// true when n is a product of 2, 3, 5 and 7
+bool fft_factor(int n, int* radix, int* nr);
+cudaError_t fft_axis_make(int n, DevBuf<float2>& tw, FftAxis* ax);
+// For `beads` grids: q (int64 fixed point, [beads][K1][K2][K3]) -> half spectra c ->
+// times theta (energy: bead 0's partials of 1/2 sum theta |F|^2) -> potential out [beads][K1][K2][K3]
+cudaError_t launch_fft_convolve(const SysConsts& sc, const FftAxis* ax, const unsigned long long* q, float2* c,
+                                float* out, int beads, double* energy, Launch L);
+
 // --- mop_pme.cu: SPME reciprocal space (forces into the j-side sums; mode 1: H eta) ----------
 struct PmePlans;
 PmePlans* pme_plans_create();
@@ -190,7 +216,12 @@ cudaError_t pme_plans_ensure(const SysConsts& sc, PmePlans* plans, int beads, st
 cudaError_t launch_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths,
                        int max_beads, int mode, PmePlans* plans, Launch L, std::string* err);
 // blocks of bead-1 energy partials written by launch_pme
-inline int pme_energy_blocks(const SysConsts& sc) { return (int)((sc.pme_nkc + kRedBlock - 1) / kRedBlock); }
+// (the blocks of the x-line pass of launch_fft_convolve)
+inline int pme_energy_blocks(const SysConsts& sc) {
+  if (sc.pme_nk == 0) return 0;
+  const int cw = sc.pme_K[1] * sc.pme_kc3, l = fft_lines_per_block(sc.pme_K[0], cw);
+  return (cw + l - 1) / l;
+}
 
 cudaError_t launch_kick(const SysConsts& sc, double* vel, const double* grad, int N, double half_dt, Launch L);
 // the Philox step counter is read from device memory (*step), so a captured step can be replayed

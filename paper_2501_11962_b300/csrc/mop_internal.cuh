@@ -141,8 +141,7 @@ struct PathDev {
   double* e_excl;          // Ewald: bead-1 energy partials of the exclusion corrections
   const float2* cwdf;      // wrapped cluster centres as double-floats [n_clu][3]
   unsigned long long* pme_q;   // SPME: fixed-point charge grids [beads][nk]
-  float* pme_r;                // float grids (FFT input) [beads][nk]
-  float2* pme_c;               // spectra [beads][nkc] (cufftComplex)
+  float2* pme_c;               // half spectra [beads][nkc]
   float* pme_phi;              // potential grids of the force pass [beads][nk]
   float* pme_phd;              // potential grids of the derivative grids (HVP pass) [beads][nk]
   double* pme_e;               // bead-1 energy partials

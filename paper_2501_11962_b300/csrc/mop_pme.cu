@@ -9,25 +9,21 @@
 //     (H eta)_i = q_i sum_k [(eta_i . grad) grad M_i](k) phi(k) + q_i sum_k grad M_i(k) phi'(k),
 // with phi the potential grid of the force pass and phi' that of the derivative grid.
 // Grids of charges are summed as int64 fixed point, so results do not depend on the order of
-// the atomics; forces go into the path's fixed-point j-side sums.  The FFTs are cuFFT calls.
-#include <cufft.h>
-
+// the atomics; forces go into the path's fixed-point j-side sums.  The FFT convolution (grid ->
+// spectrum -> times theta -> potential) is the batched transform of mop_fft.cu.
 #include <algorithm>
-#include <map>
-#include <utility>
 
 #include "mop_host.h"
 
 namespace mop {
 
-// cuFFT plans per batch size (beads of one pass), created outside any stream capture
+// twiddle tables and radix plans of the three grid axes, made outside any stream capture
 struct PmePlans {
-  std::map<int, std::pair<cufftHandle, cufftHandle>> by_batch;   // R2C, C2R
+  DevBuf<float2> tw[3];
+  FftAxis ax[3];
+  bool ready = false;
   ~PmePlans() {
-    for (auto& kv : by_batch) {
-      cufftDestroy(kv.second.first);
-      cufftDestroy(kv.second.second);
-    }
+    for (auto& t : tw) t.release();
   }
 };
 
@@ -164,37 +160,6 @@ __global__ void __launch_bounds__(kRedBlock) k_pme_spread(SysConsts sc, const Pa
         atomicAdd(g + row + ix[2][t2], (unsigned long long)__float2ll_rn(v * kGridFixF));
       }
     }
-}
-
-// int64 fixed-point grids -> float grids (the FFT input), for beads [0, n_pass) of a path
-__global__ void k_pme_tofloat(const unsigned long long* __restrict__ q, float* r, long long n) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) r[t] = (float)(long long)q[t] * kGridInv;
-}
-
-// multiplies the spectra by theta (shared by all beads); with `energy`, bead 0's block partials
-// of E = 1/2 sum_m theta |F(m)|^2 over the half spectrum (weight 2 for 0 < m3 < K3/2)
-__global__ void __launch_bounds__(kRedBlock) k_pme_scale(SysConsts sc, cufftComplex* c, long long nkc, int beads,
-                                                         double* energy) {
-  __shared__ double sh[32];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = blockIdx.y;
-  double e = 0.0;
-  if (n < beads && t < nkc) {
-    const float th = sc.pme_theta[t];
-    cufftComplex& v = c[(size_t)n * nkc + t];
-    if (energy && n == 0) {
-      const int m3 = (int)(t % sc.pme_kc3);
-      const double wgt = (m3 == 0 || 2 * m3 == sc.pme_K[2]) ? 1.0 : 2.0;
-      e = 0.5 * wgt * (double)th * ((double)v.x * v.x + (double)v.y * v.y);
-    }
-    v.x *= th;
-    v.y *= th;
-  }
-  if (energy && n == 0) {
-    e = block_sum<kRedBlock>(e, sh);
-    if (threadIdx.x == 0) energy[blockIdx.x] = e;
-  }
 }
 
 // forces (MODE 0: F_i = -q_i sum_k grad M_i(k) phi(k)) or H eta (MODE 1) of every slot, added
@@ -395,32 +360,17 @@ cudaError_t run_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* 
   ++*L.counter;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (!plans.ready) {
+    if (err) *err = "no FFT plan for this grid (evaluate once without stream capture first)";
+    return cudaErrorNotReady;
+  }
   for (int p = 0; p < n_paths; ++p) {
     const PathDev& D = h_paths[p];
     const int beads = mode ? D.n_hvp : D.n_force;
     if (beads <= 0) continue;
-    const long long nr = (long long)sc.pme_nk * beads;
-    k_pme_tofloat<<<(int)((nr + 255) / 256), 256, 0, L.st>>>(D.pme_q, D.pme_r, nr);
-    ++*L.counter;
-    auto it = plans.by_batch.find(beads);
-    if (it == plans.by_batch.end()) {
-      if (err) *err = "no FFT plan for this bead count (evaluate once without stream capture first)";
-      return cudaErrorNotReady;
-    }
-    cufftSetStream(it->second.first, L.st);
-    cufftSetStream(it->second.second, L.st);
-    if (cufftExecR2C(it->second.first, D.pme_r, D.pme_c) != CUFFT_SUCCESS) {
-      if (err) *err = "cufftExecR2C failed";
-      return cudaErrorUnknown;
-    }
-    const dim3 cgrid((unsigned)((sc.pme_nkc + kRedBlock - 1) / kRedBlock), beads);
-    k_pme_scale<<<cgrid, kRedBlock, 0, L.st>>>(sc, D.pme_c, sc.pme_nkc, beads, mode == 0 ? D.pme_e : nullptr);
-    ++*L.counter;
-    float* out = mode ? D.pme_phd : D.pme_phi;
-    if (cufftExecC2R(it->second.second, D.pme_c, out) != CUFFT_SUCCESS) {
-      if (err) *err = "cufftExecC2R failed";
-      return cudaErrorUnknown;
-    }
+    e = launch_fft_convolve(sc, plans.ax, D.pme_q, D.pme_c, mode ? D.pme_phd : D.pme_phi, beads,
+                            mode == 0 ? D.pme_e : nullptr, L);
+    if (e != cudaSuccess) return e;
   }
   if (mode == 0) k_pme_gather<P, 0><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
   else k_pme_gather<P, 1><<<sgrid, kRedBlock, 0, L.st>>>(sc, d_paths);
@@ -433,18 +383,18 @@ cudaError_t run_pme(const SysConsts& sc, const PathDev* d_paths, const PathDev* 
 PmePlans* pme_plans_create() { return new PmePlans(); }
 void pme_plans_destroy(PmePlans* p) { delete p; }
 
-// makes sure plans exist for a batch of `beads` transforms (never inside a stream capture)
+// makes the twiddle tables of the grid once (never inside a stream capture); any bead count
 cudaError_t pme_plans_ensure(const SysConsts& sc, PmePlans* plans, int beads, std::string* err) {
-  if (beads <= 0 || plans->by_batch.count(beads)) return cudaSuccess;
-  int n[3] = {sc.pme_K[0], sc.pme_K[1], sc.pme_K[2]};
-  cufftHandle f = 0, b = 0;
-  if (cufftPlanMany(&f, 3, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, beads) != CUFFT_SUCCESS ||
-      cufftPlanMany(&b, 3, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, beads) != CUFFT_SUCCESS) {
-    if (f) cufftDestroy(f);
-    if (err) *err = "cufftPlanMany failed";
-    return cudaErrorMemoryAllocation;
+  (void)beads;
+  if (plans->ready) return cudaSuccess;
+  for (int d = 0; d < 3; ++d) {
+    cudaError_t e = fft_axis_make(sc.pme_K[d], plans->tw[d], &plans->ax[d]);
+    if (e != cudaSuccess) {
+      if (err) *err = "FFT tables of the SPME grid";
+      return e == cudaErrorInvalidValue ? cudaErrorInvalidValue : cudaErrorMemoryAllocation;
+    }
   }
-  plans->by_batch[beads] = {f, b};
+  plans->ready = true;
   return cudaSuccess;
 }
 
