@@ -459,3 +459,23 @@ def test_cfg3_autograd_gradient_matches_central_differences():
     print(f"cfg3 autograd gradient vs FP64 central differences on {len(jobs)} coordinates: "
           f"relative 2-norm {e:.2e}, largest relative {emax:.2e}")
     assert e < TOL_F, e
+
+
+@pytest.mark.parametrize("hvp_mode", [mop.MOP_HVP_ADJOINT, mop.MOP_HVP_FD])
+def test_half_list_kernels_match_oracle(monkeypatch, hvp_mode):
+    """The half-list pair kernels (MOP_PAIR_KERNELS=half, kept beside the bead-lane kernels for
+    comparison) against the oracle on the water box: forces, H eta (the FD mode against the
+    oracle's own Eq. 5 at the same h) and the gradient."""
+    monkeypatch.setenv("MOP_PAIR_KERNELS", "half")
+    w = workload(2, n_beads=16)
+    X = w.paths[0]
+    N = X.shape[0]
+    kw = dict(hvp_mode=hvp_mode, fd_h=1e-3) if hvp_mode == mop.MOP_HVP_FD else {}
+    eng, g = gpu_eval(w, **kw)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "Heta"),
+                                     **(dict(hvp_mode=oracle.HVP_FD_EQ5, fd_h=1e-3) if kw else {}))
+    errs = dict(F=rel(g["F"][:N - 1], r["F"][:N - 1]), Heta=rel(g["Heta"][:N - 1], r["Heta"][:N - 1]),
+                G=rel(g["G"], r["G"]), V=abs(g["veff"] - r["veff"]) / abs(r["veff"]))
+    print("half-list kernels", hvp_mode, errs)
+    assert errs["F"] < TOL_F and errs["V"] < TOL_V
+    assert errs["Heta"] < (1e-4 if kw else TOL_H) and errs["G"] < (1e-4 if kw else TOL_F)
