@@ -37,9 +37,9 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 FD_SWEEP = (1e-5, 3e-5, 1e-4, 3e-4, 1e-3)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels on
-# this workload, from the ncu launch list in profiles/launches_cfg5_Q150k_N64.md.  Valid only
+# this workload, from the --set full capture in profiles/k_pairb_cfg5_Q150k_N64.md.  Valid only
 # for the kernel sources they were measured on: any change to them makes `traffic` null.
-PAIR_TRAFFIC = {"sources_sha256_16": "", "k_pairb<0,RF>": None, "k_pairb<1,RF>": None}
+PAIR_TRAFFIC = {"sources_sha256_16": "041e50e535584b68", "k_pairb<0,RF>": 408.6e6, "k_pairb<1,RF>": 495.9e6}
 PAIR_SOURCES = ("mop_pairb.cu", "mop_pairmath.cuh", "mop_prep.cu", "mop_internal.cuh")
 # arithmetic of the mixed-precision path, quantity by quantity
 PRECISION = {"pair_arithmetic": "f32 (two beads per f32x2 instruction)",
