@@ -43,9 +43,12 @@ PAIR_TRAFFIC = {"sources_sha256_16": "041e50e535584b68", "k_pairb<0,RF>": 408.6e
 PAIR_SOURCES = ("mop_pairb.cu", "mop_pairmath.cuh", "mop_prep.cu", "mop_internal.cuh")
 # arithmetic of the mixed-precision path, quantity by quantity
 PRECISION = {"pair_arithmetic": "f32 (two beads per f32x2 instruction)",
-             "forces_F": "double-float (f32 hi + lo): f32 pair sums folded by TwoSum, bonded f32 added exactly",
+             "forces_F": "double-float (f32 hi + lo): i-side f32 pair sums folded by TwoSum; j-side shares as "
+                         "40-bit fixed point carried by two f32 atomic sums (exact, order-independent), added by "
+                         "TwoSum; bonded f32 added exactly",
              "eta": "double-float from the exact R^{n+1} - R^n and the double-float c F; f32 copy for the HVP",
-             "H_eta": "f32 (pair and bonded terms)",
+             "H_eta": "f32 (pair and bonded terms; j-side shares on the same exact fixed-point grids, "
+                      "scaled per bead by a power of two)",
              "gradient_G": "double-float K (eta^{n-1} - eta^n) + H eta / 2 (- F^1), written as f64",
              "energies": "double-float per warp, f64 per block and across blocks",
              "ewald_j_side_and_grids": "int64 fixed point (2^-23 forces, 2^-40 SPME charge grids)"}
@@ -290,10 +293,11 @@ def run_ours(args, world, rank, local):
     achieved_it = flops_it[dom] / (mean_pass[dom] * 1e-3) / 1e12
     fma_peak = mop.measure_fp32_peak(local)      # dependent-FMA microkernel on this GPU, now
     ach_force = flops["pair_force"] / (mean_pass["pair_force"] * 1e-3) / 1e12
-    half = os.environ.get("MOP_PAIR_KERNELS") == "half" or prec == mop.MOP_PREC_FP64
+    pk = os.environ.get("MOP_PAIR_KERNELS", "")
+    half = pk == "half" or prec == mop.MOP_PREC_FP64
     mode = "0" if dom == "pair_force" else "1"
     kname = (f"k_pair<float,{mode}>" if prec != mop.MOP_PREC_FP64 else f"k_pair<double,{mode}>") if half \
-        else f"k_pairb<{mode},RF>"
+        else f"k_pairb<{mode},RF,{'half' if pk == 'blhalf' or (mode == '1' and pk != 'blfull') else 'full'}>"
     traffic = PAIR_TRAFFIC.get(kname) if (args.config == 5 and N == 64 and not half and
                                           pair_sources_sha() == PAIR_TRAFFIC["sources_sha256_16"]) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

@@ -225,8 +225,9 @@ mop_status mop_get_gaussians(mop_handle* h, int32_t path_id, double* centers, do
  * pair lists keep the capacity sized by the last synchronous evaluation (with 25% headroom).  If a
  * list outgrows it during the replays, mop_step restores the positions, velocities, gradients and
  * noise counter it held before them, grows the capacity to 1.25 times the largest list the replays
- * met, captures the step again and replays the n_steps again (mop_get_list_overflows counts these
- * repeats); after three attempts it returns MOP_ERR_STATE and the steps are invalid. */
+ * met and at least to twice the old one, captures the step again and replays the n_steps again
+ * (mop_get_list_overflows counts these repeats); after four attempts it returns MOP_ERR_STATE and
+ * the steps are invalid. */
 mop_status mop_set_graph_mode(mop_handle* h, int32_t on);
 
 /* *overflows = number of graph-mode step batches of path `path_id` that were run again because a

@@ -280,6 +280,12 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
       CK(h, P.xb.ensure((size_t)bl_groups(n_force) * Qpad * 3 * 32));
       CK(h, launch_bl_transpose(P.xq.p, n_force, Qpad, h->grid.max_clu, P.meta.p, P.xb.p, L));
       if (n_hvp > 0) CK(h, P.etab.ensure((size_t)bl_groups(n_hvp) * Qpad * 3 * 32));
+      // j-side sums: the H eta pass (bl 1, 2) and the force pass of the half list (bl 2)
+      const int jrows = sc.bl == 2 ? std::max(n_force, n_hvp) : (sc.bl == 1 ? n_hvp : 0);
+      if (jrows > 0) {
+        CK(h, P.jF.ensure((size_t)bl_groups(jrows) * Qpad * 3 * 32));
+        CK(h, P.jL.ensure((size_t)bl_groups(jrows) * Qpad * 3 * 32));
+      }
     }
     // j-side sums: the half-list kernels, and the Ewald exclusion and SPME passes
     const bool use_jacc = h->precision == MOP_PREC_MIXED && (!sc.bl || sc.elec == 1);
@@ -292,6 +298,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.Hnb.ensure(nq3));
     CK(h, P.Heta.ensure(nq3));
     CK(h, P.etamax.ensure(N));
+    CK(h, P.gmax.ensure(N));
     if (use_jacc) CK(h, P.jacc.ensure(nq3));
     CK(h, P.e_pair.ensure(h->grid.max_clu));
     if (sc.elec == 1) CK(h, P.e_excl.ensure(std::max(1, excl_energy_blocks(sc))));
@@ -314,6 +321,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     CK(h, P.veff_int.ensure(1));
     CK(h, P.grad_int.ensure(3 * (size_t)N * sc.Q));
     CK(h, cudaMemsetAsync(P.etamax.p, 0, sizeof(unsigned) * N, st));
+    CK(h, cudaMemsetAsync(P.gmax.p, 0, sizeof(unsigned) * N, st));
     PathDev& D = pd[k];
     memset(&D, 0, sizeof(D));
     D.N = N;
@@ -353,9 +361,12 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.Hnb = P.Hnb.p;
     D.Heta = P.Heta.p;
     D.etamax = P.etamax.p;
+    D.gmax = P.gmax.p;
     D.jacc = use_jacc ? P.jacc.p : nullptr;
     D.xb = sc.bl ? P.xb.p : nullptr;
     D.etab = sc.bl && n_hvp > 0 ? P.etab.p : nullptr;
+    D.jF = sc.bl == 1 || sc.bl == 2 ? P.jF.p : nullptr;
+    D.jL = sc.bl == 1 || sc.bl == 2 ? P.jL.p : nullptr;
     D.e_pair = P.e_pair.p;
     D.e_excl = sc.elec == 1 ? P.e_excl.p : nullptr;
     D.cwdf = P.cwdf.p;
@@ -406,10 +417,24 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     }
     return cudaSuccess;
   };
+  // bead-lane passes with j-side sums add them into zeroed buffers, added to the pass's rows after it
+  auto clear_jf = [&](bool hvp) -> cudaError_t {
+    if (!(hvp ? (sc.bl == 1 || sc.bl == 2) : sc.bl == 2)) return cudaSuccess;
+    for (const PathDev& D : pd) {
+      const int rows = hvp ? D.n_hvp : D.n_force;
+      if (rows == 0) continue;
+      cudaError_t e = cudaMemsetAsync(D.jF, 0, sizeof(float4) * bl_groups(rows) * D.Qpad * 3 * 32, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(D.jL, 0, sizeof(float2) * bl_groups(rows) * D.Qpad * 3 * 32, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
   CK(h, mark(1));
   CK(h, clear_jacc(false));
   if (sc.bl) {
+    CK(h, clear_jf(false));
     CK(h, launch_pairb(sc, h->d_paths.p, np, units, 0, L));
+    if (sc.bl == 2) CK(h, launch_bl_combine(sc, h->d_paths.p, pd.data(), np, 0, L));
     CK(h, launch_energy1(sc, h->d_paths.p, np, h->grid.max_clu, L));
   } else {
     CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
@@ -481,8 +506,13 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   }
   if (units_h > 0) {
     CK(h, clear_jacc(true));
-    if (sc.bl) CK(h, launch_pairb(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, L));
-    else CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+    if (sc.bl) {
+      CK(h, clear_jf(true));
+      CK(h, launch_pairb(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, L));
+      if (sc.bl == 1 || sc.bl == 2) CK(h, launch_bl_combine(sc, h->d_paths.p, pd.data(), np, fd ? 2 : 1, L));
+    } else {
+      CK(h, launch_pair(sc, h->d_paths.p, np, units_h, fd ? 2 : 1, h->num_sms, L));
+    }
     CK(h, launch_excl(sc, h->d_paths.p, np, max_n, fd ? 2 : 1, L));
     if (sc.pme_nk > 0) {
       cudaError_t e = launch_pme(sc, h->d_paths.p, pd.data(), np, max_n, 1, h->pme, L, &perr);
@@ -678,11 +708,19 @@ mop_status mop_create(const mop_system_desc* d, int device, mop_handle** out) {
   sc.cutoff_mode = d->cutoff_mode;
   sc.precision = d->precision;
   sc.hvp_mode = d->hvp_mode;
-  // mixed precision runs the bead-lane pair kernels; MOP_PAIR_KERNELS=half selects the
-  // half-list kernels instead (kept for comparison)
+  // mixed precision runs the bead-lane pair kernels on the full list: the force pass over every
+  // entry, the H eta pass over the owner entries with exact j-side sums.  MOP_PAIR_KERNELS=blfull
+  // runs every entry in both passes, =blhalf both passes on the half list, =half the earlier
+  // half-list kernels (all kept for comparison)
   {
     const char* pk = getenv("MOP_PAIR_KERNELS");
-    sc.bl = (d->precision == MOP_PREC_MIXED && !(pk && strcmp(pk, "half") == 0)) ? 1 : 0;
+    sc.bl = 0;
+    if (d->precision == MOP_PREC_MIXED) {
+      if (pk && strcmp(pk, "half") == 0) sc.bl = 0;
+      else if (pk && strcmp(pk, "blfull") == 0) sc.bl = 3;
+      else if (pk && strcmp(pk, "blhalf") == 0) sc.bl = 2;
+      else sc.bl = 1;
+    }
   }
   for (int k = 0; k < 3; ++k) {
     sc.L[k] = d->box[k];
@@ -884,7 +922,7 @@ mop_status mop_destroy(mop_handle* h) {
     P.cwrap.release(); P.cwdf.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
-    P.eta32.release(); P.etalo.release(); P.etamax.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
+    P.eta32.release(); P.etalo.release(); P.etamax.release(); P.gmax.release(); P.jF.release(); P.jL.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
     P.gA.release(); P.gB.release(); P.gc.release(); P.gh.release(); P.gw.release();
   }
   delete h;
@@ -1262,7 +1300,9 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
   // The replays rebuild every list on the device with the capacity of the last synchronous build
   // (25% headroom).  A list that outgrows it sets a sticky flag and invalidates the replayed
   // steps: the integrator state is then restored from a snapshot taken here, the capacity grows
-  // to 1.25 x the largest count the replays met, and the steps run again (at most 3 attempts).
+  // to 1.25 x the largest count the replays met and at least doubles (the replays after an
+  // overflow miss pairs, so their counts can fall short of what the true steps need), and the
+  // steps run again (at most 4 attempts).
   for (int id : ids) {
     PathHost& P = h->paths[id];
     const size_t n = 3 * (size_t)P.N * h->sc.Q;
@@ -1289,13 +1329,13 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
       if (!meta[3]) continue;
       over = true;
       ++P.overflows;
-      P.cap = std::max(P.cap, (meta[2] + meta[2] / 4 + 31) / 32 * 32);
+      P.cap = std::max(2 * P.cap, (meta[2] + meta[2] / 4 + 31) / 32 * 32);
       P.sized = false;
       CK(h, cudaMemset(P.meta.p + 3, 0, sizeof(int)));
     }
     if (!over) break;
     drop_graph(h);
-    if (attempt == 2)
+    if (attempt == 3)
       return fail(h, MOP_ERR_STATE,
                   "pair lists kept outgrowing their capacity during graph replay; steps since the last "
                   "synchronous call are invalid (set the paths again)");

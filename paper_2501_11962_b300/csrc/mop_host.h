@@ -80,13 +80,15 @@ struct PathHost {
   DevBuf<float4> xq;
   DevBuf<double4_32a> xq64;
   DevBuf<float2> xb, etab;   // bead-lane kernels: transposed coordinates and eta
+  DevBuf<float4> jF;         // bead-lane half list: j-side sums of a pass [G][Qpad][3][32]
+  DevBuf<float2> jL;
   DevBuf<int4> ent;
   DevBuf<double4_32a> ent64;
   DevBuf<unsigned long long> emask;
   // fields
   DevBuf<double> Fnb, F, eta, Hnb, Heta, grad_int;
   DevBuf<float4> eta32, etalo;
-  DevBuf<unsigned> etamax;
+  DevBuf<unsigned> etamax, gmax;
   DevBuf<unsigned long long> jacc;   // mixed mode: fixed-point j-side sums [N][Qpad][3]
   DevBuf<double> e_pair, diag, veff_int;
   DevBuf<double> e_excl;   // Ewald: bead-1 energy partials of the exclusion corrections
@@ -160,6 +162,11 @@ cudaError_t launch_energy1(const SysConsts& sc, const PathDev* d_paths, int n_pa
 cudaError_t launch_bl_transpose(const float4* src, int n_valid, int Qpad, int max_clu, const int* meta, float2* dst,
                                 Launch L);
 inline int bl_groups(int beads) { return (beads + kBLBeads - 1) / kBLBeads; }
+// bead-lane half list: adds the j-side sums jF of every path's pass (mode 0: into the
+// double-float Fnb rows [0, n_force); 1, 2: into the FP32 Hnb rows [0, n_hvp), mode 2 scaled
+// by -1 / (2 eps) of each bead like the i-side sums)
+cudaError_t launch_bl_combine(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths,
+                              int mode, Launch L);
 
 // --- mop_path.cu: bonded terms, eta, path gradient, bias, reductions, integrator ----------
 // grids: (slot blocks of 256, beads, paths); e_bond gets nbx partials per path, e_spring

@@ -25,6 +25,9 @@ constexpr float kDummyCoord = 1.0e5f;      // padding slots sit far outside ever
 // list entry word x: j-cluster index | self-entry flag << 28 | half mask << 29 | exclusions << 31
 constexpr int kCluMask = 0x0fffffff;
 constexpr int kSelfFlag = 1 << 28;
+// bead-lane lists: the entry that owns its unordered cluster pair (of an entry and its mirror
+// image in the full list, one; every entry of the half list)
+constexpr int kOwnerFlag = (int)0x80000000;
 // j-side sums of the half-list pair kernels are fixed point with 23 fractional bits in int64:
 // integer addition makes the atomics order-independent, so results stay bitwise reproducible
 constexpr float kFixScale = 8388608.0f;           // 2^23
@@ -78,9 +81,12 @@ struct SysConsts {
   // type-pair tables: (12 c12, 6 c6, phi'_LJ(rc) if shifted else 0, phi_LJ(rc))
   const float4* tab;
   const double4_32a* tab64;
-  // mixed precision: 1 = bead-lane pair kernels on a full list whose entries carry a 64-bit mask
-  // of the candidate atom pairs (emask bit j * 8 + i: the atoms' union spheres come within rc
-  // and the pair is not excluded); 0 = the half-list kernels
+  // mixed precision, bead-lane pair kernels on lists whose entries carry a 64-bit mask of the
+  // candidate atom pairs (emask bit j * 8 + i: the atoms' union spheres come within rc and the
+  // pair is not excluded).  1 = full list (every cluster pair from both sides); the force pass
+  // evaluates every entry, the H eta pass only the owner entries, adding the j-atoms' shares to
+  // exact fixed-point sums; 2 = half list for both passes; 3 = full list, every entry in both
+  // passes (no j-side sums).  0 = the earlier half-list kernels.
   int bl;
 };
 
@@ -103,7 +109,8 @@ struct PathDev {
   const int* lcnt;          // list length of each i-cluster
   int cap;                  // entries of cluster ci start at ci * cap
   const unsigned* ctype;    // packed LJ types of each cluster (4 bits per atom)
-  const int4* ent;          // x = cj | self << 28 | half mask << 29 | has-exclusions << 31; y,z,w = FP32 Delta
+  const int4* ent;          // x = cj | self << 28 | half mask << 29 | has-exclusions << 31 (bead-lane
+                            // lists: owner << 31); y,z,w = FP32 Delta
   const double4_32a* ent64;
   const unsigned long long* emask;   // excluded atom pairs of an entry (bit j * 8 + i), or with
                                      // bead-lane kernels the candidate pairs of the entry
@@ -111,6 +118,11 @@ struct PathDev {
   // with G = ceil(beads / 64); element (g, s, c, l) = (bead 64 g + l, bead 64 g + 32 + l)
   const float2* xb;
   const float2* etab;
+  // bead-lane half list: j-side sums of the current pass, [G][Qpad][3][32] per lane for its two
+  // beads: the high and middle parts of a 56-bit fixed-point sum (float4) and the low part (float2),
+  // each carried by FP32 (see mop_pairb.cu); zeroed before the pass
+  float4* jF;
+  float2* jL;
   // FP64 mode: [N][Qpad][3] doubles.  Mixed mode views of the same buffers: Fnb and F as
   // double-float (hi, lo) x 3 (float2 [N][Qpad][3]), Hnb and Heta as float4 [N][Qpad].
   double* Fnb;
@@ -121,6 +133,7 @@ struct PathDev {
   double* Hnb;
   double* Heta;
   unsigned* etamax;        // [N] float bits of max_i |eta_i|
+  unsigned* gmax;          // [N] float bits of the largest |g| of the force pass (bead-lane half list)
   // mixed mode: the list holds each cluster pair once and the pair kernels add the j-side sums
   // here, fixed point (kFixScale), [n_pass][Qpad][3]; NULL in FP64 mode (full list)
   unsigned long long* jacc;

@@ -1075,7 +1075,8 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
         const bool vj = P.perm[sj] >= 0;
         // a half-list entry holds each unordered pair once, the self entry (and the full list)
         // each pair in both orders
-        const int wgt = (P.jacc && !(en.x & kSelfFlag)) ? 2 : 1;
+        // (the bead-lane half list holds the self entry's pairs once as well)
+        const int wgt = sc.bl == 2 ? 2 : ((P.jacc && !(en.x & kSelfFlag) && !sc.bl) ? 2 : 1);
         listed += 1;
         const bool excluded = !sc.bl && ((m >> (jl * kCL + i)) & 1ull);
         inside += (vi && vj && r2 < sc.rc2 && !excluded) ? wgt : 0;

@@ -11,16 +11,23 @@
 // of pairs is warp-uniform: the list entry's 64-bit mask of candidate pairs (the atoms' union
 // spheres over all beads come within rc, excluded pairs removed) selects them, with no
 // per-bead screening and no divergence.  The list holds every cluster pair from both sides, so
-// an atom's sum is complete in its own warp: no j-side sums and no atomics.
+// an atom's sum is complete in its own warp: no j-side sums and no atomics.  On the half list
+// (each atom pair once) the warp also sums each j-atom's share over its i-atoms and adds it, with
+// the sign reversed, to j-side sums by vector atomics; a later pass adds those to the rows.
 //
-// Pair potential (r < rc; shifted-force modifier, or potential shift as an option), with
-// d = r_i - r_j and u = eta_i - eta_j:
-//   phi(r) = c12 r^-12 - c6 r^-6 + f q_i q_j (1/r + k_rf r^2 - c_rf)   (reaction field), or
-//            f q_i q_j erfc(beta r) / r in place of the reaction field  (Ewald real space)
-//   g = -phi'_sf(r) / r          force on i: g d
-//   b = (phi''(r) + g) / r^2     (H u)_i = b (d.u) d - g u
-// FP32 sums are folded every kBLFold entries into (hi, lo) pairs (TwoSum), and the result is
-// stored as a double-float force or an FP32 H eta.
+// The j-side sums are exact and order-independent: a share v (forces in kJ mol^-1 nm^-1; H eta
+// scaled per bead by a power of two, see bl_jscale) is split into three parts on fixed grids:
+// h, v rounded to a multiple of 2^4; m, the rest rounded to a multiple of 2^-12; l, what remains
+// rounded to a multiple of 2^-28.  Each part goes to its own FP32 sum (h and m as one float4 with
+// the lane's two beads, l as a float2).  Sums of multiples of 2^4 below 2^28, of 2^-12 below
+// 2^12 and of 2^-28 below 2^-4 are exact in FP32, so the atomics give the same bits in any
+// order: 56-bit fixed point in three FP32 words (|m| <= 8 and |l| <= 2^-13 per share, and an
+// atom-bead receives a few hundred shares at most).  Below 2^-29 per share is dropped, far under
+// the FP32 rounding of the pair terms; shares beyond 2^26 (forces: atoms pressed to within
+// ~0.1 nm) round as ordinary FP32 sums do.
+
+#include <algorithm>
+
 #include "mop_host.h"
 #include "mop_pairmath.cuh"
 
@@ -35,6 +42,24 @@ namespace {
 #define MOP_BL_WARPS_H 1
 #endif
 template <int MODE> struct BLWarps { static constexpr int value = MODE == 0 ? MOP_BL_WARPS_F : MOP_BL_WARPS_H; };
+// unrolling of the walk over an entry's 8 j-atoms (force / HVP and FD, full list / half list):
+// full unrolling makes every offset a constant, partial unrolling keeps the hot loop within the
+// instruction cache
+#ifndef MOP_BL_JU_F
+#define MOP_BL_JU_F 8
+#endif
+#ifndef MOP_BL_JU_H
+#define MOP_BL_JU_H 8
+#endif
+#ifndef MOP_BL_JU_FH
+#define MOP_BL_JU_FH 8
+#endif
+#ifndef MOP_BL_JU_HH
+#define MOP_BL_JU_HH 2
+#endif
+template <int MODE, bool HALF> struct BLJUnroll {
+  static constexpr int value = HALF ? (MODE == 0 ? MOP_BL_JU_FH : MOP_BL_JU_HH) : (MODE == 0 ? MOP_BL_JU_F : MOP_BL_JU_H);
+};
 #ifndef MOP_BL_FOLD
 #define MOP_BL_FOLD 8
 #endif
@@ -119,10 +144,11 @@ __device__ __forceinline__ float2 cut2(float2 v, float2 r2, float rc2) {
   return make_float2(r2.x < rc2 ? v.x : 0.f, r2.y < rc2 ? v.y : 0.f);
 }
 
-// MODE 0: acc += g d.  d = x_i - (x_j - Delta).
-template <bool EW>
+// MODE 0: acc += g d.  d = x_i - (x_j - Delta).  HALF: fj += g d as well (the j-atom's share,
+// negated when it is stored)
+template <bool EW, bool HALF>
 __device__ __forceinline__ void bl_force(const BLConst& k, const BLPair& c, float rc2, const float2 (&xi)[3],
-                                         const float2 (&xj)[3], float2 (&acc)[3]) {
+                                         const float2 (&xj)[3], float2 (&acc)[3], float2 (&fj)[3], float2& gm) {
   const float2 d[3] = {sub2(xi[0], xj[0]), sub2(xi[1], xj[1]), sub2(xi[2], xj[2])};
   const float2 r2 = fma2(d[0], d[0], fma2(d[1], d[1], mul2(d[2], d[2])));
   const float2 rinv = rsq2(r2);
@@ -131,14 +157,18 @@ __device__ __forceinline__ void bl_force(const BLConst& k, const BLPair& c, floa
   float2 ec, c2e;
   const float2 g = cut2(bl_g<EW>(k, c, r2, rinv, rinv2, rinv6, &ec, &c2e), r2, rc2);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) acc[q] = fma2(g, d[q], acc[q]);
+  for (int q = 0; q < 3; ++q) {
+    acc[q] = fma2(g, d[q], acc[q]);
+    if constexpr (HALF) fj[q] = fma2(g, d[q], fj[q]);
+  }
+  gm = make_float2(fmaxf(gm.x, fabsf(g.x)), fmaxf(gm.y, fabsf(g.y)));
 }
 
 // MODE 1: acc += b (d.u) d - g u with u = eta_i - eta_j.  A14B8 = (14 A, 14 A, -8 B, -8 B).
-template <bool EW>
+template <bool EW, bool HALF>
 __device__ __forceinline__ void bl_hvp(const BLConst& k, const BLPair& c, float rc2, float4 A14B8, const float2 (&xi)[3],
                                        const float2 (&xj)[3], const float2 (&ei)[3], const float2 (&ej)[3],
-                                       float2 (&acc)[3]) {
+                                       float2 (&acc)[3], float2 (&fj)[3]) {
   const float2 d[3] = {sub2(xi[0], xj[0]), sub2(xi[1], xj[1]), sub2(xi[2], xj[2])};
   const float2 r2 = fma2(d[0], d[0], fma2(d[1], d[1], mul2(d[2], d[2])));
   const float2 u[3] = {sub2(ei[0], ej[0]), sub2(ei[1], ej[1]), sub2(ei[2], ej[2])};
@@ -165,14 +195,17 @@ __device__ __forceinline__ void bl_hvp(const BLConst& k, const BLPair& c, float 
   const float2 t = cut2(mul2(b, s), r2, rc2);
   const float2 ng = cut2(make_float2(-g.x, -g.y), r2, rc2);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) acc[q] = fma2(ng, u[q], fma2(t, d[q], acc[q]));
+  for (int q = 0; q < 3; ++q) {
+    acc[q] = fma2(ng, u[q], fma2(t, d[q], acc[q]));
+    if constexpr (HALF) fj[q] = fma2(ng, u[q], fma2(t, d[q], fj[q]));
+  }
 }
 
 // MODE 2: acc += F_pair(d + eps u) - F_pair(d - eps u), eps per half (bead)
-template <bool EW>
+template <bool EW, bool HALF>
 __device__ __forceinline__ void bl_fd(const BLConst& k, const BLPair& c, float rc2, float2 eps2, const float2 (&xi)[3],
                                       const float2 (&xj)[3], const float2 (&ei)[3], const float2 (&ej)[3],
-                                      float2 (&acc)[3]) {
+                                      float2 (&acc)[3], float2 (&fj)[3]) {
   const float2 d[3] = {sub2(xi[0], xj[0]), sub2(xi[1], xj[1]), sub2(xi[2], xj[2])};
   const float2 u[3] = {mul2(eps2, sub2(ei[0], ej[0])), mul2(eps2, sub2(ei[1], ej[1])),
                        mul2(eps2, sub2(ei[2], ej[2]))};
@@ -188,7 +221,10 @@ __device__ __forceinline__ void bl_fd(const BLConst& k, const BLPair& c, float r
     float2 g = cut2(bl_g<EW>(k, c, r2, rinv, rinv2, rinv6, &ec, &c2e), r2, rc2);
     if (sgn) g = make_float2(-g.x, -g.y);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) acc[q] = fma2(g, p[q], acc[q]);
+    for (int q = 0; q < 3; ++q) {
+      acc[q] = fma2(g, p[q], acc[q]);
+      if constexpr (HALF) fj[q] = fma2(g, p[q], fj[q]);
+    }
   }
 }
 
@@ -215,6 +251,27 @@ __device__ __forceinline__ void bl_fold(W& S, float2 (&acc)[kBLI][3], int lane) 
     }
 }
 
+// Grids of the j-side sums: adding and subtracting 1.5 * 2^27 rounds |v| < 2^26 to a multiple of
+// 2^4, 1.5 * 2^11 rounds |r| <= 2^3 to a multiple of 2^-12, 1.5 * 2^-5 rounds |r| <= 2^-13 to a
+// multiple of 2^-28.
+constexpr float kJGridHi = 201326592.f, kJGridMid = 3072.f, kJGridLo = 0.046875f;
+
+// Power-of-two scale of a bead's j-side shares in the H eta pass (forces use 1).  A share sums at
+// most 4 pairs' (|b| r^2 + |g|) |u|, with |u| <= 2 max_i |eta_i| and |b| r^2 <= 14 |g| where the
+// repulsion dominates (the LJ and Coulomb parts of b r^2 are 14 and 3 times those of g; near the LJ
+// minimum, where g vanishes, b r^2 stays below ~1e3), so with gmax the largest |g| of the force
+// pass of the same bead the bound is 8 max|eta| (16 gmax + 1e3).  The scale takes that bound
+// below 2^24: shares stay inside the exact range with room for the sums, and the grids resolve
+// them to 2^-52 of the largest share.
+__device__ __forceinline__ float bl_jscale(float etamax, float gmax) {
+  if (!(etamax > 0.f)) return 1.f;
+  const float bound = 8.f * etamax * fmaf(16.f, gmax, 1e3f);
+  int e;
+  const float f = frexpf(bound, &e);   // bound = f 2^e, f in [0.5, 1): bound < 2^e
+  (void)f;
+  return ldexpf(1.f, 24 - max(-90, min(120, e)));
+}
+
 // bit 8 jj of the result is set iff byte jj of m is nonzero
 __device__ __forceinline__ unsigned long long nonzero_bytes(unsigned long long m) {
   m |= m >> 4;
@@ -232,7 +289,7 @@ struct BLJ {
 
 // One unit: i-atoms ih * kBLI .. ih * kBLI + kBLI - 1 of i-cluster ci for beads 64 g + lane and
 // 64 g + 32 + lane of the pass.
-template <int MODE, bool EW>
+template <int MODE, bool EW, bool HALF>
 __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, const PathDev& P, int g, int ci,
                                         int ih, int lane) {
   const int a0 = ih * kBLI;   // first i-atom of the unit within the cluster
@@ -258,6 +315,16 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
     eps2 = make_float2((float)(m0 > 0.f ? sc.fd_h / (double)m0 : sc.fd_h),
                        (float)(m1 > 0.f ? sc.fd_h / (double)m1 : sc.fd_h));
   }
+  // half list: a j-atom's share fj goes to the sums as -fj jmul (FD: in the units of H eta)
+  float2 jmul = make_float2(1.f, 1.f);
+  if constexpr (HALF && MODE >= 1) {
+    const int c0 = min(b0, n_pass - 1), c1 = min(b1, n_pass - 1);
+    jmul = make_float2(bl_jscale(__uint_as_float(P.etamax[c0]), __uint_as_float(P.gmax[c0])),
+                       bl_jscale(__uint_as_float(P.etamax[c1]), __uint_as_float(P.gmax[c1])));
+    if constexpr (MODE == 2) jmul = mul2(jmul, make_float2(-0.5f / eps2.x, -0.5f / eps2.y));
+  }
+  const float2 njmul = make_float2(-jmul.x, -jmul.y);
+  float2 gm = make_float2(0.f, 0.f);   // force pass: largest |g| of each bead (scale of the H eta j-side sums)
   float2 xi[kBLI][3], ei[kBLI][3], acc[kBLI][3];
 #pragma unroll
   for (int a = 0; a < kBLI; ++a)
@@ -319,8 +386,13 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
     __syncwarp();
     for (int e = 0; e < nc; ++e) {
       const int4 E = S.ent[e];
-      const unsigned long long M = S.m[e];
+      unsigned long long M = S.m[e];
       const int cj = E.x & kCluMask;
+      if constexpr (HALF) {
+        // each unordered cluster pair once: its owner entry, and a self entry's pairs j > i
+        if (!(E.x & kOwnerFlag)) continue;   // warp-uniform
+        if (E.x & kSelfFlag) M &= 0x7f3f1f0f07030100ull;
+      }
       const float2 D[3] = {dup2(__int_as_float(E.y)), dup2(__int_as_float(E.z)), dup2(__int_as_float(E.w))};
       // this unit's candidate bits: i-atoms a0 .. a0 + kBLI - 1 of every j byte
       const unsigned long long Mi = (M >> a0) & (0x0101010101010101ull * ((1u << kBLI) - 1u));
@@ -329,6 +401,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       // evaluate the candidate pairs of one j-atom (the i-loop is unrolled: registers stay static)
       auto eval_j = [&](const BLJ& cur, int jj) __attribute__((always_inline)) {
         const unsigned byte = (unsigned)(Mi >> (8 * jj)) & 0xffu;
+        float2 fj[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         float2 xj[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) xj[c] = sub2(cur.x[c], D[c]);
@@ -342,13 +415,13 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
           c.qq = mul2(make_float2(t1.x, t1.y), cur.qj);
           c.sh = fma2(c.qq, k.drf, make_float2(t1.z, t1.w));
           if constexpr (MODE == 0) {
-            bl_force<EW>(k, c, sc.rc2f, xi[i], xj, acc[i]);
+            bl_force<EW, HALF>(k, c, sc.rc2f, xi[i], xj, acc[i], fj, gm);
           } else {
             float2 eii[3];
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) eii[cc] = MOP_BL_EISH ? S.ei[i * 3 + cc][lane] : ei[i][cc];
-            if constexpr (MODE == 1) bl_hvp<EW>(k, c, sc.rc2f, tp[2], xi[i], xj, eii, cur.e, acc[i]);
-            else bl_fd<EW>(k, c, sc.rc2f, eps2, xi[i], xj, eii, cur.e, acc[i]);
+            if constexpr (MODE == 1) bl_hvp<EW, HALF>(k, c, sc.rc2f, tp[2], xi[i], xj, eii, cur.e, acc[i], fj);
+            else bl_fd<EW, HALF>(k, c, sc.rc2f, eps2, xi[i], xj, eii, cur.e, acc[i], fj);
           }
         };
         // groups of kBLIlp i-atoms whose candidate bits are all set are evaluated together (their
@@ -364,6 +437,22 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
 #pragma unroll
             for (int i = i0; i < i0 + kBLIlp; ++i)
               if ((bits >> (i - i0)) & 1u) pair(i);   // warp-uniform
+          }
+        }
+        if constexpr (HALF) {
+          // the j-atom's share of these pairs, for both beads of the lane, with the sign reversed,
+          // on the two grids of the exact j-side sums
+          const size_t jo = g * gstride + lane + (size_t)(cj * kCL + jj) * 3 * 32;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float2 v = mul2(fj[q], njmul);
+            const float2 hv = sub2(add2(v, dup2(kJGridHi)), dup2(kJGridHi));
+            const float2 r = sub2(v, hv);   // exact
+            const float2 mv = sub2(add2(r, dup2(kJGridMid)), dup2(kJGridMid));
+            const float2 r2 = sub2(r, mv);  // exact
+            const float2 lv = sub2(add2(r2, dup2(kJGridLo)), dup2(kJGridLo));
+            atomicAdd(P.jF + jo + q * 32, make_float4(hv.x, hv.y, mv.x, mv.y));
+            atomicAdd(P.jL + jo + q * 32, lv);
           }
         }
       };
@@ -383,7 +472,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
         cur = nxt;
       }
       } else {
-#pragma unroll
+#pragma unroll (BLJUnroll<MODE, HALF>::value)
       for (int jj = 0; jj < kCL; ++jj) {
         if (!((Mi >> (8 * jj)) & 0xffull)) continue;   // warp-uniform
         if constexpr (MOP_BL_L1PF) {
@@ -424,6 +513,11 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
   }
   bl_fold(S, acc, lane);
   const bool v0 = b0 < n_pass, v1 = b1 < n_pass;
+  if constexpr (MODE == 0) {
+    // non-negative floats order like their bit patterns
+    if (v0) atomicMax(&P.gmax[b0], __float_as_uint(gm.x));
+    if (v1) atomicMax(&P.gmax[b1], __float_as_uint(gm.y));
+  }
 #pragma unroll
   for (int a = 0; a < kBLI; ++a) {
     const int s = ci * kCL + a0 + a;
@@ -471,12 +565,23 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
 #ifndef MOP_BL_MINB_D
 #define MOP_BL_MINB_D (12 / MOP_BL_WARPS_H)
 #endif
-template <int MODE> struct BLMinBlocks {
-  static constexpr int value = MODE == 0 ? MOP_BL_MINB_F : (MODE == 1 ? MOP_BL_MINB_H : MOP_BL_MINB_D);
+// half list: 16 warps (128 registers) for the force and HVP kernels, 12 for the FD kernel
+#ifndef MOP_BL_MINB_FH
+#define MOP_BL_MINB_FH (16 / MOP_BL_WARPS_F)
+#endif
+#ifndef MOP_BL_MINB_HH
+#define MOP_BL_MINB_HH (16 / MOP_BL_WARPS_H)
+#endif
+#ifndef MOP_BL_MINB_DH
+#define MOP_BL_MINB_DH (12 / MOP_BL_WARPS_H)
+#endif
+template <int MODE, bool HALF> struct BLMinBlocks {
+  static constexpr int value = HALF ? (MODE == 0 ? MOP_BL_MINB_FH : (MODE == 1 ? MOP_BL_MINB_HH : MOP_BL_MINB_DH))
+                                    : (MODE == 0 ? MOP_BL_MINB_F : (MODE == 1 ? MOP_BL_MINB_H : MOP_BL_MINB_D));
 };
 
-template <int MODE, bool EW>
-__global__ void __launch_bounds__(32 * BLWarps<MODE>::value, BLMinBlocks<MODE>::value)
+template <int MODE, bool EW, bool HALF>
+__global__ void __launch_bounds__(32 * BLWarps<MODE>::value, BLMinBlocks<MODE, HALF>::value)
     k_pairb(SysConsts sc, const PathDev* __restrict__ paths, int n_paths, long long n_units) {
   extern __shared__ __align__(16) unsigned char smem[];
   BLWarp<MODE>* W = reinterpret_cast<BLWarp<MODE>*>(smem);
@@ -497,30 +602,31 @@ __global__ void __launch_bounds__(32 * BLWarps<MODE>::value, BLMinBlocks<MODE>::
   const int g = (int)(v / per_group);
   const int r = (int)(v - g * per_group), ci = r / kBLSplit, ih = r - ci * kBLSplit;
   if (ci >= __ldg(&P.meta[0])) return;   // past the clusters of the current sort
-  bl_unit<MODE, EW>(sc, W[w], P, g, ci, ih, lane);
+  bl_unit<MODE, EW, HALF>(sc, W[w], P, g, ci, ih, lane);
 }
 
-template <int MODE, bool EW>
+template <int MODE, bool EW, bool HALF>
 cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, Launch L) {
   constexpr int W = BLWarps<MODE>::value;
   const size_t smem = sizeof(BLWarp<MODE>) * W;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pairb<MODE, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_pairb<MODE, EW, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const long long blocks = (n_units + W - 1) / W;
-  k_pairb<MODE, EW><<<(unsigned)blocks, 32 * W, smem, L.st>>>(sc, d_paths, n_paths, n_units);
+  k_pairb<MODE, EW, HALF><<<(unsigned)blocks, 32 * W, smem, L.st>>>(sc, d_paths, n_paths, n_units);
   ++*L.counter;
   return cudaGetLastError();
 }
 
 // ---- bead-1 pair energy --------------------------------------------------------------------
 // One warp per i-cluster, lane (i = lane & 7, jq = lane >> 3) against j-atoms jq and jq + 4 of
-// every entry; each pair of the full list is met from both sides, so the sum is halved.
+// every entry; each pair of the full list is met from both sides, so the sum is halved (HALF:
+// the half list holds each pair once).
 // phi_sf(r) = phi(r) - phi(rc) - (r - rc) phi'(rc) (sh = phi'(rc) = 0 with the potential shift).
-template <bool EW>
+template <bool EW, bool HALF>
 __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __restrict__ paths, int max_clu) {
   __shared__ int4 sent[4][32];
   __shared__ unsigned long long sm[4][32];
@@ -582,7 +688,7 @@ __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __
   }
   two_sum_add(hi, lo, acc);
   const df v = df_warp_sum(df{hi, lo});
-  if (lane == 0) P.e_pair[ci] = 0.5 * ((double)v.hi + (double)v.lo);
+  if (lane == 0) P.e_pair[ci] = (HALF ? 1.0 : 0.5) * ((double)v.hi + (double)v.lo);
 }
 
 // ---- transposition into the bead-lane layout -------------------------------------------------
@@ -607,25 +713,113 @@ __global__ void __launch_bounds__(256) k_bl_transpose(const float4* __restrict__
   }
 }
 
+// ---- j-side sums of the half list into the rows -----------------------------------------------
+// Block (cluster c, group g, path): the 8 slots x 64 beads of jF through shared memory; force
+// rows are double-floats (TwoSum of the high part with the FP32 sum), H eta rows FP32.
+// The three FP32 sums (h, m, l) of a value are added as a double-float, the H eta ones divided by
+// the bead's scale (a power of two).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bl_combine(SysConsts sc, const PathDev* __restrict__ paths) {
+  (void)sc;
+  __shared__ float4 t[kCL * 3][32];
+  __shared__ float2 tl[kCL * 3][32];
+  const PathDev& P = paths[blockIdx.z];
+  const int c = blockIdx.x, g = blockIdx.y;
+  const int rows = MODE == 0 ? P.n_force : P.n_hvp;
+  if (c >= P.n_clu || c >= __ldg(&P.meta[0]) || g * kBLBeads >= rows) return;   // block-uniform
+  const size_t o = ((size_t)g * P.Qpad + (size_t)c * kCL) * 3 * 32;
+  for (int k = threadIdx.x; k < kCL * 3 * 32; k += blockDim.x) {
+    t[k >> 5][k & 31] = P.jF[o + k];
+    tl[k >> 5][k & 31] = P.jL[o + k];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kBLBeads * kCL; k += blockDim.x) {
+    const int bb = k / kCL, a = k - bb * kCL;
+    const int b = g * kBLBeads + bb;
+    if (b >= rows) continue;
+    const int l = bb & 31;
+    const size_t s = (size_t)c * kCL + a;
+    float jh[3], jl[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 v = t[a * 3 + q][l];
+      const float2 w = tl[a * 3 + q][l];
+      const float hv = bb < 32 ? v.x : v.y, mv = bb < 32 ? v.z : v.w, lv = bb < 32 ? w.x : w.y;
+      jh[q] = hv + mv;   // (jh, jl) = hv + mv exactly (TwoSum), then + lv
+      const float bp = jh[q] - hv;
+      jl[q] = ((hv - (jh[q] - bp)) + (mv - bp)) + lv;
+    }
+    if constexpr (MODE == 0) {
+      float2* F = reinterpret_cast<float2*>(P.Fnb) + 3 * ((size_t)b * P.Qpad + s);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float2 f = F[q];
+        const float sum = f.x + jh[q], bp = sum - f.x;
+        const float err = (f.x - (sum - bp)) + (jh[q] - bp);
+        F[q] = make_float2(sum, f.y + (err + jl[q]));
+      }
+    } else {
+      const float inv = 1.f / bl_jscale(__uint_as_float(P.etamax[b]), __uint_as_float(P.gmax[b]));   // 2^k
+      float4* H = reinterpret_cast<float4*>(P.Hnb) + (size_t)b * P.Qpad + s;
+      float4 h = *H;
+      h.x += (jh[0] + jl[0]) * inv;
+      h.y += (jh[1] + jl[1]) * inv;
+      h.z += (jh[2] + jl[2]) * inv;
+      *H = h;
+    }
+  }
+}
+
 }  // namespace
 
 int pairb_units_per_cluster() { return kBLSplit; }
+
+cudaError_t launch_bl_combine(const SysConsts& sc, const PathDev* d_paths, const PathDev* h_paths, int n_paths,
+                              int mode, Launch L) {
+  int groups = 0, clu = 0;
+  for (int p = 0; p < n_paths; ++p) {
+    groups = std::max(groups, bl_groups(mode == 0 ? h_paths[p].n_force : h_paths[p].n_hvp));
+    clu = std::max(clu, h_paths[p].n_clu);
+  }
+  if (groups == 0 || clu == 0) return cudaSuccess;
+  const dim3 grid((unsigned)clu, (unsigned)groups, (unsigned)n_paths);
+  if (mode == 0) k_bl_combine<0><<<grid, 256, 0, L.st>>>(sc, d_paths);
+  else if (mode == 1) k_bl_combine<1><<<grid, 256, 0, L.st>>>(sc, d_paths);
+  else k_bl_combine<2><<<grid, 256, 0, L.st>>>(sc, d_paths);
+  ++*L.counter;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pairb(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
                          Launch L) {
   if (n_units <= 0) return cudaSuccess;
   const bool ew = sc.elec == 1;
+  // j-side sums: the half list in both passes, the owner entries of the full list in the H eta pass
+  const bool half = mode == 0 ? sc.bl == 2 : (sc.bl == 1 || sc.bl == 2);
+  if (half) {
+    switch (mode) {
+      case 0: return ew ? launch_b<0, true, true>(sc, d_paths, n_paths, n_units, L) : launch_b<0, false, true>(sc, d_paths, n_paths, n_units, L);
+      case 1: return ew ? launch_b<1, true, true>(sc, d_paths, n_paths, n_units, L) : launch_b<1, false, true>(sc, d_paths, n_paths, n_units, L);
+      default: return ew ? launch_b<2, true, true>(sc, d_paths, n_paths, n_units, L) : launch_b<2, false, true>(sc, d_paths, n_paths, n_units, L);
+    }
+  }
   switch (mode) {
-    case 0: return ew ? launch_b<0, true>(sc, d_paths, n_paths, n_units, L) : launch_b<0, false>(sc, d_paths, n_paths, n_units, L);
-    case 1: return ew ? launch_b<1, true>(sc, d_paths, n_paths, n_units, L) : launch_b<1, false>(sc, d_paths, n_paths, n_units, L);
-    default: return ew ? launch_b<2, true>(sc, d_paths, n_paths, n_units, L) : launch_b<2, false>(sc, d_paths, n_paths, n_units, L);
+    case 0: return ew ? launch_b<0, true, false>(sc, d_paths, n_paths, n_units, L) : launch_b<0, false, false>(sc, d_paths, n_paths, n_units, L);
+    case 1: return ew ? launch_b<1, true, false>(sc, d_paths, n_paths, n_units, L) : launch_b<1, false, false>(sc, d_paths, n_paths, n_units, L);
+    default: return ew ? launch_b<2, true, false>(sc, d_paths, n_paths, n_units, L) : launch_b<2, false, false>(sc, d_paths, n_paths, n_units, L);
   }
 }
 
 cudaError_t launch_energy1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_clu, Launch L) {
   const dim3 grid((unsigned)((max_clu + 3) / 4), (unsigned)n_paths);
-  if (sc.elec == 1) k_energy1<true><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
-  else k_energy1<false><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
+  const bool half = sc.bl == 2;
+  if (sc.elec == 1) {
+    if (half) k_energy1<true, true><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
+    else k_energy1<true, false><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
+  } else {
+    if (half) k_energy1<false, true><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
+    else k_energy1<false, false><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
+  }
   ++*L.counter;
   return cudaGetLastError();
 }

@@ -386,7 +386,9 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
         }
         ef = make_float4(e[0], e[1], e[2], 0.f);
         efl = make_float4(el[0], el[1], el[2], 0.f);
-        if (sc.hvp_mode == 1) nbits = __float_as_uint(sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) * 1.000001f);
+        // max_i |eta_i| per bead: the FD step, and the scale of the half list's j-side sums
+        if (sc.hvp_mode == 1 || sc.bl == 1 || sc.bl == 2)
+          nbits = __float_as_uint(sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) * 1.000001f);
       }
     }
     for (int c = 0; c < 3; ++c) Fo[c] = make_float2(F[c].hi, F[c].lo);
@@ -395,7 +397,7 @@ __global__ void MOP_E1_BOUNDS k_e1_mixed(SysConsts sc, const PathDev* __restrict
       P.etalo[k] = efl;
     }
   }
-  if (sc.hvp_mode == 1) {
+  if (sc.hvp_mode == 1 || sc.bl == 1 || sc.bl == 2) {
     // one atomic per warp (all lanes belong to bead n)
     const unsigned mx = __reduce_max_sync(0xffffffffu, nbits);
     if ((threadIdx.x & 31) == 0) atomicMax(&P.etamax[n], mx);

@@ -465,13 +465,13 @@ __global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype)
 // go to ent[ci * cap ...] in bin order (deterministic); lcnt[ci] = their number; meta[2] =
 // largest count (a count above cap means the list must be rebuilt with a larger cap).
 // HALF: every unordered cluster pair once (half-list kernels).  Otherwise every pair from both
-// sides; without F64 (bead-lane kernels) emask then holds the entry's candidate atom pairs (the
-// union spheres within reach, exclusions removed, bit j * 8 + i) and an entry whose candidates
-// are all excluded is dropped.
+// sides.  PM (bead-lane kernels): emask holds the entry's candidate atom pairs (the union
+// spheres within reach, exclusions removed, bit j * 8 + i), an entry whose candidates are all
+// excluded is dropped, and with HALF the self entry keeps its pairs j > i only.
 #ifndef MOP_LIST_MINB
 #define MOP_LIST_MINB 6   // 80 registers: 6 blocks (24 warps) per SM hide the latency of the bin walk
 #endif
-template <bool F64, bool HALF>
+template <bool F64, bool HALF, bool PM>
 __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, const int* meta_in, int max_clu,
                                                    const double* cwrap, const float2* cwdf, const float* hext,
                                                    const unsigned* emax,
@@ -531,18 +531,16 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
         for (int t0 = 0; t0 < nbin; t0 += 32) {
           const int t = t0 + lane;
           int cj = -1;
-          bool self = false;
+          bool self = false, own = false;
           double D[3] = {0.0, 0.0, 0.0};
           if (t < nbin) {
             cj = binlist[s0 + t];
-            if (HALF) {
-              // half list: every unordered cluster pair (with its image) once; the parity rule
-              // gives each cluster about half of its neighbours
-              self = cj == ci && kk[0] == 0 && kk[1] == 0 && kk[2] == 0;
-              const bool keep = cj != ci ? (((ci ^ cj) & 1) ? ci < cj : ci > cj)
-                                         : (kk[0] > 0 || (kk[0] == 0 && (kk[1] > 0 || (kk[1] == 0 && kk[2] >= 0))));
-              if (!keep) cj = -1;
-            }
+            // the owner of an unordered cluster pair (with its image): the parity rule gives each
+            // cluster about half of its neighbours
+            self = cj == ci && kk[0] == 0 && kk[1] == 0 && kk[2] == 0;
+            own = cj != ci ? (((ci ^ cj) & 1) ? ci < cj : ci > cj)
+                           : (kk[0] > 0 || (kk[0] == 0 && (kk[1] > 0 || (kk[1] == 0 && kk[2] >= 0))));
+            if (HALF && !own) cj = -1;   // half list: owners only
           }
           bool box = false;
           if (cj >= 0) {
@@ -582,6 +580,7 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
             const int src = __ffs(pend) - 1;
             pend &= pend - 1;
             const int cs = __shfl_sync(0xffffffffu, cj, src);
+            const bool self_s = __shfl_sync(0xffffffffu, (int)self, src) != 0;
             const float Dx = __shfl_sync(0xffffffffu, Df[0], src);
             const float Dy = __shfl_sync(0xffffffffu, Df[1], src);
             const float Dz = __shfl_sync(0xffffffffu, Df[2], src);
@@ -602,7 +601,6 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
             const unsigned b0 = __ballot_sync(0xffffffffu, in0), b1 = __ballot_sync(0xffffffffu, in1);
             const unsigned hm = (b0 ? 1u : 0u) | (b1 ? 2u : 0u);
             if (!hm) continue;   // warp-uniform
-            constexpr bool PM = !F64 && !HALF;   // candidate-pair masks
             unsigned long long pm = 0ull;
             if (PM) {
               // exclusions only matter for clusters whose molecule ranges overlap
@@ -618,9 +616,12 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
                 pm &= ~((unsigned long long)__ballot_sync(0xffffffffu, x0) |
                         ((unsigned long long)__ballot_sync(0xffffffffu, x1) << 32));
               }
+              // a self entry of the half list: each atom pair once (bits j * 8 + i with j > i)
+              if (HALF && self_s) pm &= 0x7f3f1f0f07030100ull;
               if (!pm) continue;   // warp-uniform: every candidate pair is excluded
               if (count < cap && lane == src) {
-                ent[base + count] = make_int4(cj | (int)(hm << 29) | (self ? kSelfFlag : 0), __float_as_int(Df[0]),
+                ent[base + count] = make_int4(cj | (int)(hm << 29) | (self ? kSelfFlag : 0) | (own ? kOwnerFlag : 0),
+                                              __float_as_int(Df[0]),
                                               __float_as_int(Df[1]), __float_as_int(Df[2]));
                 emask[base + count] = pm;
               }
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
                     ((unsigned long long)__ballot_sync(0xffffffffu, x1) << 32);
               }
               if (lane == src) {
-                const bool slf = self;
+                const bool slf = HALF && self;   // the full FP64 list flags no self entry
                 const int flags = (int)(hm << 29) | (m ? (int)0x80000000 : 0) | (slf ? kSelfFlag : 0);
                 ent[base + count] = make_int4(cj | flags, __float_as_int(Df[0]), __float_as_int(Df[1]),
                                               __float_as_int(Df[2]));
@@ -822,18 +823,24 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
     if (sync) MOP_CK(cudaMemsetAsync(P.meta.p + 2, 0, 2 * sizeof(int), st));
     const int blocks = nblk(max_clu, 4);
     if (f64)
-      k_pair_list<true, false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
+      k_pair_list<true, false, false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p, P.cbin.p,
                                                 g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.binstart.p,
                                                 P.binlist.p, P.perm.p, P.molr.p, P.abox.p, P.cbox.p, P.cap, P.lcnt.p,
                                                 P.ent.p, P.ent64.p, P.emask.p, P.meta.p);
-    else if (sc.bl)
-      k_pair_list<false, false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
+    else if (sc.bl == 2)   // bead-lane half list
+      k_pair_list<false, true, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
+                                                             P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1],
+                                                             g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p,
+                                                             P.abox.p, P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr,
+                                                             P.emask.p, P.meta.p);
+    else if (sc.bl)        // bead-lane full list
+      k_pair_list<false, false, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
                                                         P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2],
                                                         P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.abox.p,
                                                         P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr, P.emask.p,
                                                         P.meta.p);
     else
-      k_pair_list<false, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
+      k_pair_list<false, true, false><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
                                                        P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2],
                                                        P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.abox.p,
                                                        P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr, P.emask.p,

@@ -49,14 +49,14 @@ def test_graph_recaptures_on_new_parameters():
 
 def test_graph_replay_recovers_from_list_overflow():
     """Every bead starts at the same relaxed structure, so the lists are sized for beads with no
-    spread; 300 steps of 0.2 fs with a 3000 K thermostat then spread the beads and the lists
+    spread; 300 steps of 0.2 fs with a 6000 K thermostat then spread the beads and the lists
     outgrow that capacity during the replays.  mop_step must notice, restore the state it held
     before the replays, grow the capacity and run the steps again: the trajectory equals the
     eager one bit for bit, stays finite, and the repeat is counted."""
     import dataclasses
     w = workload(4, relaxed=True)
     base = np.asarray(w.system.extra["base"], np.float32)
-    hot = dataclasses.replace(w.system, temperature=3000.0)
+    hot = dataclasses.replace(w.system, temperature=6000.0)
     engines = []
     for graph in (False, True):
         eng = mop.Engine(hot)

@@ -479,3 +479,90 @@ def test_half_list_kernels_match_oracle(monkeypatch, hvp_mode):
     print("half-list kernels", hvp_mode, errs)
     assert errs["F"] < TOL_F and errs["V"] < TOL_V
     assert errs["Heta"] < (1e-4 if kw else TOL_H) and errs["G"] < (1e-4 if kw else TOL_F)
+
+
+@pytest.mark.parametrize("kernels", ["default", "blhalf", "blfull"])
+@pytest.mark.parametrize("relaxed", [False, True])
+@pytest.mark.parametrize("hvp_mode", [mop.MOP_HVP_ADJOINT, mop.MOP_HVP_FD])
+def test_bead_lane_lists_match_oracle(monkeypatch, hvp_mode, relaxed, kernels):
+    """The bead-lane kernels in their three arrangements against the oracle on the water box with
+    70 beads (two bead groups, the second ragged): the default (full list; the H eta pass over the
+    owner entries only, the j-atom's share added by vector atomics to exact fixed-point sums, a
+    self entry's pairs j > i), MOP_PAIR_KERNELS=blhalf (the half list in both passes) and =blfull
+    (every entry in both passes, no atomics).  Forces, eta, H eta (FD: against the oracle's own
+    Eq. 5 at the same h), the gradient, V_eff, and the per-row bars."""
+    if kernels == "default":
+        monkeypatch.delenv("MOP_PAIR_KERNELS", raising=False)
+    else:
+        monkeypatch.setenv("MOP_PAIR_KERNELS", kernels)
+    w = workload(2, n_beads=70, relaxed=relaxed)
+    X = w.paths[0]
+    N = X.shape[0]
+    fd = hvp_mode == mop.MOP_HVP_FD
+    kw = dict(hvp_mode=hvp_mode, fd_h=1e-3) if fd else {}
+    eng, g = gpu_eval(w, **kw)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "eta", "Heta"),
+                                     **(dict(hvp_mode=oracle.HVP_FD_EQ5, fd_h=1e-3) if fd else {}))
+    errs = dict(F=rel(g["F"][:N - 1], r["F"][:N - 1]), eta=rel(g["eta"][:N - 1], r["eta"][:N - 1]),
+                Heta=rel(g["Heta"][:N - 1], r["Heta"][:N - 1]), G=rel(g["G"], r["G"]),
+                V=abs(g["veff"] - r["veff"]) / abs(r["veff"]), U1=abs(g["U1"] - r["U1"]) / abs(r["U1"]))
+    print("bead-lane", kernels, hvp_mode, relaxed, errs)
+    assert errs["F"] < TOL_F and errs["eta"] < TOL_F and errs["V"] < TOL_V and errs["U1"] < TOL_V
+    assert_rows(g["F"][:N - 1], r["F"][:N - 1], TOL_F, "F")
+    assert_rows(g["eta"][:N - 1], r["eta"][:N - 1], TOL_F, "eta")
+    if fd:
+        # FP32 central differences at h = 1e-3 nm: 30 times the rounding scale, as for the
+        # full-list FD kernel
+        assert errs["Heta"] < 1e-4 and errs["G"] < 1e-4
+    else:
+        assert errs["Heta"] < TOL_H and errs["G"] < TOL_F
+        assert_rows(g["Heta"][:N - 1], r["Heta"][:N - 1], TOL_H, "Heta")
+        assert_rows(g["G"], r["G"], TOL_F, "G")
+
+
+@pytest.mark.parametrize("kernels", ["blhalf", "blfull"])
+def test_bead_lane_lists_ewald_match_oracle(monkeypatch, kernels):
+    """The bead-lane kernels on both lists with Ewald real space and SPME against the oracle."""
+    from paper_2501_11962_b300 import synth
+    monkeypatch.setenv("MOP_PAIR_KERNELS", kernels)
+    w = workload(2, n_beads=6)
+    sys = synth.with_pme(w.system)
+    X = w.paths[0]
+    N = X.shape[0]
+    eng = mop.Engine(sys)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    r = oracle.Oracle(sys).veff_pme(X.astype(np.float64))
+    F = eng.get_field(0, mop.MOP_FIELD_FORCE)[:N - 1]
+    H = eng.get_field(0, mop.MOP_FIELD_HETA)[:N - 1]
+    errs = dict(F=rel(F, r["F"][:N - 1]), Heta=rel(H, r["Heta"][:N - 1]), G=rel(G, r["G"]),
+                V=abs(v[0] - r["veff"]) / abs(r["veff"]))
+    print("bead-lane", kernels, "SPME", errs)
+    assert errs["F"] < TOL_F and errs["G"] < TOL_F and errs["Heta"] < TOL_H and errs["V"] < TOL_V, errs
+
+
+@pytest.mark.parametrize("kernels", ["default", "blhalf"])
+@pytest.mark.parametrize("relaxed", [False, True])
+@pytest.mark.parametrize("hvp_mode", [mop.MOP_HVP_ADJOINT, mop.MOP_HVP_FD])
+def test_j_side_sums_are_bitwise_reproducible(monkeypatch, hvp_mode, relaxed, kernels):
+    """The j-side sums (the H eta pass over the owner entries of the full list, by default, and
+    both passes of the half list) are added by atomics in whatever order the warps run; they are
+    carried on three fixed-point grids in FP32, which makes every addition exact, so two handles
+    give the same bits (config 4's 96-bead path, around the generated structure with forces up to
+    2e5 kJ/mol/nm, and around the relaxed one)."""
+    if kernels == "default":
+        monkeypatch.delenv("MOP_PAIR_KERNELS", raising=False)
+    else:
+        monkeypatch.setenv("MOP_PAIR_KERNELS", kernels)
+    w = workload(4, relaxed=relaxed)
+    kw = dict(hvp_mode=hvp_mode, fd_h=1e-3) if hvp_mode == mop.MOP_HVP_FD else {}
+    outs = []
+    for _ in range(2):
+        eng = mop.Engine(w.system, **kw)
+        eng.set_path(0, w.paths[3])
+        v, G = eng.veff_and_grad(0)
+        outs.append((v[0], G, eng.get_field(0, mop.MOP_FIELD_FORCE), eng.get_field(0, mop.MOP_FIELD_HETA)))
+        eng.close()
+    for name, a, b in zip(("V", "G", "F", "Heta"), outs[0], outs[1]):
+        d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
+        assert np.array_equal(a, b), (name, int(np.count_nonzero(d)), float(np.abs(d).max()))
