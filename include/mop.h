@@ -70,6 +70,8 @@ enum { MOP_PREC_MIXED = 0,
 #define MOP_INPUT_F64 2    /* mop_set_path: xyz is double* instead of float* */
 #define MOP_E2E 4          /* mop_add_bias: CV = s(R^N) - s(R^1) (Eq. 8) instead of s(R^N) */
 #define MOP_COM 8          /* mop_add_bias: mass-weighted group centres (centres of mass) */
+#define MOP_ASYNC 16       /* mop_set_path / mop_veff_and_grad with host pointers: enqueue and
+                              return (see mop_wait) */
 
 #define MOP_ELEC_RF 0      /* reaction-field electrostatics */
 #define MOP_ELEC_PME 1     /* Ewald electrostatics (real space + smooth particle-mesh Ewald) */
@@ -143,14 +145,26 @@ mop_status mop_get_path(mop_handle* h, int32_t path_id, float* xyz, int32_t flag
  * for every set path when path_id = -1, in one pass of the kernels.  veff: [1] or [P] doubles
  * (P = number of set paths, in path-id order); grad: [N][Q][3] doubles (concatenated over
  * paths in path-id order when path_id = -1), dV_eff/dR (not the force); grad may be NULL.
- * Host buffers: the call returns when they are filled.  A pinned (page-locked) host grad of one
- * mixed-precision path without an SPME grid is filled while the kernels run: the HVP pass runs
- * in bead chunks and each chunk's rows are copied on a second stream as soon as they are final
- * (the rows the bias changes, last); the result is bitwise that of the other paths.
+ * Host buffers: the call returns when they are filled.  (With MOP_PAIR_KERNELS=half, a pinned
+ * host grad of one mixed-precision path without an SPME grid is filled while the kernels run:
+ * the HVP pass runs in bead chunks and each chunk's rows are copied on a second stream as soon
+ * as they are final; the bead-lane kernels take 64 beads at once, so there the copy follows the
+ * kernels.)  The result is bitwise that of a device-pointer call.
  * Errors: MOP_ERR_STATE (path not set), MOP_ERR_NONFINITE (non-finite V_eff, host calls
  * only), MOP_ERR_CUDA, MOP_ERR_OOM. */
 mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, double* grad,
                              int32_t flags, void* cuda_stream);
+
+/* Asynchronous host calls.  With MOP_ASYNC, mop_set_path and mop_veff_and_grad take host
+ * pointers but only enqueue their work: the coordinates are copied to one of two staging buffers
+ * on an upload stream of the handle, the evaluation runs on `cuda_stream`, and V_eff and the
+ * gradient are copied back on a download stream, so that the copies of one call overlap the
+ * evaluation of the next (page-locked host buffers are needed for that).  The host arrays must
+ * stay valid and untouched until mop_wait returns; a later evaluation's gradient kernel waits
+ * for the earlier download on the device.  Non-finite input is not reported by these calls: it
+ * shows in V_eff.  mop_step and mop_metadynamics wait for pending downloads first.
+ * mop_wait returns when every enqueued upload and download has finished.  Errors: MOP_ERR_CUDA. */
+mop_status mop_wait(mop_handle* h);
 
 /* Copies one field of the last evaluation of `path_id` into out [N][Q][3] doubles (rows of
  * beads where the field is undefined are zero). */

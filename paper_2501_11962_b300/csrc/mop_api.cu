@@ -106,7 +106,7 @@ struct mop_handle {
   DevBuf<double> e_bond, e_spring, scratch;
   DevBuf<int> excl_off, excl_nb;          // Ewald exclusion partners of every atom (CSR)
   DevBuf<float> pme_theta;                // SPME kernel [K1][K2][K3 / 2 + 1]
-  PmePlans* pme = nullptr;                // cuFFT plans per bead count
+  PmePlans* pme = nullptr;                // FFT twiddle tables and axis factorisations
   double skin = 0.0;                      // Verlet skin of the pair lists (0: rebuild every time)
   DevBuf<unsigned long long> counts;
   mop_tuning tuning{1.0, 0.5};
@@ -119,6 +119,15 @@ struct mop_handle {
   // gradient copies to pinned host memory overlapped with the HVP pass (mop_veff_and_grad)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t cev[kCopyChunks] = {};
+  // asynchronous host calls (MOP_ASYNC): coordinates staged through two device buffers on their
+  // own stream, results copied on another while the next evaluation runs
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  DevBuf<unsigned char> stg[2];
+  cudaEvent_t stg_ready[2] = {}, stg_free[2] = {};
+  bool stg_used[2] = {false, false};
+  int stg_next = 0;
+  cudaEvent_t d2h_done = nullptr;   // recorded after the last asynchronous result copy
+  bool d2h_pending = false;         // that copy reads grad_int / veff_int: E2 waits for it
   // CUDA-graph mode of mop_step
   bool graph_mode = false;
   cudaGraphExec_t graph_exec = nullptr;
@@ -162,18 +171,23 @@ bool finite_all(const double* p, size_t n) {
 }
 
 // precision copies of a path; *bad (if non-NULL) is set when a coordinate is not finite
-__global__ void k_f2d(const float* in, double* out, long long n, int* bad) {
+// coordinates in both precisions; `copy` (may be NULL) receives the input as it is, so that
+// device input needs no separate device-to-device copy (which would queue on a copy engine behind
+// an asynchronous download)
+__global__ void k_f2d(const float* in, float* copy, double* out, long long n, int* bad) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     const float v = in[t];
+    if (copy) copy[t] = v;
     out[t] = widen(v);
     if (bad && !isfinite(v)) atomicOr(bad, 1);
   }
 }
-__global__ void k_d2f(const double* in, float* out, long long n, int* bad) {
+__global__ void k_d2f(const double* in, double* copy, float* out, long long n, int* bad) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     const double v = in[t];
+    if (copy) copy[t] = v;
     out[t] = (float)v;
     if (bad && !isfinite(v)) atomicOr(bad, 1);
   }
@@ -467,6 +481,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     const size_t row = 3 * (size_t)sc.Q;
     std::vector<std::pair<int, int>> after_bias;
     CK(h, clear_jacc(true));
+    if (h->d2h_pending) CK(h, cudaStreamWaitEvent(st, h->d2h_done, 0));
     for (int c = 0; c < kCopyChunks; ++c) {
       const int p0 = pairs * c / kCopyChunks, p1 = pairs * (c + 1) / kCopyChunks;
       const int b0 = 2 * p0, hb1 = std::min(2 * p1, nh);          // HVP beads of the chunk
@@ -520,6 +535,8 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     }
   }
   CK(h, mark(4));
+  // an asynchronous copy of the previous results may still be reading the gradient and V_eff
+  if (h->d2h_pending) CK(h, cudaStreamWaitEvent(st, h->d2h_done, 0));
   CK(h, launch_e2(sc, h->d_paths.p, np, max_qpad, max_n, L, h->e_spring.p, nbx));
   CK(h, mark(5));
   CK(h, launch_bias(sc, h->d_paths.p, np, L));
@@ -532,6 +549,27 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
 }
 
 void drop_graph(mop_handle* h);
+
+// streams and events of the asynchronous host calls, created on first use
+cudaError_t async_streams(mop_handle* h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->h2d_stream) e = cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !h->d2h_stream) e = cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    if (!h->stg_ready[k]) e = cudaEventCreateWithFlags(&h->stg_ready[k], cudaEventDisableTiming);
+    if (e == cudaSuccess && !h->stg_free[k]) e = cudaEventCreateWithFlags(&h->stg_free[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && !h->d2h_done) e = cudaEventCreateWithFlags(&h->d2h_done, cudaEventDisableTiming);
+  return e;
+}
+
+// the host waits for the asynchronous result copies (before work that is captured in a graph)
+cudaError_t settle_copies(mop_handle* h) {
+  if (!h->d2h_pending) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(h->d2h_done);
+  if (e == cudaSuccess) h->d2h_pending = false;
+  return e;
+}
 
 // M_p(t) at the integers t = 0..p-1, by the B-spline recursion
 // M_n(x) = (x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)) / (n - 1) from M_2(0) = 0, M_2(1) = 1
@@ -909,6 +947,14 @@ mop_status mop_destroy(mop_handle* h) {
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   for (auto& e : h->cev)
     if (e) cudaEventDestroy(e);
+  if (h->h2d_stream) cudaStreamSynchronize(h->h2d_stream), cudaStreamDestroy(h->h2d_stream);
+  if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream), cudaStreamDestroy(h->d2h_stream);
+  for (int k = 0; k < 2; ++k) {
+    if (h->stg_ready[k]) cudaEventDestroy(h->stg_ready[k]);
+    if (h->stg_free[k]) cudaEventDestroy(h->stg_free[k]);
+    h->stg[k].release();
+  }
+  if (h->d2h_done) cudaEventDestroy(h->d2h_done);
   h->step_dev.release();
   h->d_one.release(); h->counts.release();
   h->d_paths.release(); h->e_bond.release(); h->e_spring.release(); h->scratch.release(); h->excl_off.release(); h->excl_nb.release();
@@ -945,10 +991,27 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
   if (P.set) drop_graph(h);
   P.set = false;
   const size_t n = 3 * (size_t)n_beads * h->sc.Q;
-  const bool dev = flags & MOP_DEVPTR, f64 = flags & MOP_INPUT_F64;
+  const bool f64 = flags & MOP_INPUT_F64;
+  const bool async = !(flags & MOP_DEVPTR) && (flags & MOP_ASYNC);
   CK(h, P.x32.ensure(n));
   CK(h, P.x64.ensure(n));
   CK(h, P.vel.ensure(n));
+  if (async) {
+    // the host array goes to a staging buffer on the handle's upload stream (two buffers, so the
+    // next upload overlaps the evaluation that uses this one); the rest reads it on the device
+    CK(h, async_streams(h));
+    const int k = h->stg_next;
+    h->stg_next ^= 1;
+    const size_t bytes = n * (f64 ? sizeof(double) : sizeof(float));
+    CK(h, h->stg[k].ensure(bytes));
+    if (h->stg_used[k]) CK(h, cudaStreamWaitEvent(h->h2d_stream, h->stg_free[k], 0));
+    CK(h, cudaMemcpyAsync(h->stg[k].p, xyz, bytes, cudaMemcpyHostToDevice, h->h2d_stream));
+    CK(h, cudaEventRecord(h->stg_ready[k], h->h2d_stream));
+    CK(h, cudaStreamWaitEvent(st, h->stg_ready[k], 0));
+    xyz = h->stg[k].p;
+    h->stg_used[k] = true;
+  }
+  const bool dev = async || (flags & MOP_DEVPTR);
   // host input is checked for non-finite values on the device, during the precision copy
   int* bad = nullptr;
   if (!dev) {
@@ -956,15 +1019,17 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
     CK(h, cudaMemsetAsync(h->flag.p, 0, sizeof(int), st));
     bad = h->flag.p;
   }
-  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (f64) {
-    CK(h, cudaMemcpyAsync(P.x64.p, xyz, n * sizeof(double), kind, st));
-    k_d2f<<<nblk(n, 256), 256, 0, st>>>(P.x64.p, P.x32.p, (long long)n, bad);
+    if (!dev) CK(h, cudaMemcpyAsync(P.x64.p, xyz, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_d2f<<<nblk(n, 256), 256, 0, st>>>(dev ? (const double*)xyz : P.x64.p, dev ? P.x64.p : nullptr, P.x32.p,
+                                         (long long)n, bad);
   } else {
-    CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), kind, st));
-    k_f2d<<<nblk(n, 256), 256, 0, st>>>(P.x32.p, P.x64.p, (long long)n, bad);
+    if (!dev) CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), cudaMemcpyHostToDevice, st));
+    k_f2d<<<nblk(n, 256), 256, 0, st>>>(dev ? (const float*)xyz : P.x32.p, dev ? P.x32.p : nullptr, P.x64.p,
+                                         (long long)n, bad);
   }
   CK(h, cudaGetLastError());
+  if (async) CK(h, cudaEventRecord(h->stg_free[(h->stg_next ^ 1)], st));   // the staging buffer may be reused
   CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
   if (!dev) {
     int flag = 0;
@@ -1011,6 +1076,25 @@ mop_status mop_veff_and_grad(mop_handle* h, int32_t path_id, double* veff, doubl
   CK(h, cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const bool dev = flags & MOP_DEVPTR;
+  if (!dev && (flags & MOP_ASYNC)) {
+    // enqueue the evaluation on st and the result copies on the download stream; they overlap
+    // the next call's work, and mop_wait ends them
+    CK(h, async_streams(h));
+    if ((s = evaluate(h, ids, nullptr, nullptr, st, true))) return s;
+    CK(h, cudaEventRecord(h->d2h_done, st));
+    CK(h, cudaStreamWaitEvent(h->d2h_stream, h->d2h_done, 0));
+    size_t goff = 0;
+    for (size_t k = 0; k < ids.size(); ++k) {
+      PathHost& P = h->paths[ids[k]];
+      if (veff) CK(h, cudaMemcpyAsync(veff + k, P.veff_int.p, sizeof(double), cudaMemcpyDeviceToHost, h->d2h_stream));
+      const size_t n = 3 * (size_t)P.N * h->sc.Q;
+      if (grad) CK(h, cudaMemcpyAsync(grad + goff, P.grad_int.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->d2h_stream));
+      goff += n;
+    }
+    CK(h, cudaEventRecord(h->d2h_done, h->d2h_stream));
+    h->d2h_pending = true;
+    return MOP_OK;
+  }
   // a pinned host gradient buffer lets the gradient copy overlap the HVP pass (one path)
   double* host_grad = nullptr;
   if (!dev && grad && ids.size() == 1) {
@@ -1244,6 +1328,15 @@ void drop_graph(mop_handle* h) {
 
 extern "C" {
 
+mop_status mop_wait(mop_handle* h) {
+  if (!h) return MOP_ERR_ARG;
+  CK(h, cudaSetDevice(h->device));
+  if (h->h2d_stream) CK(h, cudaStreamSynchronize(h->h2d_stream));
+  if (h->d2h_stream) CK(h, cudaStreamSynchronize(h->d2h_stream));
+  h->d2h_pending = false;
+  return MOP_OK;
+}
+
 mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, uint64_t seed, void* cuda_stream) {
   if (!h) return MOP_ERR_ARG;
   h->err.clear();
@@ -1253,6 +1346,7 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
   mop_status s = select_paths(h, -1, &ids);
   if (s) return s;
   CK(h, cudaSetDevice(h->device));
+  CK(h, settle_copies(h));   // no captured step waits on an asynchronous copy
   cudaStream_t st = (cudaStream_t)cuda_stream;
   CK(h, h->step_dev.ensure(1));
   if (!h->step_ready) {

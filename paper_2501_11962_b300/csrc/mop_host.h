@@ -49,11 +49,28 @@ struct Grid {
   int max_clu;            // upper bound of the cluster count
 };
 
+// page-locked host words that kernels write directly (mapped memory): small results the host
+// waits for travel without a copy engine, so they do not queue behind a large download
+struct HostMailbox {
+  int* h = nullptr;   // host address
+  int* d = nullptr;   // device address of the same words
+  cudaError_t ensure() {
+    if (h) return cudaSuccess;
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&h), 4 * sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0);
+    return e;
+  }
+  ~HostMailbox() {
+    if (h) cudaFreeHost(h);
+  }
+};
+
 struct PathHost {
   bool set = false;
   int N = 0;
   int n_clu = 0;
   int cap = 256;          // list entries reserved per i-cluster
+  HostMailbox mbox;       // the list counts read after a synchronous build
   int max_count = 0;      // largest list of the last synchronous build
   bool sized = false;     // cap has been checked on the host at least once
   // state

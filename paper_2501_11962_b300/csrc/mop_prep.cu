@@ -668,6 +668,11 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
 
 inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
+// meta[0..3] into mapped host memory (read by the host after the stream synchronises)
+__global__ void k_post_meta(const int* meta, int* host_mapped) {
+  if (threadIdx.x < 4) reinterpret_cast<volatile int*>(host_mapped)[threadIdx.x] = meta[threadIdx.x];
+}
+
 }  // namespace
 
 #define MOP_CK(x)                                          \
@@ -847,9 +852,12 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                                                        P.meta.p);
     MOP_KL();
     if (!sync) return cudaSuccess;   // capture-safe: an overflow shows up in the sticky flag
-    int meta[4];
-    MOP_CK(cudaMemcpyAsync(meta, P.meta.p, sizeof(meta), cudaMemcpyDeviceToHost, st));
+    MOP_CK(P.mbox.ensure());
+    k_post_meta<<<1, 32, 0, st>>>(P.meta.p, P.mbox.d);
+    MOP_KL();
     MOP_CK(cudaStreamSynchronize(st));
+    int meta[4];
+    for (int k = 0; k < 4; ++k) meta[k] = reinterpret_cast<volatile int*>(P.mbox.h)[k];
     P.n_clu = meta[0];
     if (meta[2] <= P.cap) {
       P.max_count = meta[2];

@@ -18,7 +18,7 @@ STATUS_NAMES = ["MOP_OK", "MOP_ERR_ARG", "MOP_ERR_CUDA", "MOP_ERR_OOM", "MOP_ERR
 MOP_SHIFTED_FORCE, MOP_POT_SHIFT = 0, 1
 MOP_HVP_ADJOINT, MOP_HVP_FD = 0, 1
 MOP_PREC_MIXED, MOP_PREC_FP64 = 0, 1
-MOP_DEVPTR, MOP_INPUT_F64, MOP_E2E, MOP_COM = 1, 2, 4, 8
+MOP_DEVPTR, MOP_INPUT_F64, MOP_E2E, MOP_COM, MOP_ASYNC = 1, 2, 4, 8, 16
 MOP_ELEC_RF, MOP_ELEC_PME = 0, 1
 MOP_FIELD_FORCE, MOP_FIELD_ETA, MOP_FIELD_HETA = 0, 1, 2
 
@@ -27,7 +27,7 @@ EXPORTS = ("mop_create", "mop_destroy", "mop_set_path", "mop_get_path", "mop_vef
            "mop_set_profiling", "mop_last_pass_ms", "mop_count_pairs", "mop_spring_energy_noalloc",
            "mop_set_graph_mode", "mop_set_tuning", "mop_get_tuning", "mop_autotune", "mop_measure_fp32_peak",
            "mop_metadynamics", "mop_get_gaussians", "mop_add_cv", "mop_add_gaussian",
-           "mop_set_list_skin", "mop_get_list_stats", "mop_get_list_overflows", "mop_last_error")
+           "mop_set_list_skin", "mop_get_list_stats", "mop_get_list_overflows", "mop_wait", "mop_last_error")
 
 
 class MopError(RuntimeError):
@@ -223,6 +223,25 @@ class Engine:
                                       C.c_void_p(grad.data_ptr()) if grad is not None else None, MOP_DEVPTR,
                                       _stream_ptr(stream))
         self._check(st, "mop_veff_and_grad")
+
+    def set_path_async(self, path_id: int, xyz, stream=None):
+        """Enqueue coordinates from a page-locked float32 host tensor [N, Q, 3] (MOP_ASYNC); the
+        tensor must stay untouched until wait()."""
+        N = int(xyz.shape[0])
+        self._check(self.L.mop_set_path(self.h, path_id, N, C.c_void_p(xyz.data_ptr()), MOP_ASYNC,
+                                        _stream_ptr(stream)), "mop_set_path")
+        self.n_beads[path_id] = N
+
+    def veff_and_grad_async(self, veff, grad, path_id: int = -1, stream=None):
+        """Enqueue an evaluation whose V_eff and gradient land in page-locked float64 host tensors
+        (MOP_ASYNC); they are filled when wait() returns."""
+        st = self.L.mop_veff_and_grad(self.h, path_id, C.c_void_p(veff.data_ptr()),
+                                      C.c_void_p(grad.data_ptr()) if grad is not None else None, MOP_ASYNC,
+                                      _stream_ptr(stream))
+        self._check(st, "mop_veff_and_grad")
+
+    def wait(self):
+        self._check(self.L.mop_wait(self.h), "mop_wait")
 
     def get_field(self, path_id: int, field: int) -> np.ndarray:
         out = np.empty((self.n_beads[path_id], self.Q, 3))

@@ -1,6 +1,8 @@
-"""mop_veff_and_grad into pinned host memory: the HVP pass runs in bead chunks and each chunk's
-gradient rows are copied while later chunks compute (the rows the bias touches after the last
-chunk).  The result must equal, bit for bit, the device-pointer call and the pageable-host call."""
+"""mop_veff_and_grad into pinned host memory.  With the earlier half-list kernels
+(MOP_PAIR_KERNELS=half) the HVP pass runs in bead chunks and each chunk's gradient rows are
+copied while later chunks compute (the rows the bias touches after the last chunk); the bead-lane
+kernels copy after the kernels.  The result must equal, bit for bit, the device-pointer call and
+the pageable-host call."""
 import ctypes as C
 
 import numpy as np
@@ -13,8 +15,13 @@ from tests.conftest import workload
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("kernels", ["default", "half"])
 @pytest.mark.parametrize("bias", [None, "end", "e2e"])
-def test_pinned_host_gradient_equals_device_result(bias):
+def test_pinned_host_gradient_equals_device_result(monkeypatch, bias, kernels):
+    if kernels == "half":
+        monkeypatch.setenv("MOP_PAIR_KERNELS", "half")
+    else:
+        monkeypatch.delenv("MOP_PAIR_KERNELS", raising=False)
     w = workload(4, n_beads=24)
     X = w.paths[0]
     N, Q = X.shape[:2]
@@ -37,3 +44,37 @@ def test_pinned_host_gradient_equals_device_result(bias):
     assert vp[0] == vd.item() == v_page[0]
     assert np.array_equal(gp.numpy(), gd.cpu().numpy())
     assert np.array_equal(g_page, gd.cpu().numpy())
+
+
+def test_async_pipeline_equals_synchronous_calls():
+    """MOP_ASYNC: three evaluations enqueued back to back from page-locked buffers (uploads and
+    downloads on the handle's streams, overlapping the next evaluation) give, after mop_wait, the
+    bits of the synchronous calls on the same coordinates; a mop_step after them waits for the
+    downloads and continues from the last path."""
+    w = workload(4, n_beads=24)
+    X = w.paths[0]
+    N, Q = X.shape[:2]
+    rng = np.random.default_rng(3)
+    xs = [(X + rng.normal(0.0, 0.002, X.shape)).astype(np.float32) for _ in range(3)]
+    ref = []
+    eng = mop.Engine(w.system)
+    for x in xs:
+        eng.set_path(0, x)
+        ref.append(eng.veff_and_grad(0))
+    xh = [torch.tensor(x).pin_memory() for x in xs]
+    vh = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in xs]
+    gh = [torch.empty((N, Q, 3), dtype=torch.float64).pin_memory() for _ in xs]
+    for k in range(3):
+        eng.set_path_async(0, xh[k])
+        eng.veff_and_grad_async(vh[k], gh[k], 0)
+    eng.wait()
+    for k in range(3):
+        assert vh[k].item() == ref[k][0][0]
+        assert np.array_equal(gh[k].numpy(), ref[k][1])
+    # a step right after asynchronous calls (no wait in between) starts from the last path
+    eng.set_path_async(0, xh[0])
+    eng.veff_and_grad_async(vh[0], gh[0], 0)
+    eng.step(1, 1e-5, 0.0, seed=1)
+    eng.wait()
+    assert np.array_equal(gh[0].numpy(), ref[0][1])
+    assert np.isfinite(eng.get_path(0)).all()
