@@ -39,7 +39,8 @@ FD_SWEEP = (1e-5, 3e-5, 1e-4, 3e-4, 1e-3)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels on
 # this workload, from the --set full capture in profiles/k_pairb_cfg5_Q150k_N64.md.  Valid only
 # for the kernel sources they were measured on: any change to them makes `traffic` null.
-PAIR_TRAFFIC = {"sources_sha256_16": "041e50e535584b68", "k_pairb<0,RF>": 408.6e6, "k_pairb<1,RF>": 495.9e6}
+PAIR_TRAFFIC = {"sources_sha256_16": "b97b39606f95e906", "k_pairb<0,RF,full>": 407.3e6,
+                "k_pairb<1,RF,half>": 2198.2e6}
 PAIR_SOURCES = ("mop_pairb.cu", "mop_pairmath.cuh", "mop_prep.cu", "mop_internal.cuh")
 # arithmetic of the mixed-precision path, quantity by quantity
 PRECISION = {"pair_arithmetic": "f32 (two beads per f32x2 instruction)",
@@ -63,7 +64,7 @@ def pair_sources_sha() -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--config", type=int, default=5)
@@ -111,7 +112,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
