@@ -44,12 +44,11 @@ PAIR_TRAFFIC = {"sources_sha256_16": "b97b39606f95e906", "k_pairb<0,RF,full>": 4
 PAIR_SOURCES = ("mop_pairb.cu", "mop_pairmath.cuh", "mop_prep.cu", "mop_internal.cuh")
 # arithmetic of the mixed-precision path, quantity by quantity
 PRECISION = {"pair_arithmetic": "f32 (two beads per f32x2 instruction)",
-             "forces_F": "double-float (f32 hi + lo): i-side f32 pair sums folded by TwoSum; j-side shares as "
-                         "40-bit fixed point carried by two f32 atomic sums (exact, order-independent), added by "
-                         "TwoSum; bonded f32 added exactly",
+             "forces_F": "double-float (f32 hi + lo): f32 pair sums folded by TwoSum (full list, no j-side "
+                         "sums); bonded f32 added exactly",
              "eta": "double-float from the exact R^{n+1} - R^n and the double-float c F; f32 copy for the HVP",
-             "H_eta": "f32 (pair and bonded terms; j-side shares on the same exact fixed-point grids, "
-                      "scaled per bead by a power of two)",
+             "H_eta": "f32 (pair and bonded terms); the j-atoms' shares of the owner-entry pass as 64-bit "
+                      "fixed point (integer atomics: exact, order-independent), scaled per bead by a power of two",
              "gradient_G": "double-float K (eta^{n-1} - eta^n) + H eta / 2 (- F^1), written as f64",
              "energies": "double-float per warp, f64 per block and across blocks",
              "ewald_j_side_and_grids": "int64 fixed point (2^-23 forces, 2^-40 SPME charge grids)"}

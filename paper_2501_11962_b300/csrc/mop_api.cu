@@ -297,8 +297,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
       // j-side sums: the H eta pass (bl 1, 2) and the force pass of the half list (bl 2)
       const int jrows = sc.bl == 2 ? std::max(n_force, n_hvp) : (sc.bl == 1 ? n_hvp : 0);
       if (jrows > 0) {
-        CK(h, P.jF.ensure((size_t)bl_groups(jrows) * Qpad * 3 * 32));
-        CK(h, P.jL.ensure((size_t)bl_groups(jrows) * Qpad * 3 * 32));
+        CK(h, P.jI.ensure((size_t)bl_groups(jrows) * Qpad * 3 * 64));
       }
     }
     // j-side sums: the half-list kernels, and the Ewald exclusion and SPME passes
@@ -379,8 +378,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     D.jacc = use_jacc ? P.jacc.p : nullptr;
     D.xb = sc.bl ? P.xb.p : nullptr;
     D.etab = sc.bl && n_hvp > 0 ? P.etab.p : nullptr;
-    D.jF = sc.bl == 1 || sc.bl == 2 ? P.jF.p : nullptr;
-    D.jL = sc.bl == 1 || sc.bl == 2 ? P.jL.p : nullptr;
+    D.jI = sc.bl == 1 || sc.bl == 2 ? P.jI.p : nullptr;
     D.e_pair = P.e_pair.p;
     D.e_excl = sc.elec == 1 ? P.e_excl.p : nullptr;
     D.cwdf = P.cwdf.p;
@@ -437,8 +435,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     for (const PathDev& D : pd) {
       const int rows = hvp ? D.n_hvp : D.n_force;
       if (rows == 0) continue;
-      cudaError_t e = cudaMemsetAsync(D.jF, 0, sizeof(float4) * bl_groups(rows) * D.Qpad * 3 * 32, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(D.jL, 0, sizeof(float2) * bl_groups(rows) * D.Qpad * 3 * 32, st);
+      cudaError_t e = cudaMemsetAsync(D.jI, 0, sizeof(unsigned long long) * bl_groups(rows) * D.Qpad * 3 * 64, st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -968,7 +965,7 @@ mop_status mop_destroy(mop_handle* h) {
     P.cwrap.release(); P.cwdf.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
-    P.eta32.release(); P.etalo.release(); P.etamax.release(); P.gmax.release(); P.jF.release(); P.jL.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
+    P.eta32.release(); P.etalo.release(); P.etamax.release(); P.gmax.release(); P.jI.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();
     P.gA.release(); P.gB.release(); P.gc.release(); P.gh.release(); P.gw.release();
   }
   delete h;

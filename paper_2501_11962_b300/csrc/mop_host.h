@@ -97,8 +97,7 @@ struct PathHost {
   DevBuf<float4> xq;
   DevBuf<double4_32a> xq64;
   DevBuf<float2> xb, etab;   // bead-lane kernels: transposed coordinates and eta
-  DevBuf<float4> jF;         // bead-lane half list: j-side sums of a pass [G][Qpad][3][32]
-  DevBuf<float2> jL;
+  DevBuf<unsigned long long> jI;   // bead-lane j-side sums of a pass [G][Qpad][3][2][32]
   DevBuf<int4> ent;
   DevBuf<double4_32a> ent64;
   DevBuf<unsigned long long> emask;

@@ -118,11 +118,9 @@ struct PathDev {
   // with G = ceil(beads / 64); element (g, s, c, l) = (bead 64 g + l, bead 64 g + 32 + l)
   const float2* xb;
   const float2* etab;
-  // bead-lane half list: j-side sums of the current pass, [G][Qpad][3][32] per lane for its two
-  // beads: the high and middle parts of a 56-bit fixed-point sum (float4) and the low part (float2),
-  // each carried by FP32 (see mop_pairb.cu); zeroed before the pass
-  float4* jF;
-  float2* jL;
+  // bead-lane j-side sums of the current pass: 64-bit fixed-point words [G][Qpad][3][2][32]
+  // (component, bead half, lane; see mop_pairb.cu), zeroed before the pass
+  unsigned long long* jI;
   // FP64 mode: [N][Qpad][3] doubles.  Mixed mode views of the same buffers: Fnb and F as
   // double-float (hi, lo) x 3 (float2 [N][Qpad][3]), Hnb and Heta as float4 [N][Qpad].
   double* Fnb;

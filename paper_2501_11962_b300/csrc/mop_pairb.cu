@@ -16,15 +16,15 @@
 // the sign reversed, to j-side sums by vector atomics; a later pass adds those to the rows.
 //
 // The j-side sums are exact and order-independent: a share v (forces in kJ mol^-1 nm^-1; H eta
-// scaled per bead by a power of two, see bl_jscale) is split into three parts on fixed grids:
-// h, v rounded to a multiple of 2^4; m, the rest rounded to a multiple of 2^-12; l, what remains
-// rounded to a multiple of 2^-28.  Each part goes to its own FP32 sum (h and m as one float4 with
-// the lane's two beads, l as a float2).  Sums of multiples of 2^4 below 2^28, of 2^-12 below
-// 2^12 and of 2^-28 below 2^-4 are exact in FP32, so the atomics give the same bits in any
-// order: 56-bit fixed point in three FP32 words (|m| <= 8 and |l| <= 2^-13 per share, and an
-// atom-bead receives a few hundred shares at most).  Below 2^-29 per share is dropped, far under
-// the FP32 rounding of the pair terms; shares beyond 2^26 (forces: atoms pressed to within
-// ~0.1 nm) round as ordinary FP32 sums do.
+// scaled per bead by a power of two, see bl_jscale) becomes the integer V = round(v 2^19) as two
+// 32-bit parts, hi = round(v / 16) and lo = round((v - 16 hi) 2^19) (FP32 arithmetic, exact for
+// |v| < 2^26; larger shares take the conversion instruction), packed into one 64-bit word as
+// hi 2^32 + lo; a 64-bit integer atomic adds it.
+// Integer sums do not depend on the order of the additions, so the result has the same bits
+// whatever order the warps run in.  The low 32 bits of a sum hold the sum of the lo parts
+// exactly while it stays below 2^31 (|lo| <= 2^22 per share, a few hundred shares per atom-bead),
+// so both sums come back and the value is (sum hi) 16 + (sum lo) 2^-19: 64-bit fixed point.
+// What falls below 2^-20 per share is dropped, far under the FP32 rounding of the pair terms.
 
 #include <algorithm>
 
@@ -251,18 +251,51 @@ __device__ __forceinline__ void bl_fold(W& S, float2 (&acc)[kBLI][3], int lane) 
     }
 }
 
-// Grids of the j-side sums: adding and subtracting 1.5 * 2^27 rounds |v| < 2^26 to a multiple of
-// 2^4, 1.5 * 2^11 rounds |r| <= 2^3 to a multiple of 2^-12, 1.5 * 2^-5 rounds |r| <= 2^-13 to a
-// multiple of 2^-28.
-constexpr float kJGridHi = 201326592.f, kJGridMid = 3072.f, kJGridLo = 0.046875f;
+// x + 1.5 * 2^23 rounds |x| < 2^22 to an integer whose two's complement is the low bits of the
+// sum's bit pattern minus that of 1.5 * 2^23
+constexpr float kMagic = 12582912.f;
+constexpr int kMagicBits = 0x4B400000;
+
+// hi 2^32 + lo as a 64-bit two's complement word: a negative lo borrows one from hi
+__device__ __forceinline__ unsigned long long bl_pack(int hi, int lo) {
+  return ((unsigned long long)(unsigned)(hi + (lo >> 31)) << 32) | (unsigned)lo;
+}
+
+// a share of 2^25 or more (atoms pressed into each other): V = round(v 2^19) by the conversion
+// instruction, split as hi = V >> 23, lo = the low 23 bits; v is clamped to |v| <= 2^34 so that
+// hi stays within 32 bits
+__device__ __noinline__ unsigned long long bl_fix_large(float v) {
+  const long long V = __float2ll_rn(fminf(fmaxf(v, -17179869184.f), 17179869184.f) * 524288.f);
+  return bl_pack((int)(V >> 23), (int)(V & 0x7fffff));
+}
+
+// the 64-bit fixed-point words (hi 2^32 + lo) of the shares v of the lane's two beads
+__device__ __forceinline__ void bl_fix(float2 v, unsigned long long& w0, unsigned long long& w1) {
+  const float2 t = fma2(v, dup2(0.0625f), dup2(kMagic));   // v / 16 rounded (|v| < 2^26)
+  const float2 hf = sub2(t, dup2(kMagic));                  // that integer, exactly
+  const float2 r = fma2(hf, dup2(-16.f), v);                // v - 16 hi, exact, |r| <= 8
+  const float2 u = fma2(r, dup2(524288.f), dup2(kMagic));   // r 2^19 rounded
+  w0 = bl_pack(__float_as_int(t.x) - kMagicBits, __float_as_int(u.x) - kMagicBits);
+  w1 = bl_pack(__float_as_int(t.y) - kMagicBits, __float_as_int(u.y) - kMagicBits);
+  if (!(fabsf(v.x) < 33554432.f)) w0 = bl_fix_large(v.x);
+  if (!(fabsf(v.y) < 33554432.f)) w1 = bl_fix_large(v.y);
+}
+
+// value of a sum of such words (units of 2^-19): (sum hi) 2^23 + (sum lo)
+__device__ __forceinline__ double bl_unfix(unsigned long long w) {
+  const long long W = (long long)w;
+  const int lo = (int)(unsigned)(w & 0xffffffffull);
+  const long long hi = (W - (long long)lo) >> 32;
+  return ((double)hi * 8388608.0 + (double)lo) * (1.0 / 524288.0);
+}
 
 // Power-of-two scale of a bead's j-side shares in the H eta pass (forces use 1).  A share sums at
 // most 4 pairs' (|b| r^2 + |g|) |u|, with |u| <= 2 max_i |eta_i| and |b| r^2 <= 14 |g| where the
 // repulsion dominates (the LJ and Coulomb parts of b r^2 are 14 and 3 times those of g; near the LJ
 // minimum, where g vanishes, b r^2 stays below ~1e3), so with gmax the largest |g| of the force
 // pass of the same bead the bound is 8 max|eta| (16 gmax + 1e3).  The scale takes that bound
-// below 2^24: shares stay inside the exact range with room for the sums, and the grids resolve
-// them to 2^-52 of the largest share.
+// below 2^24: shares stay inside the exact range with room for the sums, and the grid resolves
+// them to 2^-43 of the largest share.
 __device__ __forceinline__ float bl_jscale(float etamax, float gmax) {
   if (!(etamax > 0.f)) return 1.f;
   const float bound = 8.f * etamax * fmaf(16.f, gmax, 1e3f);
@@ -442,17 +475,14 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
         if constexpr (HALF) {
           // the j-atom's share of these pairs, for both beads of the lane, with the sign reversed,
           // on the two grids of the exact j-side sums
-          const size_t jo = g * gstride + lane + (size_t)(cj * kCL + jj) * 3 * 32;
+          // [component][bead half][lane] words of the j-atom: 256 contiguous bytes per atomic
+          unsigned long long* jp = P.jI + (g * (size_t)P.Qpad + (size_t)(cj * kCL + jj)) * 3 * 64 + lane;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            const float2 v = mul2(fj[q], njmul);
-            const float2 hv = sub2(add2(v, dup2(kJGridHi)), dup2(kJGridHi));
-            const float2 r = sub2(v, hv);   // exact
-            const float2 mv = sub2(add2(r, dup2(kJGridMid)), dup2(kJGridMid));
-            const float2 r2 = sub2(r, mv);  // exact
-            const float2 lv = sub2(add2(r2, dup2(kJGridLo)), dup2(kJGridLo));
-            atomicAdd(P.jF + jo + q * 32, make_float4(hv.x, hv.y, mv.x, mv.y));
-            atomicAdd(P.jL + jo + q * 32, lv);
+            unsigned long long w0, w1;
+            bl_fix(mul2(fj[q], njmul), w0, w1);
+            atomicAdd(jp + q * 64, w0);
+            atomicAdd(jp + q * 64 + 32, w1);
           }
         }
       };
@@ -716,55 +746,46 @@ __global__ void __launch_bounds__(256) k_bl_transpose(const float4* __restrict__
 // ---- j-side sums of the half list into the rows -----------------------------------------------
 // Block (cluster c, group g, path): the 8 slots x 64 beads of jF through shared memory; force
 // rows are double-floats (TwoSum of the high part with the FP32 sum), H eta rows FP32.
-// The three FP32 sums (h, m, l) of a value are added as a double-float, the H eta ones divided by
-// the bead's scale (a power of two).
+// The fixed-point sums are added to the rows: to the double-float forces exactly rounded, to the
+// FP32 H eta rows divided by the bead's scale (a power of two).
 template <int MODE>
 __global__ void __launch_bounds__(256) k_bl_combine(SysConsts sc, const PathDev* __restrict__ paths) {
   (void)sc;
-  __shared__ float4 t[kCL * 3][32];
-  __shared__ float2 tl[kCL * 3][32];
+  __shared__ unsigned long long t[kCL * 3][64];
   const PathDev& P = paths[blockIdx.z];
   const int c = blockIdx.x, g = blockIdx.y;
   const int rows = MODE == 0 ? P.n_force : P.n_hvp;
   if (c >= P.n_clu || c >= __ldg(&P.meta[0]) || g * kBLBeads >= rows) return;   // block-uniform
-  const size_t o = ((size_t)g * P.Qpad + (size_t)c * kCL) * 3 * 32;
-  for (int k = threadIdx.x; k < kCL * 3 * 32; k += blockDim.x) {
-    t[k >> 5][k & 31] = P.jF[o + k];
-    tl[k >> 5][k & 31] = P.jL[o + k];
-  }
+  const size_t o = ((size_t)g * P.Qpad + (size_t)c * kCL) * 3 * 64;
+  for (int k = threadIdx.x; k < kCL * 3 * 64; k += blockDim.x) t[k >> 6][k & 63] = P.jI[o + k];
   __syncthreads();
   for (int k = threadIdx.x; k < kBLBeads * kCL; k += blockDim.x) {
     const int bb = k / kCL, a = k - bb * kCL;
     const int b = g * kBLBeads + bb;
     if (b >= rows) continue;
-    const int l = bb & 31;
+    // bead bb is half bb / 32 of lane bb % 32
+    const int l = (bb & 31) + (bb & 32);
     const size_t s = (size_t)c * kCL + a;
-    float jh[3], jl[3];
+    double j[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float4 v = t[a * 3 + q][l];
-      const float2 w = tl[a * 3 + q][l];
-      const float hv = bb < 32 ? v.x : v.y, mv = bb < 32 ? v.z : v.w, lv = bb < 32 ? w.x : w.y;
-      jh[q] = hv + mv;   // (jh, jl) = hv + mv exactly (TwoSum), then + lv
-      const float bp = jh[q] - hv;
-      jl[q] = ((hv - (jh[q] - bp)) + (mv - bp)) + lv;
-    }
+    for (int q = 0; q < 3; ++q) j[q] = bl_unfix(t[a * 3 + q][l]);
     if constexpr (MODE == 0) {
       float2* F = reinterpret_cast<float2*>(P.Fnb) + 3 * ((size_t)b * P.Qpad + s);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
+        // (hi + lo + j) rounded to a double-float: hi + lo is exact in FP64
         const float2 f = F[q];
-        const float sum = f.x + jh[q], bp = sum - f.x;
-        const float err = (f.x - (sum - bp)) + (jh[q] - bp);
-        F[q] = make_float2(sum, f.y + (err + jl[q]));
+        const double sum = ((double)f.x + (double)f.y) + j[q];
+        const float nh = (float)sum;
+        F[q] = make_float2(nh, (float)(sum - (double)nh));
       }
     } else {
-      const float inv = 1.f / bl_jscale(__uint_as_float(P.etamax[b]), __uint_as_float(P.gmax[b]));   // 2^k
+      const double inv = 1.0 / bl_jscale(__uint_as_float(P.etamax[b]), __uint_as_float(P.gmax[b]));   // 2^k
       float4* H = reinterpret_cast<float4*>(P.Hnb) + (size_t)b * P.Qpad + s;
       float4 h = *H;
-      h.x += (jh[0] + jl[0]) * inv;
-      h.y += (jh[1] + jl[1]) * inv;
-      h.z += (jh[2] + jl[2]) * inv;
+      h.x = (float)((double)h.x + j[0] * inv);
+      h.y = (float)((double)h.y + j[1] * inv);
+      h.z = (float)((double)h.z + j[2] * inv);
       *H = h;
     }
   }

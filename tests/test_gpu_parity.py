@@ -487,7 +487,7 @@ def test_half_list_kernels_match_oracle(monkeypatch, hvp_mode):
 def test_bead_lane_lists_match_oracle(monkeypatch, hvp_mode, relaxed, kernels):
     """The bead-lane kernels in their three arrangements against the oracle on the water box with
     70 beads (two bead groups, the second ragged): the default (full list; the H eta pass over the
-    owner entries only, the j-atom's share added by vector atomics to exact fixed-point sums, a
+    owner entries only, the j-atom's share added by 64-bit integer atomics to fixed-point sums, a
     self entry's pairs j > i), MOP_PAIR_KERNELS=blhalf (the half list in both passes) and =blfull
     (every entry in both passes, no atomics).  Forces, eta, H eta (FD: against the oracle's own
     Eq. 5 at the same h), the gradient, V_eff, and the per-row bars."""
@@ -547,9 +547,9 @@ def test_bead_lane_lists_ewald_match_oracle(monkeypatch, kernels):
 def test_j_side_sums_are_bitwise_reproducible(monkeypatch, hvp_mode, relaxed, kernels):
     """The j-side sums (the H eta pass over the owner entries of the full list, by default, and
     both passes of the half list) are added by atomics in whatever order the warps run; they are
-    carried on three fixed-point grids in FP32, which makes every addition exact, so two handles
-    give the same bits (config 4's 96-bead path, around the generated structure with forces up to
-    2e5 kJ/mol/nm, and around the relaxed one)."""
+    64-bit fixed-point integers, so every addition is exact and two handles give the same bits
+    (config 4's 96-bead path, around the generated structure with forces up to 2e5 kJ/mol/nm, and
+    around the relaxed one)."""
     if kernels == "default":
         monkeypatch.delenv("MOP_PAIR_KERNELS", raising=False)
     else:
