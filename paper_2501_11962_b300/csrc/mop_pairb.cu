@@ -16,15 +16,13 @@
 // the sign reversed, to j-side sums by vector atomics; a later pass adds those to the rows.
 //
 // The j-side sums are exact and order-independent: a share v (forces in kJ mol^-1 nm^-1; H eta
-// scaled per bead by a power of two, see bl_jscale) becomes the integer V = round(v 2^19) as two
-// 32-bit parts, hi = round(v / 16) and lo = round((v - 16 hi) 2^19) (FP32 arithmetic, exact for
-// |v| < 2^26; larger shares take the conversion instruction), packed into one 64-bit word as
-// hi 2^32 + lo; a 64-bit integer atomic adds it.
-// Integer sums do not depend on the order of the additions, so the result has the same bits
-// whatever order the warps run in.  The low 32 bits of a sum hold the sum of the lo parts
-// exactly while it stays below 2^31 (|lo| <= 2^22 per share, a few hundred shares per atom-bead),
-// so both sums come back and the value is (sum hi) 16 + (sum lo) 2^-19: 64-bit fixed point.
-// What falls below 2^-20 per share is dropped, far under the FP32 rounding of the pair terms.
+// scaled per bead by a power of two, see bl_jscale) becomes an integer on a fixed grid, carried as
+// two 32-bit parts hi = round(v / kHi) and lo = round((v - kHi hi) kLo) (FP32 magic-number
+// roundings, see BLGrid) packed into one 64-bit word hi 2^32 + lo; a 64-bit integer atomic adds
+// it.  Integer sums do not depend on the order of the additions, so the result has the same bits
+// whatever order the warps run in.  The low 32 bits of a sum hold the sum of the lo parts exactly
+// while it stays below 2^31 (|lo| <= 2^21 per share, a few hundred shares per atom-bead), so both
+// sums come back and the value is (sum hi) kHi + (sum lo) / kLo: 64-bit fixed point.
 
 #include <algorithm>
 
@@ -261,32 +259,36 @@ __device__ __forceinline__ unsigned long long bl_pack(int hi, int lo) {
   return ((unsigned long long)(unsigned)(hi + (lo >> 31)) << 32) | (unsigned)lo;
 }
 
-// a share of 2^25 or more (atoms pressed into each other): V = round(v 2^19) by the conversion
-// instruction, split as hi = V >> 23, lo = the low 23 bits; v is clamped to |v| <= 2^34 so that
-// hi stays within 32 bits
-__device__ __noinline__ unsigned long long bl_fix_large(float v) {
-  const long long V = __float2ll_rn(fminf(fmaxf(v, -17179869184.f), 17179869184.f) * 524288.f);
-  return bl_pack((int)(V >> 23), (int)(V & 0x7fffff));
-}
+// Grids of the j-side words: a share v is clamped to |v| <= kMax, hi = round(v / kHi) and
+// lo = round((v - kHi hi) kLo), so |lo| <= kHi kLo / 2 = 2^21 and the magic-number roundings
+// stay exact.  Force shares (kJ mol^-1 nm^-1, unscaled): kHi = 2^10, kLo = 2^12, |v| <= 2^31;
+// H eta shares (scaled to at most 2^24): kHi = 2^4, kLo = 2^18, |v| <= 2^25.
+template <int MODE> struct BLGrid {
+  static constexpr float kHi = MODE == 0 ? 1024.f : 16.f;
+  static constexpr float kLo = MODE == 0 ? 4096.f : 262144.f;
+  static constexpr float kMax = MODE == 0 ? 2147483648.f : 33554432.f;
+};
 
 // the 64-bit fixed-point words (hi 2^32 + lo) of the shares v of the lane's two beads
+template <int MODE>
 __device__ __forceinline__ void bl_fix(float2 v, unsigned long long& w0, unsigned long long& w1) {
-  const float2 t = fma2(v, dup2(0.0625f), dup2(kMagic));   // v / 16 rounded (|v| < 2^26)
-  const float2 hf = sub2(t, dup2(kMagic));                  // that integer, exactly
-  const float2 r = fma2(hf, dup2(-16.f), v);                // v - 16 hi, exact, |r| <= 8
-  const float2 u = fma2(r, dup2(524288.f), dup2(kMagic));   // r 2^19 rounded
+  using Gd = BLGrid<MODE>;
+  v = make_float2(fminf(fmaxf(v.x, -Gd::kMax), Gd::kMax), fminf(fmaxf(v.y, -Gd::kMax), Gd::kMax));
+  const float2 t = fma2(v, dup2(1.f / Gd::kHi), dup2(kMagic));   // v / kHi rounded
+  const float2 hf = sub2(t, dup2(kMagic));                        // that integer, exactly
+  const float2 r = fma2(hf, dup2(-Gd::kHi), v);                   // v - kHi hi, exact
+  const float2 u = fma2(r, dup2(Gd::kLo), dup2(kMagic));          // r kLo rounded
   w0 = bl_pack(__float_as_int(t.x) - kMagicBits, __float_as_int(u.x) - kMagicBits);
   w1 = bl_pack(__float_as_int(t.y) - kMagicBits, __float_as_int(u.y) - kMagicBits);
-  if (!(fabsf(v.x) < 33554432.f)) w0 = bl_fix_large(v.x);
-  if (!(fabsf(v.y) < 33554432.f)) w1 = bl_fix_large(v.y);
 }
 
-// value of a sum of such words (units of 2^-19): (sum hi) 2^23 + (sum lo)
+// value of a sum of such words: (sum hi) kHi + (sum lo) / kLo
+template <int MODE>
 __device__ __forceinline__ double bl_unfix(unsigned long long w) {
   const long long W = (long long)w;
   const int lo = (int)(unsigned)(w & 0xffffffffull);
   const long long hi = (W - (long long)lo) >> 32;
-  return ((double)hi * 8388608.0 + (double)lo) * (1.0 / 524288.0);
+  return (double)hi * (double)BLGrid<MODE>::kHi + (double)lo * (1.0 / (double)BLGrid<MODE>::kLo);
 }
 
 // Power-of-two scale of a bead's j-side shares in the H eta pass (forces use 1).  A share sums at
@@ -294,8 +296,7 @@ __device__ __forceinline__ double bl_unfix(unsigned long long w) {
 // repulsion dominates (the LJ and Coulomb parts of b r^2 are 14 and 3 times those of g; near the LJ
 // minimum, where g vanishes, b r^2 stays below ~1e3), so with gmax the largest |g| of the force
 // pass of the same bead the bound is 8 max|eta| (16 gmax + 1e3).  The scale takes that bound
-// below 2^24: shares stay inside the exact range with room for the sums, and the grid resolves
-// them to 2^-43 of the largest share.
+// below 2^24: shares stay inside the grid's range, which resolves them to 2^-42 of the largest.
 __device__ __forceinline__ float bl_jscale(float etamax, float gmax) {
   if (!(etamax > 0.f)) return 1.f;
   const float bound = 8.f * etamax * fmaf(16.f, gmax, 1e3f);
@@ -480,7 +481,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             unsigned long long w0, w1;
-            bl_fix(mul2(fj[q], njmul), w0, w1);
+            bl_fix<MODE == 0 ? 0 : 1>(mul2(fj[q], njmul), w0, w1);
             atomicAdd(jp + q * 64, w0);
             atomicAdd(jp + q * 64 + 32, w1);
           }
@@ -768,7 +769,7 @@ __global__ void __launch_bounds__(256) k_bl_combine(SysConsts sc, const PathDev*
     const size_t s = (size_t)c * kCL + a;
     double j[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) j[q] = bl_unfix(t[a * 3 + q][l]);
+    for (int q = 0; q < 3; ++q) j[q] = bl_unfix<MODE == 0 ? 0 : 1>(t[a * 3 + q][l]);
     if constexpr (MODE == 0) {
       float2* F = reinterpret_cast<float2*>(P.Fnb) + 3 * ((size_t)b * P.Qpad + s);
 #pragma unroll
