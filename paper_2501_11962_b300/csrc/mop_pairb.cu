@@ -654,10 +654,9 @@ cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, l
 
 // ---- bead-1 pair energy --------------------------------------------------------------------
 // One warp per i-cluster, lane (i = lane & 7, jq = lane >> 3) against j-atoms jq and jq + 4 of
-// every entry; each pair of the full list is met from both sides, so the sum is halved (HALF:
-// the half list holds each pair once).
+// every owner entry (a self entry's pairs j > i), so each pair is met once.
 // phi_sf(r) = phi(r) - phi(rc) - (r - rc) phi'(rc) (sh = phi'(rc) = 0 with the potential shift).
-template <bool EW, bool HALF>
+template <bool EW>
 __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __restrict__ paths, int max_clu) {
   __shared__ int4 sent[4][32];
   __shared__ unsigned long long sm[4][32];
@@ -684,7 +683,9 @@ __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __
     __syncwarp();
     for (int e = 0; e < nc; ++e) {
       const int4 E = sent[w][e];
-      const unsigned long long M = sm[w][e];
+      if (!(E.x & kOwnerFlag)) continue;   // warp-uniform
+      unsigned long long M = sm[w][e];
+      if (E.x & kSelfFlag) M &= 0x7f3f1f0f07030100ull;
       const int cj = E.x & kCluMask;
       const float Dx = __int_as_float(E.y), Dy = __int_as_float(E.z), Dz = __int_as_float(E.w);
 #pragma unroll
@@ -719,7 +720,7 @@ __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __
   }
   two_sum_add(hi, lo, acc);
   const df v = df_warp_sum(df{hi, lo});
-  if (lane == 0) P.e_pair[ci] = (HALF ? 1.0 : 0.5) * ((double)v.hi + (double)v.lo);
+  if (lane == 0) P.e_pair[ci] = (double)v.hi + (double)v.lo;
 }
 
 // ---- transposition into the bead-lane layout -------------------------------------------------
@@ -834,14 +835,8 @@ cudaError_t launch_pairb(const SysConsts& sc, const PathDev* d_paths, int n_path
 
 cudaError_t launch_energy1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_clu, Launch L) {
   const dim3 grid((unsigned)((max_clu + 3) / 4), (unsigned)n_paths);
-  const bool half = sc.bl == 2;
-  if (sc.elec == 1) {
-    if (half) k_energy1<true, true><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
-    else k_energy1<true, false><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
-  } else {
-    if (half) k_energy1<false, true><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
-    else k_energy1<false, false><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
-  }
+  if (sc.elec == 1) k_energy1<true><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
+  else k_energy1<false><<<grid, 128, 0, L.st>>>(sc, d_paths, max_clu);
   ++*L.counter;
   return cudaGetLastError();
 }
