@@ -768,26 +768,33 @@ __global__ void __launch_bounds__(256) k_bl_combine(SysConsts sc, const PathDev*
     // bead bb is half bb / 32 of lane bb % 32
     const int l = (bb & 31) + (bb & 32);
     const size_t s = (size_t)c * kCL + a;
-    double j[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) j[q] = bl_unfix<MODE == 0 ? 0 : 1>(t[a * 3 + q][l]);
     if constexpr (MODE == 0) {
+      // forces: (hi + lo + j) rounded to a double-float, in FP64 (hi + lo is exact there)
       float2* F = reinterpret_cast<float2*>(P.Fnb) + 3 * ((size_t)b * P.Qpad + s);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        // (hi + lo + j) rounded to a double-float: hi + lo is exact in FP64
         const float2 f = F[q];
-        const double sum = ((double)f.x + (double)f.y) + j[q];
+        const double sum = ((double)f.x + (double)f.y) + bl_unfix<0>(t[a * 3 + q][l]);
         const float nh = (float)sum;
         F[q] = make_float2(nh, (float)(sum - (double)nh));
       }
     } else {
-      const double inv = 1.0 / bl_jscale(__uint_as_float(P.etamax[b]), __uint_as_float(P.gmax[b]));   // 2^k
+      // H eta rows are FP32: the sums are decoded in FP32 (the FP64 pipe of this part would make
+      // the decode the bound of the pass), divided by the bead's scale (a power of two)
+      const float inv = 1.f / bl_jscale(__uint_as_float(P.etamax[b]), __uint_as_float(P.gmax[b]));
+      float j[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const unsigned long long w = t[a * 3 + q][l];
+        const int lo = (int)(unsigned)(w & 0xffffffffull);
+        const int hi = (int)(((long long)w - (long long)lo) >> 32);
+        j[q] = fmaf(__int2float_rn(hi), BLGrid<1>::kHi, __int2float_rn(lo) * (1.f / BLGrid<1>::kLo)) * inv;
+      }
       float4* H = reinterpret_cast<float4*>(P.Hnb) + (size_t)b * P.Qpad + s;
       float4 h = *H;
-      h.x = (float)((double)h.x + j[0] * inv);
-      h.y = (float)((double)h.y + j[1] * inv);
-      h.z = (float)((double)h.z + j[2] * inv);
+      h.x += j[0];
+      h.y += j[1];
+      h.z += j[2];
       *H = h;
     }
   }
