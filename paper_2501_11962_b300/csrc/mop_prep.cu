@@ -528,6 +528,9 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
         const int nbin = binstart[binbase + (zl - kz * nb[2]) + 1] - s0;
         z0 = zl + 1;
         const int kk[3] = {kx, ky, kz};
+        // the image shift of this piece in FP32, converted once (not per candidate)
+        const float kf[3] = {(float)kx, (float)ky, (float)kz};
+        const float kL[3] = {kf[0] * Lf[0], kf[1] * Lf[1], kf[2] * Lf[2]};
         for (int t0 = 0; t0 < nbin; t0 += 32) {
           const int t = t0 + lane;
           int cj = -1;
@@ -546,9 +549,9 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
           if (cj >= 0) {
             // FP32 pre-test of the union boxes (slack covers the FP32 rounding of the centres)
             const float4 cw = cbox[2 * cj], ce = cbox[2 * cj + 1];
-            const float gx = fmaxf(0.f, fabsf(wif[0] - (cw.x + kk[0] * Lf[0])) - eif[0] - ce.x);
-            const float gy = fmaxf(0.f, fabsf(wif[1] - (cw.y + kk[1] * Lf[1])) - eif[1] - ce.y);
-            const float gz = fmaxf(0.f, fabsf(wif[2] - (cw.z + kk[2] * Lf[2])) - eif[2] - ce.z);
+            const float gx = fmaxf(0.f, fabsf(wif[0] - (cw.x + kL[0])) - eif[0] - ce.x);
+            const float gy = fmaxf(0.f, fabsf(wif[1] - (cw.y + kL[1])) - eif[1] - ce.y);
+            const float gz = fmaxf(0.f, fabsf(wif[2] - (cw.z + kL[2])) - eif[2] - ce.z);
             box = gx * gx + gy * gy + gz * gz < rcs2;
           }
           float Df[3] = {0.f, 0.f, 0.f};   // FP32 Delta for the warp's exact test and the entry
@@ -561,11 +564,10 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
                 // the same difference exactly as a double-float on the FP32 pipes, rounded once:
                 // w_i - w_j by TwoSum plus the low parts, minus k L with k Lf exact by an FMA
                 const float2 wj = cwdf[3 * cj + d];
-                const float kf = (float)kk[d];
-                const float p = kf * sc.Lf[d];
+                const float p = kL[d];
                 df t = two_sum(widf[d].x, -wj.x);
-                t = df_add(t, df{-p, (widf[d].y - wj.y) - fmaf(kf, sc.Lf[d], -p)});
-                Df[d] = t.hi + (t.lo - kf * sc.Llo[d]);
+                t = df_add(t, df{-p, (widf[d].y - wj.y) - fmaf(kf[d], sc.Lf[d], -p)});
+                Df[d] = t.hi + (t.lo - kf[d] * sc.Llo[d]);
               }
             }
             // the atom spheres of this lane's candidate, read by the whole warp below
