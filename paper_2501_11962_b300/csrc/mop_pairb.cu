@@ -68,6 +68,15 @@ constexpr int kBLFold = MOP_BL_FOLD;   // list entries between folds of the FP32
 #define MOP_BL_ILP 1
 #endif
 constexpr int kBLIlp = MOP_BL_ILP;
+// the entry's j-atom charges and types loaded once per entry and shuffled to the j-loop (force
+// kernel: 5.69 -> 5.45 ms at config 5), or loaded per j-atom (H eta and FD kernels: faster there)
+#ifndef MOP_BL_QTSHFL_F
+#define MOP_BL_QTSHFL_F 1
+#endif
+#ifndef MOP_BL_QTSHFL_H
+#define MOP_BL_QTSHFL_H 0
+#endif
+template <int MODE> struct BLQtShfl { static constexpr bool value = MODE == 0 ? MOP_BL_QTSHFL_F : MOP_BL_QTSHFL_H; };
 #ifndef MOP_BL_JSTATIC
 #define MOP_BL_JSTATIC 1
 #endif
@@ -390,7 +399,8 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
   const int cnt = __ldg(&P.lcnt[ci]);
   const size_t eb = (size_t)ci * P.cap;
   int since_fold = 0;
-  auto load_j = [&](int cj, int jj, BLJ& J) __attribute__((always_inline)) {
+  // qv, tv: lane jj < 8 holds the charge and pair-table offset of j-atom jj of the entry
+  auto load_j = [&](int cj, int jj, BLJ& J, float qv, int tv) __attribute__((always_inline)) {
     const int sj = cj * kCL + jj;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -398,8 +408,15 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       J.x[c] = __ldg(xg + o);
       if (MODE >= 1) J.e[c] = __ldg(eg + o);
     }
-    J.qj = dup2(__ldg(&P.xq[sj]).w);
-    J.tj = __ldg(&P.ts[sj]) * NR;
+    if constexpr (BLQtShfl<MODE>::value) {
+      J.qj = dup2(__shfl_sync(0xffffffffu, qv, jj));
+      J.tj = __shfl_sync(0xffffffffu, tv, jj);
+    } else {
+      (void)qv;
+      (void)tv;
+      J.qj = dup2(__ldg(&P.xq[sj]).w);
+      J.tj = __ldg(&P.ts[sj]) * NR;
+    }
   };
   auto prefetch_j = [&](int cj, int jj) __attribute__((always_inline)) {
     const int sj = cj * kCL + jj;
@@ -432,6 +449,14 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       const unsigned long long Mi = (M >> a0) & (0x0101010101010101ull * ((1u << kBLI) - 1u));
       if (!Mi) continue;   // warp-uniform: no candidate pair for these i-atoms
       unsigned long long nz = nonzero_bytes(Mi);
+      // charges and pair-table offsets of the entry's 8 j-atoms, one load per entry (the j-loop
+      // takes them by shuffle instead of two dependent loads per j-atom)
+      float qv = 0.f;
+      int tv = 0;
+      if (BLQtShfl<MODE>::value && lane < kCL) {
+        qv = __ldg(&P.xq[cj * kCL + lane]).w;
+        tv = __ldg(&P.ts[cj * kCL + lane]) * NR;
+      }
       // evaluate the candidate pairs of one j-atom (the i-loop is unrolled: registers stay static)
       auto eval_j = [&](const BLJ& cur, int jj) __attribute__((always_inline)) {
         const unsigned byte = (unsigned)(Mi >> (8 * jj)) & 0xffu;
@@ -494,11 +519,11 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       // software pipeline: the next j-atom's loads are issued before the current one is
       // evaluated (after unrolling, handing the registers on costs nothing)
       BLJ cur;
-      if ((Mi & 0xffull) != 0ull) load_j(cj, 0, cur);
+      if ((Mi & 0xffull) != 0ull) load_j(cj, 0, cur, qv, tv);
 #pragma unroll
       for (int jj = 0; jj < kCL; ++jj) {
         BLJ nxt;
-        if (jj + 1 < kCL && ((Mi >> (8 * (jj + 1))) & 0xffull)) load_j(cj, jj + 1, nxt);   // warp-uniform
+        if (jj + 1 < kCL && ((Mi >> (8 * (jj + 1))) & 0xffull)) load_j(cj, jj + 1, nxt, qv, tv);   // warp-uniform
         if ((Mi >> (8 * jj)) & 0xffull) eval_j(cur, jj);
         cur = nxt;
       }
@@ -511,7 +536,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
           if (jj + 1 < kCL && ((Mi >> (8 * (jj + 1))) & 0xffull)) prefetch_j(cj, jj + 1);
         }
         BLJ cur;
-        load_j(cj, jj, cur);
+        load_j(cj, jj, cur, qv, tv);
         eval_j(cur, jj);
       }
       }
@@ -519,7 +544,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       int jj = (__ffsll((long long)nz) - 1) >> 3;
       nz &= nz - 1;
       BLJ cur;
-      load_j(cj, jj, cur);
+      load_j(cj, jj, cur, qv, tv);
       while (true) {
         // the next j-atom of this entry is loaded while the current one is evaluated
         const bool more = nz != 0ull;
@@ -528,7 +553,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
         if (more) {
           jn = (__ffsll((long long)nz) - 1) >> 3;
           nz &= nz - 1;
-          load_j(cj, jn, nxt);
+          load_j(cj, jn, nxt, qv, tv);
         }
         eval_j(cur, jj);
         if (!more) break;
