@@ -10,10 +10,13 @@
 // list of j-clusters.  Every lane evaluates the same atom pair at the same time, so the choice
 // of pairs is warp-uniform: the list entry's 64-bit mask of candidate pairs (the atoms' union
 // spheres over all beads come within rc, excluded pairs removed) selects them, with no
-// per-bead screening and no divergence.  The list holds every cluster pair from both sides, so
-// an atom's sum is complete in its own warp: no j-side sums and no atomics.  On the half list
-// (each atom pair once) the warp also sums each j-atom's share over its i-atoms and adds it, with
-// the sign reversed, to j-side sums by vector atomics; a later pass adds those to the rows.
+// per-bead screening and no divergence.  The list holds every cluster pair from both sides, and
+// one entry of each mirror pair carries an owner flag.  Without HALF a kernel walks every entry,
+// so an atom's sum is complete in its own warp: no j-side sums and no atomics (the force pass).
+// With HALF it walks the owner entries only (each atom pair once; a self entry's pairs j > i),
+// and the warp also sums each j-atom's share over its i-atoms and adds it, with the sign
+// reversed, to j-side sums; a later pass (k_bl_combine) adds those to the rows (the H eta and FD
+// passes, and both passes of a half list, which holds owner entries only).
 //
 // The j-side sums are exact and order-independent: a share v (forces in kJ mol^-1 nm^-1; H eta
 // scaled per bead by a power of two, see bl_jscale) becomes an integer on a fixed grid, carried as
