@@ -47,8 +47,9 @@ PRECISION = {"pair_arithmetic": "f32 (two beads per f32x2 instruction)",
              "forces_F": "double-float (f32 hi + lo): f32 pair sums folded by TwoSum (full list, no j-side "
                          "sums); bonded f32 added exactly",
              "eta": "double-float from the exact R^{n+1} - R^n and the double-float c F; f32 copy for the HVP",
-             "H_eta": "f32 (pair and bonded terms); the j-atoms' shares of the owner-entry pass as 64-bit "
-                      "fixed point (integer atomics: exact, order-independent), scaled per bead by a power of two",
+             "H_eta": "f32 pair terms; i-side sums folded into double-floats, the j-atoms' shares of the "
+                      "owner-entry pass as 64-bit fixed point (integer atomics: exact, order-independent, scaled "
+                      "per bead by a power of two); stored as f32, bonded f32 added",
              "gradient_G": "double-float K (eta^{n-1} - eta^n) + H eta / 2 (- F^1), written as f64",
              "energies": "double-float per warp, f64 per block and across blocks",
              "ewald_j_side_and_grids": "int64 fixed point (2^-23 forces, 2^-40 SPME charge grids)"}
