@@ -78,3 +78,21 @@ def test_async_pipeline_equals_synchronous_calls():
     eng.wait()
     assert np.array_equal(gh[0].numpy(), ref[0][1])
     assert np.isfinite(eng.get_path(0)).all()
+
+
+def test_async_all_paths_equals_synchronous_call():
+    """MOP_ASYNC with path_id = -1: the V_eff of every set path and the concatenated gradient land
+    in the page-locked buffers as the synchronous call returns them; mop_wait on a handle with
+    nothing pending returns at once."""
+    w = workload(4)
+    eng = mop.Engine(w.system)
+    eng.wait()
+    for p in (0, 1, 2):
+        eng.set_path(p, w.paths[p])
+    v_ref, g_ref = eng.veff_and_grad(-1)
+    vh = torch.zeros(3, dtype=torch.float64).pin_memory()
+    gh = torch.empty(g_ref.shape, dtype=torch.float64).pin_memory()
+    eng.veff_and_grad_async(vh, gh, -1)
+    eng.wait()
+    assert np.array_equal(vh.numpy(), v_ref)
+    assert np.array_equal(gh.numpy(), g_ref)
