@@ -9,6 +9,8 @@ from pathlib import Path
 HERE = Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 LIB = HERE / "libmop.so"
+# the same library with the range check of the j-side shares compiled in (for the tests only)
+CHECK_LIB = HERE / "libmop_jcheck.so"
 SOURCES = ["mop_api.cu", "mop_prep.cu", "mop_pair.cu", "mop_pairb.cu", "mop_path.cu", "mop_pme.cu", "mop_fft.cu",
            "mop_noalloc.cu", "mop_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -18,10 +20,10 @@ PER_FILE = {"mop_pair.cu": ["-ftz=true"], "mop_pairb.cu": ["-ftz=true"], "mop_pa
             "mop_pme.cu": ["-ftz=true"]}
 
 
-def _stale() -> bool:
-    if not LIB.exists():
+def _stale(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return True
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     deps = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h"))
     deps.append(HERE.parent / "include" / "mop.h")
     return any(d.stat().st_mtime > t for d in deps)
@@ -53,5 +55,23 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     return LIB
 
 
+def build_check(force: bool = False) -> Path:
+    """libmop_jcheck.so: the objects of build() with mop_pairb.cu compiled with MOP_BL_JCHECK=1."""
+    build(force)
+    if not force and not _stale(CHECK_LIB):
+        return CHECK_LIB
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    objdir = HERE / "_build"
+    obj = objdir / "mop_pairb_jcheck.o"
+    subprocess.run([nvcc, *ARCH, *FLAGS, *PER_FILE["mop_pairb.cu"], "-DMOP_BL_JCHECK=1", "-c",
+                    str(CSRC / "mop_pairb.cu"), "-o", str(obj)], check=True)
+    objs = [str(objdir / (Path(s).stem + ".o")) for s in SOURCES if s != "mop_pairb.cu"] + [str(obj)]
+    tmp = CHECK_LIB.with_suffix(".so.tmp")
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", str(tmp), *objs, "-lcudart"], check=True)
+    tmp.replace(CHECK_LIB)
+    return CHECK_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    print(build_check(force="--force" in sys.argv))

@@ -71,6 +71,13 @@ constexpr int kBLFold = MOP_BL_FOLD;   // list entries between folds of the FP32
 #define MOP_BL_ILP 1
 #endif
 constexpr int kBLIlp = MOP_BL_ILP;
+// check build (a second library for the tests, never the product): a lane whose j-side share
+// for a bead exceeds what the scale promises (2^24 for H eta, 2^30 for unscaled forces) writes
+// NaN into that bead's rows of the unit, so that a violated bound cannot pass unnoticed
+#ifndef MOP_BL_JCHECK
+#define MOP_BL_JCHECK 0
+#endif
+
 // the entry's j-atom charges and types loaded once per entry and shuffled to the j-loop (force
 // kernel: 5.69 -> 5.45 ms at config 5), or loaded per j-atom (H eta and FD kernels: faster there)
 #ifndef MOP_BL_QTSHFL_F
@@ -370,6 +377,7 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
     if constexpr (MODE == 2) jmul = mul2(jmul, make_float2(-0.5f / eps2.x, -0.5f / eps2.y));
   }
   const float2 njmul = make_float2(-jmul.x, -jmul.y);
+  float2 jbig = make_float2(0.f, 0.f);   // check build: the largest |share| of each bead
   float2 gm = make_float2(0.f, 0.f);   // force pass: largest |g| of each bead (scale of the H eta j-side sums)
   float2 xi[kBLI][3], ei[kBLI][3], acc[kBLI][3];
 #pragma unroll
@@ -509,7 +517,10 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             unsigned long long w0, w1;
-            bl_fix<MODE == 0 ? 0 : 1>(mul2(fj[q], njmul), w0, w1);
+            const float2 v = mul2(fj[q], njmul);
+            if constexpr (MOP_BL_JCHECK)
+              jbig = make_float2(fmaxf(jbig.x, fabsf(v.x)), fmaxf(jbig.y, fabsf(v.y)));
+            bl_fix<MODE == 0 ? 0 : 1>(v, w0, w1);
             atomicAdd(jp + q * 64, w0);
             atomicAdd(jp + q * 64 + 32, w1);
           }
@@ -572,6 +583,9 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
   }
   bl_fold(S, acc, lane);
   const bool v0 = b0 < n_pass, v1 = b1 < n_pass;
+  // check build: poison the rows of a bead whose shares left the promised range
+  const float jlim = MODE == 0 ? 1073741824.f : 16777216.f;
+  const bool bad0 = MOP_BL_JCHECK && !(jbig.x <= jlim), bad1 = MOP_BL_JCHECK && !(jbig.y <= jlim);
   if constexpr (MODE == 0) {
     // non-negative floats order like their bit patterns
     if (v0) atomicMax(&P.gmax[b0], __float_as_uint(gm.x));
@@ -591,23 +605,26 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       if (v0) {
         float2* dst = F + 3 * ((size_t)b0 * P.Qpad + s);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[c] = make_float2(h[c].x, l[c].x);
+        for (int c = 0; c < 3; ++c) dst[c] = bad0 ? make_float2(__int_as_float(0x7fc00000), 0.f) : make_float2(h[c].x, l[c].x);
       }
       if (v1) {
         float2* dst = F + 3 * ((size_t)b1 * P.Qpad + s);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[c] = make_float2(h[c].y, l[c].y);
+        for (int c = 0; c < 3; ++c) dst[c] = bad1 ? make_float2(__int_as_float(0x7fc00000), 0.f) : make_float2(h[c].y, l[c].y);
       }
     } else {
       // H eta of the pair terms in FP32; FD: -(F(+) - F(-)) / (2 eps)
       const float2 sc2 = MODE == 2 ? make_float2(-0.5f / eps2.x, -0.5f / eps2.y) : make_float2(1.f, 1.f);
       float4* H = reinterpret_cast<float4*>(P.Hnb);
+      const float poison = __int_as_float(0x7fc00000);
       if (v0)
-        H[(size_t)b0 * P.Qpad + s] = make_float4((h[0].x + l[0].x) * sc2.x, (h[1].x + l[1].x) * sc2.x,
-                                                 (h[2].x + l[2].x) * sc2.x, 0.f);
+        H[(size_t)b0 * P.Qpad + s] = bad0 ? make_float4(poison, poison, poison, 0.f)
+                                          : make_float4((h[0].x + l[0].x) * sc2.x, (h[1].x + l[1].x) * sc2.x,
+                                                        (h[2].x + l[2].x) * sc2.x, 0.f);
       if (v1)
-        H[(size_t)b1 * P.Qpad + s] = make_float4((h[0].y + l[0].y) * sc2.y, (h[1].y + l[1].y) * sc2.y,
-                                                 (h[2].y + l[2].y) * sc2.y, 0.f);
+        H[(size_t)b1 * P.Qpad + s] = bad1 ? make_float4(poison, poison, poison, 0.f)
+                                          : make_float4((h[0].y + l[0].y) * sc2.y, (h[1].y + l[1].y) * sc2.y,
+                                                        (h[2].y + l[2].y) * sc2.y, 0.f);
     }
   }
 }
