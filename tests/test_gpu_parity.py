@@ -571,3 +571,23 @@ def test_j_side_sums_are_bitwise_reproducible(monkeypatch, hvp_mode, relaxed, ke
     for name, a, b in zip(("V", "G", "F", "Heta"), outs[0], outs[1]):
         d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
         assert np.array_equal(a, b), (name, int(np.count_nonzero(d)), float(np.abs(d).max()))
+
+
+@pytest.mark.parametrize("relaxed", [False, True])
+def test_cfg3_fields_match_oracle(relaxed):
+    """Config 3 (Q = 24,000 waters, N = 128: two full bead groups, the second one bead short in
+    the force and H eta passes): F, eta, H eta and G element by element and per row, V_eff."""
+    w = workload(3, relaxed=relaxed)
+    X = w.paths[0]
+    N = X.shape[0]
+    eng, g = gpu_eval(w)
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F", "eta", "Heta"))
+    errs = dict(F=rel(g["F"][:N - 1], r["F"][:N - 1]), eta=rel(g["eta"][:N - 1], r["eta"][:N - 1]),
+                Heta=rel(g["Heta"][:N - 1], r["Heta"][:N - 1]), G=rel(g["G"], r["G"]),
+                V=abs(g["veff"] - r["veff"]) / abs(r["veff"]))
+    print("cfg3", relaxed, errs)
+    assert errs["F"] < TOL_F and errs["eta"] < TOL_F and errs["G"] < TOL_F
+    assert errs["Heta"] < TOL_H and errs["V"] < TOL_V
+    assert_rows(g["F"][:N - 1], r["F"][:N - 1], TOL_F, "cfg3 F")
+    assert_rows(g["Heta"][:N - 1], r["Heta"][:N - 1], TOL_H, "cfg3 Heta")
+    assert_rows(g["G"], r["G"], TOL_F, "cfg3 G")
