@@ -74,6 +74,11 @@ constexpr int kBLIlp = MOP_BL_ILP;
 // check build (a second library for the tests, never the product): a lane whose j-side share
 // for a bead exceeds what the scale promises (2^24 for H eta, 2^30 for unscaled forces) writes
 // NaN into that bead's rows of the unit, so that a violated bound cannot pass unnoticed
+// j-side words formed by one 64-bit subtraction (1; H eta pass 7.39 -> 7.34 ms at config 5) or
+// by packing the two 32-bit parts (0)
+#ifndef MOP_BL_PACK64
+#define MOP_BL_PACK64 1
+#endif
 #ifndef MOP_BL_JCHECK
 #define MOP_BL_JCHECK 0
 #endif
@@ -98,6 +103,17 @@ template <int MODE> struct BLQtShfl { static constexpr bool value = MODE == 0 ? 
 #ifndef MOP_BL_L1PF
 #define MOP_BL_L1PF 0
 #endif
+// L1 prefetch, while an entry is evaluated, of the rows of the next walked entry's candidate
+// j-atoms (force / HVP and FD kernels): an entry's 8 j-atoms are 8 consecutive slots, so their
+// rows are 6 KB of consecutive 128-byte lines per array, and two warp instructions per array
+// cover the lines of every candidate j-atom
+#ifndef MOP_BL_EPF_F
+#define MOP_BL_EPF_F 0
+#endif
+#ifndef MOP_BL_EPF_H
+#define MOP_BL_EPF_H 0
+#endif
+template <int MODE> struct BLEpf { static constexpr bool value = MODE == 0 ? MOP_BL_EPF_F : MOP_BL_EPF_H; };
 // HVP and FD kernels: the i-atoms' eta in shared memory instead of registers (more warps)
 #ifndef MOP_BL_EISH
 #define MOP_BL_EISH 0
@@ -297,8 +313,16 @@ __device__ __forceinline__ void bl_fix(float2 v, unsigned long long& w0, unsigne
   const float2 hf = sub2(t, dup2(kMagic));                        // that integer, exactly
   const float2 r = fma2(hf, dup2(-Gd::kHi), v);                   // v - kHi hi, exact
   const float2 u = fma2(r, dup2(Gd::kLo), dup2(kMagic));          // r kLo rounded
+#if MOP_BL_PACK64
+  // (t 2^32 + u) - M (2^32 + 1) = (t - M) 2^32 + (u - M): the same word as bl_pack, formed by one
+  // 64-bit subtraction (the borrow of a negative lo is the subtraction's own)
+  constexpr unsigned long long kMM = ((unsigned long long)(unsigned)kMagicBits << 32) | (unsigned)kMagicBits;
+  w0 = (((unsigned long long)__float_as_uint(t.x) << 32) | __float_as_uint(u.x)) - kMM;
+  w1 = (((unsigned long long)__float_as_uint(t.y) << 32) | __float_as_uint(u.y)) - kMM;
+#else
   w0 = bl_pack(__float_as_int(t.x) - kMagicBits, __float_as_int(u.x) - kMagicBits);
   w1 = bl_pack(__float_as_int(t.y) - kMagicBits, __float_as_int(u.y) - kMagicBits);
+#endif
 }
 
 // value of a sum of such words: (sum hi) kHi + (sum lo) / kLo
@@ -459,6 +483,37 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
       // this unit's candidate bits: i-atoms a0 .. a0 + kBLI - 1 of every j byte
       const unsigned long long Mi = (M >> a0) & (0x0101010101010101ull * ((1u << kBLI) - 1u));
       if (!Mi) continue;   // warp-uniform: no candidate pair for these i-atoms
+      if constexpr (BLEpf<MODE>::value) {
+        // the next entry of this chunk that the walk evaluates (warp-uniform scan in shared memory)
+        unsigned long long Mn = 0ull;
+        int cn = 0;
+        for (int e2 = e + 1; e2 < nc && !Mn; ++e2) {
+          const int x2 = S.ent[e2].x;
+          unsigned long long M2 = S.m[e2];
+          if (HALF) {
+            if (!(x2 & kOwnerFlag)) continue;
+            if (x2 & kSelfFlag) M2 &= 0x7f3f1f0f07030100ull;
+          }
+          Mn = (M2 >> a0) & (0x0101010101010101ull * ((1u << kBLI) - 1u));
+          cn = x2 & kCluMask;
+        }
+        if (Mn) {
+          // lane t < 24: line t % 6 of j-atom t / 6 (first instruction) or t / 6 + 4 (second)
+          const int pj = lane / 6, pl = lane - 6 * pj;
+          const char* bx = reinterpret_cast<const char*>(P.xb + g * gstride) + (size_t)cn * (kCL * 3 * 32 * 8) +
+                           pj * (3 * 32 * 8) + pl * 128;
+          const char* be = MODE >= 1 ? reinterpret_cast<const char*>(P.etab + g * gstride) +
+                                           (size_t)cn * (kCL * 3 * 32 * 8) + pj * (3 * 32 * 8) + pl * 128
+                                     : nullptr;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (lane < 24 && ((Mn >> (8 * (pj + 4 * h))) & 0xffull)) {
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(bx + h * (4 * 3 * 32 * 8)));
+              if (MODE >= 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(be + h * (4 * 3 * 32 * 8)));
+            }
+          }
+        }
+      }
       unsigned long long nz = nonzero_bytes(Mi);
       // charges and pair-table offsets of the entry's 8 j-atoms, one load per entry (the j-loop
       // takes them by shuffle instead of two dependent loads per j-atom)
