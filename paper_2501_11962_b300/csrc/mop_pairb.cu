@@ -289,10 +289,12 @@ __device__ __forceinline__ void bl_fold(W& S, float2 (&acc)[kBLI][3], int lane) 
 constexpr float kMagic = 12582912.f;
 constexpr int kMagicBits = 0x4B400000;
 
+#if !MOP_BL_PACK64
 // hi 2^32 + lo as a 64-bit two's complement word: a negative lo borrows one from hi
 __device__ __forceinline__ unsigned long long bl_pack(int hi, int lo) {
   return ((unsigned long long)(unsigned)(hi + (lo >> 31)) << 32) | (unsigned)lo;
 }
+#endif
 
 // Grids of the j-side words: a share v is clamped to |v| <= kMax, hi = round(v / kHi) and
 // lo = round((v - kHi hi) kLo), so |lo| <= kHi kLo / 2 = 2^21 and the magic-number roundings
