@@ -444,9 +444,10 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
   CK(h, clear_jacc(false));
   if (sc.bl) {
     CK(h, clear_jf(false));
-    CK(h, launch_pairb(sc, h->d_paths.p, np, units, 0, L));
+    const bool fuse_e1 = pairb_fuses_energy1(sc);
+    CK(h, launch_pairb(sc, h->d_paths.p, np, units, 0, L, fuse_e1 ? h->grid.max_clu : 0));
     if (sc.bl == 2) CK(h, launch_bl_combine(sc, h->d_paths.p, pd.data(), np, 0, L));
-    CK(h, launch_energy1(sc, h->d_paths.p, np, h->grid.max_clu, L));
+    if (!fuse_e1) CK(h, launch_energy1(sc, h->d_paths.p, np, h->grid.max_clu, L));
   } else {
     CK(h, launch_pair(sc, h->d_paths.p, np, units, 0, h->num_sms, L));
   }

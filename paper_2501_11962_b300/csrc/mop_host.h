@@ -168,8 +168,11 @@ cudaError_t launch_count_pairs(const SysConsts& sc, const PathDev* d_paths, int 
 // ceil(beads / kBLBeads) x n_clu x pairb_units_per_cluster() units, group-major.  mode 0 =
 // force, 1 = adjoint HVP, 2 = FD HVP.
 int pairb_units_per_cluster();
+// e1_clu > 0 (force pass, full list, where pairb_fuses_energy1): the launch also sums the bead-1
+// pair energy of clusters 0 .. e1_clu - 1 of every path, in place of launch_energy1
 cudaError_t launch_pairb(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
-                         Launch L);
+                         Launch L, int e1_clu = 0);
+bool pairb_fuses_energy1(const SysConsts& sc);
 // bead-1 pair energy of every path into e_pair (one warp per i-cluster); grid over max_clu
 cudaError_t launch_energy1(const SysConsts& sc, const PathDev* d_paths, int n_paths, int max_clu, Launch L);
 // rows [0, n_valid) of src float4 [rows][Qpad] (x, y, z, *) into the transposed bead-lane

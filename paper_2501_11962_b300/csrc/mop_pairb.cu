@@ -74,6 +74,16 @@ constexpr int kBLIlp = MOP_BL_ILP;
 // check build (a second library for the tests, never the product): a lane whose j-side share
 // for a bead exceeds what the scale promises (2^24 for H eta, 2^30 for unscaled forces) writes
 // NaN into that bead's rows of the unit, so that a violated bound cannot pass unnoticed
+// the j-atoms' rows loaded through L2 only (ld.global.cg): a warp reads each row once per entry
+#ifndef MOP_BL_JCG
+#define MOP_BL_JCG 0
+#endif
+// the force kernel over the full list also runs the bead-1 pair energy, as one-warp units after its
+// own (they fill the kernel's last wave instead of a launch of their own; force pass 5.45 -> 5.39 ms
+// at config 5)
+#ifndef MOP_BL_E1FUSE
+#define MOP_BL_E1FUSE 1
+#endif
 // j-side words formed by one 64-bit subtraction (1; H eta pass 7.39 -> 7.34 ms at config 5) or
 // by packing the two 32-bit parts (0)
 #ifndef MOP_BL_PACK64
@@ -442,8 +452,13 @@ __device__ __forceinline__ void bl_unit(const SysConsts& sc, BLWarp<MODE>& S, co
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t o = ((size_t)sj * 3 + c) * 32;
-      J.x[c] = __ldg(xg + o);
-      if (MODE >= 1) J.e[c] = __ldg(eg + o);
+      if constexpr (MOP_BL_JCG) {
+        J.x[c] = __ldcg(xg + o);
+        if (MODE >= 1) J.e[c] = __ldcg(eg + o);
+      } else {
+        J.x[c] = __ldg(xg + o);
+        if (MODE >= 1) J.e[c] = __ldg(eg + o);
+      }
     }
     if constexpr (BLQtShfl<MODE>::value) {
       J.qj = dup2(__shfl_sync(0xffffffffu, qv, jj));
@@ -713,13 +728,30 @@ template <int MODE, bool HALF> struct BLMinBlocks {
                                     : (MODE == 0 ? MOP_BL_MINB_F : (MODE == 1 ? MOP_BL_MINB_H : MOP_BL_MINB_D));
 };
 
+template <bool EW>
+__device__ __forceinline__ void energy1_warp(const SysConsts& sc, const PathDev& P, int ci, int lane, int4* sent,
+                                             unsigned long long* sm);
+
+// e1_clu > 0 (force pass over the full list): units n_units .. n_units + n_paths e1_clu - 1 are the
+// bead-1 pair energy of cluster (u - n_units) % e1_clu of path (u - n_units) / e1_clu
 template <int MODE, bool EW, bool HALF>
 __global__ void __launch_bounds__(32 * BLWarps<MODE>::value, BLMinBlocks<MODE, HALF>::value)
-    k_pairb(SysConsts sc, const PathDev* __restrict__ paths, int n_paths, long long n_units) {
+    k_pairb(SysConsts sc, const PathDev* __restrict__ paths, int n_paths, long long n_units, int e1_clu) {
   extern __shared__ __align__(16) unsigned char smem[];
   BLWarp<MODE>* W = reinterpret_cast<BLWarp<MODE>*>(smem);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long u = (long long)blockIdx.x * BLWarps<MODE>::value + w;
+  if constexpr (MODE == 0 && !HALF) {
+    if (u >= n_units && e1_clu > 0) {
+      const long long e = u - n_units;
+      const int p = (int)(e / e1_clu), ci = (int)(e - (long long)p * e1_clu);
+      if (p >= n_paths) return;
+      const PathDev& P = paths[p];
+      if (ci >= __ldg(&P.meta[0])) return;   // warp-uniform
+      energy1_warp<EW>(sc, P, ci, lane, W[w].ent, W[w].m);
+      return;
+    }
+  }
   if (u >= n_units) return;
   int p = 0;
   if (MODE == 0) {
@@ -739,7 +771,8 @@ __global__ void __launch_bounds__(32 * BLWarps<MODE>::value, BLMinBlocks<MODE, H
 }
 
 template <int MODE, bool EW, bool HALF>
-cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, Launch L) {
+cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, Launch L,
+                     int e1_clu = 0) {
   constexpr int W = BLWarps<MODE>::value;
   const size_t smem = sizeof(BLWarp<MODE>) * W;
   static bool attr = false;
@@ -748,8 +781,10 @@ cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, l
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const long long blocks = (n_units + W - 1) / W;
-  k_pairb<MODE, EW, HALF><<<(unsigned)blocks, 32 * W, smem, L.st>>>(sc, d_paths, n_paths, n_units);
+  const long long n_e1 = (MODE == 0 && !HALF && e1_clu > 0) ? (long long)n_paths * e1_clu : 0;
+  const long long blocks = (n_units + n_e1 + W - 1) / W;
+  k_pairb<MODE, EW, HALF><<<(unsigned)blocks, 32 * W, smem, L.st>>>(sc, d_paths, n_paths, n_units,
+                                                                     n_e1 > 0 ? e1_clu : 0);
   ++*L.counter;
   return cudaGetLastError();
 }
@@ -758,14 +793,10 @@ cudaError_t launch_b(const SysConsts& sc, const PathDev* d_paths, int n_paths, l
 // One warp per i-cluster, lane (i = lane & 7, jq = lane >> 3) against j-atoms jq and jq + 4 of
 // every owner entry (a self entry's pairs j > i), so each pair is met once.
 // phi_sf(r) = phi(r) - phi(rc) - (r - rc) phi'(rc) (sh = phi'(rc) = 0 with the potential shift).
+// One warp: i-cluster ci of path P; sent and sm hold the warp's chunk of 32 list entries.
 template <bool EW>
-__global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __restrict__ paths, int max_clu) {
-  __shared__ int4 sent[4][32];
-  __shared__ unsigned long long sm[4][32];
-  const PathDev& P = paths[blockIdx.y];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int ci = blockIdx.x * 4 + w;
-  if (ci >= max_clu || ci >= __ldg(&P.meta[0])) return;   // warp-uniform
+__device__ __forceinline__ void energy1_warp(const SysConsts& sc, const PathDev& P, int ci, int lane, int4* sent,
+                                             unsigned long long* sm) {
   const int i = lane & 7, jq = lane >> 3;
   const int si = ci * kCL + i;
   const float4 xi = __ldg(&P.xq[si]);   // bead 1 is row 0
@@ -779,14 +810,14 @@ __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __
     const int nc = min(32, cnt - c0);
     __syncwarp();
     if (lane < nc) {
-      sent[w][lane] = __ldg(&P.ent[eb + c0 + lane]);
-      sm[w][lane] = __ldg(&P.emask[eb + c0 + lane]);
+      sent[lane] = __ldg(&P.ent[eb + c0 + lane]);
+      sm[lane] = __ldg(&P.emask[eb + c0 + lane]);
     }
     __syncwarp();
     for (int e = 0; e < nc; ++e) {
-      const int4 E = sent[w][e];
+      const int4 E = sent[e];
       if (!(E.x & kOwnerFlag)) continue;   // warp-uniform
-      unsigned long long M = sm[w][e];
+      unsigned long long M = sm[e];
       if (E.x & kSelfFlag) M &= 0x7f3f1f0f07030100ull;
       const int cj = E.x & kCluMask;
       const float Dx = __int_as_float(E.y), Dy = __int_as_float(E.z), Dz = __int_as_float(E.w);
@@ -823,6 +854,17 @@ __global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __
   two_sum_add(hi, lo, acc);
   const df v = df_warp_sum(df{hi, lo});
   if (lane == 0) P.e_pair[ci] = (double)v.hi + (double)v.lo;
+}
+
+template <bool EW>
+__global__ void __launch_bounds__(128) k_energy1(SysConsts sc, const PathDev* __restrict__ paths, int max_clu) {
+  __shared__ int4 sent[4][32];
+  __shared__ unsigned long long sm[4][32];
+  const PathDev& P = paths[blockIdx.y];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ci = blockIdx.x * 4 + w;
+  if (ci >= max_clu || ci >= __ldg(&P.meta[0])) return;   // warp-uniform
+  energy1_warp<EW>(sc, P, ci, lane, sent[w], sm[w]);
 }
 
 // ---- transposition into the bead-lane layout -------------------------------------------------
@@ -922,8 +964,10 @@ cudaError_t launch_bl_combine(const SysConsts& sc, const PathDev* d_paths, const
   return cudaGetLastError();
 }
 
+bool pairb_fuses_energy1(const SysConsts& sc) { return MOP_BL_E1FUSE && (sc.bl == 1 || sc.bl == 3); }
+
 cudaError_t launch_pairb(const SysConsts& sc, const PathDev* d_paths, int n_paths, long long n_units, int mode,
-                         Launch L) {
+                         Launch L, int e1_clu) {
   if (n_units <= 0) return cudaSuccess;
   const bool ew = sc.elec == 1;
   // j-side sums: the half list in both passes, the owner entries of the full list in the H eta pass
@@ -936,7 +980,8 @@ cudaError_t launch_pairb(const SysConsts& sc, const PathDev* d_paths, int n_path
     }
   }
   switch (mode) {
-    case 0: return ew ? launch_b<0, true, false>(sc, d_paths, n_paths, n_units, L) : launch_b<0, false, false>(sc, d_paths, n_paths, n_units, L);
+    case 0: return ew ? launch_b<0, true, false>(sc, d_paths, n_paths, n_units, L, e1_clu)
+                      : launch_b<0, false, false>(sc, d_paths, n_paths, n_units, L, e1_clu);
     case 1: return ew ? launch_b<1, true, false>(sc, d_paths, n_paths, n_units, L) : launch_b<1, false, false>(sc, d_paths, n_paths, n_units, L);
     default: return ew ? launch_b<2, true, false>(sc, d_paths, n_paths, n_units, L) : launch_b<2, false, false>(sc, d_paths, n_paths, n_units, L);
   }
