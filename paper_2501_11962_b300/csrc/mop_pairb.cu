@@ -74,9 +74,11 @@ constexpr int kBLIlp = MOP_BL_ILP;
 // check build (a second library for the tests, never the product): a lane whose j-side share
 // for a bead exceeds what the scale promises (2^24 for H eta, 2^30 for unscaled forces) writes
 // NaN into that bead's rows of the unit, so that a violated bound cannot pass unnoticed
-// the j-atoms' rows loaded through L2 only (ld.global.cg): a warp reads each row once per entry
+// the j-atoms' rows loaded through L2 only (ld.global.cg): a warp reads each row once per entry,
+// and the two warps of a cluster rarely share an SM, so L1 would only hold them at the expense
+// of the atomics (config 5: force 5.38 -> 5.33 ms, H eta 7.33 -> 7.28 ms)
 #ifndef MOP_BL_JCG
-#define MOP_BL_JCG 0
+#define MOP_BL_JCG 1
 #endif
 // the force kernel over the full list also runs the bead-1 pair energy, as one-warp units after its
 // own (they fill the kernel's last wave instead of a launch of their own; force pass 5.45 -> 5.39 ms
