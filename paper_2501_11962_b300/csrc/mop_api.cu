@@ -179,7 +179,7 @@ __global__ void k_f2d(const float* in, float* copy, double* out, long long n, in
   if (t < n) {
     const float v = in[t];
     if (copy) copy[t] = v;
-    out[t] = widen(v);
+    if (out) out[t] = widen(v);
     if (bad && !isfinite(v)) atomicOr(bad, 1);
   }
 }
@@ -1018,17 +1018,20 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
     bad = h->flag.p;
   }
   if (f64) {
+    P.dyn_stale = false;
     if (!dev) CK(h, cudaMemcpyAsync(P.x64.p, xyz, n * sizeof(double), cudaMemcpyHostToDevice, st));
     k_d2f<<<nblk(n, 256), 256, 0, st>>>(dev ? (const double*)xyz : P.x64.p, dev ? P.x64.p : nullptr, P.x32.p,
                                          (long long)n, bad);
   } else {
     if (!dev) CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), cudaMemcpyHostToDevice, st));
-    k_f2d<<<nblk(n, 256), 256, 0, st>>>(dev ? (const float*)xyz : P.x32.p, dev ? P.x32.p : nullptr, P.x64.p,
-                                         (long long)n, bad);
+    // mixed precision evaluates from x32 alone: the FP64 integrator copy waits for the integrator
+    P.dyn_stale = h->precision == MOP_PREC_MIXED;
+    k_f2d<<<nblk(n, 256), 256, 0, st>>>(dev ? (const float*)xyz : P.x32.p, dev ? P.x32.p : nullptr,
+                                         P.dyn_stale ? nullptr : P.x64.p, (long long)n, bad);
   }
   CK(h, cudaGetLastError());
   if (async) CK(h, cudaEventRecord(h->stg_free[(h->stg_next ^ 1)], st));   // the staging buffer may be reused
-  CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
+  if (!P.dyn_stale) CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
   if (!dev) {
     int flag = 0;
     CK(h, cudaMemcpyAsync(&flag, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1296,6 +1299,21 @@ mop_status mop_add_gaussian(mop_handle* h, int32_t path_id, double height, const
 
 namespace {
 
+// the integrator state of paths whose mop_set_path deferred it: x64 = x32 widened, velocities 0
+mop_status ensure_dynamics(mop_handle* h, const std::vector<int>& ids, cudaStream_t st) {
+  for (int id : ids) {
+    PathHost& P = h->paths[id];
+    if (!P.dyn_stale) continue;
+    const size_t n = 3 * (size_t)P.N * h->sc.Q;
+    k_f2d<<<nblk(n, 256), 256, 0, st>>>(P.x32.p, nullptr, P.x64.p, (long long)n, nullptr);
+    CK(h, cudaGetLastError());
+    ++h->launches;
+    CK(h, cudaMemsetAsync(P.vel.p, 0, n * sizeof(double), st));
+    P.dyn_stale = false;
+  }
+  return MOP_OK;
+}
+
 // one MD step of every listed path: B (half kick), A O A (drift with Langevin noise), evaluation
 // of dV_eff/dR at the new positions, B; then the Philox step counter advances
 mop_status step_body(mop_handle* h, const std::vector<int>& ids, double dt_md, double gamma, uint64_t seed,
@@ -1346,6 +1364,7 @@ mop_status mop_step(mop_handle* h, int32_t n_steps, double dt_md, double gamma, 
   CK(h, cudaSetDevice(h->device));
   CK(h, settle_copies(h));   // no captured step waits on an asynchronous copy
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if ((s = ensure_dynamics(h, ids, st))) return s;
   CK(h, h->step_dev.ensure(1));
   if (!h->step_ready) {
     CK(h, cudaMemsetAsync(h->step_dev.p, 0, sizeof(unsigned long long), st));
@@ -1626,6 +1645,7 @@ mop_status mop_kinetic_energy(mop_handle* h, int32_t path_id, double* ke) {
   if (s || path_id < 0) return s ? s : fail(h, MOP_ERR_ARG, "path_id must be >= 0");
   CK(h, cudaSetDevice(h->device));
   PathHost& P = h->paths[path_id];
+  if ((s = ensure_dynamics(h, ids, nullptr))) return s;
   CK(h, h->scratch.ensure(1));
   Launch L{nullptr, &h->launches};
   CK(h, launch_kinetic(h->sc, P.vel.p, P.N, h->scratch.p, L));

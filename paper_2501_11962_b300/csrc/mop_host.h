@@ -67,6 +67,9 @@ struct HostMailbox {
 
 struct PathHost {
   bool set = false;
+  // mixed precision, FP32 input: the integrator state (x64 from x32, zero velocities) is formed
+  // by the first mop_step or mop_kinetic_energy after mop_set_path, not by mop_set_path itself
+  bool dyn_stale = false;
   int N = 0;
   int n_clu = 0;
   int cap = 256;          // list entries reserved per i-cluster
