@@ -132,7 +132,9 @@ mop_status mop_destroy(mop_handle* h);
 
 /* Stores the coordinates of path `path_id` (0 <= path_id < 64): n_beads >= 1 beads of
  * [n_beads][Q][3] float (double with MOP_INPUT_F64), copied into the handle.  Resets the
- * path's velocities to zero.  Errors: MOP_ERR_ARG, MOP_ERR_NONFINITE (host input is checked
+ * path's velocities to zero.  In mixed precision with float input, the integrator's FP64 copy
+ * of the coordinates and the zeroed velocities are formed by the next mop_step or
+ * mop_kinetic_energy on the path (the evaluation reads the float coordinates only).  Errors: MOP_ERR_ARG, MOP_ERR_NONFINITE (host input is checked
  * here; device input is checked by mop_veff_and_grad through the result), MOP_ERR_CUDA,
  * MOP_ERR_OOM. */
 mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const void* xyz,
