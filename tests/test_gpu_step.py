@@ -135,3 +135,32 @@ def test_baoab_thermostat_holds_the_temperature():
     dof = 3 * w.system.n_atoms * w.paths[0].shape[0]
     T_kin = 2.0 * np.mean(kin) / (dof * 0.0083144626)
     assert abs(T_kin - T) / T < 0.05, T_kin
+
+
+@pytest.mark.parametrize("gamma", [0.0, 5.0])
+def test_deferred_integrator_state_matches_eager(gamma):
+    """Mixed precision with float input: mop_set_path leaves the FP64 integrator copy and the zero
+    velocities to the first mop_step.  The trajectory must equal, bit for bit, the one from the
+    same coordinates given as doubles (whose integrator copy mop_set_path forms at once), and
+    again after a second mop_set_path on a handle that has already stepped."""
+    w = workload(2, n_beads=4)
+    X32 = np.ascontiguousarray(w.paths[0], dtype=np.float32)
+    X64 = X32.astype(np.float64)
+    out = []
+    for X in (X32, X64):
+        eng = mop.Engine(w.system)
+        eng.set_path(0, X)
+        assert eng.kinetic_energy(0) == 0.0
+        eng.step(3, 2e-4, gamma, 7)
+        a = eng.get_path(0)
+        ke_a = eng.kinetic_energy(0)
+        eng.set_path(0, X)                  # back to the start: positions and velocities reset
+        assert eng.kinetic_energy(0) == 0.0
+        eng.step(3, 2e-4, gamma, 7)
+        b = eng.get_path(0)
+        out.append((a, ke_a, b))
+        eng.close()
+    (a32, ke32, b32), (a64, ke64, b64) = out
+    assert np.abs(a32 - X32).max() > 0.0    # the atoms moved
+    assert np.array_equal(a32, a64) and ke32 == ke64
+    assert np.array_equal(b32.view(np.uint32), b64.view(np.uint32))
