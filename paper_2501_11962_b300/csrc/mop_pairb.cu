@@ -16,7 +16,9 @@
 // With HALF it walks the owner entries only (each atom pair once; a self entry's pairs j > i),
 // and the warp also sums each j-atom's share over its i-atoms and adds it, with the sign
 // reversed, to j-side sums; a later pass (k_bl_combine) adds those to the rows (the H eta and FD
-// passes, and both passes of a half list, which holds owner entries only).
+// passes, and both passes of a half list, which holds owner entries only).  The force launch over
+// the full list ends with one-warp units that sum the bead-1 pair energy U(R^1) (energy1_warp),
+// so that they fill its last wave.
 //
 // The j-side sums are exact and order-independent: a share v (forces in kJ mol^-1 nm^-1; H eta
 // scaled per bead by a power of two, see bl_jscale) becomes an integer on a fixed grid, carried as
