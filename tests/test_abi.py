@@ -94,6 +94,9 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.mop_destroy(None) == mop.MOP_OK
     assert lib.mop_veff_and_grad(None, 0, None, None, 0, None) == mop.MOP_ERR_ARG
     assert lib.mop_last_launch_count(None) == 0
+    assert lib.mop_last_error(None) == b"null handle"
+    assert lib.mop_count_pairs(None, 0, None, None) == mop.MOP_ERR_ARG
+    assert lib.mop_set_profiling(None, 1) == mop.MOP_ERR_ARG
 
 
 def _pme(d, grid=(24, 24, 24), order=4, beta=3.0, hvp=0):
