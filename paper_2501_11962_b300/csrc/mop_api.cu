@@ -292,7 +292,7 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     if (sc.bl) {
       // bead-lane kernels read the coordinates transposed (beads innermost)
       CK(h, P.xb.ensure((size_t)bl_groups(n_force) * Qpad * 3 * 32));
-      CK(h, launch_bl_transpose(P.xq.p, n_force, Qpad, h->grid.max_clu, P.meta.p, P.xb.p, L));
+      if (!bl_direct_coords(sc)) CK(h, launch_bl_transpose(P.xq.p, n_force, Qpad, h->grid.max_clu, P.meta.p, P.xb.p, L));
       if (n_hvp > 0) CK(h, P.etab.ensure((size_t)bl_groups(n_hvp) * Qpad * 3 * 32));
       // j-side sums: the H eta pass (bl 1, 2) and the force pass of the half list (bl 2)
       const int jrows = sc.bl == 2 ? std::max(n_force, n_hvp) : (sc.bl == 1 ? n_hvp : 0);

@@ -154,6 +154,9 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
 // +inf for non-finite input), and the cluster-local coordinates of a kept sort and list.
 cudaError_t launch_max_disp(const float* x, const float* xref, long long n_atoms_beads, unsigned* dmax2, Launch L);
 cudaError_t prep_coords(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L);
+// true when the prep kernels write the bead-lane coordinates xb themselves (mixed precision,
+// reaction field, bead-lane kernels); xq then holds bead 1 only
+bool bl_direct_coords(const SysConsts& sc);
 
 // --- mop_pair.cu: pair kernels over every unit of every path -------------------------------
 // mode 0 = force (+ bead-0 energy), 1 = adjoint HVP, 2 = FD HVP.  A unit is one i-cluster for

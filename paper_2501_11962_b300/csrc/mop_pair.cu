@@ -1063,6 +1063,17 @@ __global__ void k_count_pairs(SysConsts sc, const PathDev* __restrict__ paths, i
         if (P.xq64) {
           const double4_32a x = P.xq64[bo + ci * kCL + i], y = P.xq64[bo + sj];
           a[0] = x.x; a[1] = x.y; a[2] = x.z; b[0] = y.x; b[1] = y.y; b[2] = y.z;
+        } else if (sc.bl && sc.elec != 1) {
+          // the bead-lane coordinates (xq holds bead 1 only): bead n at group n / 64, lane n % 32,
+          // half (n / 32) % 2
+          const size_t gb = ((size_t)(n / kBLBeads) * P.Qpad) * 3 * 32;
+          const int l = n & 31, hh = (n >> 5) & 1;
+          for (int c = 0; c < 3; ++c) {
+            const float2 x = P.xb[gb + ((size_t)(ci * kCL + i) * 3 + c) * 32 + l];
+            const float2 y = P.xb[gb + ((size_t)sj * 3 + c) * 32 + l];
+            a[c] = hh ? x.y : x.x;
+            b[c] = hh ? y.y : y.x;
+          }
         } else {
           const float4 x = P.xq[bo + ci * kCL + i], y = P.xq[bo + sj];
           a[0] = x.x; a[1] = x.y; a[2] = x.z; b[0] = y.x; b[1] = y.y; b[2] = y.z;

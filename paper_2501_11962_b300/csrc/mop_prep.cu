@@ -262,6 +262,99 @@ __global__ void k_local_box32(SysConsts sc, const float* x32, int N, const float
   abox[s] = make_float4(cf[0], cf[1], cf[2], sqrtf(h2) * 1.000001f + (float)margin + 1e-6f);
 }
 
+// Mixed precision, reaction field, bead-lane pair kernels: the same cluster-local coordinates and
+// atom spheres as k_local_box32, written directly in the bead-lane layout the pair kernels read,
+// xb [group][slot][3][32] float2 (lane l holds beads 64 g + l and 64 g + 32 + l; beads past
+// n_rows repeat the last row, as the transposition does), and in xq for bead 1 only (its row
+// carries the charges and the bead-1 energy's coordinates).  One warp per slot, lanes over
+// beads, so that the stores of xb are whole 256-byte rows.  The sphere's bounds are warp minima
+// and maxima, which do not depend on the order, so abox has the bits of k_local_box32's.
+__global__ void __launch_bounds__(256) k_local_box32_bl(SysConsts sc, const float* x32, int N, int n_rows,
+                                                        const float* reff, const int* perm, const int* meta,
+                                                        int max_slots, const double* center, double margin,
+                                                        float4* xq, float2* xb, int* ts, float4* eta32, float4* abox) {
+  const int lane = threadIdx.x & 31;
+  const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (s >= max_slots || s >= meta[0] * kCL) return;   // warp-uniform
+  const int a = perm[s];
+  const int groups = (n_rows + kBLBeads - 1) / kBLBeads;
+  if (a < 0) {
+    const float dmy = kDummyCoord + 3.0f * (float)(s & (kCL - 1));
+    for (int g = 0; g < groups; ++g) {
+      float2* o = xb + ((size_t)g * max_slots + s) * 3 * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[c * 32] = make_float2(dmy, dmy);
+    }
+    for (int b = lane; b < N; b += 32) eta32[(size_t)b * max_slots + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane == 0) {
+      xq[s] = make_float4(dmy, dmy, dmy, 0.0f);
+      ts[s] = 0;
+      abox[s] = make_float4(kDummyCoord, kDummyCoord, kDummyCoord, -1.0f);
+    }
+    return;
+  }
+  const int c = s / kCL;
+  float cen[3], r[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    cen[d] = (float)center[3 * c + d];   // exactly representable
+    r[d] = reff[3 * a + d];
+  }
+  const float q = (float)sc.qs[a];
+  const size_t Q3 = 3 * (size_t)sc.Q;
+  // local coordinates of bead b, as k_local_box32 forms them
+  auto local = [&](int b, float* v) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const df A = aligned_df(sc, x32[b * Q3 + 3 * (size_t)a + d], r[d], d);
+      const df t = two_sum(A.hi, -cen[d]);
+      v[d] = t.hi + (t.lo + A.lo);
+    }
+  };
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  const int nb = max(N, groups * kBLBeads);
+  for (int g = 0; g * kBLBeads < nb; ++g) {
+    float v0[3], v1[3];
+    const int b0 = g * kBLBeads + lane, b1 = b0 + 32;
+    local(min(b0, N - 1), v0);
+    local(min(b1, N - 1), v1);
+    // the sphere covers the beads 0 .. N-1
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (b0 < N) { lo[d] = fminf(lo[d], v0[d]); hi[d] = fmaxf(hi[d], v0[d]); }
+      if (b1 < N) { lo[d] = fminf(lo[d], v1[d]); hi[d] = fmaxf(hi[d], v1[d]); }
+    }
+    if (g < groups) {
+      // rows past n_rows repeat row n_rows - 1
+      float w0[3], w1[3];
+      if (b0 < n_rows) { w0[0] = v0[0]; w0[1] = v0[1]; w0[2] = v0[2]; } else local(n_rows - 1, w0);
+      if (b1 < n_rows) { w1[0] = v1[0]; w1[1] = v1[1]; w1[2] = v1[2]; } else local(n_rows - 1, w1);
+      float2* o = xb + ((size_t)g * max_slots + s) * 3 * 32 + lane;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) o[d * 32] = make_float2(w0[d], w1[d]);
+    }
+    if (g == 0 && lane == 0) xq[s] = make_float4(v0[0], v0[1], v0[2], q);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+  if (lane == 0) {
+    ts[s] = sc.type[a];
+    float cf[3], h2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cf[d] = 0.5f * (lo[d] + hi[d]);
+      const float h = fmaxf(hi[d] - cf[d], cf[d] - lo[d]);
+      h2 = fmaf(h, h, h2);
+    }
+    abox[s] = make_float4(cf[0], cf[1], cf[2], sqrtf(h2) * 1.000001f + (float)margin + 1e-6f);
+  }
+}
+
 // union bounding box of each cluster over all beads; one warp per cluster, lanes over beads
 __global__ void k_cluster_bbox(SysConsts sc, const float* x32, const double* x64, int N, const double* ref,
                                const int* perm, const int* meta, int max_clu, double margin, double* center,
@@ -720,12 +813,28 @@ cudaError_t launch_max_disp(const float* x, const float* xref, long long n, unsi
   return cudaGetLastError();
 }
 
-cudaError_t prep_coords(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L) {
+bool bl_direct_coords(const SysConsts& sc) { return sc.precision == 0 && sc.bl != 0 && sc.elec != 1; }
+
+// the cluster-local coordinates, atom spheres and types of the current sort (mixed precision)
+cudaError_t local_box32(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L) {
   const int max_slots = g.max_clu * kCL;
-  k_local_box32<<<nblk(max_slots, 256), 256, 0, L.st>>>(sc, P.x32.p, P.N, P.reff.p, P.perm.p, P.meta.p, max_slots,
-                                                        P.center.p, margin, P.xq.p, P.ts.p, P.eta32.p, P.abox.p);
+  if (bl_direct_coords(sc)) {
+    const int n_rows = P.N == 1 ? 1 : P.N - 1;   // the beads that need forces
+    cudaError_t e = P.xb.ensure((size_t)bl_groups(n_rows) * max_slots * 3 * 32);
+    if (e != cudaSuccess) return e;
+    k_local_box32_bl<<<nblk((long long)max_slots * 32, 256), 256, 0, L.st>>>(
+        sc, P.x32.p, P.N, n_rows, P.reff.p, P.perm.p, P.meta.p, max_slots, P.center.p, margin, P.xq.p, P.xb.p,
+        P.ts.p, P.eta32.p, P.abox.p);
+  } else {
+    k_local_box32<<<nblk(max_slots, 256), 256, 0, L.st>>>(sc, P.x32.p, P.N, P.reff.p, P.perm.p, P.meta.p, max_slots,
+                                                          P.center.p, margin, P.xq.p, P.ts.p, P.eta32.p, P.abox.p);
+  }
   ++*L.counter;
   return cudaGetLastError();
+}
+
+cudaError_t prep_coords(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L) {
+  return local_box32(sc, g, P, margin, L);
 }
 
 cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double margin, Launch L, std::string* err,
@@ -800,9 +909,7 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                                                                        max_clu, margin, P.center.p, P.hext.p,
                                                                        P.molr.p, P.emax.p);
     MOP_KL();
-    k_local_box32<<<nblk(max_slots, bs), bs, 0, st>>>(sc, x32, N, P.reff.p, P.perm.p, P.meta.p, max_slots,
-                                                      P.center.p, margin, P.xq.p, P.ts.p, P.eta32.p, P.abox.p);
-    MOP_KL();
+    MOP_CK(local_box32(sc, g, P, margin, Launch{st, L.counter}));
   }
   k_bin_clusters<<<nblk(max_clu, bs), bs, 0, st>>>(sc, P.meta.p, max_clu, P.center.p, P.hext.p, g.nb[0], g.nb[1],
                                                    g.nb[2], g.bw[0], g.bw[1], g.bw[2], P.cwrap.p, P.cwdf.p, P.cbox.p,
