@@ -290,7 +290,8 @@ mop_status evaluate(mop_handle* h, const std::vector<int>& ids, double* dev_veff
     const int N = P.N, Qpad = h->grid.max_clu * kCL;   // fixed slot stride (capture safe)
     const int n_force = N == 1 ? 1 : N - 1, n_hvp = N - 1;
     if (sc.bl) {
-      // bead-lane kernels read the coordinates transposed (beads innermost)
+      // bead-lane kernels read the coordinates with the beads innermost: written so by the prep
+      // kernel with the reaction field, transposed from xq otherwise
       CK(h, P.xb.ensure((size_t)bl_groups(n_force) * Qpad * 3 * 32));
       if (!bl_direct_coords(sc)) CK(h, launch_bl_transpose(P.xq.p, n_force, Qpad, h->grid.max_clu, P.meta.p, P.xb.p, L));
       if (n_hvp > 0) CK(h, P.etab.ensure((size_t)bl_groups(n_hvp) * Qpad * 3 * 32));
