@@ -264,7 +264,8 @@ def run_ours(args, world, rank, local):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    launches_per_step = eng.last_launch_count() + 1   # + the conversion kernel of mop_set_path
+    # mop_set_path copies device input with cudaMemcpyAsync (no kernel of the library)
+    launches_per_step = eng.last_launch_count()
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -1027,8 +1027,13 @@ mop_status mop_set_path(mop_handle* h, int32_t path_id, int32_t n_beads, const v
     if (!dev) CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), cudaMemcpyHostToDevice, st));
     // mixed precision evaluates from x32 alone: the FP64 integrator copy waits for the integrator
     P.dyn_stale = h->precision == MOP_PREC_MIXED;
-    k_f2d<<<nblk(n, 256), 256, 0, st>>>(dev ? (const float*)xyz : P.x32.p, dev ? P.x32.p : nullptr,
-                                         P.dyn_stale ? nullptr : P.x64.p, (long long)n, bad);
+    if (dev && P.dyn_stale && !bad) {
+      // device input: a plain copy (the non-finite check is the evaluation's, through V_eff)
+      CK(h, cudaMemcpyAsync(P.x32.p, xyz, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_f2d<<<nblk(n, 256), 256, 0, st>>>(dev ? (const float*)xyz : P.x32.p, dev ? P.x32.p : nullptr,
+                                           P.dyn_stale ? nullptr : P.x64.p, (long long)n, bad);
+    }
   }
   CK(h, cudaGetLastError());
   if (async) CK(h, cudaEventRecord(h->stg_free[(h->stg_next ^ 1)], st));   // the staging buffer may be reused
