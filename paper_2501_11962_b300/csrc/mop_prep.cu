@@ -561,11 +561,6 @@ __global__ void k_cluster_types(const int* meta, const int* ts, unsigned* ctype)
 // sides.  PM (bead-lane kernels): emask holds the entry's candidate atom pairs (the union
 // spheres within reach, exclusions removed, bit j * 8 + i), an entry whose candidates are all
 // excluded is dropped, and with HALF the self entry keeps its pairs j > i only.
-// the molecule-range overlap of a candidate tested in the lane-parallel box phase (1) or in the
-// warp's serial exact-test loop (0)
-#ifndef MOP_LIST_OVL
-#define MOP_LIST_OVL 0
-#endif
 #ifndef MOP_LIST_MINB
 #define MOP_LIST_MINB 6   // 80 registers: 6 blocks (24 warps) per SM hide the latency of the bin walk
 #endif
@@ -632,7 +627,7 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
         for (int t0 = 0; t0 < nbin; t0 += 32) {
           const int t = t0 + lane;
           int cj = -1;
-          bool self = false, own = false, ovl = false;
+          bool self = false, own = false;
           double D[3] = {0.0, 0.0, 0.0};
           if (t < nbin) {
             cj = binlist[s0 + t];
@@ -671,11 +666,6 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
             // the atom spheres of this lane's candidate, read by the whole warp below
 #pragma unroll
             for (int j = 0; j < kCL; ++j) jbox[warp][lane][j] = abox[cj * kCL + j];
-#if MOP_LIST_OVL
-            // exclusions only matter for clusters whose molecule ranges overlap (tested here, lane
-            // by lane, instead of in the warp's serial loop below)
-            ovl = mi0 <= molr[2 * cj + 1] && molr[2 * cj] <= mi1;
-#endif
           }
           __syncwarp();
           // exact test of each surviving candidate by the whole warp, in bin order: lane
@@ -685,8 +675,7 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
             const int src = __ffs(pend) - 1;
             pend &= pend - 1;
             const int cs = __shfl_sync(0xffffffffu, cj, src);
-            const int fl_s = __shfl_sync(0xffffffffu, (int)self | ((int)ovl << 1), src);
-            const bool self_s = (fl_s & 1) != 0;
+            const bool self_s = __shfl_sync(0xffffffffu, (int)self, src) != 0;
             const float Dx = __shfl_sync(0xffffffffu, Df[0], src);
             const float Dy = __shfl_sync(0xffffffffu, Df[1], src);
             const float Dz = __shfl_sync(0xffffffffu, Df[2], src);
@@ -711,12 +700,8 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
             if (PM) {
               // exclusions only matter for clusters whose molecule ranges overlap
               pm = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
-#if MOP_LIST_OVL
-              if (fl_s & 2) {
-#else
               const int mj0 = molr[2 * cs], mj1 = molr[2 * cs + 1];
               if (mi0 <= mj1 && mj0 <= mi1) {
-#endif
                 bool x0 = false, x1 = false;
                 if (ai >= 0) {
                   const int a0 = perm[cs * kCL + jq], a1 = perm[cs * kCL + jq + 4];
@@ -742,12 +727,8 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
               // exclusions, bit j * 8 + i (the lane index for j < 4, + 32 for j >= 4); only
               // clusters whose molecule ranges overlap can hold excluded pairs
               unsigned long long m = 0ull;
-#if MOP_LIST_OVL
-              if (fl_s & 2) {
-#else
               const int mj0 = molr[2 * cs], mj1 = molr[2 * cs + 1];
               if (mi0 <= mj1 && mj0 <= mi1) {
-#endif
                 bool x0 = false, x1 = false;
                 if (ai >= 0) {
                   const int b0 = perm[cs * kCL + jq], b1 = perm[cs * kCL + jq + 4];
