@@ -64,7 +64,7 @@ template <int MODE, bool HALF> struct BLJUnroll {
   static constexpr int value = HALF ? (MODE == 0 ? MOP_BL_JU_FH : MOP_BL_JU_HH) : (MODE == 0 ? MOP_BL_JU_F : MOP_BL_JU_H);
 };
 #ifndef MOP_BL_FOLD
-#define MOP_BL_FOLD 8
+#define MOP_BL_FOLD 16
 #endif
 constexpr int kBLFold = MOP_BL_FOLD;   // list entries between folds of the FP32 sums
 // i-atoms evaluated together under one warp-uniform branch when all of them are candidates of
