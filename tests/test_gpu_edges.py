@@ -189,3 +189,26 @@ def test_non_cubic_spme_grid_matches_oracle():
     assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V
     assert rel(G, r["G"]) < TOL_F
     assert rel(H, r["Heta"][:N - 1]) < TOL_H
+
+
+@pytest.mark.parametrize("N", [1, 2])
+@pytest.mark.parametrize("prec", [mop.MOP_PREC_MIXED, mop.MOP_PREC_FP64])
+def test_one_and_two_bead_paths_match_oracle(N, prec):
+    """The shortest paths: one bead (no spring, so V_eff = U(R^1) and the gradient is -F^1) and two
+    beads (one spring, one H eta row).  In mixed precision each fills one bead group with 63 or 62
+    idle lanes, and the coordinate and list kernels see a single force row."""
+    w = workload(2, relaxed=True, n_beads=N)
+    X = w.paths[0]
+    eng = mop.Engine(w.system, precision=prec)
+    eng.set_path(0, X)
+    v, G = eng.veff_and_grad(0)
+    F = eng.get_field(0, mop.MOP_FIELD_FORCE)[:1]
+    eng.close()
+    r = oracle.Oracle(w.system).veff(X.astype(np.float64), want=("G", "F"), hvp_mode=oracle.HVP_ANALYTIC)
+    # FP64: sums over thousands of pair terms with cancellation round at ~1e-13 of the result
+    tol = 1e-6 if prec == mop.MOP_PREC_FP64 else 1.0
+    assert abs(v[0] - r["veff"]) / abs(r["veff"]) < TOL_V * tol
+    assert rel(G, r["G"]) < TOL_F * tol
+    assert rel(F, r["F"][:1]) < TOL_F * tol
+    if N == 1:
+        assert rel(G, -r["F"][:1]) < TOL_F * tol   # V_eff = U(R^1): the gradient is minus the force
