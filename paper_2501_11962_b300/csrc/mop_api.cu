@@ -964,7 +964,7 @@ mop_status mop_destroy(mop_handle* h) {
     P.colcnt.release(); P.colinfo.release(); P.colatoms.release(); P.perm.release(); P.slot.release();
     P.ts.release(); P.center.release(); P.hext.release(); P.molr.release(); P.emax.release();
     P.cbin.release(); P.bincnt.release(); P.binstart.release(); P.bincur.release(); P.binlist.release();
-    P.cwrap.release(); P.cwdf.release(); P.cbox.release(); P.lcnt.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
+    P.cwrap.release(); P.cwdf.release(); P.cbox.release(); P.lcnt.release(); P.mcnt.release(); P.ekey.release(); P.abox.release(); P.ctype.release(); P.meta.release(); P.xq.release();
     P.xq64.release(); P.ent.release(); P.ent64.release(); P.emask.release(); P.Fnb.release();
     P.F.release(); P.eta.release(); P.Hnb.release(); P.Heta.release(); P.grad_int.release();
     P.eta32.release(); P.etalo.release(); P.etamax.release(); P.gmax.release(); P.jI.release(); P.jacc.release(); P.e_excl.release(); P.e_pair.release(); P.diag.release(); P.veff_int.release();

@@ -94,6 +94,7 @@ struct PathHost {
   DevBuf<float2> cwdf;    // [max_clu][3] the same as double-floats (mixed precision)
   DevBuf<float4> cbox;    // [max_clu][2]: FP32 wrapped centre, half extents
   DevBuf<int> lcnt;
+  DevBuf<int> mcnt, ekey;   // mirrored full list: mirror entries per cluster, their sort keys
   DevBuf<float4> abox;    // [max_slots] union sphere of each atom over the beads
   DevBuf<unsigned> ctype; // [max_clu] packed LJ types
   DevBuf<int> meta;       // [4]: clusters, (scan total), largest list, sticky overflow flag

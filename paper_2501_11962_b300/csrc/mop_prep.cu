@@ -763,6 +763,98 @@ __global__ void __launch_bounds__(128, MOP_LIST_MINB) k_pair_list(SysConsts sc, 
 
 inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
+// ---- the full list from the owner entries ---------------------------------------------------
+// With MOP_LIST_MIRROR the bead-lane full list is built from the half list: the list kernel tests
+// every unordered cluster pair once (its owner entry), and the entries of the other side are
+// that entry's mirror images.  A mirror entry in cluster cj's list names ci, carries -Delta (the
+// list forms Delta as a rounded difference, so the image of cj's own Delta is its exact negation)
+// and the candidate mask transposed (bit j 8 + i becomes bit i 8 + j); a self entry gets its
+// mask's transpose added (the half list keeps only its pairs j > i).  Each cluster's list is its
+// owner entries in bin order, then its mirror entries ordered by (source cluster, position in the
+// source list), so the list does not depend on the order of the atomics that place them.
+#ifndef MOP_LIST_MIRROR
+#define MOP_LIST_MIRROR 1
+#endif
+
+// the 8 x 8 bit matrix of m transposed: bit r 8 + c of the result is bit c 8 + r of m (three
+// exchanges of off-diagonal blocks of 1, 2 and 4 bits)
+__device__ __forceinline__ unsigned long long transpose8x8(unsigned long long m) {
+  unsigned long long t = (m ^ (m >> 7)) & 0x00AA00AA00AA00AAull;
+  m ^= t ^ (t << 7);
+  t = (m ^ (m >> 14)) & 0x0000CCCC0000CCCCull;
+  m ^= t ^ (t << 14);
+  t = (m ^ (m >> 28)) & 0x00000000F0F0F0F0ull;
+  m ^= t ^ (t << 28);
+  return m;
+}
+
+// one warp per cluster ci over its owner entries: mirror images into the j-clusters' lists at
+// lcnt[cj] + (arrival order) with their sort key, self entries completed in place
+__global__ void __launch_bounds__(128) k_mirror_fill(const int* meta, int max_clu, int cap, const int* lcnt,
+                                                     int4* ent, unsigned long long* emask, int* mcnt, int* ekey) {
+  const int lane = threadIdx.x & 31;
+  const int ci = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (ci >= max_clu || ci >= meta[0]) return;   // warp-uniform
+  const int n = lcnt[ci];
+  const size_t base = (size_t)ci * cap;
+  for (int k = lane; k < n; k += 32) {
+    const int4 E = ent[base + k];
+    const unsigned long long m = emask[base + k];
+    const unsigned long long mt = transpose8x8(m);
+    if (E.x & kSelfFlag) {
+      emask[base + k] = m | mt;
+      continue;
+    }
+    const int cj = E.x & kCluMask;
+    const int pos = lcnt[cj] + atomicAdd(&mcnt[cj], 1);
+    if (pos >= cap) continue;   // counted: k_mirror_sort reports the overflow
+    const unsigned hm = ((unsigned)mt ? 1u : 0u) | ((unsigned)(mt >> 32) ? 2u : 0u);
+    const size_t d = (size_t)cj * cap + pos;
+    ent[d] = make_int4(ci | (int)(hm << 29), __float_as_int(-__int_as_float(E.y)), __float_as_int(-__int_as_float(E.z)),
+                       __float_as_int(-__int_as_float(E.w)));
+    emask[d] = mt;
+    ekey[d] = ci * cap + k;
+  }
+}
+
+// one warp per cluster: its mirror entries put in key order (rank = number of smaller keys), the
+// list count and the largest count (capacity check) updated.  Shared memory: 4 warps x cap x
+// (key + entry + mask).
+__global__ void __launch_bounds__(128) k_mirror_sort(int* meta, int max_clu, int cap, int* lcnt, int4* ent,
+                                                     unsigned long long* emask, const int* mcnt, const int* ekey) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int4* se = reinterpret_cast<int4*>(smem) + (size_t)w * cap;
+  unsigned long long* sm = reinterpret_cast<unsigned long long*>(reinterpret_cast<int4*>(smem) + 4 * (size_t)cap) +
+                           (size_t)w * cap;
+  int* sk = reinterpret_cast<int*>(reinterpret_cast<unsigned long long*>(reinterpret_cast<int4*>(smem) + 4 * (size_t)cap) +
+                                   4 * (size_t)cap) + (size_t)w * cap;
+  const int c = blockIdx.x * 4 + w;
+  if (c >= max_clu || c >= meta[0]) return;   // warp-uniform; no block barrier below
+  const int o = lcnt[c], m = mcnt[c];
+  const int total = o + m, mm = max(0, min(m, cap - o));
+  if (lane == 0) {
+    atomicMax(&meta[2], total);
+    if (total > cap) atomicOr(&meta[3], 1);
+  }
+  const size_t base = (size_t)c * cap + o;
+  for (int t = lane; t < mm; t += 32) {
+    se[t] = ent[base + t];
+    sm[t] = emask[base + t];
+    sk[t] = ekey[base + t];
+  }
+  __syncwarp();
+  for (int t = lane; t < mm; t += 32) {
+    const int key = sk[t];
+    int r = 0;
+    for (int u = 0; u < mm; ++u) r += sk[u] < key;
+    ent[base + r] = se[t];
+    emask[base + r] = sm[t];
+  }
+  __syncwarp();
+  if (lane == 0) lcnt[c] = o + mm;
+}
+
 // meta[0..3] into mapped host memory (read by the host after the stream synchronises)
 __global__ void k_post_meta(const int* meta, int* host_mapped) {
   if (threadIdx.x < 4) reinterpret_cast<volatile int*>(host_mapped)[threadIdx.x] = meta[threadIdx.x];
@@ -947,7 +1039,23 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                                                              g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p,
                                                              P.abox.p, P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr,
                                                              P.emask.p, P.meta.p);
-    else if (sc.bl)        // bead-lane full list
+    else if (sc.bl && MOP_LIST_MIRROR) {   // bead-lane full list: owner entries, then their images
+      k_pair_list<false, true, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
+                                                             P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1],
+                                                             g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p,
+                                                             P.abox.p, P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr,
+                                                             P.emask.p, P.meta.p);
+      MOP_KL();
+      MOP_CK(P.mcnt.ensure(max_clu));
+      MOP_CK(P.ekey.ensure((size_t)max_clu * P.cap));
+      MOP_CK(cudaMemsetAsync(P.mcnt.p, 0, sizeof(int) * max_clu, st));
+      k_mirror_fill<<<blocks, 128, 0, st>>>(P.meta.p, max_clu, P.cap, P.lcnt.p, P.ent.p, P.emask.p, P.mcnt.p, P.ekey.p);
+      MOP_KL();
+      const size_t sbytes = 4 * (size_t)P.cap * (sizeof(int4) + sizeof(unsigned long long) + sizeof(int));
+      if (sbytes > 48 * 1024) MOP_CK(cudaFuncSetAttribute(k_mirror_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes));
+      k_mirror_sort<<<blocks, 128, sbytes, st>>>(P.meta.p, max_clu, P.cap, P.lcnt.p, P.ent.p, P.emask.p, P.mcnt.p,
+                                                 P.ekey.p);
+    } else if (sc.bl)      // bead-lane full list
       k_pair_list<false, false, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
                                                         P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1], g.bw[2],
                                                         P.binstart.p, P.binlist.p, P.perm.p, P.molr.p, P.abox.p,
