@@ -1039,7 +1039,9 @@ cudaError_t prep_path(const SysConsts& sc, const Grid& g, PathHost& P, double ma
                                                              g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p,
                                                              P.abox.p, P.cbox.p, P.cap, P.lcnt.p, P.ent.p, nullptr,
                                                              P.emask.p, P.meta.p);
-    else if (sc.bl && MOP_LIST_MIRROR) {   // bead-lane full list: owner entries, then their images
+    else if (sc.bl && MOP_LIST_MIRROR && (size_t)max_clu * P.cap < (1u << 31)) {
+      // bead-lane full list: owner entries, then their images (the sort keys ci cap + k are
+      // 32-bit; a larger list is built from both sides directly)
       k_pair_list<false, true, true><<<blocks, 128, 0, st>>>(sc, P.meta.p, max_clu, P.cwrap.p, P.cwdf.p, P.hext.p, P.emax.p,
                                                              P.cbin.p, g.nb[0], g.nb[1], g.nb[2], g.bw[0], g.bw[1],
                                                              g.bw[2], P.binstart.p, P.binlist.p, P.perm.p, P.molr.p,
